@@ -1,0 +1,240 @@
+"""CPU oracle for the random-walk spanning-centrality path (test infrastructure).
+
+Only the tests, the smoke check and the bench's CPU-baseline leg may use this
+package.  The product library never imports it and shares no code with it.
+
+Two parts:
+  * ``walks.c`` (compiled here with gcc into ``_build/liboracle.so``): the
+    hash-keyed walks, walk-batch visit counts, AESC counters, the certified
+    planner and the FP64 finalize, as plain single-threaded loops.
+  * ``exact.py`` (numpy, FP64): exact spanning centrality by the Laplacian
+    pseudoinverse and by the matrix-tree theorem, the spectrum of
+    D^-1/2 A D^-1/2, the truncated walk series, and E(eta) of Sec. 5.6.
+
+Parity status: every function here has at least one pin in
+``tests/test_oracle_*.py`` (known-answer vectors, closed forms, brute force,
+statistical tests); none is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "walks.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+EINVAL = -1
+ENOEDGE = -4
+EOVERFLOW = -5
+
+
+def build(force: bool = False) -> str:
+    """Compile walks.c with gcc (no FMA contraction) and return the .so path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)) or (
+        os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            f64p = ctypes.POINTER(ctypes.c_double)
+            c = ctypes
+            L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_philox4x32_10.restype = None
+            L.orc_splitmix64_next.argtypes = [u64p]
+            L.orc_splitmix64_next.restype = c.c_uint64
+            L.orc_walk_key.argtypes = [c.c_uint64, c.c_uint64, c.c_uint64]
+            L.orc_walk_key.restype = c.c_uint64
+            L.orc_step_hash.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32]
+            L.orc_step_hash.restype = c.c_uint32
+            L.orc_choose.argtypes = [c.c_uint32, c.c_uint32]
+            L.orc_choose.restype = c.c_uint32
+            L.orc_walk_batch.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_uint64, c.c_uint32,
+                c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, u32p, u32p]
+            L.orc_walk_batch.restype = c.c_int
+            L.orc_edge_ids.argtypes = [c.c_uint32, i64p, u32p, c.c_uint64, u32p, u64p]
+            L.orc_edge_ids.restype = c.c_int
+            L.orc_aesc_counts.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, c.c_uint64, u32p, u32p, u32p,
+                c.c_uint32, c.c_uint32, c.c_uint32, u32p]
+            L.orc_aesc_counts.restype = c.c_int
+            L.orc_aesc_finalize.argtypes = [c.c_uint32, i64p, c.c_uint64, u32p, u32p, u32p, f64p]
+            L.orc_aesc_finalize.restype = c.c_int
+            L.orc_trunc_bound.argtypes = [c.c_double, c.c_double, c.c_double, c.c_uint32]
+            L.orc_trunc_bound.restype = c.c_double
+            L.orc_plan_certified.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double,
+                c.c_double, c.c_double, c.c_uint32, u32p, u32p]
+            L.orc_plan_certified.restype = c.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with code {code}")
+        self.code = code
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise OracleError(rc, what)
+
+
+# ----------------------------------------------------------------- hashes
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32),
+                            _p(out, ctypes.c_uint32))
+    return out
+
+
+def splitmix64_sequence(seed: int, count: int) -> list[int]:
+    st = ctypes.c_uint64(seed)
+    return [int(lib().orc_splitmix64_next(ctypes.byref(st))) for _ in range(count)]
+
+
+def walk_key(seed: int, stream: int, k: int) -> int:
+    return int(lib().orc_walk_key(seed, stream, k))
+
+
+def step_hash(kw: int, step: int, cur: int) -> int:
+    return int(lib().orc_step_hash(kw, step, cur))
+
+
+def choose(r: int, d: int) -> int:
+    return int(lib().orc_choose(r, d))
+
+
+BATCH_STREAM = 0x4000000000000000
+GROUP_BIT = 0x8000000000000000
+
+
+# ------------------------------------------------------------- walk batch
+
+def _graph_arrays(g):
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    nb = np.ascontiguousarray(g.nbrs, dtype=np.uint32)
+    return off, nb
+
+
+def _sampler(sampler):
+    if sampler is None:
+        return 0, 0, 1
+    kind, t, width = sampler
+    return int(kind), int(t), int(width)
+
+
+def walk_batch(g, seed: int, starts: np.ndarray, n_steps: int, sampler=None,
+               include_start: bool = False, visits: np.ndarray | None = None,
+               want_paths: bool = False):
+    """Visit counts (uint32[n]) and optionally paths (uint32[n_walks, n_steps+1])."""
+    off, nb = _graph_arrays(g)
+    st = np.ascontiguousarray(starts, dtype=np.uint32)
+    vis = np.zeros(g.n, np.uint32) if visits is None else visits
+    paths = np.zeros((st.size, n_steps + 1), np.uint32) if want_paths else None
+    kind, t, width = _sampler(sampler)
+    rc = lib().orc_walk_batch(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed,
+        _p(st, ctypes.c_uint32), st.size, n_steps, kind, t, width,
+        1 if include_start else 0, _p(vis, ctypes.c_uint32),
+        _p(paths, ctypes.c_uint32) if paths is not None else None)
+    _check(rc, "walk_batch")
+    return (vis, paths) if want_paths else vis
+
+
+# ------------------------------------------------------------------- AESC
+
+def edge_ids(g, uv: np.ndarray) -> np.ndarray:
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ids = np.zeros(q.shape[0], np.uint64)
+    rc = lib().orc_edge_ids(g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32),
+                            q.shape[0], _p(q, ctypes.c_uint32), _p(ids, ctypes.c_uint64))
+    _check(rc, "edge_ids")
+    return ids
+
+
+def plan_certified(g, uv: np.ndarray, eps: float, delta: float, lambda2: float,
+                   lambda_neg: float, tau_max: int = 1 << 20):
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    tau = np.zeros(q.shape[0], np.uint32)
+    nw = np.zeros(q.shape[0], np.uint32)
+    rc = lib().orc_plan_certified(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), q.shape[0],
+        _p(q, ctypes.c_uint32), eps, delta, lambda2, lambda_neg, tau_max,
+        _p(tau, ctypes.c_uint32), _p(nw, ctypes.c_uint32))
+    _check(rc, "plan_certified")
+    return tau, nw
+
+
+def trunc_bound(s_e: float, lambda2: float, lambda_neg: float, tau: int) -> float:
+    return float(lib().orc_trunc_bound(s_e, lambda2, lambda_neg, tau))
+
+
+def aesc_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
+                sampler=None) -> np.ndarray:
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    counts = np.zeros(4 * q.shape[0], np.uint32)
+    kind, t, width = _sampler(sampler)
+    rc = lib().orc_aesc_counts(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed, q.shape[0],
+        _p(q, ctypes.c_uint32), _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
+        kind, t, width, _p(counts, ctypes.c_uint32))
+    _check(rc, "aesc_counts")
+    return counts
+
+
+def aesc_finalize(g, uv: np.ndarray, nwalks: np.ndarray, counts: np.ndarray) -> np.ndarray:
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    cn = np.ascontiguousarray(counts, dtype=np.uint32)
+    sc = np.zeros(q.shape[0], np.float64)
+    rc = lib().orc_aesc_finalize(g.n, _p(off, ctypes.c_int64), q.shape[0],
+                                 _p(q, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
+                                 _p(cn, ctypes.c_uint32), _p(sc, ctypes.c_double))
+    _check(rc, "aesc_finalize")
+    return sc
+
+
+def aesc_estimate(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
+                  sampler=None):
+    counts = aesc_counts(g, seed, uv, tau, nwalks, sampler)
+    return counts, aesc_finalize(g, uv, nwalks, counts)

@@ -1,0 +1,456 @@
+/*
+ * Plain, slow, single-threaded CPU oracle for the random-walk hot path of
+ * "Approximating Spanning Centrality with Random Bouquets" (arXiv 2410.14056).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this file; only the tests, the smoke check and the bench's CPU-baseline
+ * leg load it.  It shares no code with the CUDA library: the hash, the walk
+ * loop, the edge numbering, the planner and the finalize formula are all
+ * written out here independently.
+ *
+ * Build: gcc -O2 -std=c99 -ffp-contract=off -fPIC -shared walks.c -lm
+ * (no FMA contraction: the finalize must round each operation separately).
+ *
+ * Contents and the passages they follow:
+ *   philox4x32_10   - Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw,
+ *                     "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ *   splitmix_mix    - the output function of SplitMix64 (Steele, Lea, Flood,
+ *                     "Fast splittable pseudorandom number generators",
+ *                     OOPSLA'14).
+ *   walk key / step hash - the paper's hash-based RNG: one seed per random
+ *                     process combined with a hash of the current state
+ *                     (vertex, walk length), Sec. 3.1 Eq. (hash_prob) and
+ *                     Sec. 3.3 Eq. (select-xor); keyed by walk id, vertex and
+ *                     length as in Sec. 2.2.
+ *   choose index    - Eq. (select-proposed): floor(r / 2^32 * d), i.e. the
+ *                     high word of r * d, no modulus.
+ *   walk batch      - Alg. 2 (RandomWalk), one walk after another, visits
+ *                     counted as in the synthetic benchmark of Sec. 4.
+ *   AESC counters   - the walk loop of Alg. 1 at zero push depth: two walks
+ *                     per sample, from each endpoint of the edge, hits of the
+ *                     endpoints weighted 2 (steps before tau) and 1 (step tau).
+ *   plan            - CalculateTau / NWalks of Alg. 1, which the paper does
+ *                     not define; here the spectral truncation bound and
+ *                     Hoeffding's inequality (readings listed in the design
+ *                     notes).
+ *   finalize        - the estimate s(e) = g(u,v) + g(v,u) of Alg. 1, with
+ *                     g initialised to 1/d and incremented by the walk sums.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOEDGE -4
+#define ORC_EOVERFLOW -5
+
+/* Stream reserved for walk-batch walks (AESC streams are 2*edge + side). */
+#define ORC_BATCH_STREAM 0x4000000000000000ULL
+/* Top stream bit marks the shared (group) key of the coupled sampler. */
+#define ORC_GROUP_BIT 0x8000000000000000ULL
+
+/* ---------------------------------------------------------------- hashes */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    int round;
+    for (round = 0; round < 10; round++) {
+        uint64_t prod0, prod1;
+        uint32_t n0, n1, n2, n3;
+        if (round > 0) {
+            k0 += 0x9E3779B9u; /* Weyl key schedule */
+            k1 += 0xBB67AE85u;
+        }
+        prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        n0 = (uint32_t)(prod1 >> 32) ^ c1 ^ k0;
+        n1 = (uint32_t)prod1;
+        n2 = (uint32_t)(prod0 >> 32) ^ c3 ^ k1;
+        n3 = (uint32_t)prod0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+static uint64_t splitmix_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* SplitMix64 generator: advance the state by the golden gamma, then mix. */
+uint64_t orc_splitmix64_next(uint64_t *state)
+{
+    *state += 0x9E3779B97F4A7C15ULL;
+    return splitmix_mix(*state);
+}
+
+/* 64-bit key of walk k in stream s: one Philox block serves walks 2j and
+ * 2j+1 (low and high half of its output). */
+uint64_t orc_walk_key(uint64_t seed, uint64_t stream, uint64_t k)
+{
+    uint32_t ctr[4], key[2], out[4];
+    uint64_t block = k >> 1;
+    ctr[0] = (uint32_t)block;
+    ctr[1] = (uint32_t)(block >> 32);
+    ctr[2] = (uint32_t)stream;
+    ctr[3] = (uint32_t)(stream >> 32);
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    orc_philox4x32_10(ctr, key, out);
+    if (k & 1)
+        return (uint64_t)out[2] | ((uint64_t)out[3] << 32);
+    return (uint64_t)out[0] | ((uint64_t)out[1] << 32);
+}
+
+/* Random word of step l (1-based walk length) taken at vertex cur by the walk
+ * whose key is kw: the l-th SplitMix64 state of seed kw, xor the vertex id,
+ * mixed; the high 32 bits are kept. */
+uint32_t orc_step_hash(uint64_t kw, uint32_t l, uint32_t cur)
+{
+    uint64_t state = kw + (uint64_t)l * 0x9E3779B97F4A7C15ULL;
+    return (uint32_t)(splitmix_mix(state ^ (uint64_t)cur) >> 32);
+}
+
+/* Eq. (select-proposed): k = floor(r / 2^32 * d) with r in [0, 2^32). */
+uint32_t orc_choose(uint32_t r, uint32_t d)
+{
+    return (uint32_t)(((uint64_t)r * (uint64_t)d) >> 32);
+}
+
+/* Sampler: kind 0 = independent walks; kind 1 = coupled bouquets: walks
+ * k with the same floor(k / width) share the top t bits of their random word
+ * at the same (length, vertex). */
+typedef struct {
+    uint32_t kind;
+    uint32_t t;
+    uint32_t width;
+} orc_sampler;
+
+static uint32_t sample_word(const orc_sampler *smp, uint64_t kw, uint64_t kg,
+                            uint32_t l, uint32_t cur)
+{
+    uint32_t own = orc_step_hash(kw, l, cur);
+    if (smp->kind == 0)
+        return own;
+    {
+        uint32_t shared = orc_step_hash(kg, l, cur);
+        uint32_t mine = smp->t >= 32 ? 0u : (own >> smp->t);
+        return shared ^ mine;
+    }
+}
+
+static int sampler_ok(const orc_sampler *smp)
+{
+    if (smp->kind == 0)
+        return 1;
+    return smp->kind == 1 && smp->width >= 1 && smp->t <= 32;
+}
+
+/* ------------------------------------------------------------ walk batch */
+
+/* Alg. 2 for every walk i in input order.  Walk i starts at starts[i]; for
+ * l = 1..n_steps it moves to the chosen neighbour of the current vertex (a
+ * vertex with no neighbour keeps the walk where it is).  visits[v] is
+ * incremented for every position l >= 1 (and l = 0 when include_start) at
+ * which the walk stands on v; counts accumulate on top of the caller's
+ * values.  paths, when not NULL, receives row i = positions 0..n_steps. */
+int orc_walk_batch(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                   uint64_t seed, const uint32_t *starts, uint64_t n_walks,
+                   uint32_t n_steps, uint32_t kind, uint32_t t, uint32_t width,
+                   uint32_t include_start, uint32_t *visits, uint32_t *paths)
+{
+    orc_sampler smp;
+    uint64_t i;
+    smp.kind = kind;
+    smp.t = t;
+    smp.width = width;
+    if (!sampler_ok(&smp))
+        return ORC_EINVAL;
+    for (i = 0; i < n_walks; i++) {
+        uint32_t cur = starts[i];
+        uint64_t kw, kg = 0;
+        uint32_t l;
+        if (cur >= n)
+            return ORC_EINVAL;
+        kw = orc_walk_key(seed, ORC_BATCH_STREAM, i);
+        if (kind == 1)
+            kg = orc_walk_key(seed, ORC_BATCH_STREAM | ORC_GROUP_BIT, i / width);
+        if (paths)
+            paths[i * ((uint64_t)n_steps + 1)] = cur;
+        if (include_start) {
+            if (visits[cur] == UINT32_MAX)
+                return ORC_EOVERFLOW;
+            visits[cur] += 1;
+        }
+        for (l = 1; l <= n_steps; l++) {
+            int64_t lo = offsets[cur];
+            uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
+            if (d > 0) {
+                uint32_t r = sample_word(&smp, kw, kg, l, cur);
+                cur = nbrs[lo + orc_choose(r, d)];
+            }
+            if (visits[cur] == UINT32_MAX)
+                return ORC_EOVERFLOW;
+            visits[cur] += 1;
+            if (paths)
+                paths[i * ((uint64_t)n_steps + 1) + l] = cur;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------- edge numbering */
+
+/* Canonical id of the undirected edge {a, b}: edges are numbered by their
+ * lower endpoint u, then by the higher endpoint v, in CSR order.  Returns 0
+ * and writes the id, or ORC_ENOEDGE. */
+static int edge_id_of(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                      const uint64_t *upper_before, uint32_t a, uint32_t b,
+                      uint64_t *id)
+{
+    uint32_t u = a < b ? a : b;
+    uint32_t v = a < b ? b : a;
+    uint64_t rank = 0;
+    int64_t j;
+    if (a >= n || b >= n || a == b)
+        return ORC_ENOEDGE;
+    for (j = offsets[u]; j < offsets[u + 1]; j++) {
+        if (nbrs[j] == v) {
+            *id = upper_before[u] + rank;
+            return ORC_OK;
+        }
+        if (nbrs[j] > u)
+            rank++;
+    }
+    return ORC_ENOEDGE;
+}
+
+/* upper_before[u] = number of edges {x, y}, x < y, with x < u. */
+static uint64_t *count_upper(uint32_t n, const int64_t *offsets, const uint32_t *nbrs)
+{
+    uint64_t *ub = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint32_t u;
+    uint64_t acc = 0;
+    if (!ub)
+        return NULL;
+    for (u = 0; u < n; u++) {
+        int64_t j;
+        ub[u] = acc;
+        for (j = offsets[u]; j < offsets[u + 1]; j++)
+            if (nbrs[j] > u)
+                acc++;
+    }
+    ub[n] = acc;
+    return ub;
+}
+
+int orc_edge_ids(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                 uint64_t k, const uint32_t *uv, uint64_t *ids)
+{
+    uint64_t *ub = count_upper(n, offsets, nbrs);
+    uint64_t q;
+    int rc = ORC_OK;
+    if (!ub)
+        return ORC_EINVAL;
+    for (q = 0; q < k && rc == ORC_OK; q++)
+        rc = edge_id_of(n, offsets, nbrs, ub, uv[2 * q], uv[2 * q + 1], &ids[q]);
+    free(ub);
+    return rc;
+}
+
+/* ------------------------------------------------------------ AESC walks */
+
+/* Counters for query edge q = {u, v}, u < v (the pair is normalised), with
+ * truncation tau[q] and nwalks[q] samples.  A sample is a walk from u
+ * (side 0, stream 2e) and a walk from v (side 1, stream 2e + 1), both with
+ * walk index k in [0, nwalks[q]).  At step l = 1..tau the walk adds weight
+ * w_l (2 for l < tau, 1 for l = tau) to
+ *   side 0:  C_uu if it stands on u,  C_uv if it stands on v
+ *   side 1:  C_vu if it stands on u,  C_vv if it stands on v
+ * counts[4q + 0..3] = C_uu, C_uv, C_vu, C_vv (overwritten). */
+int orc_aesc_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                    uint64_t seed, uint64_t k, const uint32_t *uv,
+                    const uint32_t *tau, const uint32_t *nwalks, uint32_t kind,
+                    uint32_t t, uint32_t width, uint32_t *counts)
+{
+    orc_sampler smp;
+    uint64_t *ub;
+    uint64_t q;
+    smp.kind = kind;
+    smp.t = t;
+    smp.width = width;
+    if (!sampler_ok(&smp))
+        return ORC_EINVAL;
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub)
+        return ORC_EINVAL;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b;
+        uint32_t v = a < b ? b : a;
+        uint64_t e, c[4] = {0, 0, 0, 0};
+        uint32_t side;
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &e) != ORC_OK) {
+            free(ub);
+            return ORC_ENOEDGE;
+        }
+        for (side = 0; side < 2; side++) {
+            uint64_t stream = 2 * e + side;
+            uint64_t w;
+            for (w = 0; w < nwalks[q]; w++) {
+                uint64_t kw = orc_walk_key(seed, stream, w);
+                uint64_t kg = 0;
+                uint32_t cur = side == 0 ? u : v;
+                uint32_t l;
+                if (kind == 1)
+                    kg = orc_walk_key(seed, stream | ORC_GROUP_BIT, w / width);
+                for (l = 1; l <= tau[q]; l++) {
+                    int64_t lo = offsets[cur];
+                    uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
+                    uint32_t weight = l < tau[q] ? 2u : 1u;
+                    uint32_t r = sample_word(&smp, kw, kg, l, cur);
+                    cur = nbrs[lo + orc_choose(r, d)];
+                    if (cur == u)
+                        c[2 * side + 0] += weight;
+                    if (cur == v)
+                        c[2 * side + 1] += weight;
+                }
+            }
+        }
+        if (c[0] > UINT32_MAX || c[1] > UINT32_MAX || c[2] > UINT32_MAX || c[3] > UINT32_MAX) {
+            free(ub);
+            return ORC_EOVERFLOW;
+        }
+        counts[4 * q + 0] = (uint32_t)c[0];
+        counts[4 * q + 1] = (uint32_t)c[1];
+        counts[4 * q + 2] = (uint32_t)c[2];
+        counts[4 * q + 3] = (uint32_t)c[3];
+    }
+    free(ub);
+    return ORC_OK;
+}
+
+/* --------------------------------------------------------------- finalize */
+
+/* SC(e) estimate from the four counters:
+ *   s_e = 1/d_u + 1/d_v  (the zero-length term; g initialised to 1/d)
+ *   est = s_e + ((C_uu - C_vu)/d_u + (C_vv - C_uv)/d_v) / (2 N)
+ * Each operation is rounded on its own, in this order. */
+int orc_aesc_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
+                      const uint32_t *uv, const uint32_t *nwalks,
+                      const uint32_t *counts, double *sc)
+{
+    uint64_t q;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b;
+        uint32_t v = a < b ? b : a;
+        double du, dv, s, x, y, mean;
+        if (u >= n || v >= n)
+            return ORC_EINVAL;
+        du = (double)(offsets[u + 1] - offsets[u]);
+        dv = (double)(offsets[v + 1] - offsets[v]);
+        s = 1.0 / du + 1.0 / dv;
+        x = (double)((int64_t)counts[4 * q + 0] - (int64_t)counts[4 * q + 2]);
+        y = (double)((int64_t)counts[4 * q + 3] - (int64_t)counts[4 * q + 1]);
+        mean = (x / du + y / dv) / (2.0 * (double)nwalks[q]);
+        sc[q] = s + mean;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ plan */
+
+/* Worst-case truncation error factor of the half-weighted series after tau
+ * terms for eigenvalues in (0, lambda2] (P) and [lambda_neg, 0) (Q), where
+ * the error of one eigen-component lambda is lambda^tau (1 + lambda) /
+ * (2 (1 - lambda)) times its weight, and the weights sum to s_e. */
+static double trunc_p(double lambda2, uint32_t tau)
+{
+    if (lambda2 <= 0.0)
+        return 0.0;
+    return pow(lambda2, (double)tau) * (1.0 + lambda2) / (2.0 * (1.0 - lambda2));
+}
+
+static double trunc_q(double lambda_neg, uint32_t tau)
+{
+    double a = -lambda_neg, xs, x;
+    if (a <= 0.0)
+        return 0.0;
+    /* x^tau (1-x)/(1+x) on [0, 1) peaks at the positive root of
+     * tau x^2 + 2x - tau = 0. */
+    xs = (sqrt(1.0 + (double)tau * (double)tau) - 1.0) / (double)tau;
+    x = a < xs ? a : xs;
+    return pow(x, (double)tau) * (1.0 - x) / (2.0 * (1.0 + x));
+}
+
+double orc_trunc_bound(double s_e, double lambda2, double lambda_neg, uint32_t tau)
+{
+    double p = trunc_p(lambda2, tau), q = trunc_q(lambda_neg, tau);
+    return s_e * (p > q ? p : q);
+}
+
+/* Certified plan for each query edge:
+ *   tau = smallest tau >= 1 with s_e * max(P(tau), Q(tau)) <= eps / 2
+ *   N   = ceil(8 (tau - 1/2)^2 s_e^2 ln(2 m / delta) / eps^2)
+ * (Hoeffding on samples bounded by (tau - 1/2) s_e in absolute value,
+ * deviation eps/2, failure delta/m per edge, m = edges of the whole graph).
+ * Returns ORC_EOVERFLOW when tau exceeds tau_max or 2 N tau >= 2^32. */
+int orc_plan_certified(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                       uint64_t k, const uint32_t *uv, double eps, double delta,
+                       double lambda2, double lambda_neg, uint32_t tau_max,
+                       uint32_t *tau, uint32_t *nwalks)
+{
+    uint64_t m = (uint64_t)(offsets[n] / 2);
+    uint64_t *ub, q, id;
+    double logterm;
+    if (!(eps > 0.0) || !(delta > 0.0) || !(delta < 1.0) || m == 0)
+        return ORC_EINVAL;
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub)
+        return ORC_EINVAL;
+    logterm = log(2.0 * (double)m / delta);
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        double du, dv, s, nw, h;
+        uint32_t tq = 1;
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &id) != ORC_OK) {
+            free(ub);
+            return ORC_ENOEDGE;
+        }
+        du = (double)(offsets[a + 1] - offsets[a]);
+        dv = (double)(offsets[b + 1] - offsets[b]);
+        s = 1.0 / du + 1.0 / dv;
+        while (orc_trunc_bound(s, lambda2, lambda_neg, tq) > eps / 2.0) {
+            if (tq >= tau_max) {
+                free(ub);
+                return ORC_EOVERFLOW;
+            }
+            tq++;
+        }
+        h = (double)tq - 0.5;
+        nw = ceil(8.0 * h * h * s * s * logterm / (eps * eps));
+        if (nw < 1.0)
+            nw = 1.0;
+        if (nw * 2.0 * (double)tq >= 4294967296.0) {
+            free(ub);
+            return ORC_EOVERFLOW;
+        }
+        tau[q] = tq;
+        nwalks[q] = (uint32_t)nw;
+    }
+    free(ub);
+    return ORC_OK;
+}
