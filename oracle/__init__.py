@@ -77,6 +77,10 @@ def lib():
                 c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_uint64, c.c_uint32,
                 c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32, u32p, u32p]
             L.orc_walk_batch.restype = c.c_int
+            L.orc_walk_paths_by_id.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, u64p, u32p, c.c_uint64, c.c_uint32,
+                c.c_uint32, c.c_uint32, c.c_uint32, u32p]
+            L.orc_walk_paths_by_id.restype = c.c_int
             L.orc_edge_ids.argtypes = [c.c_uint32, i64p, u32p, c.c_uint64, u32p, u64p]
             L.orc_edge_ids.restype = c.c_int
             L.orc_aesc_counts.argtypes = [
@@ -173,6 +177,21 @@ def walk_batch(g, seed: int, starts: np.ndarray, n_steps: int, sampler=None,
         _p(paths, ctypes.c_uint32) if paths is not None else None)
     _check(rc, "walk_batch")
     return (vis, paths) if want_paths else vis
+
+
+def walk_paths_by_id(g, seed: int, ids: np.ndarray, starts: np.ndarray, n_steps: int,
+                     sampler=None) -> np.ndarray:
+    """Paths (uint32[len(ids), n_steps+1]) of the batch walks with these ids."""
+    off, nb = _graph_arrays(g)
+    idv = np.ascontiguousarray(ids, dtype=np.uint64)
+    st = np.ascontiguousarray(starts, dtype=np.uint32)
+    paths = np.zeros((idv.size, n_steps + 1), np.uint32)
+    kind, t, width = _sampler(sampler)
+    rc = lib().orc_walk_paths_by_id(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed, _p(idv, ctypes.c_uint64),
+        _p(st, ctypes.c_uint32), idv.size, n_steps, kind, t, width, _p(paths, ctypes.c_uint32))
+    _check(rc, "walk_paths_by_id")
+    return paths
 
 
 # ------------------------------------------------------------------- AESC

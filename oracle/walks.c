@@ -211,6 +211,42 @@ int orc_walk_batch(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
     return ORC_OK;
 }
 
+/* The walks with the given batch ids (walk ids[q] starting at starts[q]),
+ * positions 0..n_steps written to paths row q: the same walks a batch with
+ * those ids would take, for checking sampled walks of a large batch. */
+int orc_walk_paths_by_id(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                         uint64_t seed, const uint64_t *ids, const uint32_t *starts,
+                         uint64_t count, uint32_t n_steps, uint32_t kind, uint32_t t,
+                         uint32_t width, uint32_t *paths)
+{
+    orc_sampler smp;
+    uint64_t q;
+    smp.kind = kind;
+    smp.t = t;
+    smp.width = width;
+    if (!sampler_ok(&smp))
+        return ORC_EINVAL;
+    for (q = 0; q < count; q++) {
+        uint32_t cur = starts[q];
+        uint64_t kw, kg = 0;
+        uint32_t l;
+        if (cur >= n)
+            return ORC_EINVAL;
+        kw = orc_walk_key(seed, ORC_BATCH_STREAM, ids[q]);
+        if (kind == 1)
+            kg = orc_walk_key(seed, ORC_BATCH_STREAM | ORC_GROUP_BIT, ids[q] / width);
+        paths[q * ((uint64_t)n_steps + 1)] = cur;
+        for (l = 1; l <= n_steps; l++) {
+            int64_t lo = offsets[cur];
+            uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
+            if (d > 0)
+                cur = nbrs[lo + orc_choose(sample_word(&smp, kw, kg, l, cur), d)];
+            paths[q * ((uint64_t)n_steps + 1) + l] = cur;
+        }
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------- edge numbering */
 
 /* Canonical id of the undirected edge {a, b}: edges are numbered by their

@@ -136,3 +136,15 @@ def test_rmat_batch_sum_invariant():
     starts = uniform_starts(g, 5000, 4)
     vis = oracle.walk_batch(g, 1, starts, 64)
     assert int(vis.sum()) == 5000 * 64
+
+
+def test_paths_by_id_replays_batch_walks():
+    g = gnp_connected(50, 0.1, 8)
+    starts = uniform_starts(g, 400, 3)
+    _, paths = oracle.walk_batch(g, 55, starts, 12, want_paths=True)
+    ids = np.array([0, 7, 399, 123, 8], np.uint64)
+    sub = oracle.walk_paths_by_id(g, 55, ids, starts[ids.astype(np.int64)], 12)
+    assert np.array_equal(sub, paths[ids.astype(np.int64)])
+    _, cp = oracle.walk_batch(g, 55, starts, 12, sampler=(1, 4, 8), want_paths=True)
+    sub = oracle.walk_paths_by_id(g, 55, ids, starts[ids.astype(np.int64)], 12, sampler=(1, 4, 8))
+    assert np.array_equal(sub, cp[ids.astype(np.int64)])

@@ -28,6 +28,8 @@ from .graphs import (  # noqa: F401
     chung_lu,
     grid_deleted,
     uniform_starts,
+    cached,
+    rmat20,
     all_edges,
     edges_of,
 )

@@ -278,6 +278,34 @@ def grid_deleted(rows: int, cols: int, delete_fraction: float, seed: int) -> Gra
     return g
 
 
+def cached(key: str, builder) -> Graph:
+    """builder() memoised on disk under $BQ_WORKLOAD_CACHE (default
+    .workload_cache/ at the repository root), keyed by `key`."""
+    import os
+
+    root = os.environ.get("BQ_WORKLOAD_CACHE") or os.path.join(
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".workload_cache")
+    path = os.path.join(root, key + ".npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return Graph(int(z["n"]), z["offsets"], z["nbrs"], str(z["name"]))
+    g = builder()
+    try:
+        os.makedirs(root, exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, n=g.n, offsets=g.offsets, nbrs=g.nbrs, name=g.name)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return g
+
+
+def rmat20() -> Graph:
+    """The random-walk benchmark graph: R-MAT scale 20, edge factor 16,
+    (a, b, c) = (0.57, 0.19, 0.19), seed 20."""
+    return cached("rmat20_ef16_s20", lambda: rmat(20, 16, 0.57, 0.19, 0.19, seed=20))
+
+
 def uniform_starts(g: Graph, n_walks: int, seed: int) -> np.ndarray:
     """uint32[n_walks] start vertices drawn uniformly over the vertices that
     have at least one neighbour (an isolated vertex has no walk to take)."""
