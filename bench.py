@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the random-walk hot path on one GB300 (or N, one process each).
+
+Workload (one step): the synthetic random-walk benchmark on an R-MAT graph
+(scale 20, edge factor 16, a = 0.57, b = c = 0.19, symmetrised, no self-loops
+or duplicates): 2^24 walks of 64 steps from uniform start vertices, grouped
+into bouquets by start vertex (bq_walk_batch, BOUQUET mode): the grouping
+kernels plus the bouquet walk kernel with visit counting.  Inputs are resident
+in HBM; L2 is flushed (256 MiB write) between timed steps.
+
+Beside it, on the same line:
+  naive         the one-walk-per-thread kernel on the same batch;
+  aesc          AESC at eps = 0.1 (certified plan) on the tiny ER graph
+                (n = 1000, m = 5000 plus a spanning path), all edges;
+  e2e           the same walk batch through the C ABI with host buffers
+                (starts in, visits out, copies inside the timed region);
+  roofline      the bouquet walk kernel against the measured HBM copy peak,
+                20 algorithmic bytes per walk step;
+  cpu_baseline  the CPU oracle on a bounded sample of the same batch.
+
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("walk-steps/s and AESC edges/s at ε (Bouquet vs naive GPU), % memory roofline; "
+          "p50/p99 query latency")
+N_WALKS = 1 << 24
+N_STEPS = 64
+BYTES_PER_STEP = 20  # 16-byte {row start, row end} + 4-byte neighbour id
+WORKLOAD = "rmat20_ef16_walks2^24_len64"
+CPU_SAMPLE_WALKS = 1 << 20
+REF_SAMPLE_WALKS = 1 << 18
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-aesc", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--walk-lanes", type=int, default=None)
+    ap.add_argument("--aggregate", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def walk_kernel_traffic(kernel_file: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    prof = os.path.join(ROOT, "profiles", "walk_bouquet_kernel_rmat20.md")
+    src = os.path.join(ROOT, "paper_2410_14056_gb300", "csrc", kernel_file)
+    if not os.path.exists(prof):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(prof):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(g, starts, seed):
+    import oracle
+    sample = starts[:CPU_SAMPLE_WALKS]
+    t0 = time.perf_counter()
+    oracle.walk_batch(g, seed, sample, N_STEPS)
+    dt = time.perf_counter() - t0
+    return {"value": sample.size * N_STEPS / dt, "unit": "walk-steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"first {sample.size} walks of the batch x {N_STEPS} steps, "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from workloads import rmat20, uniform_starts
+    g = rmat20()
+    starts = uniform_starts(g, N_WALKS, 21)
+    sample = starts[:REF_SAMPLE_WALKS]
+    for _ in range(args.warmup):
+        oracle.walk_batch(g, 2024, sample[:4096], N_STEPS)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.walk_batch(g, 2024, sample, N_STEPS)
+        times.append(time.perf_counter() - t0)
+    per_step = sum(times) / len(times)
+    value = sample.size * N_STEPS / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "walk-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_walks_per_step": int(sample.size)},
+        "cpu_baseline": {"value": value, "unit": "walk-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample.size} walks x {N_STEPS} steps per step"},
+        "e2e": {"value": value, "unit": "walk-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def aesc_measure(bq, torch, steps, warmup):
+    """AESC at eps = 0.1 on the tiny ER graph, all edges, certified plan."""
+    import numpy as np
+    from workloads import er_with_path
+    g = er_with_path(1000, 5000, 1)
+    # spectrum of D^-1/2 A D^-1/2 (planner input, computed once on the host)
+    A = np.zeros((g.n, g.n))
+    for v in range(g.n):
+        A[v, g.row(v).astype(np.int64)] = 1.0
+    s = 1.0 / np.sqrt(g.degrees.astype(np.float64))
+    lam = np.linalg.eigvalsh(A * s[:, None] * s[None, :])
+    graph = bq.Graph.from_csr(g)
+    graph.set_spectrum(float(lam[-2]), float(min(lam[0], 0.0)))
+    tau, nw = bq.aesc_plan(graph, None, 0.1, 0.01)
+    steps_per_call = float(np.sum(2.0 * tau.astype(np.float64) * nw))
+    dtau = torch.from_numpy(tau.view(np.int32)).cuda()
+    dnw = torch.from_numpy(nw.view(np.int32)).cuda()
+    counts = torch.empty(4 * tau.size, dtype=torch.int32, device="cuda")
+    sc = torch.empty(tau.size, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        bq.aesc_estimate(graph, 5, None, dtau, dnw, counts=counts, sc=sc)
+    bq.sync()
+    bq.profile_read()
+    bq.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    for _ in range(steps):
+        ev0.record()
+        bq.aesc_estimate(graph, 5, None, dtau, dnw, counts=counts, sc=sc)
+        ev1.record()
+        ev1.synchronize()
+        lat.append(ev0.elapsed_time(ev1))
+    bq.sync()
+    prof = bq.profile_read()
+    bq.profile_enable(False)
+    ms = sum(lat) / len(lat)
+    kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
+    return {
+        "workload": "er1000_m5000_path, all 5990 edges, eps=0.1, delta=0.01, certified",
+        "edges": int(tau.size), "edges_per_s": tau.size / (ms / 1e3),
+        "walk_steps_per_call": steps_per_call,
+        "walk_steps_per_s": steps_per_call / (ms / 1e3),
+        "ms_per_estimate": ms, "p50_ms": statistics.median(lat),
+        "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "count_kernel_ms": kern_ms,
+        "count_kernel_gbs": steps_per_call * BYTES_PER_STEP / (kern_ms / 1e3) / 1e9,
+    }
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_2410_14056_gb300 as bq
+    from workloads import rmat20, uniform_starts
+
+    if args.walk_lanes or args.aggregate is not None:
+        t = bq.get_tuning()
+        bq.set_tuning(walk_lanes=args.walk_lanes or t["walk_lanes"],
+                      aggregate_visits=t["aggregate_visits"] if args.aggregate is None else args.aggregate)
+
+    g = rmat20()
+    seed = 2024 + rank
+    starts = uniform_starts(g, N_WALKS, 21 + rank)
+    graph = bq.Graph.from_csr(g)
+    st = torch.from_numpy(starts.view(np.int32)).cuda()
+    visits = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def one_step(mode):
+        visits.zero_()
+        bq.walk_batch(graph, seed, st, N_STEPS, mode=mode, visits=visits)
+
+    def timed(mode, steps, warmup):
+        for _ in range(warmup):
+            one_step(mode)
+        bq.sync()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        bq.profile_read()
+        bq.profile_enable(True)
+        evs = []
+        for k in range(steps):
+            flush.fill_(k)  # evict the previous step's lines from L2 (untimed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            one_step(mode)
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        bq.sync()
+        if dist:
+            dist.barrier()
+        prof = bq.profile_read()
+        bq.profile_enable(False)
+        total_ms = sum(a.elapsed_time(b) for a, b in evs)
+        if dist:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, prof
+
+    with ClockSampler(local) as clocks:
+        total_ms, prof = timed(bq.MODE_BOUQUET, args.steps, args.warmup)
+    ms_per_step = total_ms / args.steps
+    steps_per_batch = N_WALKS * N_STEPS
+    value = world * steps_per_batch / (ms_per_step / 1e3)
+    walk_ms = prof["walk_ms"] / max(prof["walk_launches"], 1)
+    group_ms = prof["group_ms"] / max(prof["group_launches"], 1)
+    launches = prof["kernel_launches"]
+
+    naive_ms, _ = timed(bq.MODE_NAIVE, max(3, args.steps // 2), 1)
+    naive_ms /= max(3, args.steps // 2)
+
+    peak, peak_kind = measured_peaks()
+    algo_bytes = BYTES_PER_STEP * steps_per_batch
+    achieved = algo_bytes / (walk_ms / 1e3) / 1e9
+    traffic = walk_kernel_traffic("walks.cu")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "walk_bouquet_kernel", "kernel_ms": walk_ms,
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    e2e = None
+    if not args.no_e2e:
+        host_starts = torch.from_numpy(starts.view(np.int32)).pin_memory().numpy().view(np.uint32)
+        host_visits = torch.zeros(g.n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        for _ in range(2):
+            bq.walk_batch_host(graph, seed, host_starts, N_STEPS, visits=host_visits)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_visits[:] = 0
+            bq.walk_batch_host(graph, seed, host_starts, N_STEPS, visits=host_visits)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * steps_per_batch / e2e_s, "unit": "walk-steps/s",
+               "h2d_bytes_per_step": int(starts.nbytes + 4 * g.n),
+               "d2h_bytes_per_step": int(4 * g.n), "ms_per_step": e2e_s * 1e3,
+               "api": "bq_walk_batch with BQ_HOST_IO (pinned host buffers)"}
+
+    aesc = None
+    if not args.no_aesc and rank == 0:
+        aesc = aesc_measure(bq, torch, max(5, args.steps), args.warmup)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        cpu = cpu_baseline(g, starts, seed)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "walk-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph": g.describe(),
+                       "n_walks_per_gpu": N_WALKS, "n_steps": N_STEPS,
+                       "starts": "uniform over non-isolated vertices (seeded)",
+                       "mode": "BOUQUET, independent sampler", "tuning": bq.get_tuning(),
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world} (each GPU its own batch)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps,
+            "clocks": clocks.summary(),
+            "grouping_ms_per_step": group_ms,
+            "naive": {"value": world * steps_per_batch / (naive_ms / 1e3), "unit": "walk-steps/s",
+                      "ms_per_step": naive_ms,
+                      "bouquet_speedup": naive_ms / ms_per_step},
+            "aesc": aesc,
+        }
+        print(json.dumps(line), flush=True)
+    graph.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,281 @@
+/*
+ * bouquet.h - C ABI of the GB300 random-walk spanning-centrality library.
+ *
+ * The library implements the walk hot path of "Approximating Spanning
+ * Centrality with Random Bouquets" (arXiv 2410.14056): hash-keyed neighbour
+ * sampling (Sec. 3.1, Sec. 3.3 Eq. select-proposed), walks advanced in
+ * lockstep bouquets (Alg. 3), visit counting (Sec. 4), and the walk loop of
+ * TGT+ (Alg. 1) turned into per-edge hit counters and an FP64 estimate of
+ * spanning centrality SC(e) = R_eff(u, v) (Sec. 2.1) to absolute error eps
+ * (the eps-approximation problem of Sec. 2.1).
+ *
+ * Conventions for every call:
+ *   - Return value: BQ_OK (0) or a negative BQ_E* code.  A failed call leaves
+ *     a message readable with bq_last_error() on the calling thread.
+ *   - Pointers suffixed _dev are device pointers on the graph's device; other
+ *     array pointers are host pointers unless a flag says otherwise.
+ *   - Calls taking a stream enqueue their work on it (a CUDA stream handle,
+ *     cudaStream_t passed as void*; NULL = the legacy default stream) and
+ *     return without waiting, unless BQ_HOST_IO is given.  Errors found by
+ *     the kernels are recorded in a per-device status word and returned by
+ *     bq_sync().
+ *   - The library never reads or writes caller memory after a call returns,
+ *     except the device buffers of asynchronous calls, which the caller must
+ *     keep alive until the stream reaches the call.
+ *   - Vertex ids are uint32, CSR offsets int64; a graph is undirected and
+ *     unweighted: symmetric CSR, rows sorted increasingly, no self-loops, no
+ *     duplicate entries.
+ */
+#ifndef BOUQUET_H
+#define BOUQUET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define BQ_OK 0
+#define BQ_EINVAL (-1)    /* bad argument (null pointer, size, flag, range) */
+#define BQ_ENOMEM (-2)    /* device or host allocation failed */
+#define BQ_EGRAPH (-3)    /* graph rejected by validation (message says why) */
+#define BQ_ENOEDGE (-4)   /* a queried vertex pair is not an edge */
+#define BQ_EOVERFLOW (-5) /* a uint32 counter would wrap, or tau too large */
+#define BQ_ETIMEOUT (-6)  /* a bounded device wait gave up */
+#define BQ_EBUSY (-7)     /* admission refused: not enough free memory/slots */
+#define BQ_ECUDA (-8)     /* a CUDA runtime call failed (message has it) */
+
+/* ------------------------------------------------------- bq_graph_create */
+#define BQ_HOST_PTRS 0x0u         /* offsets / nbrs are host pointers */
+#define BQ_DEVICE_PTRS 0x1u       /* offsets / nbrs are device pointers */
+#define BQ_BORROW 0x2u            /* with BQ_DEVICE_PTRS: use the caller's
+                                     buffers in place, no copy; they must stay
+                                     alive and unchanged until destroy */
+#define BQ_SKIP_VALIDATE 0x4u     /* skip the symmetry and sortedness checks
+                                     (bounds of offsets and ids are always
+                                     checked, so no kernel can read outside
+                                     the arrays) */
+#define BQ_REQUIRE_CONNECTED 0x8u /* reject a graph with more than one
+                                     connected component */
+
+typedef struct bq_graph bq_graph;
+
+/*
+ * Load an undirected graph (the notation of Sec. 2: Gamma(v) = row v of the
+ * CSR, d(v) = its length).  n vertices, offsets[n + 1] (int64, offsets[0] =
+ * 0, non-decreasing), nbrs[offsets[n]] (uint32 ids < n).  The library builds
+ * its device-side derived arrays (per-vertex records of row offset and
+ * degree, the canonical edge numbering) on `cuda_stream` and synchronises
+ * that stream before returning.  Validation failures return BQ_EGRAPH with a
+ * message naming the first bad vertex.  On success *out owns the device
+ * memory it allocated; release it with bq_graph_destroy.
+ */
+int bq_graph_create(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                    uint32_t flags, void *cuda_stream, bq_graph **out);
+
+/* Free a graph and everything it owns (not borrowed buffers).  NULL is a no-op.
+ * The caller must not destroy a graph while work using it is in flight. */
+int bq_graph_destroy(bq_graph *g);
+
+typedef struct bq_graph_info_t {
+    uint64_t n;            /* vertices */
+    uint64_t m;            /* undirected edges (nnz / 2) */
+    uint64_t nnz;          /* CSR entries */
+    uint32_t min_degree;
+    uint32_t max_degree;
+    int32_t bipartite;     /* 1 / 0 (computed on first request) */
+    int32_t n_components;  /* connected components, isolated vertices included */
+    uint64_t device_bytes; /* device memory owned by the graph */
+    int32_t has_spectrum;  /* bq_graph_set_spectrum was called */
+    int32_t device;        /* CUDA device ordinal */
+    double lambda2;        /* as set by bq_graph_set_spectrum */
+    double lambda_neg;
+} bq_graph_info_t;
+
+/* Fill *info (host struct).  May copy the CSR to the host once to find the
+ * bipartite flag and the component count. */
+int bq_graph_info(bq_graph *g, bq_graph_info_t *info);
+
+/*
+ * Spectral inputs of the certified planner: eigenvalues of
+ * D^-1/2 A D^-1/2, the matrix whose eigenpairs CalculateTau uses (Sec. 2.3).
+ * lambda2 = second-largest eigenvalue (< 1 for a connected graph);
+ * lambda_neg = the most negative eigenvalue once one exact -1 is removed for
+ * a bipartite graph (0.0 when none is left).  Requires -1 <= lambda_neg <= 0
+ * and lambda2 < 1.
+ */
+int bq_graph_set_spectrum(bq_graph *g, double lambda2, double lambda_neg);
+
+/* ---------------------------------------------------------- bq_walk_batch */
+#define BQ_MODE_NAIVE 0u   /* one walk per thread, walks in input order */
+#define BQ_MODE_BOUQUET 1u /* walks grouped by start vertex, one bouquet of
+                              lanes per warp (Alg. 3), several walks per lane */
+
+#define BQ_VISIT_START 0x1u /* also count position 0 (the start) */
+#define BQ_HOST_IO 0x2u     /* starts / visits / paths (walk batch) or
+                               edges / tau / nwalks / counts / sc (AESC) are
+                               host pointers: the call copies them in and out
+                               and waits for the stream before returning */
+
+#define BQ_SAMPLER_IND 0u     /* every walk independent */
+#define BQ_SAMPLER_COUPLED 1u /* walks k with equal floor(k / width) share the
+                                 top t bits of their random word at the same
+                                 (step, vertex): similar walks stay together
+                                 (the aim of SABA, Sec. 3.3), each walk still
+                                 an exact random walk */
+
+typedef struct bq_sampler {
+    uint32_t kind;  /* BQ_SAMPLER_IND or BQ_SAMPLER_COUPLED */
+    uint32_t t;     /* COUPLED: shared bits, 0..32 (32 = move together) */
+    uint32_t width; /* COUPLED: group size, >= 1 */
+} bq_sampler;
+
+/*
+ * Walk batch (Alg. 2 / Alg. 3 with the hash-keyed choice of Eq.
+ * select-proposed; the synthetic random-walk benchmark of Sec. 4).
+ * Walk i (0 <= i < n_walks) starts at starts_dev[i] and takes n_steps steps;
+ * at step l = 1..n_steps it moves from cur to
+ *     Gamma(cur)[ floor(H(seed, batch stream, i, l, cur) * d(cur) / 2^32) ],
+ * a vertex without neighbours keeping the walk in place.  Walk i's path
+ * depends only on (seed, i, starts[i], sampler, graph): mode (NAIVE or
+ * BOUQUET) changes the speed, never the result.
+ *   visits_dev  uint32[n], ACCUMULATED: visits[v] += number of positions
+ *               l = 1..n_steps (and l = 0 with BQ_VISIT_START) at v.
+ *   paths_dev   NULL or uint32[n_walks][n_steps + 1], row i = positions
+ *               0..n_steps of walk i (row-major, written).
+ *   sampler     NULL = BQ_SAMPLER_IND.
+ * A start id >= n skips that walk and makes bq_sync report BQ_EINVAL.  When
+ * n_walks * positions > UINT32_MAX a checked counter path is used and a wrap
+ * is reported as BQ_EOVERFLOW by bq_sync; below that bound a counter that
+ * starts at zero cannot wrap.  BOUQUET mode needs n_walks < 2^32 and
+ * allocates scratch from the stream-ordered pool (freed on the stream).
+ */
+int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev,
+                  uint64_t n_walks, uint32_t n_steps, uint32_t mode,
+                  const bq_sampler *sampler, uint32_t flags, uint32_t *visits_dev,
+                  uint32_t *paths_dev, void *stream);
+
+/* ---------------------------------------------------------- bq_aesc_plan */
+#define BQ_PLAN_CERTIFIED 0u
+#define BQ_PLAN_SCHEDULED 1u
+
+typedef struct bq_schedule {
+    /* SCHEDULED plans: tau = clamp(ceil(tau_scale * ln(s_e / eps)) + tau_add,
+     * 1, tau_max) and N = max(n_min, ceil(n_scale * s_e^2 / eps^2)). */
+    double tau_scale;
+    uint32_t tau_add;
+    uint32_t tau_max;
+    double n_scale;
+    uint32_t n_min;
+    uint32_t reserved;
+} bq_schedule;
+
+/*
+ * Per-edge truncation length tau and walk count N (CalculateTau and NWalks
+ * of Alg. 1, which the paper leaves to the TGT+ paper).  edges_uv = k vertex
+ * pairs (host, uint32[2k], either orientation), or NULL for all m edges in
+ * canonical order (k must then equal m).  Outputs host uint32[k].
+ *   CERTIFIED: needs bq_graph_set_spectrum.  With s_e = 1/d_u + 1/d_v,
+ *     tau = least tau >= 1 with s_e * max(P(tau), Q(tau)) <= eps / 2, where
+ *     P(tau) = lambda2^tau (1 + lambda2) / (2 (1 - lambda2)) (0 if lambda2 <= 0)
+ *     Q(tau) = max over 0 <= x <= -lambda_neg of x^tau (1 - x) / (2 (1 + x)),
+ *     N = ceil(8 (tau - 1/2)^2 s_e^2 ln(2 m / delta) / eps^2),
+ *     so that |SC_hat(e) - SC(e)| <= eps for all edges with probability at
+ *     least 1 - delta (truncation eps/2 + Hoeffding eps/2).
+ *   SCHEDULED: sched gives tau and N from s_e and eps (no guarantee).
+ * Errors: BQ_ENOEDGE (a pair is not an edge), BQ_EOVERFLOW (2 N tau >= 2^32
+ * or tau > tau_max), BQ_EINVAL (eps, delta out of range, no spectrum).
+ */
+int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps,
+                 double delta, uint32_t plan_mode, const bq_schedule *sched,
+                 uint32_t *tau, uint32_t *nwalks);
+
+/* ------------------------------------------------------ bq_aesc_estimate */
+/*
+ * Estimate SC for k query edges (the walk loop and final sum of Alg. 1 at
+ * zero push depth).  For query q = {u, v} (normalised to u < v; e = its
+ * canonical id: edges ordered by u, then v, as in the CSR) and walk index
+ * w < nwalks[q], side 0 walks from u on stream 2e, side 1 from v on stream
+ * 2e + 1, tau[q] steps each.  A hit at step l weighs 2 (l < tau) or 1
+ * (l = tau):
+ *   counts_dev[4q + 0] = C_uu   (side 0 on u)    [+1] = C_uv (side 0 on v)
+ *   counts_dev[4q + 2] = C_vu   (side 1 on u)    [+3] = C_vv (side 1 on v)
+ *   sc_dev[q] = s_e + ((C_uu - C_vu)/d_u + (C_vv - C_uv)/d_v) / (2 nwalks[q]),
+ *   s_e = 1/d_u + 1/d_v, each FP64 operation rounded separately in that order.
+ * edges_uv_dev = NULL means all m edges in canonical order (k = m).  counts
+ * are overwritten.  A pair that is not an edge gets sc = NaN and bq_sync
+ * reports BQ_ENOEDGE; 2 nwalks tau >= 2^32 gets NaN and BQ_EOVERFLOW.
+ * Results depend only on (seed, graph, the pair, its tau and nwalks,
+ * sampler): not on the other queried edges.  sampler NULL = independent.
+ * Scratch comes from the stream-ordered pool.
+ */
+int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev,
+                     uint64_t k, const uint32_t *tau_dev, const uint32_t *nwalks_dev,
+                     const bq_sampler *sampler, uint32_t flags, uint32_t *counts_dev,
+                     double *sc_dev, void *stream);
+
+/* ---------------------------------------------------------------- tuning */
+/*
+ * Process-wide performance knobs of the kernels (the choices an autotuner
+ * makes).  They never change a result: visit counts, AESC counters and
+ * estimates are identical for every setting.  The paper's bouquet width B is
+ * the number of lockstep lanes (Alg. 3); on the GPU a bouquet is one warp of
+ * 32 lanes, each lane advancing `walk_lanes` (walk batch) or `aesc_lanes`
+ * (AESC) walks, so the paper's B corresponds to 32 x lanes here.
+ */
+typedef struct bq_tuning {
+    uint32_t walk_lanes;       /* walks per lane, bouquet walk batch: 1, 2, 4, 8 */
+    uint32_t aggregate_visits; /* 1: merge equal-vertex visits in a warp first */
+    uint32_t aesc_lanes;       /* walks per lane, AESC counting: 2, 4, 8 */
+    uint32_t reserved;
+} bq_tuning;
+
+int bq_get_tuning(bq_tuning *out);
+int bq_set_tuning(const bq_tuning *in);
+
+/* ------------------------------------------------------------- profiling */
+/*
+ * Kernel timing for roofline measurement (the paper has no counterpart).
+ * While enabled, the library brackets its kernels with CUDA events recorded
+ * on the caller's stream (no extra synchronisation) and counts every kernel
+ * it launches.  bq_profile_read waits for the recorded events, returns the
+ * summed device time per kernel group since the previous read, and resets
+ * the sums.  Counting launches is always on.
+ */
+typedef struct bq_profile {
+    double walk_ms;          /* walk kernels (bouquet or naive) */
+    uint64_t walk_launches;
+    double group_ms;         /* grouping of walks by start vertex */
+    uint64_t group_launches;
+    double aesc_ms;          /* AESC counting kernel */
+    uint64_t aesc_launches;
+    double aesc_aux_ms;      /* AESC edge preparation, task scan, finalize */
+    uint64_t aesc_aux_launches;
+    uint64_t kernel_launches; /* every kernel the library launched */
+} bq_profile;
+
+int bq_profile_enable(int enable);
+int bq_profile_read(bq_profile *out);
+
+/* ------------------------------------------------------------ errors */
+/* Wait for `stream`, then read and clear the status word of the current
+ * device: BQ_OK, or the code of the first error a kernel recorded since the
+ * last bq_sync (BQ_EINVAL bad start, BQ_ENOEDGE, BQ_EOVERFLOW, ...). */
+int bq_sync(void *stream);
+
+/* Static English text of a status code. */
+const char *bq_strerror(int code);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bq_last_error(void);
+
+/* Library version string. */
+const char *bq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOUQUET_H */

@@ -1,0 +1,354 @@
+"""ctypes binding of libbouquet (the C ABI in include/bouquet.h).
+
+Argument marshalling only: every step of the walk path runs in the CUDA
+kernels of the library.  PyTorch supplies device memory and streams (a
+tensor's ``data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``).
+There is no CPU fallback: if ``libbouquet.so`` is missing the first call
+raises ``RuntimeError``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbouquet.so")
+
+OK = 0
+EINVAL = -1
+ENOMEM = -2
+EGRAPH = -3
+ENOEDGE = -4
+EOVERFLOW = -5
+ETIMEOUT = -6
+EBUSY = -7
+ECUDA = -8
+
+HOST_PTRS = 0x0
+DEVICE_PTRS = 0x1
+BORROW = 0x2
+SKIP_VALIDATE = 0x4
+REQUIRE_CONNECTED = 0x8
+
+MODE_NAIVE = 0
+MODE_BOUQUET = 1
+VISIT_START = 0x1
+HOST_IO = 0x2
+
+SAMPLER_IND = 0
+SAMPLER_COUPLED = 1
+
+PLAN_CERTIFIED = 0
+PLAN_SCHEDULED = 1
+
+
+class Sampler(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("t", ctypes.c_uint32), ("width", ctypes.c_uint32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("tau_scale", ctypes.c_double), ("tau_add", ctypes.c_uint32),
+                ("tau_max", ctypes.c_uint32), ("n_scale", ctypes.c_double),
+                ("n_min", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("walk_lanes", ctypes.c_uint32), ("aggregate_visits", ctypes.c_uint32),
+                ("aesc_lanes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint64), ("nnz", ctypes.c_uint64),
+                ("min_degree", ctypes.c_uint32), ("max_degree", ctypes.c_uint32),
+                ("bipartite", ctypes.c_int32), ("n_components", ctypes.c_int32),
+                ("device_bytes", ctypes.c_uint64), ("has_spectrum", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("lambda2", ctypes.c_double),
+                ("lambda_neg", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("walk_ms", ctypes.c_double), ("walk_launches", ctypes.c_uint64),
+                ("group_ms", ctypes.c_double), ("group_launches", ctypes.c_uint64),
+                ("aesc_ms", ctypes.c_double), ("aesc_launches", ctypes.c_uint64),
+                ("aesc_aux_ms", ctypes.c_double), ("aesc_aux_launches", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64)]
+
+
+# every symbol include/bouquet.h declares
+EXPORTS = (
+    "bq_graph_create", "bq_graph_destroy", "bq_graph_info", "bq_graph_set_spectrum",
+    "bq_walk_batch", "bq_aesc_plan", "bq_aesc_estimate", "bq_sync", "bq_strerror",
+    "bq_last_error", "bq_version", "bq_get_tuning", "bq_set_tuning", "bq_profile_enable",
+    "bq_profile_read",
+)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libbouquet.so (no GPU needed to load it)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"{p} is missing: build it with paper_2410_14056_gb300.build.build() "
+                "(the library has no CPU fallback)")
+        L = ctypes.CDLL(p)
+        c = ctypes
+        vp = c.c_void_p
+        u32, u64, f64, i32 = c.c_uint32, c.c_uint64, c.c_double, c.c_int
+        L.bq_graph_create.argtypes = [u32, vp, vp, u32, vp, c.POINTER(vp)]
+        L.bq_graph_destroy.argtypes = [vp]
+        L.bq_graph_info.argtypes = [vp, c.POINTER(GraphInfo)]
+        L.bq_graph_set_spectrum.argtypes = [vp, f64, f64]
+        L.bq_walk_batch.argtypes = [vp, u64, vp, u64, u32, u32, c.POINTER(Sampler), u32, vp, vp, vp]
+        L.bq_aesc_plan.argtypes = [vp, vp, u64, f64, f64, u32, c.POINTER(Schedule), vp, vp]
+        L.bq_aesc_estimate.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp, vp]
+        L.bq_sync.argtypes = [vp]
+        L.bq_strerror.argtypes = [i32]
+        L.bq_strerror.restype = c.c_char_p
+        L.bq_last_error.argtypes = []
+        L.bq_last_error.restype = c.c_char_p
+        L.bq_version.restype = c.c_char_p
+        L.bq_get_tuning.argtypes = [c.POINTER(Tuning)]
+        L.bq_set_tuning.argtypes = [c.POINTER(Tuning)]
+        L.bq_profile_enable.argtypes = [i32]
+        L.bq_profile_read.argtypes = [c.POINTER(Profile)]
+        for name in EXPORTS:
+            if name not in ("bq_strerror", "bq_last_error", "bq_version"):
+                getattr(L, name).restype = i32
+        if path is None:
+            _lib = L
+        return L
+
+
+class BouquetError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"[{code}] {message}")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != OK:
+        L = load_library()
+        msg = L.bq_last_error().decode() or L.bq_strerror(rc).decode()
+        raise BouquetError(rc, msg)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _sampler(sampler):
+    if sampler is None:
+        return None
+    if isinstance(sampler, Sampler):
+        return ctypes.byref(sampler)
+    kind, t, width = sampler
+    return ctypes.byref(Sampler(int(kind), int(t), int(width)))
+
+
+def _dptr(t, what, elem=4):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if t.element_size() != elem or not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous with {elem}-byte elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, what, dtype):
+    if a is None:
+        return None
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what} must be a C-contiguous {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Graph:
+    """A graph resident on the current CUDA device."""
+
+    def __init__(self, n: int, offsets, nbrs, flags: int = HOST_PTRS, stream=None):
+        L = load_library()
+        self._h = ctypes.c_void_p()
+        if flags & DEVICE_PTRS:
+            self._keep = (offsets, nbrs)  # borrowed buffers stay alive
+            po = _dptr(offsets, "offsets", 8)
+            pn = _dptr(nbrs, "nbrs", 4)
+        else:
+            offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+            nbrs = np.ascontiguousarray(nbrs, dtype=np.uint32)
+            if offsets.size != int(n) + 1 or (n >= 0 and nbrs.size < int(offsets[-1])):
+                raise ValueError("offsets must have n + 1 entries and nbrs at least offsets[n]")
+            self._keep = None
+            po = _hptr(offsets, "offsets", np.int64)
+            pn = _hptr(nbrs, "nbrs", np.uint32)
+        _check(L.bq_graph_create(int(n), po, pn, int(flags), _stream_handle(stream),
+                                 ctypes.byref(self._h)))
+        self.n = int(n)
+
+    @classmethod
+    def from_csr(cls, g, flags: int = HOST_PTRS, stream=None) -> "Graph":
+        """From any object with n, offsets, nbrs (e.g. workloads.Graph)."""
+        return cls(g.n, g.offsets, g.nbrs, flags, stream)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("graph has been closed")
+        return self._h
+
+    def info(self) -> dict:
+        gi = GraphInfo()
+        _check(load_library().bq_graph_info(self.handle, ctypes.byref(gi)))
+        return {name: getattr(gi, name) for name, _ in GraphInfo._fields_}
+
+    def set_spectrum(self, lambda2: float, lambda_neg: float):
+        _check(load_library().bq_graph_set_spectrum(self.handle, float(lambda2), float(lambda_neg)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().bq_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def walk_batch(graph: Graph, seed: int, starts, n_steps: int, mode: int = MODE_BOUQUET,
+               sampler=None, visit_start: bool = False, visits=None, paths=None, stream=None):
+    """Enqueue a walk batch on device tensors; returns `visits` (accumulated)."""
+    import torch
+    L = load_library()
+    n_walks = starts.numel()
+    if visits is None:
+        visits = torch.zeros(graph.n, dtype=torch.int32, device=starts.device)
+    flags = VISIT_START if visit_start else 0
+    _check(L.bq_walk_batch(graph.handle, int(seed) & (2**64 - 1), _dptr(starts, "starts"), n_walks,
+                           int(n_steps), int(mode), _sampler(sampler), flags,
+                           _dptr(visits, "visits"), _dptr(paths, "paths"), _stream_handle(stream)))
+    return visits
+
+
+def walk_batch_host(graph: Graph, seed: int, starts: np.ndarray, n_steps: int,
+                    mode: int = MODE_BOUQUET, sampler=None, visit_start: bool = False,
+                    visits: np.ndarray | None = None, paths: np.ndarray | None = None,
+                    stream=None) -> np.ndarray:
+    """Walk batch on host arrays (the library copies in and out and waits)."""
+    L = load_library()
+    starts = np.ascontiguousarray(starts, dtype=np.uint32)
+    if visits is None:
+        visits = np.zeros(graph.n, np.uint32)
+    flags = HOST_IO | (VISIT_START if visit_start else 0)
+    _check(L.bq_walk_batch(graph.handle, int(seed) & (2**64 - 1), _hptr(starts, "starts", np.uint32),
+                           starts.size, int(n_steps), int(mode), _sampler(sampler), flags,
+                           _hptr(visits, "visits", np.uint32), _hptr(paths, "paths", np.uint32),
+                           _stream_handle(stream)))
+    return visits
+
+
+def aesc_plan(graph: Graph, uv: np.ndarray | None, eps: float, delta: float = 0.01,
+              mode: int = PLAN_CERTIFIED, schedule: Schedule | None = None):
+    """Host planner: returns (tau, nwalks) as uint32 numpy arrays."""
+    L = load_library()
+    if uv is None:
+        k = graph.info()["m"]
+        puv = None
+    else:
+        uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+        k = uv.shape[0]
+        puv = _hptr(uv, "edges", np.uint32)
+    tau = np.zeros(k, np.uint32)
+    nw = np.zeros(k, np.uint32)
+    _check(L.bq_aesc_plan(graph.handle, puv, k, float(eps), float(delta), int(mode),
+                          ctypes.byref(schedule) if schedule is not None else None,
+                          _hptr(tau, "tau", np.uint32), _hptr(nw, "nwalks", np.uint32)))
+    return tau, nw
+
+
+def aesc_estimate(graph: Graph, seed: int, uv, tau, nwalks, sampler=None, counts=None,
+                  sc=None, stream=None):
+    """Enqueue an AESC estimate on device tensors; returns (counts, sc)."""
+    import torch
+    L = load_library()
+    k = tau.numel()
+    dev = tau.device
+    if counts is None:
+        counts = torch.empty(4 * k, dtype=torch.int32, device=dev)
+    if sc is None:
+        sc = torch.empty(k, dtype=torch.float64, device=dev)
+    _check(L.bq_aesc_estimate(graph.handle, int(seed) & (2**64 - 1), _dptr(uv, "edges"), k,
+                              _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), _sampler(sampler), 0,
+                              _dptr(counts, "counts"), _dptr(sc, "sc", 8), _stream_handle(stream)))
+    return counts, sc
+
+
+def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.ndarray,
+                       nwalks: np.ndarray, sampler=None, stream=None):
+    """AESC estimate on host arrays; returns (counts uint32[4k], sc float64[k])."""
+    L = load_library()
+    tau = np.ascontiguousarray(tau, dtype=np.uint32)
+    nwalks = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    k = tau.size
+    puv = None
+    if uv is not None:
+        uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+        puv = _hptr(uv, "edges", np.uint32)
+    counts = np.zeros(4 * k, np.uint32)
+    sc = np.zeros(k, np.float64)
+    _check(L.bq_aesc_estimate(graph.handle, int(seed) & (2**64 - 1), puv, k,
+                              _hptr(tau, "tau", np.uint32), _hptr(nwalks, "nwalks", np.uint32),
+                              _sampler(sampler), HOST_IO, _hptr(counts, "counts", np.uint32),
+                              _hptr(sc, "sc", np.float64), _stream_handle(stream)))
+    return counts, sc
+
+
+def sync(stream=None):
+    """Wait for the stream and raise the first error its kernels recorded."""
+    _check(load_library().bq_sync(_stream_handle(stream)))
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    _check(load_library().bq_get_tuning(ctypes.byref(t)))
+    return {"walk_lanes": t.walk_lanes, "aggregate_visits": t.aggregate_visits,
+            "aesc_lanes": t.aesc_lanes}
+
+
+def set_tuning(**kw):
+    cur = get_tuning()
+    cur.update(kw)
+    t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]), 0)
+    _check(load_library().bq_set_tuning(ctypes.byref(t)))
+
+
+def profile_enable(on: bool = True):
+    """Bracket the library's kernels with CUDA events (see bq_profile_read)."""
+    _check(load_library().bq_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """Summed device time (ms) and launch counts per kernel group since the
+    previous read; waits for the recorded events."""
+    p = Profile()
+    _check(load_library().bq_profile_read(ctypes.byref(p)))
+    return {name: getattr(p, name) for name, _ in Profile._fields_}
+
+
+def version() -> str:
+    return load_library().bq_version().decode()

@@ -1,0 +1,334 @@
+// AESC kernels: the walk loop of TGT+ (Alg. 1) at zero push depth, turned
+// into integer hit counters per query edge, and the final sum
+// s(e) = g(u,v) + g(v,u) with g initialised to 1/d (Alg. 1).
+//
+// Work decomposition (GB300): a task is one bouquet of 32*W walks of one side
+// of one edge, all starting at the same endpoint (Alg. 3 with B = 32*W).  A
+// persistent grid of warps pulls tasks from a global counter; each lane
+// advances W walks in lockstep, keeps its hit counts in registers, and the
+// warp adds its two totals to the edge's counters with two atomics.
+#include <math.h>
+
+#include "hash.cuh"
+#include "internal.h"
+
+namespace bq {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct QueryInfo {
+    uint32_t u, v;    // normalised endpoints, u < v
+    uint64_t edge;    // canonical id
+    uint32_t du, dv;  // degrees
+    uint32_t tau, nwalks;
+    uint32_t valid;
+    uint32_t pad;
+};
+
+struct RecCompact {
+    const uint2 *rec;
+    __device__ __forceinline__ void load(uint32_t v, uint64_t &off, uint32_t &deg) const {
+        const uint2 r = __ldg(rec + v);
+        off = r.x;
+        deg = r.y;
+    }
+};
+
+struct RecWide {
+    const uint4 *rec;
+    __device__ __forceinline__ void load(uint32_t v, uint64_t &off, uint32_t &deg) const {
+        const uint4 r = __ldg(rec + v);
+        off = ((uint64_t)r.y << 32) | r.x;
+        deg = r.z;
+    }
+};
+
+// first index in [lo, hi) whose entry is >= key
+__device__ __forceinline__ int64_t lower_bound_row(const uint32_t *__restrict__ nbrs, int64_t lo, int64_t hi,
+                                                   uint32_t key) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (nbrs[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Canonical edge list: edge upper_before[u] + r is {u, r-th neighbour of u
+// above u}.  One warp per vertex.
+__global__ void canonical_edges_kernel(DeviceGraph g, uint32_t *__restrict__ uv) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = warp; u < g.n; u += nwarps) {
+        const int64_t lo = g.offsets[u], hi = g.offsets[u + 1];
+        const int64_t first = lower_bound_row(g.nbrs, lo, hi, (uint32_t)u + 1);
+        const uint64_t id0 = g.upper_before[u];
+        for (int64_t j = first + lane; j < hi; j += 32) {
+            const uint64_t id = id0 + (uint64_t)(j - first);
+            uv[2 * id] = (uint32_t)u;
+            uv[2 * id + 1] = g.nbrs[j];
+        }
+    }
+}
+
+__global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, uint64_t k,
+                               const uint32_t *__restrict__ tau, const uint32_t *__restrict__ nwalks,
+                               uint32_t bouquet, QueryInfo *__restrict__ info, uint32_t *__restrict__ tasks,
+                               double *__restrict__ sc, uint32_t *status) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        QueryInfo qi;
+        const uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        qi.u = a < b ? a : b;
+        qi.v = a < b ? b : a;
+        qi.tau = tau[q];
+        qi.nwalks = nwalks[q];
+        qi.valid = 0;
+        qi.edge = 0;
+        qi.du = qi.dv = 0;
+        qi.pad = 0;
+        uint32_t status_bits = 0;
+        if (a >= g.n || b >= g.n || a == b) {
+            status_bits = kStatusNoEdge;
+        } else {
+            const int64_t lo = g.offsets[qi.u], hi = g.offsets[qi.u + 1];
+            const int64_t pos = lower_bound_row(g.nbrs, lo, hi, qi.v);
+            if (pos >= hi || g.nbrs[pos] != qi.v) {
+                status_bits = kStatusNoEdge;
+            } else {
+                const int64_t first = lower_bound_row(g.nbrs, lo, hi, qi.u + 1);
+                qi.edge = g.upper_before[qi.u] + (uint64_t)(pos - first);
+                qi.du = (uint32_t)(hi - lo);
+                qi.dv = (uint32_t)(g.offsets[qi.v + 1] - g.offsets[qi.v]);
+                if (qi.tau == 0 || qi.nwalks == 0) status_bits = kStatusBadIndex;
+                else if (2ull * qi.nwalks * qi.tau >= (1ull << 32)) status_bits = kStatusOverflow;
+                else qi.valid = 1;
+            }
+        }
+        if (status_bits) atomicOr(status, status_bits);
+        info[q] = qi;
+        tasks[q] = qi.valid ? 2u * ((qi.nwalks + bouquet - 1) / bouquet) : 0u;
+        if (!qi.valid) sc[q] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+    }
+}
+
+__device__ __forceinline__ uint64_t find_query(const uint64_t *__restrict__ begin, uint64_t k, uint64_t t) {
+    // last q with begin[q] <= t (begin has k + 1 entries, begin[k] = total)
+    uint64_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (begin[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Persistent counting kernel.  Task t -> query q, side = local & 1, chunk =
+// local >> 1; the chunk's walks are [chunk*32W, min(N, (chunk+1)*32W)).
+// Independent sampler: lane l takes the W consecutive walks chunk*32W + l*W +
+// j, so walk pairs (2i, 2i+1) share one Philox block.  Coupled sampler: slot
+// j of lane l is walk chunk*32W + j*32 + l, so a coupling group of 32 fills
+// one lockstep slot.
+template <typename RL, int W, bool COUPLED>
+__global__ void __launch_bounds__(kThreads)
+aesc_count_kernel(RL rl, const uint32_t *__restrict__ nbrs, const QueryInfo *__restrict__ info,
+                  const uint64_t *__restrict__ begin, uint64_t k, uint64_t seed, Sampler smp,
+                  unsigned long long *__restrict__ next_task, uint32_t *__restrict__ counts) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t total = begin[k];
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(next_task, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        const uint64_t q = find_query(begin, k, t);
+        const QueryInfo qi = info[q];
+        const uint64_t local = t - begin[q];
+        const uint32_t side = (uint32_t)(local & 1);
+        const uint64_t chunk = local >> 1;
+        const uint64_t stream = 2 * qi.edge + side;
+        const uint32_t start = side ? qi.v : qi.u;
+        const uint64_t k0 = chunk * 32ull * W;
+
+        uint64_t st[W], gs[W];
+        uint32_t cur[W];
+        bool act[W];
+        if (!COUPLED && (W % 2 == 0)) {
+#pragma unroll
+            for (int j = 0; j < W; j += 2) {
+                const uint64_t kk = k0 + (uint64_t)lane * W + j;
+                walk_key_pair(seed, stream, kk >> 1, st[j], st[j + 1]);
+                act[j] = kk < qi.nwalks;
+                act[j + 1] = kk + 1 < qi.nwalks;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint64_t kk = COUPLED ? k0 + (uint64_t)j * 32 + lane : k0 + (uint64_t)lane * W + j;
+                st[j] = walk_key(seed, stream, kk);
+                if (COUPLED) gs[j] = walk_key(seed, stream | kGroupBit, kk / smp.width);
+                act[j] = kk < qi.nwalks;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            cur[j] = start;
+            if (!COUPLED) gs[j] = 0;
+        }
+        uint32_t hit_u = 0, hit_v = 0;
+        for (uint32_t l = 1; l <= qi.tau; ++l) {
+            const uint32_t weight = l < qi.tau ? 2u : 1u;
+            uint64_t off[W];
+            uint32_t d[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                st[j] += kGolden;
+                if (COUPLED) gs[j] += kGolden;
+                d[j] = 0;
+                off[j] = 0;
+                if (act[j]) rl.load(cur[j], off[j], d[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                if (d[j]) {
+                    cur[j] = nbrs[off[j] + choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), d[j])];
+                    hit_u += cur[j] == qi.u ? weight : 0u;
+                    hit_v += cur[j] == qi.v ? weight : 0u;
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            hit_u += __shfl_down_sync(0xffffffffu, hit_u, d);
+            hit_v += __shfl_down_sync(0xffffffffu, hit_v, d);
+        }
+        if (lane == 0) {
+            if (hit_u) atomicAdd(counts + 4 * q + 2 * side + 0, hit_u);
+            if (hit_v) atomicAdd(counts + 4 * q + 2 * side + 1, hit_v);
+        }
+    }
+}
+
+// s_e + ((C_uu - C_vu)/d_u + (C_vv - C_uv)/d_v) / (2N), every operation
+// rounded to nearest on its own (explicit _rn intrinsics: no contraction).
+__global__ void finalize_kernel(const QueryInfo *__restrict__ info, uint64_t k, const uint32_t *__restrict__ counts,
+                                double *__restrict__ sc) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const QueryInfo qi = info[q];
+        if (!qi.valid) continue;
+        const double du = (double)qi.du, dv = (double)qi.dv;
+        const double s = __dadd_rn(__ddiv_rn(1.0, du), __ddiv_rn(1.0, dv));
+        const uint32_t c_uu = counts[4 * q + 0], c_uv = counts[4 * q + 1];
+        const uint32_t c_vu = counts[4 * q + 2], c_vv = counts[4 * q + 3];
+        const double x = (double)((int64_t)c_uu - (int64_t)c_vu);
+        const double y = (double)((int64_t)c_vv - (int64_t)c_uv);
+        const double mean = __ddiv_rn(__dadd_rn(__ddiv_rn(x, du), __ddiv_rn(y, dv)), __dmul_rn(2.0, (double)qi.nwalks));
+        sc[q] = __dadd_rn(s, mean);
+    }
+}
+
+unsigned blocks_for(uint64_t items, uint64_t per_block) {
+    uint64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffull) b = 0x7fffffffull;
+    return (unsigned)b;
+}
+
+template <typename RL, int W, bool COUPLED>
+int launch_count(RL rl, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+                 uint64_t seed, const Sampler &smp, unsigned long long *next_task, uint32_t *counts,
+                 cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aesc_count_kernel<RL, W, COUPLED>, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    aesc_count_kernel<RL, W, COUPLED><<<sms * per_sm, kThreads, 0, s>>>(rl, g.nbrs, info, begin, k, seed, smp,
+                                                                         next_task, counts);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+template <typename RL>
+int launch_count_w(RL rl, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+                   uint64_t seed, const Sampler &smp, unsigned long long *next_task, uint32_t *counts,
+                   int w, cudaStream_t s) {
+    const bool coupled = smp.kind == 1;
+    switch (w) {
+    case 2:
+        return coupled ? launch_count<RL, 2, true>(rl, g, info, begin, k, seed, smp, next_task, counts, s)
+                       : launch_count<RL, 2, false>(rl, g, info, begin, k, seed, smp, next_task, counts, s);
+    case 8:
+        return coupled ? launch_count<RL, 8, true>(rl, g, info, begin, k, seed, smp, next_task, counts, s)
+                       : launch_count<RL, 8, false>(rl, g, info, begin, k, seed, smp, next_task, counts, s);
+    default:
+        return coupled ? launch_count<RL, 4, true>(rl, g, info, begin, k, seed, smp, next_task, counts, s)
+                       : launch_count<RL, 4, false>(rl, g, info, begin, k, seed, smp, next_task, counts, s);
+    }
+}
+
+}  // namespace
+
+int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k, const uint32_t *tau,
+                const uint32_t *nwalks, const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
+                cudaStream_t s) {
+    if (k == 0) return BQ_OK;
+    int w = tuning_aesc_walks_per_lane();
+    if (w != 2 && w != 4 && w != 8) w = 4;
+    const uint32_t bouquet = 32u * (uint32_t)w;
+    // scratch: info[k] | begin[k + 1] | tasks[k] | next_task | (edges[2k] if all-edges)
+    const size_t info_bytes = sizeof(QueryInfo) * k;
+    const size_t begin_bytes = sizeof(uint64_t) * (k + 1);
+    const size_t task_bytes = sizeof(uint32_t) * ((k + 1) & ~1ull);
+    const size_t edge_bytes = edges_uv ? 0 : sizeof(uint32_t) * 2 * k;
+    const size_t bytes = info_bytes + begin_bytes + task_bytes + 16 + edge_bytes;
+    char *buf = nullptr;
+    int rc = scratch_alloc((void **)&buf, bytes, s);
+    if (rc) return rc;
+    QueryInfo *info = (QueryInfo *)buf;
+    uint64_t *begin = (uint64_t *)(buf + info_bytes);
+    uint32_t *tasks = (uint32_t *)(buf + info_bytes + begin_bytes);
+    unsigned long long *next_task = (unsigned long long *)(buf + info_bytes + begin_bytes + task_bytes);
+    uint32_t *all_uv = (uint32_t *)(buf + info_bytes + begin_bytes + task_bytes + 16);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 4 * k, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next_task, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        scratch_free(buf, s);
+        return cuda_fail(e, "aesc setup");
+    }
+    const uint32_t *uv = edges_uv;
+    {
+        ProfScope prof(kProfAescAux, s);
+        if (!uv) {
+            count_launches(1);
+            canonical_edges_kernel<<<blocks_for((uint64_t)g.n * 32, kThreads), kThreads, 0, s>>>(g, all_uv);
+            uv = all_uv;
+        }
+        count_launches(1);
+        prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, info, tasks,
+                                                                    sc, status);
+        rc = scan_u32_to_u64(tasks, begin, k, s);
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAesc, s);
+        count_launches(1);
+        if (g.compact())
+            rc = launch_count_w(RecCompact{g.rec8}, g, info, begin, k, seed, smp, next_task, counts, w, s);
+        else
+            rc = launch_count_w(RecWide{g.rec16}, g, info, begin, k, seed, smp, next_task, counts, w, s);
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAescAux, s);
+        count_launches(1);
+        finalize_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, counts, sc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "finalize_kernel");
+    }
+    scratch_free(buf, s);
+    return rc;
+}
+
+}  // namespace bq

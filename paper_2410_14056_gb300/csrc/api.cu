@@ -1,0 +1,628 @@
+// C-ABI entry points of libbouquet (declared in include/bouquet.h): argument
+// checking, host-side staging for BQ_HOST_IO calls, the host planner, the
+// per-device status word, and error reporting.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace bq {
+
+namespace {
+thread_local char g_last_error[1024] = "";
+std::mutex g_dev_mutex;
+std::vector<uint32_t *> g_status;       // per device ordinal
+std::vector<char> g_pool_configured;    // per device ordinal
+
+std::atomic<int> g_walks_per_lane{4};
+std::atomic<int> g_aggregate{0};
+std::atomic<int> g_aesc_walks_per_lane{4};
+}  // namespace
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t err, const char *what) {
+    return fail(BQ_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(err), cudaGetErrorName(err));
+}
+
+int status_word(int device, uint32_t **out) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if ((int)g_status.size() <= device) {
+        g_status.resize(device + 1, nullptr);
+        g_pool_configured.resize(device + 1, 0);
+    }
+    if (!g_status[device]) {
+        uint32_t *p = nullptr;
+        BQ_CUDA(cudaMalloc(&p, sizeof(uint32_t)));
+        BQ_CUDA(cudaMemset(p, 0, sizeof(uint32_t)));
+        g_status[device] = p;
+    }
+    if (!g_pool_configured[device]) {
+        // Keep freed scratch in the device's default pool between calls
+        // instead of returning it to the driver at every synchronisation.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        g_pool_configured[device] = 1;
+    }
+    *out = g_status[device];
+    return BQ_OK;
+}
+
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(BQ_ENOMEM, "cannot allocate %zu bytes of device scratch", bytes);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    return BQ_OK;
+}
+
+void scratch_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ------------------------------------------------------------- profiling
+
+namespace {
+struct PendingTiming {
+    int kind;
+    cudaEvent_t start, stop;
+};
+std::mutex g_prof_mutex;
+std::atomic<int> g_prof_enabled{0};
+std::vector<PendingTiming> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_free_events;
+double g_prof_ms[4] = {0, 0, 0, 0};
+uint64_t g_prof_count[4] = {0, 0, 0, 0};
+std::atomic<uint64_t> g_launches{0};
+
+cudaEvent_t take_event() {
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if (!g_prof_free_events.empty()) {
+        cudaEvent_t e = g_prof_free_events.back();
+        g_prof_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+ProfScope::ProfScope(int k, cudaStream_t s) : kind(k), stream(s) {
+    if (!g_prof_enabled.load()) return;
+    start = take_event();
+    stop = take_event();
+    if (start && stop) cudaEventRecord(start, s);
+}
+
+ProfScope::~ProfScope() {
+    if (!start || !stop) return;
+    cudaEventRecord(stop, stream);
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    g_prof_pending.push_back(PendingTiming{kind, start, stop});
+}
+
+void count_launches(unsigned n) { g_launches.fetch_add(n); }
+
+int tuning_walks_per_lane() { return g_walks_per_lane.load(); }
+bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
+int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int check_sampler(const bq_sampler *in, Sampler &out) {
+    out.kind = 0;
+    out.t = 0;
+    out.width = 1;
+    if (!in) return BQ_OK;
+    if (in->kind == BQ_SAMPLER_IND) return BQ_OK;
+    if (in->kind != BQ_SAMPLER_COUPLED) return fail(BQ_EINVAL, "unknown sampler kind %u", in->kind);
+    if (in->width < 1) return fail(BQ_EINVAL, "coupled sampler needs width >= 1");
+    if (in->t > 32) return fail(BQ_EINVAL, "coupled sampler needs 0 <= t <= 32 (got %u)", in->t);
+    out.kind = 1;
+    out.t = in->t;
+    out.width = in->width;
+    return BQ_OK;
+}
+
+// Components and 2-colourability by BFS over the host copy of the CSR.
+void host_structure(bq_graph *g) {
+    if (g->n_components >= 0) return;
+    const uint32_t n = g->n;
+    std::vector<int8_t> color(n, -1);
+    std::vector<uint32_t> queue;
+    queue.reserve(1024);
+    int comps = 0;
+    bool bip = true;
+    for (uint32_t s = 0; s < n; ++s) {
+        if (color[s] >= 0) continue;
+        ++comps;
+        color[s] = 0;
+        queue.clear();
+        queue.push_back(s);
+        for (size_t h = 0; h < queue.size(); ++h) {
+            const uint32_t x = queue[h];
+            for (int64_t j = g->h_offsets[x]; j < g->h_offsets[x + 1]; ++j) {
+                const uint32_t y = g->h_nbrs[j];
+                if (color[y] < 0) {
+                    color[y] = (int8_t)(1 - color[x]);
+                    queue.push_back(y);
+                } else if (color[y] == color[x]) {
+                    bip = false;
+                }
+            }
+        }
+    }
+    g->n_components = comps;
+    g->bipartite = bip ? 1 : 0;
+}
+
+}  // namespace
+}  // namespace bq
+
+using namespace bq;
+
+extern "C" {
+
+const char *bq_version(void) { return "bouquet-gb300 0.1"; }
+
+const char *bq_last_error(void) { return g_last_error; }
+
+const char *bq_strerror(int code) {
+    switch (code) {
+    case BQ_OK: return "ok";
+    case BQ_EINVAL: return "invalid argument";
+    case BQ_ENOMEM: return "out of memory";
+    case BQ_EGRAPH: return "graph rejected by validation";
+    case BQ_ENOEDGE: return "vertex pair is not an edge";
+    case BQ_EOVERFLOW: return "counter or plan overflow";
+    case BQ_ETIMEOUT: return "bounded wait timed out";
+    case BQ_EBUSY: return "admission refused";
+    case BQ_ECUDA: return "CUDA runtime error";
+    default: return "unknown status code";
+    }
+}
+
+int bq_graph_create(uint32_t n, const int64_t *offsets, const uint32_t *nbrs, uint32_t flags, void *cuda_stream,
+                    bq_graph **out) {
+    g_last_error[0] = 0;
+    if (!out) return fail(BQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!offsets) return fail(BQ_EINVAL, "offsets is NULL");
+    if (flags & ~(BQ_DEVICE_PTRS | BQ_BORROW | BQ_SKIP_VALIDATE | BQ_REQUIRE_CONNECTED))
+        return fail(BQ_EINVAL, "unknown graph flags 0x%x", flags);
+    if ((flags & BQ_BORROW) && !(flags & BQ_DEVICE_PTRS))
+        return fail(BQ_EINVAL, "BQ_BORROW requires BQ_DEVICE_PTRS");
+    if (n == 0xffffffffu) return fail(BQ_EINVAL, "n must be < 2^32 - 1");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    uint32_t *status = nullptr;
+    int rc = status_word(dev, &status);
+    if (rc) return rc;
+
+    // nnz = offsets[n]
+    int64_t nnz = 0;
+    if (flags & BQ_DEVICE_PTRS) {
+        BQ_CUDA(cudaMemcpyAsync(&nnz, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BQ_CUDA(cudaStreamSynchronize(s));
+    } else {
+        nnz = offsets[n];
+    }
+    if (nnz < 0) return fail(BQ_EGRAPH, "offsets[n] = %lld is negative", (long long)nnz);
+    if (nnz > 0 && !nbrs) return fail(BQ_EINVAL, "nbrs is NULL");
+
+    bq_graph *g = new (std::nothrow) bq_graph();
+    if (!g) return fail(BQ_ENOMEM, "host allocation failed");
+    g->device = dev;
+    g->n = n;
+    g->nnz = (uint64_t)nnz;
+    cudaError_t e = cudaSuccess;
+    if (flags & BQ_BORROW) {
+        g->owns_csr = false;
+        g->d_offsets = const_cast<int64_t *>(offsets);
+        g->d_nbrs = const_cast<uint32_t *>(nbrs);
+    } else {
+        const cudaMemcpyKind kind = (flags & BQ_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        e = cudaMalloc(&g->d_offsets, sizeof(int64_t) * ((size_t)n + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_nbrs, sizeof(uint32_t) * std::max<uint64_t>(g->nnz, 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->d_offsets, offsets, sizeof(int64_t) * ((size_t)n + 1), kind, s);
+        if (e == cudaSuccess && g->nnz)
+            e = cudaMemcpyAsync(g->d_nbrs, nbrs, sizeof(uint32_t) * g->nnz, kind, s);
+        if (e != cudaSuccess) {
+            rc = (e == cudaErrorMemoryAllocation) ? fail(BQ_ENOMEM, "cannot allocate the device CSR")
+                                                  : cuda_fail(e, "graph upload");
+            bq_graph_destroy(g);
+            return rc;
+        }
+        g->device_bytes += sizeof(int64_t) * ((size_t)n + 1) + sizeof(uint32_t) * g->nnz;
+    }
+    rc = graph_build(g, flags, s);
+    if (rc == BQ_OK && (flags & BQ_REQUIRE_CONNECTED)) {
+        rc = graph_fetch_host(g);
+        if (rc == BQ_OK) {
+            host_structure(g);
+            if (g->n_components > 1)
+                rc = fail(BQ_EGRAPH, "graph has %d connected components (BQ_REQUIRE_CONNECTED)", g->n_components);
+        }
+    }
+    if (rc != BQ_OK) {
+        bq_graph_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return BQ_OK;
+}
+
+int bq_graph_destroy(bq_graph *g) {
+    if (!g) return BQ_OK;
+    DeviceGuard guard(g->device);
+    if (g->owns_csr) {
+        cudaFree(g->d_offsets);
+        cudaFree(g->d_nbrs);
+    }
+    cudaFree(g->d_rec8);
+    cudaFree(g->d_rec16);
+    cudaFree(g->d_upper_before);
+    delete g;
+    return BQ_OK;
+}
+
+int bq_graph_info(bq_graph *g, bq_graph_info_t *info) {
+    g_last_error[0] = 0;
+    if (!g || !info) return fail(BQ_EINVAL, "NULL argument");
+    int rc = graph_fetch_host(g);
+    if (rc) return rc;
+    host_structure(g);
+    memset(info, 0, sizeof(*info));
+    info->n = g->n;
+    info->nnz = g->nnz;
+    info->m = g->nnz / 2;
+    info->min_degree = g->n ? g->min_degree : 0;
+    info->max_degree = g->max_degree;
+    info->bipartite = g->bipartite;
+    info->n_components = g->n_components;
+    info->device_bytes = g->device_bytes;
+    info->has_spectrum = g->has_spectrum ? 1 : 0;
+    info->device = g->device;
+    info->lambda2 = g->lambda2;
+    info->lambda_neg = g->lambda_neg;
+    return BQ_OK;
+}
+
+int bq_graph_set_spectrum(bq_graph *g, double lambda2, double lambda_neg) {
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (!(lambda2 < 1.0) || !(lambda2 >= -1.0)) return fail(BQ_EINVAL, "lambda2 = %g must lie in [-1, 1)", lambda2);
+    if (!(lambda_neg <= 0.0) || !(lambda_neg >= -1.0))
+        return fail(BQ_EINVAL, "lambda_neg = %g must lie in [-1, 0]", lambda_neg);
+    g->lambda2 = lambda2;
+    g->lambda_neg = lambda_neg;
+    g->has_spectrum = true;
+    return BQ_OK;
+}
+
+int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, uint64_t n_walks, uint32_t n_steps,
+                  uint32_t mode, const bq_sampler *sampler, uint32_t flags, uint32_t *visits_dev, uint32_t *paths_dev,
+                  void *stream) {
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (mode != BQ_MODE_NAIVE && mode != BQ_MODE_BOUQUET) return fail(BQ_EINVAL, "unknown mode %u", mode);
+    if (flags & ~(BQ_VISIT_START | BQ_HOST_IO)) return fail(BQ_EINVAL, "unknown walk flags 0x%x", flags);
+    if (n_walks && (!starts_dev || !visits_dev)) return fail(BQ_EINVAL, "starts or visits is NULL");
+    if (mode == BQ_MODE_BOUQUET && n_walks >= (1ull << 32))
+        return fail(BQ_EINVAL, "bouquet mode takes fewer than 2^32 walks per call (got %llu)",
+                    (unsigned long long)n_walks);
+    if (paths_dev && n_walks > UINT64_MAX / ((uint64_t)n_steps + 1) / sizeof(uint32_t))
+        return fail(BQ_EINVAL, "paths array size overflows");
+    Sampler smp;
+    int rc = check_sampler(sampler, smp);
+    if (rc) return rc;
+    if (n_walks == 0) return BQ_OK;
+    DeviceGuard guard(g->device);
+    uint32_t *status = nullptr;
+    rc = status_word(g->device, &status);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool visit_start = (flags & BQ_VISIT_START) != 0;
+    if (!(flags & BQ_HOST_IO))
+        return launch_walk_batch(g->view(), seed, starts_dev, n_walks, n_steps, mode, smp, visit_start, visits_dev,
+                                 paths_dev, status, s);
+
+    // Host buffers: stage through stream-ordered device scratch.
+    const size_t sb = sizeof(uint32_t) * n_walks, vb = sizeof(uint32_t) * g->n;
+    const size_t pb = paths_dev ? sizeof(uint32_t) * n_walks * ((size_t)n_steps + 1) : 0;
+    char *buf = nullptr;
+    rc = scratch_alloc((void **)&buf, sb + vb + pb, s);
+    if (rc) return rc;
+    uint32_t *d_starts = (uint32_t *)buf, *d_visits = (uint32_t *)(buf + sb);
+    uint32_t *d_paths = paths_dev ? (uint32_t *)(buf + sb + vb) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_starts, starts_dev, sb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_visits, visits_dev, vb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "host-io upload");
+    if (rc == BQ_OK)
+        rc = launch_walk_batch(g->view(), seed, d_starts, n_walks, n_steps, mode, smp, visit_start, d_visits, d_paths,
+                               status, s);
+    if (rc == BQ_OK) {
+        e = cudaMemcpyAsync(visits_dev, d_visits, vb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && d_paths) e = cudaMemcpyAsync(paths_dev, d_paths, pb, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "host-io download");
+    }
+    scratch_free(buf, s);
+    if (rc == BQ_OK) rc = bq_sync(stream);
+    else cudaStreamSynchronize(s);
+    return rc;
+}
+
+// ------------------------------------------------------------- planner
+
+namespace {
+
+double trunc_factor(double lambda2, double lambda_neg, uint32_t tau) {
+    // worst eigen-component error factor lambda^tau (1+lambda)/(2(1-lambda))
+    double pos = 0.0, neg = 0.0;
+    if (lambda2 > 0.0) pos = pow(lambda2, (double)tau) * (1.0 + lambda2) / (2.0 * (1.0 - lambda2));
+    const double a = -lambda_neg;
+    if (a > 0.0) {
+        // maximiser of x^tau (1-x)/(1+x): root of tau x^2 + 2x - tau = 0
+        const double peak = (sqrt(1.0 + (double)tau * (double)tau) - 1.0) / (double)tau;
+        const double x = std::min(a, peak);
+        neg = pow(x, (double)tau) * (1.0 - x) / (2.0 * (1.0 + x));
+    }
+    return std::max(pos, neg);
+}
+
+// Position of v in the sorted row of u, or -1.
+int64_t find_in_row(const bq_graph *g, uint32_t u, uint32_t v) {
+    const uint32_t *b = g->h_nbrs.data() + g->h_offsets[u];
+    const uint32_t *e = g->h_nbrs.data() + g->h_offsets[u + 1];
+    const uint32_t *p = std::lower_bound(b, e, v);
+    return (p != e && *p == v) ? (int64_t)(p - b) : -1;
+}
+
+}  // namespace
+
+int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, double delta, uint32_t plan_mode,
+                 const bq_schedule *sched, uint32_t *tau, uint32_t *nwalks) {
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (!(eps > 0.0) || !(eps < 1e6)) return fail(BQ_EINVAL, "eps = %g must be positive", eps);
+    if (k && (!tau || !nwalks)) return fail(BQ_EINVAL, "tau or nwalks is NULL");
+    const uint64_t m = g->nnz / 2;
+    if (!edges_uv && k != m)
+        return fail(BQ_EINVAL, "all-edges plan needs k = m = %llu (got %llu)", (unsigned long long)m,
+                    (unsigned long long)k);
+    if (plan_mode == BQ_PLAN_CERTIFIED) {
+        if (!(delta > 0.0) || !(delta < 1.0)) return fail(BQ_EINVAL, "delta = %g must lie in (0, 1)", delta);
+        if (!g->has_spectrum) return fail(BQ_EINVAL, "certified plan needs bq_graph_set_spectrum first");
+    } else if (plan_mode == BQ_PLAN_SCHEDULED) {
+        if (!sched) return fail(BQ_EINVAL, "scheduled plan needs a schedule");
+        if (sched->tau_max < 1 || !(sched->tau_scale >= 0.0) || !(sched->n_scale >= 0.0))
+            return fail(BQ_EINVAL, "bad schedule");
+    } else {
+        return fail(BQ_EINVAL, "unknown plan mode %u", plan_mode);
+    }
+    if (k == 0) return BQ_OK;
+    int rc = graph_fetch_host(g);
+    if (rc) return rc;
+    const double log_term = plan_mode == BQ_PLAN_CERTIFIED ? log(2.0 * (double)m / delta) : 0.0;
+    // all-edges plan: canonical order = rows in order, neighbours above the row
+    std::vector<uint32_t> canon;
+    if (!edges_uv) {
+        canon.reserve(2 * m);
+        for (uint32_t u = 0; u < g->n; ++u)
+            for (int64_t j = g->h_offsets[u]; j < g->h_offsets[u + 1]; ++j)
+                if (g->h_nbrs[j] > u) {
+                    canon.push_back(u);
+                    canon.push_back(g->h_nbrs[j]);
+                }
+        if (canon.size() != 2 * k) return fail(BQ_EGRAPH, "graph is not symmetric");
+    }
+    const uint32_t *pairs = edges_uv ? edges_uv : canon.data();
+    for (uint64_t q = 0; q < k; ++q) {
+        const uint32_t a = pairs[2 * q], b = pairs[2 * q + 1];
+        if (edges_uv && (a >= g->n || b >= g->n || a == b || find_in_row(g, a, b) < 0))
+            return fail(BQ_ENOEDGE, "query %llu: (%u, %u) is not an edge", (unsigned long long)q, a, b);
+        const double du = (double)(g->h_offsets[a + 1] - g->h_offsets[a]);
+        const double dv = (double)(g->h_offsets[b + 1] - g->h_offsets[b]);
+        const double s_e = 1.0 / du + 1.0 / dv;
+        uint32_t t = 1;
+        double nw = 0.0;
+        if (plan_mode == BQ_PLAN_CERTIFIED) {
+            const uint32_t tau_cap = 1u << 20;
+            while (s_e * trunc_factor(g->lambda2, g->lambda_neg, t) > eps / 2.0) {
+                if (t >= tau_cap)
+                    return fail(BQ_EOVERFLOW, "query %llu: truncation length exceeds %u", (unsigned long long)q,
+                                tau_cap);
+                ++t;
+            }
+            const double half = (double)t - 0.5;
+            nw = ceil(8.0 * half * half * s_e * s_e * log_term / (eps * eps));
+        } else {
+            const double ratio = s_e / eps;
+            double tt = ratio > 1.0 ? ceil(sched->tau_scale * log(ratio)) : 0.0;
+            tt += (double)sched->tau_add;
+            if (tt < 1.0) tt = 1.0;
+            if (tt > (double)sched->tau_max) tt = (double)sched->tau_max;
+            t = (uint32_t)tt;
+            nw = ceil(sched->n_scale * s_e * s_e / (eps * eps));
+            if (nw < (double)sched->n_min) nw = (double)sched->n_min;
+        }
+        if (nw < 1.0) nw = 1.0;
+        if (nw * 2.0 * (double)t >= 4294967296.0)
+            return fail(BQ_EOVERFLOW, "query %llu: 2 * N * tau = %.3g reaches 2^32", (unsigned long long)q,
+                        nw * 2.0 * (double)t);
+        tau[q] = t;
+        nwalks[q] = (uint32_t)nw;
+    }
+    return BQ_OK;
+}
+
+int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
+                     const uint32_t *tau_dev, const uint32_t *nwalks_dev, const bq_sampler *sampler, uint32_t flags,
+                     uint32_t *counts_dev, double *sc_dev, void *stream) {
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
+    if (k && (!tau_dev || !nwalks_dev || !counts_dev || !sc_dev))
+        return fail(BQ_EINVAL, "tau, nwalks, counts or sc is NULL");
+    if (!edges_uv_dev && (k != g->nnz / 2 || k != g->m_upper))
+        return fail(BQ_EINVAL, "all-edges estimate needs k = m = %llu (got %llu; %llu edges above the diagonal)",
+                    (unsigned long long)(g->nnz / 2), (unsigned long long)k, (unsigned long long)g->m_upper);
+    Sampler smp;
+    int rc = check_sampler(sampler, smp);
+    if (rc) return rc;
+    if (k == 0) return BQ_OK;
+    DeviceGuard guard(g->device);
+    uint32_t *status = nullptr;
+    rc = status_word(g->device, &status);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(flags & BQ_HOST_IO))
+        return launch_aesc(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, smp, counts_dev, sc_dev, status, s);
+
+    const size_t eb = edges_uv_dev ? sizeof(uint32_t) * 2 * k : 0;
+    const size_t tb = sizeof(uint32_t) * k, cb = sizeof(uint32_t) * 4 * k, scb = sizeof(double) * k;
+    char *buf = nullptr;
+    rc = scratch_alloc((void **)&buf, scb + cb + 2 * tb + eb, s);
+    if (rc) return rc;
+    double *d_sc = (double *)buf;
+    uint32_t *d_counts = (uint32_t *)(buf + scb);
+    uint32_t *d_tau = (uint32_t *)(buf + scb + cb);
+    uint32_t *d_nw = (uint32_t *)(buf + scb + cb + tb);
+    uint32_t *d_uv = edges_uv_dev ? (uint32_t *)(buf + scb + cb + 2 * tb) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_tau, tau_dev, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_nw, nwalks_dev, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && d_uv) e = cudaMemcpyAsync(d_uv, edges_uv_dev, eb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "host-io upload");
+    if (rc == BQ_OK) rc = launch_aesc(g->view(), seed, d_uv, k, d_tau, d_nw, smp, d_counts, d_sc, status, s);
+    if (rc == BQ_OK) {
+        e = cudaMemcpyAsync(counts_dev, d_counts, cb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc_dev, d_sc, scb, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "host-io download");
+    }
+    scratch_free(buf, s);
+    if (rc == BQ_OK) rc = bq_sync(stream);
+    else cudaStreamSynchronize(s);
+    return rc;
+}
+
+int bq_sync(void *stream) {
+    g_last_error[0] = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    BQ_CUDA(cudaStreamSynchronize(s));
+    int dev = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    uint32_t *status = nullptr;
+    int rc = status_word(dev, &status);
+    if (rc) return rc;
+    uint32_t bits = 0;
+    BQ_CUDA(cudaMemcpy(&bits, status, sizeof(bits), cudaMemcpyDeviceToHost));
+    if (!bits) return BQ_OK;
+    BQ_CUDA(cudaMemset(status, 0, sizeof(uint32_t)));
+    if (bits & kStatusBadStart) return fail(BQ_EINVAL, "a walk start id was >= n (those walks were skipped)");
+    if (bits & kStatusNoEdge) return fail(BQ_ENOEDGE, "a queried pair is not an edge (its estimate is NaN)");
+    if (bits & kStatusOverflow) return fail(BQ_EOVERFLOW, "a uint32 counter wrapped or 2 N tau >= 2^32");
+    if (bits & kStatusBadIndex) return fail(BQ_EINVAL, "a query had tau = 0 or nwalks = 0 (its estimate is NaN)");
+    if (bits & kStatusTimeout) return fail(BQ_ETIMEOUT, "a bounded device wait gave up");
+    return fail(BQ_ECUDA, "unknown device status bits 0x%x", bits);
+}
+
+int bq_profile_enable(int enable) {
+    g_prof_enabled.store(enable ? 1 : 0);
+    return BQ_OK;
+}
+
+int bq_profile_read(bq_profile *out) {
+    g_last_error[0] = 0;
+    if (!out) return fail(BQ_EINVAL, "out is NULL");
+    std::vector<PendingTiming> pending;
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mutex);
+        pending.swap(g_prof_pending);
+    }
+    int rc = BQ_OK;
+    for (const PendingTiming &p : pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.start, p.stop);
+        if (e != cudaSuccess && rc == BQ_OK) rc = cuda_fail(e, "bq_profile_read");
+        std::lock_guard<std::mutex> lock(g_prof_mutex);
+        g_prof_ms[p.kind] += ms;
+        g_prof_count[p.kind] += 1;
+        g_prof_free_events.push_back(p.start);
+        g_prof_free_events.push_back(p.stop);
+    }
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    out->walk_ms = g_prof_ms[kProfWalk];
+    out->walk_launches = g_prof_count[kProfWalk];
+    out->group_ms = g_prof_ms[kProfGroup];
+    out->group_launches = g_prof_count[kProfGroup];
+    out->aesc_ms = g_prof_ms[kProfAesc];
+    out->aesc_launches = g_prof_count[kProfAesc];
+    out->aesc_aux_ms = g_prof_ms[kProfAescAux];
+    out->aesc_aux_launches = g_prof_count[kProfAescAux];
+    out->kernel_launches = g_launches.exchange(0);
+    for (int i = 0; i < 4; ++i) {
+        g_prof_ms[i] = 0.0;
+        g_prof_count[i] = 0;
+    }
+    return rc;
+}
+
+int bq_get_tuning(bq_tuning *out) {
+    if (!out) return fail(BQ_EINVAL, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    out->walk_lanes = (uint32_t)g_walks_per_lane.load();
+    out->aggregate_visits = (uint32_t)g_aggregate.load();
+    out->aesc_lanes = (uint32_t)g_aesc_walks_per_lane.load();
+    return BQ_OK;
+}
+
+int bq_set_tuning(const bq_tuning *in) {
+    g_last_error[0] = 0;
+    if (!in) return fail(BQ_EINVAL, "tuning is NULL");
+    const uint32_t w = in->walk_lanes, a = in->aesc_lanes;
+    if (w != 1 && w != 2 && w != 4 && w != 8) return fail(BQ_EINVAL, "walk_lanes must be 1, 2, 4 or 8");
+    if (a != 2 && a != 4 && a != 8) return fail(BQ_EINVAL, "aesc_lanes must be 2, 4 or 8");
+    if (in->aggregate_visits > 1) return fail(BQ_EINVAL, "aggregate_visits must be 0 or 1");
+    g_walks_per_lane.store((int)w);
+    g_aggregate.store((int)in->aggregate_visits);
+    g_aesc_walks_per_lane.store((int)a);
+    return BQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,392 @@
+// Graph store: validation of a device CSR, per-vertex records, canonical
+// edge numbering, and the device-wide exclusive scan used across the library.
+//
+// The adjacency Gamma(v) and degree d(v) are the notation of Sec. 2 (Table of
+// notation); Alg. 2 and Alg. 3 index Gamma(cur)[k], so every step needs the
+// row start and the row length of the current vertex.  They are packed into
+// one aligned record per vertex so that a step reads them with one load.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace bq {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;
+
+// ------------------------------------------------------------------ scan
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((threadIdx.x & 31) >= (unsigned)d) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of one block tile held as kScanItems values per thread
+// (blocked arrangement); `total` receives the tile sum in every thread.
+template <typename Out>
+__device__ void block_exclusive_scan(Out (&v)[kScanItems], Out &total) {
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ Out warp_sums[kWarps];
+    __shared__ Out tile_total;
+    Out local = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) local += v[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const Out incl = warp_inclusive_scan(local);
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const Out ws = lane < kWarps ? warp_sums[lane] : (Out)0;
+        const Out wi = warp_inclusive_scan(ws);
+        if (lane < kWarps) warp_sums[lane] = wi - ws;
+        if (lane == kWarps - 1) tile_total = wi;
+    }
+    __syncthreads();
+    Out run = warp_sums[wid] + incl - local;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const Out x = v[i];
+        v[i] = run;
+        run += x;
+    }
+    total = tile_total;
+}
+
+template <typename In, typename Out>
+__global__ void tile_reduce_kernel(const In *__restrict__ in, uint64_t n, Out *__restrict__ sums) {
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    Out local = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        const uint64_t idx = base + (uint64_t)i * kScanThreads + threadIdx.x;
+        if (idx < n) local += (Out)in[idx];
+    }
+    __shared__ Out warp_sums[kScanThreads / 32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) local += __shfl_down_sync(0xffffffffu, local, d);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Out t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += warp_sums[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// out[i] = offsets[block] + exclusive prefix within the tile; the last tile
+// also writes out[n] = grand total.
+template <typename In, typename Out>
+__global__ void tile_scan_kernel(const In *__restrict__ in, uint64_t n,
+                                 const Out *__restrict__ tile_offsets, Out *__restrict__ out) {
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    Out v[kScanItems];
+    // blocked arrangement: thread t owns items base + t*kScanItems + i
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const uint64_t idx = base + (uint64_t)threadIdx.x * kScanItems + i;
+        v[i] = idx < n ? (Out)in[idx] : (Out)0;
+    }
+    Out total;
+    block_exclusive_scan<Out>(v, total);
+    const Out off = tile_offsets ? tile_offsets[blockIdx.x] : (Out)0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const uint64_t idx = base + (uint64_t)threadIdx.x * kScanItems + i;
+        if (idx < n) out[idx] = off + v[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+}
+
+template <typename In, typename Out>
+int scan_impl(const In *in, Out *out, uint64_t n, cudaStream_t s) {
+    if (n == 0) {
+        BQ_CUDA(cudaMemsetAsync(out, 0, sizeof(Out), s));
+        return BQ_OK;
+    }
+    const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        count_launches(1);
+        tile_scan_kernel<In, Out><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+        BQ_CUDA(cudaGetLastError());
+        return BQ_OK;
+    }
+    Out *sums = nullptr;
+    int rc = scratch_alloc((void **)&sums, sizeof(Out) * (2 * tiles + 1), s);
+    if (rc) return rc;
+    Out *sum_prefix = sums + tiles;
+    count_launches(2);
+    tile_reduce_kernel<In, Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+    rc = scan_impl<Out, Out>(sums, sum_prefix, tiles, s);
+    if (rc == BQ_OK) {
+        tile_scan_kernel<In, Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sum_prefix, out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "tile_scan_kernel");
+    }
+    scratch_free(sums, s);
+    return rc;
+}
+
+// ------------------------------------------------------------ validation
+
+struct CheckResult {
+    unsigned long long bad_offset;  // first v with offsets[v] > offsets[v+1]
+    unsigned long long bad_id;      // first v whose row holds an id >= n
+    unsigned long long self_loop;   // first v whose row holds v
+    unsigned long long unsorted;    // first v whose row is not strictly increasing
+    unsigned long long asymmetric;  // first v with u in row v but v not in row u
+    unsigned int min_deg;
+    unsigned int max_deg;
+};
+
+__global__ void check_offsets_kernel(const int64_t *__restrict__ off, uint32_t n, CheckResult *res) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        if (off[v] > off[v + 1]) atomicMin(&res->bad_offset, (unsigned long long)v);
+    }
+}
+
+// One warp per vertex: bounds, self-loops, sortedness, degree range and the
+// number of neighbours above v (canonical edge numbering).
+__global__ void check_rows_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ nbrs,
+                                  uint32_t n, CheckResult *res, uint32_t *__restrict__ upper) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < n; v += nwarps) {
+        const int64_t lo = off[v], hi = off[v + 1];
+        bool bad_id = false, self = false, unsorted = false;
+        uint32_t above = 0;
+        for (int64_t j = lo + lane; j < hi; j += 32) {
+            const uint32_t x = nbrs[j];
+            bad_id |= x >= n;
+            self |= x == (uint32_t)v;
+            unsorted |= (j > lo) && (nbrs[j - 1] >= x);
+            above += x > (uint32_t)v;
+        }
+        bad_id = __any_sync(0xffffffffu, bad_id);
+        self = __any_sync(0xffffffffu, self);
+        unsorted = __any_sync(0xffffffffu, unsorted);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) above += __shfl_down_sync(0xffffffffu, above, d);
+        if (lane == 0) {
+            if (bad_id) atomicMin(&res->bad_id, (unsigned long long)v);
+            if (self) atomicMin(&res->self_loop, (unsigned long long)v);
+            if (unsorted) atomicMin(&res->unsorted, (unsigned long long)v);
+            const unsigned int deg = (unsigned int)(hi - lo);
+            atomicMin(&res->min_deg, deg);
+            atomicMax(&res->max_deg, deg);
+            upper[v] = above;
+        }
+    }
+}
+
+__device__ __forceinline__ bool row_contains(const uint32_t *__restrict__ nbrs, int64_t lo,
+                                             int64_t hi, uint32_t key) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        const uint32_t x = nbrs[mid];
+        if (x == key) return true;
+        if (x < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return false;
+}
+
+// Needs rows sorted and ids in range (checked before it runs).
+__global__ void check_symmetry_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ nbrs,
+                                      uint32_t n, CheckResult *res) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < n; v += nwarps) {
+        bool asym = false;
+        for (int64_t j = off[v] + lane; j < off[v + 1]; j += 32) {
+            const uint32_t x = nbrs[j];
+            asym |= !row_contains(nbrs, off[x], off[x + 1], (uint32_t)v);
+        }
+        if (__any_sync(0xffffffffu, asym) && lane == 0)
+            atomicMin(&res->asymmetric, (unsigned long long)v);
+    }
+}
+
+__global__ void build_records_kernel(const int64_t *__restrict__ off, uint32_t n, uint2 *rec8,
+                                     uint4 *rec16) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = off[v];
+        const uint32_t deg = (uint32_t)(off[v + 1] - lo);
+        if (rec8) rec8[v] = make_uint2((uint32_t)lo, deg);
+        else rec16[v] = make_uint4((uint32_t)lo, (uint32_t)((uint64_t)lo >> 32), deg, 0u);
+    }
+}
+
+unsigned grid_for(uint64_t items, int threads, int per_thread = 1) {
+    uint64_t blocks = (items + (uint64_t)threads * per_thread - 1) / ((uint64_t)threads * per_thread);
+    if (blocks < 1) blocks = 1;
+    if (blocks > 65535ull * 32) blocks = 65535ull * 32;
+    return (unsigned)blocks;
+}
+
+}  // namespace
+
+int scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s) {
+    return scan_impl<uint32_t, uint64_t>(in, out, n, s);
+}
+
+int scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, cudaStream_t s) {
+    return scan_impl<uint32_t, uint32_t>(in, out, n, s);
+}
+
+int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
+    const uint32_t n = g->n;
+    // offsets[0] and offsets[n] against nnz
+    int64_t ends[2] = {0, 0};
+    BQ_CUDA(cudaMemcpyAsync(&ends[0], g->d_offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BQ_CUDA(cudaMemcpyAsync(&ends[1], g->d_offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BQ_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0) return fail(BQ_EGRAPH, "offsets[0] = %lld, expected 0", (long long)ends[0]);
+    if (ends[1] < 0 || (uint64_t)ends[1] != g->nnz)
+        return fail(BQ_EGRAPH, "offsets[n] = %lld does not match nnz = %llu", (long long)ends[1],
+                    (unsigned long long)g->nnz);
+    if (g->nnz % 2 != 0) return fail(BQ_EGRAPH, "nnz = %llu is odd: an undirected CSR stores each edge twice",
+                                     (unsigned long long)g->nnz);
+
+    CheckResult *res = nullptr;
+    uint32_t *upper = nullptr;
+    BQ_CUDA(cudaMalloc(&res, sizeof(CheckResult)));
+    CheckResult init;
+    init.bad_offset = init.bad_id = init.self_loop = init.unsorted = init.asymmetric = ~0ull;
+    init.min_deg = 0xffffffffu;
+    init.max_deg = 0;
+    int rc = BQ_OK;
+    CheckResult h;
+    cudaError_t e = cudaMemcpyAsync(res, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&upper, sizeof(uint32_t) * ((size_t)n + 1));
+    if (e != cudaSuccess) {
+        cudaFree(res);
+        return cuda_fail(e, "graph validation setup");
+    }
+    if (n > 0) {
+        check_offsets_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, n, res);
+        e = cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "check_offsets_kernel");
+            goto done;
+        }
+        if (h.bad_offset != ~0ull) {
+            rc = fail(BQ_EGRAPH, "offsets decrease at vertex %llu", h.bad_offset);
+            goto done;
+        }
+        check_rows_kernel<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(g->d_offsets, g->d_nbrs, n, res,
+                                                                           upper);
+        e = cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "check_rows_kernel");
+            goto done;
+        }
+        if (h.bad_id != ~0ull) {
+            rc = fail(BQ_EGRAPH, "row %llu holds a vertex id >= n = %u", h.bad_id, n);
+            goto done;
+        }
+        if (h.self_loop != ~0ull) {
+            rc = fail(BQ_EGRAPH, "vertex %llu has a self-loop", h.self_loop);
+            goto done;
+        }
+        if (!(flags & BQ_SKIP_VALIDATE)) {
+            if (h.unsorted != ~0ull) {
+                rc = fail(BQ_EGRAPH, "row %llu is not strictly increasing (unsorted or duplicate entry)",
+                          h.unsorted);
+                goto done;
+            }
+            check_symmetry_kernel<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(g->d_offsets, g->d_nbrs,
+                                                                                   n, res);
+            e = cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "check_symmetry_kernel");
+                goto done;
+            }
+            if (h.asymmetric != ~0ull) {
+                rc = fail(BQ_EGRAPH, "row %llu lists a neighbour whose row does not list it (asymmetric)",
+                          h.asymmetric);
+                goto done;
+            }
+        }
+        g->min_degree = h.min_deg;
+        g->max_degree = h.max_deg;
+    }
+    // records
+    {
+        const bool compact = g->nnz < (1ull << 32);
+        size_t rec_bytes = (size_t)n * (compact ? sizeof(uint2) : sizeof(uint4));
+        void *rec = nullptr;
+        e = cudaMalloc(&rec, rec_bytes > 0 ? rec_bytes : 16);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMalloc(records)");
+            goto done;
+        }
+        if (compact) g->d_rec8 = (uint2 *)rec;
+        else g->d_rec16 = (uint4 *)rec;
+        g->device_bytes += rec_bytes;
+        if (n > 0)
+            build_records_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, n, g->d_rec8, g->d_rec16);
+        e = cudaMalloc(&g->d_upper_before, sizeof(uint64_t) * ((size_t)n + 1));
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMalloc(upper_before)");
+            goto done;
+        }
+        g->device_bytes += sizeof(uint64_t) * ((size_t)n + 1);
+        rc = scan_u32_to_u64(upper, g->d_upper_before, n, s);
+        if (rc) goto done;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "graph_build");
+            goto done;
+        }
+        uint64_t m_upper = 0;
+        e = cudaMemcpy(&m_upper, g->d_upper_before + n, sizeof(uint64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "graph_build readback");
+            goto done;
+        }
+        g->m_upper = m_upper;
+        if (!(flags & BQ_SKIP_VALIDATE) && 2 * m_upper != g->nnz) {
+            rc = fail(BQ_EGRAPH, "edge count mismatch: %llu entries above the diagonal, nnz %llu",
+                      (unsigned long long)m_upper, (unsigned long long)g->nnz);
+            goto done;
+        }
+    }
+done:
+    cudaFree(res);
+    cudaFree(upper);
+    return rc;
+}
+
+int graph_fetch_host(bq_graph *g) {
+    if (!g->h_offsets.empty()) return BQ_OK;
+    int prev = 0;
+    BQ_CUDA(cudaGetDevice(&prev));
+    BQ_CUDA(cudaSetDevice(g->device));
+    std::vector<int64_t> off((size_t)g->n + 1);
+    std::vector<uint32_t> nb((size_t)g->nnz);
+    cudaError_t e = cudaMemcpy(off.data(), g->d_offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && g->nnz)
+        e = cudaMemcpy(nb.data(), g->d_nbrs, sizeof(uint32_t) * nb.size(), cudaMemcpyDeviceToHost);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "graph_fetch_host");
+    g->h_offsets.swap(off);
+    g->h_nbrs.swap(nb);
+    return BQ_OK;
+}
+
+}  // namespace bq

@@ -1,0 +1,144 @@
+// Internal declarations shared by the translation units of libbouquet.
+// Host-side only types plus the launch wrappers each .cu file exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bouquet.h"
+
+namespace bq {
+
+// Bits of the per-device status word written by kernels (atomicOr).
+enum StatusBits : uint32_t {
+    kStatusBadStart = 1u << 0,   // walk start id >= n
+    kStatusNoEdge = 1u << 1,     // AESC pair is not an edge
+    kStatusOverflow = 1u << 2,   // a uint32 counter wrapped / plan too large
+    kStatusBadIndex = 1u << 3,   // (checked builds) index out of range
+    kStatusTimeout = 1u << 4,    // a bounded wait gave up
+};
+
+// Stream reserved for walk-batch walks; AESC walks use stream 2 * edge + side.
+constexpr uint64_t kBatchStream = 0x4000000000000000ull;
+// Top bit of the stream selects the shared key of the coupled sampler.
+constexpr uint64_t kGroupBit = 0x8000000000000000ull;
+
+struct Sampler {
+    uint32_t kind;   // 0 independent, 1 coupled
+    uint32_t t;      // coupled: shared top bits
+    uint32_t width;  // coupled: group width
+};
+
+// Device view of a graph.  Vertex records are 8 bytes {row offset, degree}
+// when nnz < 2^32 (compact), else 16 bytes {offset lo, offset hi, degree, 0}.
+struct DeviceGraph {
+    uint32_t n;
+    uint64_t nnz;
+    const int64_t *offsets;  // n + 1
+    const uint32_t *nbrs;    // nnz
+    const uint2 *rec8;       // n, compact records (or null)
+    const uint4 *rec16;      // n, wide records (or null)
+    const uint64_t *upper_before;  // n + 1: edges {x,y}, x<y, with x < u
+    bool compact() const { return rec8 != nullptr; }
+};
+
+}  // namespace bq
+
+struct bq_graph {
+    int device = 0;
+    uint32_t n = 0;
+    uint64_t nnz = 0;
+    int64_t *d_offsets = nullptr;
+    uint32_t *d_nbrs = nullptr;
+    bool owns_csr = true;
+    uint2 *d_rec8 = nullptr;
+    uint4 *d_rec16 = nullptr;
+    uint64_t *d_upper_before = nullptr;
+    uint32_t min_degree = 0, max_degree = 0;
+    uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
+    uint64_t device_bytes = 0;
+    // lazily filled host copies / properties
+    std::vector<int64_t> h_offsets;
+    std::vector<uint32_t> h_nbrs;
+    int bipartite = -1;
+    int n_components = -1;
+    bool has_spectrum = false;
+    double lambda2 = 0.0, lambda_neg = 0.0;
+
+    bq::DeviceGraph view() const {
+        bq::DeviceGraph v;
+        v.n = n;
+        v.nnz = nnz;
+        v.offsets = d_offsets;
+        v.nbrs = d_nbrs;
+        v.rec8 = d_rec8;
+        v.rec16 = d_rec16;
+        v.upper_before = d_upper_before;
+        return v;
+    }
+};
+
+namespace bq {
+
+// ---- error plumbing (api.cu)
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t err, const char *what);
+#define BQ_CUDA(call)                                            \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return ::bq::cuda_fail(_e, #call); \
+    } while (0)
+
+// Per-device status word (allocated on first graph creation on a device).
+int status_word(int device, uint32_t **out);
+
+// Device-pool allocation helpers on a stream.
+int scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+void scratch_free(void *p, cudaStream_t s);
+
+// Performance knobs (never change a result): walks per lane of the bouquet
+// walk-batch kernel (1, 2, 4, 8), warp-aggregated visit atomics, walks per
+// lane of the AESC counting kernel (2, 4, 8).
+int tuning_walks_per_lane();
+bool tuning_aggregate_visits();
+int tuning_aesc_walks_per_lane();
+
+// Profiling (api.cu): event brackets around kernel groups while enabled, and
+// a count of every kernel launch.
+enum ProfKind { kProfWalk = 0, kProfGroup = 1, kProfAesc = 2, kProfAescAux = 3 };
+struct ProfScope {
+    int kind;
+    cudaStream_t stream;
+    cudaEvent_t start = nullptr, stop = nullptr;
+    ProfScope(int kind, cudaStream_t s);
+    ~ProfScope();
+};
+void count_launches(unsigned n);
+
+// ---- graph.cu
+// Validate a device CSR and build records / edge numbering.  Synchronous on s.
+int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s);
+// Exclusive scan of uint32 counts into uint64 prefix (out has n + 1 entries).
+int scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
+// Exclusive scan of uint32 into uint32 (out has n + 1 entries; caller
+// guarantees the total fits).
+int scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, cudaStream_t s);
+// Copy the CSR to the host copies of g (once).
+int graph_fetch_host(bq_graph *g);
+
+// ---- walks.cu
+int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *starts,
+                      uint64_t n_walks, uint32_t n_steps, uint32_t mode,
+                      const Sampler &smp, bool visit_start, uint32_t *visits,
+                      uint32_t *paths, uint32_t *status, cudaStream_t s);
+
+// ---- aesc.cu
+int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,
+                uint64_t k, const uint32_t *tau, const uint32_t *nwalks,
+                const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
+                cudaStream_t s);
+
+}  // namespace bq

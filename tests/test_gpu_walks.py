@@ -1,0 +1,182 @@
+"""Walk-batch parity: the CUDA kernels (bouquet and naive) against the CPU
+oracle, bit for bit, through the C ABI.
+
+Sizes span several warps/blocks with ragged tails; the full-size R-MAT case
+(scale 20, 2^24 walks of 64 steps) is checked on sampled walks the oracle
+replays one by one, plus properties that hold at any size."""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import csr_from_edges, cycle, gnp_connected, path, rmat, rmat20, uniform_starts
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_14056_gb300 as bq
+    assert torch.cuda.is_available()
+    return bq, torch
+
+
+def dev_u32(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def host_u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+GRAPHS = {
+    "gnp60": gnp_connected(60, 0.1, 1),
+    "rmat12": rmat(12, 8, seed=2),
+    "cycle10": cycle(10),
+    "path7": path(7),
+    "isolated": csr_from_edges(9, [0, 1, 2, 5], [1, 2, 0, 6]),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("n_walks,n_steps", [(1, 5), (31, 1), (33, 7), (5127, 64), (70001, 3)])
+def test_visits_bit_exact(env, name, n_walks, n_steps):
+    bq, torch = env
+    g = GRAPHS[name]
+    graph = bq.Graph.from_csr(g)
+    rng = np.random.default_rng(n_walks + n_steps)
+    starts = rng.integers(0, g.n, n_walks).astype(np.uint32)  # isolated starts included
+    want = oracle.walk_batch(g, 1234, starts, n_steps)
+    st = dev_u32(torch, starts)
+    for mode in (bq.MODE_BOUQUET, bq.MODE_NAIVE):
+        vis = bq.walk_batch(graph, 1234, st, n_steps, mode=mode)
+        bq.sync()
+        assert np.array_equal(host_u32(vis), want), (name, mode)
+
+
+@pytest.mark.parametrize("sampler", [None, (1, 3, 8), (1, 32, 32), (1, 0, 5)])
+def test_paths_and_start_visits_bit_exact(env, sampler):
+    bq, torch = env
+    g = GRAPHS["rmat12"]
+    graph = bq.Graph.from_csr(g)
+    starts = uniform_starts(g, 3001, 4)
+    want_v, want_p = oracle.walk_batch(g, 77, starts, 20, sampler=sampler, include_start=True,
+                                       want_paths=True)
+    st = dev_u32(torch, starts)
+    for mode in (bq.MODE_BOUQUET, bq.MODE_NAIVE):
+        paths = torch.zeros((3001, 21), dtype=torch.int32, device="cuda")
+        vis = bq.walk_batch(graph, 77, st, 20, mode=mode, sampler=sampler, visit_start=True,
+                            paths=paths)
+        bq.sync()
+        assert np.array_equal(host_u32(vis), want_v)
+        assert np.array_equal(host_u32(paths), want_p)
+
+
+def test_zero_steps_and_accumulation(env):
+    bq, torch = env
+    g = GRAPHS["gnp60"]
+    graph = bq.Graph.from_csr(g)
+    starts = uniform_starts(g, 500, 9)
+    st = dev_u32(torch, starts)
+    vis = bq.walk_batch(graph, 5, st, 0, visit_start=True)
+    bq.sync()
+    assert np.array_equal(host_u32(vis), np.bincount(starts, minlength=g.n))
+    vis = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        bq.walk_batch(graph, 5, st, 6, visits=vis)
+    bq.sync()
+    assert np.array_equal(host_u32(vis), 3 * oracle.walk_batch(g, 5, starts, 6))
+
+
+def test_tuning_never_changes_results(env):
+    bq, torch = env
+    g = GRAPHS["rmat12"]
+    graph = bq.Graph.from_csr(g)
+    starts = uniform_starts(g, 40000, 11)
+    want = oracle.walk_batch(g, 3, starts, 12)
+    st = dev_u32(torch, starts)
+    old = bq.get_tuning()
+    try:
+        for lanes in (1, 2, 4, 8):
+            for agg in (0, 1):
+                bq.set_tuning(walk_lanes=lanes, aggregate_visits=agg)
+                vis = bq.walk_batch(graph, 3, st, 12)
+                bq.sync()
+                assert np.array_equal(host_u32(vis), want), (lanes, agg)
+    finally:
+        bq.set_tuning(**old)
+
+
+def test_host_io_matches_device(env):
+    bq, torch = env
+    g = GRAPHS["gnp60"]
+    graph = bq.Graph.from_csr(g)
+    starts = uniform_starts(g, 2000, 12)
+    paths = np.zeros((2000, 9), np.uint32)
+    vis = bq.walk_batch_host(graph, 8, starts, 8, paths=paths)
+    want_v, want_p = oracle.walk_batch(g, 8, starts, 8, want_paths=True)
+    assert np.array_equal(vis, want_v) and np.array_equal(paths, want_p)
+    base = np.arange(g.n, dtype=np.uint32)
+    vis2 = bq.walk_batch_host(graph, 8, starts, 8, visits=base.copy(), mode=bq.MODE_NAIVE)
+    assert np.array_equal(vis2, want_v + base)
+
+
+def test_bad_start_reported_and_skipped(env):
+    bq, torch = env
+    g = GRAPHS["cycle10"]
+    graph = bq.Graph.from_csr(g)
+    starts = np.array([0, 3, 10, 5, 99], np.uint32)
+    good = starts[starts < g.n]
+    for mode in (bq.MODE_BOUQUET, bq.MODE_NAIVE):
+        vis = bq.walk_batch(graph, 1, dev_u32(torch, starts), 4, mode=mode)
+        with pytest.raises(bq.BouquetError) as ei:
+            bq.sync()
+        assert ei.value.code == bq.EINVAL
+        # each valid walk keeps its own id; the bad ones are skipped
+        want = np.zeros(g.n, np.int64)
+        for i, s in enumerate(starts):
+            if s < g.n:
+                p = oracle.walk_paths_by_id(g, 1, np.array([i], np.uint64),
+                                            np.array([s], np.uint32), 4)
+                want += np.bincount(p[0, 1:], minlength=g.n)
+        assert np.array_equal(host_u32(vis), want.astype(np.uint32))
+    bq.sync()  # status was cleared
+    assert good.size == 3
+
+
+def test_full_size_rmat_batch(env):
+    """R-MAT scale 20 (edge factor 16), 2^24 uniform starts, 64 steps: the
+    workload the bench times, in the bench's launch configuration."""
+    bq, torch = env
+    g = rmat20()
+    graph = bq.Graph.from_csr(g)
+    n_walks, n_steps = 1 << 24, 64
+    starts = uniform_starts(g, n_walks, 21)
+    st = dev_u32(torch, starts)
+    vb = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_BOUQUET)
+    vn = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_NAIVE)
+    bq.sync()
+    assert torch.equal(vb, vn)
+    assert int(vb.to(torch.int64).sum()) == n_walks * n_steps
+    # paths of every walk: histogram equals the visits; sampled rows equal
+    # the oracle's replay of the same walk ids
+    paths = torch.empty((n_walks, n_steps + 1), dtype=torch.int32, device="cuda")
+    vp = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_BOUQUET, paths=paths)
+    bq.sync()
+    assert torch.equal(vp, vb)
+    hist = torch.bincount(paths[:, 1:].reshape(-1), minlength=g.n)
+    assert torch.equal(hist.to(torch.int32), vb)
+    assert torch.equal(paths[:, 0], st)
+    rng = np.random.default_rng(5)
+    ids = np.sort(rng.choice(n_walks, 3000, replace=False)).astype(np.uint64)
+    want = oracle.walk_paths_by_id(g, 2024, ids, starts[ids.astype(np.int64)], n_steps)
+    got = host_u32(paths[torch.from_numpy(ids.astype(np.int64)).cuda()])
+    assert np.array_equal(got, want)
+    del paths
+    # the host-buffer path used for the end-to-end number
+    vh = bq.walk_batch_host(graph, 2024, starts, n_steps)
+    assert np.array_equal(vh, host_u32(vb))

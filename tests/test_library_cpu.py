@@ -1,0 +1,76 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every symbol include/bouquet.h declares, and rejects bad arguments
+before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2410_14056_gb300 as bq
+from paper_2410_14056_gb300 import bouquet as binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    include = os.path.join(ROOT, "include")
+    for fn in os.listdir(include):
+        if fn.endswith(".h"):
+            text = open(os.path.join(include, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(bq_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return bq.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = header_functions()
+    assert {"bq_graph_create", "bq_walk_batch", "bq_aesc_estimate", "bq_sync"} <= declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(binding.EXPORTS) <= declared | set()
+
+
+def test_strerror_and_version(lib):
+    assert lib.bq_strerror(0) == b"ok"
+    assert lib.bq_strerror(bq.ENOEDGE) == b"vertex pair is not an edge"
+    assert lib.bq_strerror(-99) == b"unknown status code"
+    assert bq.version().startswith("bouquet-gb300")
+
+
+def test_argument_errors_without_device(lib):
+    out = ctypes.c_void_p()
+    assert lib.bq_graph_create(3, None, None, 0, None, ctypes.byref(out)) == bq.EINVAL
+    assert b"offsets" in lib.bq_last_error()
+    assert lib.bq_graph_create(3, None, None, 0, None, None) == bq.EINVAL
+    assert lib.bq_walk_batch(None, 0, None, 0, 1, 0, None, 0, None, None, None) == bq.EINVAL
+    assert lib.bq_aesc_plan(None, None, 0, 0.1, 0.01, 0, None, None, None) == bq.EINVAL
+    assert lib.bq_graph_destroy(None) == bq.OK
+
+
+def test_tuning_roundtrip_and_validation(lib):
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
+        assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8}
+        with pytest.raises(bq.BouquetError) as ei:
+            bq.set_tuning(walk_lanes=3)
+        assert ei.value.code == bq.EINVAL
+        with pytest.raises(bq.BouquetError):
+            bq.set_tuning(aesc_lanes=1)
+    finally:
+        bq.set_tuning(**old)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        binding.load_library(str(tmp_path / "libbouquet.so"))
