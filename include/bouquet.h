@@ -157,6 +157,27 @@ int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev,
                   const bq_sampler *sampler, uint32_t flags, uint32_t *visits_dev,
                   uint32_t *paths_dev, void *stream);
 
+/*
+ * Walk batch that allocates nothing (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc or any allocator during a call:
+ * a plug-in inside a host application that owns all device memory, a
+ * latency-critical loop where an allocation could block or fail at an
+ * arbitrary moment, or code under a memory cap that is already handed out.
+ * Same walks and results as bq_walk_batch in BQ_MODE_BOUQUET, on device
+ * buffers only (flags: BQ_VISIT_START; BQ_HOST_IO is rejected).  Its scratch
+ * is a fixed 32 MiB array in the library's device memory, held by every
+ * device that loads the library's module until the process exits; a batch
+ * needs 4 * (2 n + 1 + 2 n_walks) bytes plus a small scan workspace, and a
+ * larger request fails with BQ_EINVAL and a message giving both sizes.  The
+ * first call on a device looks up the array's device address (make it before
+ * any stream capture).  All calls share the array: calls whose work overlaps
+ * on the GPU race on it.  A graph must already exist on the device.
+ */
+int bq_walk_batch_noalloc(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev,
+                          uint64_t n_walks, uint32_t n_steps, const bq_sampler *sampler,
+                          uint32_t flags, uint32_t *visits_dev, uint32_t *paths_dev,
+                          void *stream);
+
 /* ---------------------------------------------------------- bq_aesc_plan */
 #define BQ_PLAN_CERTIFIED 0u
 #define BQ_PLAN_SCHEDULED 1u

@@ -83,7 +83,7 @@ EXPORTS = (
     "bq_graph_create", "bq_graph_destroy", "bq_graph_info", "bq_graph_set_spectrum",
     "bq_walk_batch", "bq_aesc_plan", "bq_aesc_estimate", "bq_sync", "bq_strerror",
     "bq_last_error", "bq_version", "bq_get_tuning", "bq_set_tuning", "bq_profile_enable",
-    "bq_profile_read",
+    "bq_profile_read", "bq_walk_batch_noalloc",
 )
 
 _lock = threading.Lock()
@@ -120,6 +120,7 @@ def load_library(path: str | None = None):
         L.bq_version.restype = c.c_char_p
         L.bq_get_tuning.argtypes = [c.POINTER(Tuning)]
         L.bq_set_tuning.argtypes = [c.POINTER(Tuning)]
+        L.bq_walk_batch_noalloc.argtypes = [vp, u64, vp, u64, u32, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_profile_enable.argtypes = [i32]
         L.bq_profile_read.argtypes = [c.POINTER(Profile)]
         for name in EXPORTS:
@@ -242,6 +243,22 @@ def walk_batch(graph: Graph, seed: int, starts, n_steps: int, mode: int = MODE_B
     _check(L.bq_walk_batch(graph.handle, int(seed) & (2**64 - 1), _dptr(starts, "starts"), n_walks,
                            int(n_steps), int(mode), _sampler(sampler), flags,
                            _dptr(visits, "visits"), _dptr(paths, "paths"), _stream_handle(stream)))
+    return visits
+
+
+def walk_batch_noalloc(graph: Graph, seed: int, starts, n_steps: int, sampler=None,
+                       visit_start: bool = False, visits=None, paths=None, stream=None):
+    """Bouquet walk batch that allocates nothing in the library (scratch is a
+    fixed 32 MiB device array); device tensors only; returns `visits`."""
+    import torch
+    L = load_library()
+    if visits is None:
+        visits = torch.zeros(graph.n, dtype=torch.int32, device=starts.device)
+    flags = VISIT_START if visit_start else 0
+    _check(L.bq_walk_batch_noalloc(graph.handle, int(seed) & (2**64 - 1), _dptr(starts, "starts"),
+                                   starts.numel(), int(n_steps), _sampler(sampler), flags,
+                                   _dptr(visits, "visits"), _dptr(paths, "paths"),
+                                   _stream_handle(stream)))
     return visits
 
 

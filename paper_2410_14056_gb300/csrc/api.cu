@@ -64,6 +64,14 @@ int status_word(int device, uint32_t **out) {
     return BQ_OK;
 }
 
+int existing_status_word(int device, uint32_t **out) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if ((int)g_status.size() <= device || !g_status[device])
+        return fail(BQ_EINVAL, "no status word on device %d: create a graph on it first", device);
+    *out = g_status[device];
+    return BQ_OK;
+}
+
 int scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
@@ -123,6 +131,8 @@ ProfScope::~ProfScope() {
 }
 
 void count_launches(unsigned n) { g_launches.fetch_add(n); }
+
+int validate_sampler(const bq_sampler *in, Sampler &out);
 
 int tuning_walks_per_lane() { return g_walks_per_lane.load(); }
 bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
@@ -190,6 +200,9 @@ void host_structure(bq_graph *g) {
 }
 
 }  // namespace
+
+int validate_sampler(const bq_sampler *in, Sampler &out) { return check_sampler(in, out); }
+
 }  // namespace bq
 
 using namespace bq;

@@ -134,6 +134,44 @@ int scan_impl(const In *in, Out *out, uint64_t n, cudaStream_t s) {
     return rc;
 }
 
+// Workspace bytes scan_ws_impl needs for n items (tile sums and their prefix
+// at every level of the recursion).
+template <typename Out>
+size_t scan_ws_bytes_impl(uint64_t n) {
+    const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles <= 1) return 0;
+    const size_t here = (sizeof(Out) * (2 * tiles + 1) + 255) & ~(size_t)255;
+    return here + scan_ws_bytes_impl<Out>(tiles);
+}
+
+// The same scan as scan_impl, with its temporary tile sums taken from a
+// caller-provided workspace instead of the stream-ordered pool.
+template <typename In, typename Out>
+int scan_ws_impl(const In *in, Out *out, uint64_t n, char *ws, size_t ws_bytes, cudaStream_t s) {
+    if (n == 0) {
+        BQ_CUDA(cudaMemsetAsync(out, 0, sizeof(Out), s));
+        return BQ_OK;
+    }
+    const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        count_launches(1);
+        tile_scan_kernel<In, Out><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+        BQ_CUDA(cudaGetLastError());
+        return BQ_OK;
+    }
+    const size_t here = (sizeof(Out) * (2 * tiles + 1) + 255) & ~(size_t)255;
+    if (ws_bytes < here) return fail(BQ_EINVAL, "scan workspace too small");
+    Out *sums = (Out *)ws;
+    Out *sum_prefix = sums + tiles;
+    count_launches(2);
+    tile_reduce_kernel<In, Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+    int rc = scan_ws_impl<Out, Out>(sums, sum_prefix, tiles, ws + here, ws_bytes - here, s);
+    if (rc) return rc;
+    tile_scan_kernel<In, Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sum_prefix, out);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
 // ------------------------------------------------------------ validation
 
 struct CheckResult {
@@ -243,6 +281,12 @@ int scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t 
 
 int scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, cudaStream_t s) {
     return scan_impl<uint32_t, uint32_t>(in, out, n, s);
+}
+
+size_t scan_u32_ws_bytes(uint64_t n) { return scan_ws_bytes_impl<uint32_t>(n); }
+
+int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
+    return scan_ws_impl<uint32_t, uint32_t>(in, out, n, (char *)ws, ws_bytes, s);
 }
 
 int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {

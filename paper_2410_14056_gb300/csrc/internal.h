@@ -135,6 +135,18 @@ int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *start
                       const Sampler &smp, bool visit_start, uint32_t *visits,
                       uint32_t *paths, uint32_t *status, cudaStream_t s);
 
+// Bouquet walk batch in a caller-provided scratch region (no allocation).
+size_t walk_batch_scratch_bytes(uint32_t n, uint64_t n_walks);
+int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
+                         uint32_t n_steps, const Sampler &smp, bool visit_start, uint32_t *visits, uint32_t *paths,
+                         uint32_t *status, void *scratch, size_t scratch_bytes, cudaStream_t s);
+// graph.cu: the scan with its tile sums in a caller workspace.
+size_t scan_u32_ws_bytes(uint64_t n);
+int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s);
+// api.cu: the device's status word if it was already allocated (never allocates).
+int existing_status_word(int device, uint32_t **out);
+int validate_sampler(const bq_sampler *in, Sampler &out);
+
 // ---- aesc.cu
 int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,
                 uint64_t k, const uint32_t *tau, const uint32_t *nwalks,

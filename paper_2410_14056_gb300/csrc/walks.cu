@@ -273,7 +273,67 @@ int launch_bouquet(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *s
     return rc;
 }
 
+// The bouquet walk batch with every temporary buffer carved from a
+// caller-provided scratch region (layout of launch_bouquet, scan workspace
+// after it); used by the entry point that must not allocate.
+template <typename RL>
+int launch_bouquet_in(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
+                      uint32_t n_steps, const Sampler &smp, bool visit_start, bool checked, uint32_t *visits,
+                      uint32_t *paths, uint32_t *status, int lanes_w, bool agg, char *scratch,
+                      size_t scratch_bytes, size_t arrays_bytes, cudaStream_t s) {
+    const size_t n = g.n;
+    uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n, *sid = cursor + n + 1, *sst = sid + n_walks;
+    BQ_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n, s));
+    const unsigned grid = blocks_for(n_walks, kThreads * 4);
+    int rc;
+    {
+        ProfScope prof(kProfGroup, s);
+        hist_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, counts, status);
+        rc = scan_u32_ws(counts, cursor, n, scratch + arrays_bytes, scratch_bytes - arrays_bytes, s);
+        if (rc == BQ_OK) scatter_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, cursor, sid, sst);
+        count_launches(2);
+    }
+    if (rc) return rc;
+    switch (lanes_w) {
+    case 1: launch_bouquet_w<RL, 1>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
+                                    agg, visits, paths, status, s); break;
+    case 2: launch_bouquet_w<RL, 2>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
+                                    agg, visits, paths, status, s); break;
+    case 8: launch_bouquet_w<RL, 8>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
+                                    agg, visits, paths, status, s); break;
+    default: launch_bouquet_w<RL, 4>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
+                                     agg, visits, paths, status, s); break;
+    }
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+size_t bouquet_arrays_bytes(uint32_t n, uint64_t n_walks) {
+    return (sizeof(uint32_t) * (2 * (size_t)n + 1 + 2 * (size_t)n_walks) + 255) & ~(size_t)255;
+}
+
 }  // namespace
+
+size_t walk_batch_scratch_bytes(uint32_t n, uint64_t n_walks) {
+    return bouquet_arrays_bytes(n, n_walks) + scan_u32_ws_bytes(n);
+}
+
+int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
+                         uint32_t n_steps, const Sampler &smp, bool visit_start, uint32_t *visits, uint32_t *paths,
+                         uint32_t *status, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+    if (n_walks == 0) return BQ_OK;
+    if (walk_batch_scratch_bytes(g.n, n_walks) > scratch_bytes) return fail(BQ_EINVAL, "scratch too small");
+    const uint64_t positions = (uint64_t)n_steps + (visit_start ? 1 : 0);
+    const bool checked = positions > 0 && n_walks > 0xffffffffull / positions;
+    const int lanes_w = tuning_walks_per_lane();
+    const bool agg = tuning_aggregate_visits();
+    const size_t arrays = bouquet_arrays_bytes(g.n, n_walks);
+    if (g.compact())
+        return launch_bouquet_in(RecCompact{g.rec8}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked,
+                                 visits, paths, status, lanes_w, agg, (char *)scratch, scratch_bytes, arrays, s);
+    return launch_bouquet_in(RecWide{g.rec16}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked, visits,
+                             paths, status, lanes_w, agg, (char *)scratch, scratch_bytes, arrays, s);
+}
 
 int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
                       uint32_t n_steps, uint32_t mode, const Sampler &smp, bool visit_start, uint32_t *visits,
