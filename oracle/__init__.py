@@ -95,6 +95,10 @@ def lib():
                 c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double,
                 c.c_double, c.c_double, c.c_uint32, u32p, u32p]
             L.orc_plan_certified.restype = c.c_int
+            L.orc_plan_scheduled.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double, c.c_uint32,
+                c.c_uint32, c.c_double, c.c_uint32, u32p, u32p]
+            L.orc_plan_scheduled.restype = c.c_int
             _lib = L
     return _lib
 
@@ -217,6 +221,20 @@ def plan_certified(g, uv: np.ndarray, eps: float, delta: float, lambda2: float,
         _p(q, ctypes.c_uint32), eps, delta, lambda2, lambda_neg, tau_max,
         _p(tau, ctypes.c_uint32), _p(nw, ctypes.c_uint32))
     _check(rc, "plan_certified")
+    return tau, nw
+
+
+def plan_scheduled(g, uv: np.ndarray, eps: float, tau_scale: float, tau_add: int, tau_max: int,
+                   n_scale: float, n_min: int):
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    tau = np.zeros(q.shape[0], np.uint32)
+    nw = np.zeros(q.shape[0], np.uint32)
+    rc = lib().orc_plan_scheduled(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), q.shape[0],
+        _p(q, ctypes.c_uint32), eps, tau_scale, tau_add, tau_max, n_scale, n_min,
+        _p(tau, ctypes.c_uint32), _p(nw, ctypes.c_uint32))
+    _check(rc, "plan_scheduled")
     return tau, nw
 
 

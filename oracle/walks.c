@@ -438,6 +438,59 @@ double orc_trunc_bound(double s_e, double lambda2, double lambda_neg, uint32_t t
     return s_e * (p > q ? p : q);
 }
 
+/* Scheduled (uncertified) plan, for graphs on which the certified bounds
+ * explode (slow mixing):
+ *   tau = clamp(ceil(tau_scale * ln(s_e / eps)) + tau_add, 1, tau_max)
+ *         (the ln term counted only when s_e > eps),
+ *   N   = max(n_min, ceil(n_scale * s_e^2 / eps^2), 1).
+ * The ln(s_e / eps) form follows the truncation error s_e * lambda^tau of the
+ * half-weighted series; N follows a sample variance of order s_e^2.
+ * Returns ORC_EOVERFLOW when 2 N tau >= 2^32. */
+int orc_plan_scheduled(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                       uint64_t k, const uint32_t *uv, double eps, double tau_scale,
+                       uint32_t tau_add, uint32_t tau_max, double n_scale, uint32_t n_min,
+                       uint32_t *tau, uint32_t *nwalks)
+{
+    uint64_t *ub, q, id;
+    if (!(eps > 0.0) || tau_max < 1 || !(tau_scale >= 0.0) || !(n_scale >= 0.0))
+        return ORC_EINVAL;
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub)
+        return ORC_EINVAL;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        double du, dv, s, t, nw;
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &id) != ORC_OK) {
+            free(ub);
+            return ORC_ENOEDGE;
+        }
+        du = (double)(offsets[a + 1] - offsets[a]);
+        dv = (double)(offsets[b + 1] - offsets[b]);
+        s = 1.0 / du + 1.0 / dv;
+        t = 0.0;
+        if (s / eps > 1.0)
+            t = ceil(tau_scale * log(s / eps));
+        t = t + (double)tau_add;
+        if (t < 1.0)
+            t = 1.0;
+        if (t > (double)tau_max)
+            t = (double)tau_max;
+        nw = ceil(n_scale * s * s / (eps * eps));
+        if (nw < (double)n_min)
+            nw = (double)n_min;
+        if (nw < 1.0)
+            nw = 1.0;
+        if (nw * 2.0 * t >= 4294967296.0) {
+            free(ub);
+            return ORC_EOVERFLOW;
+        }
+        tau[q] = (uint32_t)t;
+        nwalks[q] = (uint32_t)nw;
+    }
+    free(ub);
+    return ORC_OK;
+}
+
 /* Certified plan for each query edge:
  *   tau = smallest tau >= 1 with s_e * max(P(tau), Q(tau)) <= eps / 2
  *   N   = ceil(8 (tau - 1/2)^2 s_e^2 ln(2 m / delta) / eps^2)

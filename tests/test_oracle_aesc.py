@@ -30,6 +30,24 @@ def test_plan_closed_forms_golden():
         assert np.all(n == int(nw)), name
 
 
+def test_plan_scheduled_golden():
+    for name, eps, ts, ta, tm, ns, nm, tau, nw in golden_rows("plan_scheduled.txt"):
+        g = GRAPHS[name]
+        t, n = oracle.plan_scheduled(g, all_edges(g), float(eps), float(ts), int(ta), int(tm),
+                                     float(ns), int(nm))
+        assert np.all(t == int(tau)) and np.all(n == int(nw)), name
+
+
+def test_plan_scheduled_errors():
+    g = cycle(10)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.plan_scheduled(g, np.array([[0, 5]], np.uint32), 0.1, 2.0, 1, 64, 9.0, 1)
+    assert ei.value.code == oracle.ENOEDGE
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.plan_scheduled(g, np.array([[0, 1]], np.uint32), 1e-4, 2.0, 1, 64, 9.0, 1)
+    assert ei.value.code == oracle.EOVERFLOW
+
+
 @pytest.mark.parametrize("g", [complete(8), cycle(10), cycle(9), diamond(),
                                prufer_tree(12, 2), gnp_connected(10, 0.5, 3)],
                          ids=lambda g: g.name)
