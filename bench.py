@@ -250,6 +250,74 @@ def aesc_measure(bq, torch, steps, warmup):
     }
 
 
+POWERLAW_SCHEDULE = dict(tau_scale=2.0, tau_add=2, tau_max=64, n_scale=9.0, n_min=32)
+
+
+def aesc_powerlaw(bq, torch, steps, warmup):
+    """AESC on the power-law graph (Chung-Lu n = 4M, mean degree 10,
+    exponent 2.1, largest component), all edges at eps = 0.05 with the
+    scheduled (uncertified) plan.  Accuracy checks: Foster residual
+    |sum SC - (n-1)| / (n-1), and 1000 edges re-estimated with 16 x N and
+    2 x tau."""
+    import numpy as np
+    from workloads import cached, chung_lu
+    g = cached("chunglu4m_d10_g2.1_s3", lambda: chung_lu(4_000_000, 10, 2.1, seed=3))
+    graph = bq.Graph.from_csr(g)
+    eps = 0.05
+    sched = bq.Schedule(POWERLAW_SCHEDULE["tau_scale"], POWERLAW_SCHEDULE["tau_add"],
+                        POWERLAW_SCHEDULE["tau_max"], POWERLAW_SCHEDULE["n_scale"],
+                        POWERLAW_SCHEDULE["n_min"], 0)
+    tau, nw = bq.aesc_plan(graph, None, eps, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+    work = float(np.sum(2.0 * tau.astype(np.float64) * nw))
+    dtau = torch.from_numpy(tau.view(np.int32)).cuda()
+    dnw = torch.from_numpy(nw.view(np.int32)).cuda()
+    counts = torch.empty(4 * tau.size, dtype=torch.int32, device="cuda")
+    sc = torch.empty(tau.size, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        bq.aesc_estimate(graph, 5, None, dtau, dnw, counts=counts, sc=sc)
+    bq.sync()
+    bq.profile_read()
+    bq.profile_enable(True)
+    lat = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bq.aesc_estimate(graph, 5, None, dtau, dnw, counts=counts, sc=sc)
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    bq.sync()
+    prof = bq.profile_read()
+    bq.profile_enable(False)
+    ms = sum(lat) / len(lat)
+    kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
+    est = sc.cpu().numpy()
+    foster = abs(float(est.sum()) - (g.n - 1)) / (g.n - 1)
+    # re-estimate 1000 edges with 16 x N and 2 x tau (independent seed)
+    rng = np.random.default_rng(7)
+    pick = np.sort(rng.choice(tau.size, 1000, replace=False))
+    from workloads import all_edges
+    uv = all_edges(g)[pick]
+    t2 = np.minimum(2 * tau[pick], 4096).astype(np.uint32)
+    n2 = np.minimum(16 * nw[pick].astype(np.uint64), (2**32 - 1) // (2 * t2.astype(np.uint64) + 2)).astype(np.uint32)
+    _, ref = bq.aesc_estimate_host(graph, 99, uv, t2, n2)
+    diff = np.abs(est[pick] - ref)
+    graph.close()
+    return {
+        "workload": f"chung-lu n=4M d=10 gamma=2.1 LCC (n={g.n}, m={g.m}), all edges, eps={eps}, "
+                    "scheduled plan (uncertified)",
+        "schedule": POWERLAW_SCHEDULE,
+        "edges": int(tau.size), "edges_per_s": tau.size / (ms / 1e3),
+        "walk_steps_per_call": work, "walk_steps_per_s": work / (ms / 1e3),
+        "ms_per_estimate": ms, "count_kernel_ms": kern_ms,
+        "count_kernel_gbs": work * BYTES_PER_STEP / (kern_ms / 1e3) / 1e9,
+        "tau_mean": float(tau.mean()), "nwalks_mean": float(nw.mean()),
+        "foster_residual": foster,
+        "subset_1000_max_abs_diff_vs_16N_2tau": float(diff.max()),
+        "subset_1000_frac_within_eps": float(np.mean(diff <= eps)),
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -360,9 +428,10 @@ def run_ours(args):
                "d2h_bytes_per_step": int(4 * g.n), "ms_per_step": e2e_s * 1e3,
                "api": "bq_walk_batch with BQ_HOST_IO (pinned host buffers)"}
 
-    aesc = None
+    aesc = aesc_pl = None
     if not args.no_aesc and rank == 0:
         aesc = aesc_measure(bq, torch, max(5, args.steps), args.warmup)
+        aesc_pl = aesc_powerlaw(bq, torch, 3, 1)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
@@ -391,6 +460,7 @@ def run_ours(args):
                       "ms_per_step": naive_ms,
                       "bouquet_speedup": naive_ms / ms_per_step},
             "aesc": aesc,
+            "aesc_powerlaw": aesc_pl,
         }
         print(json.dumps(line), flush=True)
     graph.close()

@@ -92,6 +92,8 @@ typedef struct bq_graph_info_t {
     int32_t device;        /* CUDA device ordinal */
     double lambda2;        /* as set by bq_graph_set_spectrum */
     double lambda_neg;
+    int32_t layout;        /* device layout built (bq_tuning.layout value, never 1) */
+    int32_t reserved;
 } bq_graph_info_t;
 
 /* Fill *info (host struct).  May copy the CSR to the host once to find the
@@ -250,7 +252,23 @@ typedef struct bq_tuning {
     uint32_t walk_lanes;       /* walks per lane, bouquet walk batch: 1, 2, 4, 8 */
     uint32_t aggregate_visits; /* 1: merge equal-vertex visits in a warp first */
     uint32_t aesc_lanes;       /* walks per lane, AESC counting: 2, 4, 8 */
-    uint32_t reserved;
+    uint32_t layout;           /* device layout of graphs created from now on
+                                  (what a walk step reads at random):
+                                  0: plain uint32 CSR + 8-byte vertex records
+                                     {row offset, degree};
+                                  1 (default): automatic: 2 when the 8-byte
+                                     edge records fit in half of L2, else 5;
+                                  2: per CSR entry an edge record {id, row
+                                     offset, degree}, 8 packed bytes when the
+                                     fields fit, else 16 (one load per step,
+                                     2-4x the bytes of plain CSR);
+                                  3: 16-byte edge records;
+                                  4: plain CSR + 16-byte vertex records (the
+                                     layout used when nnz >= 2^32);
+                                  5: neighbour ids bit-packed to ceil(log2 n)
+                                     bits, several per 16-byte chunk, + 8-byte
+                                     vertex records (plain CSR when packing
+                                     saves nothing) */
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

@@ -58,7 +58,7 @@ class Schedule(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("walk_lanes", ctypes.c_uint32), ("aggregate_visits", ctypes.c_uint32),
-                ("aesc_lanes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("aesc_lanes", ctypes.c_uint32), ("layout", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -67,7 +67,8 @@ class GraphInfo(ctypes.Structure):
                 ("bipartite", ctypes.c_int32), ("n_components", ctypes.c_int32),
                 ("device_bytes", ctypes.c_uint64), ("has_spectrum", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("lambda2", ctypes.c_double),
-                ("lambda_neg", ctypes.c_double)]
+                ("lambda_neg", ctypes.c_double), ("layout", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -344,13 +345,14 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(load_library().bq_get_tuning(ctypes.byref(t)))
     return {"walk_lanes": t.walk_lanes, "aggregate_visits": t.aggregate_visits,
-            "aesc_lanes": t.aesc_lanes}
+            "aesc_lanes": t.aesc_lanes, "layout": t.layout}
 
 
 def set_tuning(**kw):
     cur = get_tuning()
     cur.update(kw)
-    t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]), 0)
+    t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]),
+               int(cur["layout"]))
     _check(load_library().bq_set_tuning(ctypes.byref(t)))
 
 

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu"]
-HEADERS = ["internal.h", "hash.cuh"]
+HEADERS = ["internal.h", "hash.cuh", "edges.cuh"]
 
 
 def nvcc() -> str:

@@ -9,6 +9,7 @@
 // warp adds its two totals to the edge's counters with two atomics.
 #include <math.h>
 
+#include "edges.cuh"
 #include "hash.cuh"
 #include "internal.h"
 
@@ -24,24 +25,6 @@ struct QueryInfo {
     uint32_t tau, nwalks;
     uint32_t valid;
     uint32_t pad;
-};
-
-struct RecCompact {
-    const uint2 *rec;
-    __device__ __forceinline__ void load(uint32_t v, uint64_t &off, uint32_t &deg) const {
-        const uint2 r = __ldg(rec + v);
-        off = r.x;
-        deg = r.y;
-    }
-};
-
-struct RecWide {
-    const uint4 *rec;
-    __device__ __forceinline__ void load(uint32_t v, uint64_t &off, uint32_t &deg) const {
-        const uint4 r = __ldg(rec + v);
-        off = ((uint64_t)r.y << 32) | r.x;
-        deg = r.z;
-    }
 };
 
 // first index in [lo, hi) whose entry is >= key
@@ -131,9 +114,9 @@ __device__ __forceinline__ uint64_t find_query(const uint64_t *__restrict__ begi
 // j, so walk pairs (2i, 2i+1) share one Philox block.  Coupled sampler: slot
 // j of lane l is walk chunk*32W + j*32 + l, so a coupling group of 32 fills
 // one lockstep slot.
-template <typename RL, int W, bool COUPLED>
+template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kThreads)
-aesc_count_kernel(RL rl, const uint32_t *__restrict__ nbrs, const QueryInfo *__restrict__ info,
+aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *__restrict__ info,
                   const uint64_t *__restrict__ begin, uint64_t k, uint64_t seed, Sampler smp,
                   unsigned long long *__restrict__ next_task, uint32_t *__restrict__ counts) {
     const uint32_t lane = threadIdx.x & 31;
@@ -172,28 +155,28 @@ aesc_count_kernel(RL rl, const uint32_t *__restrict__ nbrs, const QueryInfo *__r
                 act[j] = kk < qi.nwalks;
             }
         }
+        uint64_t off0;
+        uint32_t deg0;
+        start_record(offsets, start, off0, deg0);
+        uint64_t off[W];
+        uint32_t deg[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             cur[j] = start;
+            off[j] = off0;
+            deg[j] = act[j] ? deg0 : 0u;  // inactive walks never move or hit
             if (!COUPLED) gs[j] = 0;
         }
         uint32_t hit_u = 0, hit_v = 0;
         for (uint32_t l = 1; l <= qi.tau; ++l) {
             const uint32_t weight = l < qi.tau ? 2u : 1u;
-            uint64_t off[W];
-            uint32_t d[W];
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 st[j] += kGolden;
                 if (COUPLED) gs[j] += kGolden;
-                d[j] = 0;
-                off[j] = 0;
-                if (act[j]) rl.load(cur[j], off[j], d[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                if (d[j]) {
-                    cur[j] = nbrs[off[j] + choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), d[j])];
+                if (deg[j]) {
+                    const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                    el.next(off[j] + kk, cur[j], off[j], deg[j]);
                     hit_u += cur[j] == qi.u ? weight : 0u;
                     hit_v += cur[j] == qi.v ? weight : 0u;
                 }
@@ -237,36 +220,36 @@ unsigned blocks_for(uint64_t items, uint64_t per_block) {
     return (unsigned)b;
 }
 
-template <typename RL, int W, bool COUPLED>
-int launch_count(RL rl, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+template <typename EL, int W, bool COUPLED>
+int launch_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
                  uint64_t seed, const Sampler &smp, unsigned long long *next_task, uint32_t *counts,
                  cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     BQ_CUDA(cudaGetDevice(&dev));
     BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aesc_count_kernel<RL, W, COUPLED>, kThreads, 0));
+    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aesc_count_kernel<EL, W, COUPLED>, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
-    aesc_count_kernel<RL, W, COUPLED><<<sms * per_sm, kThreads, 0, s>>>(rl, g.nbrs, info, begin, k, seed, smp,
+    aesc_count_kernel<EL, W, COUPLED><<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, info, begin, k, seed, smp,
                                                                          next_task, counts);
     BQ_CUDA(cudaGetLastError());
     return BQ_OK;
 }
 
-template <typename RL>
-int launch_count_w(RL rl, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+template <typename EL>
+int launch_count_w(EL el, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
                    uint64_t seed, const Sampler &smp, unsigned long long *next_task, uint32_t *counts,
                    int w, cudaStream_t s) {
     const bool coupled = smp.kind == 1;
     switch (w) {
     case 2:
-        return coupled ? launch_count<RL, 2, true>(rl, g, info, begin, k, seed, smp, next_task, counts, s)
-                       : launch_count<RL, 2, false>(rl, g, info, begin, k, seed, smp, next_task, counts, s);
+        return coupled ? launch_count<EL, 2, true>(el, g, info, begin, k, seed, smp, next_task, counts, s)
+                       : launch_count<EL, 2, false>(el, g, info, begin, k, seed, smp, next_task, counts, s);
     case 8:
-        return coupled ? launch_count<RL, 8, true>(rl, g, info, begin, k, seed, smp, next_task, counts, s)
-                       : launch_count<RL, 8, false>(rl, g, info, begin, k, seed, smp, next_task, counts, s);
+        return coupled ? launch_count<EL, 8, true>(el, g, info, begin, k, seed, smp, next_task, counts, s)
+                       : launch_count<EL, 8, false>(el, g, info, begin, k, seed, smp, next_task, counts, s);
     default:
-        return coupled ? launch_count<RL, 4, true>(rl, g, info, begin, k, seed, smp, next_task, counts, s)
-                       : launch_count<RL, 4, false>(rl, g, info, begin, k, seed, smp, next_task, counts, s);
+        return coupled ? launch_count<EL, 4, true>(el, g, info, begin, k, seed, smp, next_task, counts, s)
+                       : launch_count<EL, 4, false>(el, g, info, begin, k, seed, smp, next_task, counts, s);
     }
 }
 
@@ -315,10 +298,9 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
     if (rc == BQ_OK) {
         ProfScope prof(kProfAesc, s);
         count_launches(1);
-        if (g.compact())
-            rc = launch_count_w(RecCompact{g.rec8}, g, info, begin, k, seed, smp, next_task, counts, w, s);
-        else
-            rc = launch_count_w(RecWide{g.rec16}, g, info, begin, k, seed, smp, next_task, counts, w, s);
+        rc = with_edges(g, [&](auto el) {
+            return launch_count_w(el, g, info, begin, k, seed, smp, next_task, counts, w, s);
+        });
     }
     if (rc == BQ_OK) {
         ProfScope prof(kProfAescAux, s);

@@ -24,6 +24,7 @@ std::vector<char> g_pool_configured;    // per device ordinal
 std::atomic<int> g_walks_per_lane{4};
 std::atomic<int> g_aggregate{0};
 std::atomic<int> g_aesc_walks_per_lane{4};
+std::atomic<int> g_edge_records{1};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -137,6 +138,7 @@ int validate_sampler(const bq_sampler *in, Sampler &out);
 int tuning_walks_per_lane() { return g_walks_per_lane.load(); }
 bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
 int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
+int tuning_layout() { return g_edge_records.load(); }
 
 namespace {
 
@@ -310,6 +312,9 @@ int bq_graph_destroy(bq_graph *g) {
     cudaFree(g->d_rec8);
     cudaFree(g->d_rec16);
     cudaFree(g->d_upper_before);
+    cudaFree(g->d_edge8);
+    cudaFree(g->d_edge16);
+    cudaFree(g->d_pk);
     delete g;
     return BQ_OK;
 }
@@ -333,6 +338,7 @@ int bq_graph_info(bq_graph *g, bq_graph_info_t *info) {
     info->device = g->device;
     info->lambda2 = g->lambda2;
     info->lambda_neg = g->lambda_neg;
+    info->layout = g->layout;
     return BQ_OK;
 }
 
@@ -622,6 +628,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->walk_lanes = (uint32_t)g_walks_per_lane.load();
     out->aggregate_visits = (uint32_t)g_aggregate.load();
     out->aesc_lanes = (uint32_t)g_aesc_walks_per_lane.load();
+    out->layout = (uint32_t)g_edge_records.load();
     return BQ_OK;
 }
 
@@ -632,9 +639,11 @@ int bq_set_tuning(const bq_tuning *in) {
     if (w != 1 && w != 2 && w != 4 && w != 8) return fail(BQ_EINVAL, "walk_lanes must be 1, 2, 4 or 8");
     if (a != 2 && a != 4 && a != 8) return fail(BQ_EINVAL, "aesc_lanes must be 2, 4 or 8");
     if (in->aggregate_visits > 1) return fail(BQ_EINVAL, "aggregate_visits must be 0 or 1");
+    if (in->layout > 5) return fail(BQ_EINVAL, "layout must be 0 to 5");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
+    g_edge_records.store((int)in->layout);
     return BQ_OK;
 }
 

@@ -266,6 +266,47 @@ __global__ void build_records_kernel(const int64_t *__restrict__ off, uint32_t n
     }
 }
 
+// Edge record of CSR entry j: the neighbour's id, row offset and degree.
+__global__ void build_edges_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ nbrs,
+                                   uint64_t nnz, uint32_t sh_off, uint32_t sh_deg, uint64_t *edge8,
+                                   uint4 *edge16) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nnz;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = nbrs[j];
+        const uint64_t lo = (uint64_t)off[x];
+        const uint64_t deg = (uint64_t)off[x + 1] - lo;
+        if (edge8) edge8[j] = (uint64_t)x | (lo << sh_off) | (deg << sh_deg);
+        else edge16[j] = make_uint4(x, (uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)deg);
+    }
+}
+
+// Chunk c of the packed ids holds entries c*q .. c*q + q - 1, entry i of the
+// chunk at bits [i*bits, (i+1)*bits) of the 128-bit chunk (word 0 = bits
+// 0..31).
+__global__ void build_packed_ids_kernel(const uint32_t *__restrict__ nbrs, uint64_t nnz, uint32_t bits, uint32_t q,
+                                        uint64_t chunks, uint4 *__restrict__ pk) {
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < chunks;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (uint32_t i = 0; i < q; ++i) {
+            const uint64_t j = c * q + i;
+            if (j >= nnz) break;
+            const uint64_t v = nbrs[j];
+            const uint32_t bit = i * bits;
+            const uint32_t wi = bit >> 5, sh = bit & 31;
+            w[wi] |= (uint32_t)(v << sh);
+            if (sh + bits > 32) w[wi + 1] |= (uint32_t)(v >> (32 - sh));
+        }
+        pk[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+uint32_t bits_for(uint64_t max_value) {
+    uint32_t b = 1;
+    while (b < 64 && (max_value >> b) != 0) ++b;
+    return b;
+}
+
 unsigned grid_for(uint64_t items, int threads, int per_thread = 1) {
     uint64_t blocks = (items + (uint64_t)threads * per_thread - 1) / ((uint64_t)threads * per_thread);
     if (blocks < 1) blocks = 1;
@@ -371,7 +412,8 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
     }
     // records
     {
-        const bool compact = g->nnz < (1ull << 32);
+        const int layout = tuning_layout();
+        const bool compact = g->nnz < (1ull << 32) && layout != 4;
         size_t rec_bytes = (size_t)n * (compact ? sizeof(uint2) : sizeof(uint4));
         void *rec = nullptr;
         e = cudaMalloc(&rec, rec_bytes > 0 ? rec_bytes : 16);
@@ -409,6 +451,72 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
                       (unsigned long long)m_upper, (unsigned long long)g->nnz);
             goto done;
         }
+        // Automatic layout: when the 8-byte edge records fit in half of L2,
+        // a step is one cached load; otherwise the smallest array a step
+        // reads at random (bit-packed ids) keeps the most of it in L2.
+        int use = layout;
+        if (layout == 1) {
+            int dev = 0, l2 = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2 = 0;
+            const bool fits = bits_for(n > 0 ? n - 1 : 0) + bits_for(g->nnz) + bits_for(g->max_degree) <= 64;
+            use = (compact && fits && (g->nnz + n) * 8ull <= (uint64_t)l2 / 2) ? 2 : 5;
+        }
+        if (g->nnz > 0 && use == 5 && compact) {
+            const uint32_t bits = bits_for(n > 0 ? n - 1 : 0);
+            const uint32_t q = 128 / bits;
+            if (q > 4) {  // fewer than 32 bits per id: packing saves memory
+                const uint64_t chunks = (g->nnz + q - 1) / q;
+                const size_t bytes = sizeof(uint4) * chunks;
+                e = cudaMalloc(&g->d_pk, bytes);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "cudaMalloc(packed ids)");
+                    goto done;
+                }
+                g->device_bytes += bytes;
+                g->pk_bits = bits;
+                g->pk_q = q;
+                g->pk_mask = bits >= 32 ? 0xffffffffu : ((1u << bits) - 1u);
+                build_packed_ids_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(g->d_nbrs, g->nnz, bits, q, chunks,
+                                                                              g->d_pk);
+                e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "build_packed_ids_kernel");
+                    goto done;
+                }
+            }
+        }
+        if (g->nnz > 0 && (use == 2 || use == 3)) {
+            const uint32_t b_id = bits_for(n > 0 ? n - 1 : 0);
+            const uint32_t b_off = bits_for(g->nnz);
+            const uint32_t b_deg = bits_for(g->max_degree);
+            const bool packed = use == 2 && b_id + b_off + b_deg <= 64;
+            const size_t bytes = g->nnz * (packed ? sizeof(uint64_t) : sizeof(uint4));
+            void *edges = nullptr;
+            e = cudaMalloc(&edges, bytes);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "cudaMalloc(edge records)");
+                goto done;
+            }
+            g->device_bytes += bytes;
+            if (packed) {
+                g->d_edge8 = (uint64_t *)edges;
+                g->sh_off = b_id;
+                g->sh_deg = b_id + b_off;
+                g->mask_id = b_id >= 32 ? 0xffffffffu : ((1u << b_id) - 1u);
+                g->mask_off = (b_off >= 64) ? ~0ull : ((1ull << b_off) - 1ull);
+            } else {
+                g->d_edge16 = (uint4 *)edges;
+            }
+            build_edges_kernel<<<grid_for(g->nnz, 256, 4), 256, 0, s>>>(g->d_offsets, g->d_nbrs, g->nnz, g->sh_off,
+                                                                        g->sh_deg, g->d_edge8, g->d_edge16);
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "build_edges_kernel");
+                goto done;
+            }
+        }
+        g->layout = g->d_pk ? 5 : (g->d_edge8 ? 2 : (g->d_edge16 ? 3 : (compact ? 0 : 4)));
     }
 done:
     cudaFree(res);

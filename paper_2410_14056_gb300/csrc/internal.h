@@ -42,6 +42,21 @@ struct DeviceGraph {
     const uint2 *rec8;       // n, compact records (or null)
     const uint4 *rec16;      // n, wide records (or null)
     const uint64_t *upper_before;  // n + 1: edges {x,y}, x<y, with x < u
+    // Edge records: entry j of the CSR carries everything the next step
+    // needs about its neighbour x = nbrs[j]: {x, row offset of x, degree of
+    // x}.  Packed into 64 bits (id | offset << sh_off | degree << sh_deg)
+    // when the three fields fit, else 16 bytes {x, offset lo, offset hi,
+    // degree}; null when the graph was built without them.
+    const uint64_t *edge8;
+    const uint4 *edge16;
+    uint32_t sh_off, sh_deg;
+    uint32_t mask_id;
+    uint64_t mask_off;
+    // Packed neighbour ids: `pk_q` ids of `pk_bits` bits per 16-byte chunk
+    // (id i of chunk c at bits [i*pk_bits, (i+1)*pk_bits)), so that an id
+    // never straddles a chunk and one aligned vector load reads it.
+    const uint4 *pk;
+    uint32_t pk_bits, pk_q, pk_mask;
     bool compact() const { return rec8 != nullptr; }
 };
 
@@ -57,6 +72,13 @@ struct bq_graph {
     uint2 *d_rec8 = nullptr;
     uint4 *d_rec16 = nullptr;
     uint64_t *d_upper_before = nullptr;
+    uint64_t *d_edge8 = nullptr;
+    uint4 *d_edge16 = nullptr;
+    uint32_t sh_off = 0, sh_deg = 0, mask_id = 0;
+    uint64_t mask_off = 0;
+    uint4 *d_pk = nullptr;
+    uint32_t pk_bits = 0, pk_q = 0, pk_mask = 0;
+    int layout = 0;  // layout chosen at creation (bq_tuning.layout values)
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
     uint64_t device_bytes = 0;
@@ -77,6 +99,16 @@ struct bq_graph {
         v.rec8 = d_rec8;
         v.rec16 = d_rec16;
         v.upper_before = d_upper_before;
+        v.edge8 = d_edge8;
+        v.edge16 = d_edge16;
+        v.sh_off = sh_off;
+        v.sh_deg = sh_deg;
+        v.mask_id = mask_id;
+        v.mask_off = mask_off;
+        v.pk = d_pk;
+        v.pk_bits = pk_bits;
+        v.pk_q = pk_q;
+        v.pk_mask = pk_mask;
         return v;
     }
 };
@@ -105,6 +137,7 @@ void scratch_free(void *p, cudaStream_t s);
 int tuning_walks_per_lane();
 bool tuning_aggregate_visits();
 int tuning_aesc_walks_per_lane();
+int tuning_layout();  // graph layout built at creation (bq_tuning.layout)
 
 // Profiling (api.cu): event brackets around kernel groups while enabled, and
 // a count of every kernel launch.

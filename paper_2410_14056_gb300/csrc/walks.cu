@@ -8,11 +8,14 @@
 // depends only on (seed, i, start, graph); only the order in which the walks
 // are executed differs.
 //
-// Memory per step (the random gathers Sec. 3.2 names as the bottleneck):
-// one vertex record {row offset, degree} (8 B, or 16 B for graphs with
-// nnz >= 2^32) and one 4-byte neighbour id, plus a 4-byte visit atomic.
+// Memory per step (the random gathers Sec. 3.2 names as the bottleneck): the
+// naive kernel reads the 4-byte neighbour id and the neighbour's 8-byte
+// vertex record (two dependent loads); the bouquet kernel, on graphs built
+// with edge records, reads one 8-byte edge record.  Plus a 4-byte visit
+// atomic.
 #include <algorithm>
 
+#include "edges.cuh"
 #include "hash.cuh"
 #include "internal.h"
 
@@ -112,18 +115,19 @@ __global__ void scatter_starts_kernel(const uint32_t *__restrict__ starts, uint6
 
 // -------------------------------------------------------------- bouquet
 
-// Warp w owns sorted slots [w * 32 * W, (w + 1) * 32 * W); slot j of lane l
+// Warp w owns grouped slots [w * 32 * W, (w + 1) * 32 * W); slot j of lane l
 // is position w*32*W + j*32 + l, so each of the W lockstep groups is 32
 // consecutive walks of the grouped order (a bouquet: mostly one start
-// vertex).  Each lane advances W independent walks per step, which keeps W
-// dependent gather chains in flight per thread.  With AGG, lanes standing on
-// the same vertex merge their visit increments (match + popc) before one
-// atomic.
-template <typename RL, int W, bool COUPLED, bool AGG>
+// vertex).  Each lane advances W independent walks per step, keeping W
+// dependent gather chains in flight per thread.  A walk carries (vertex, row
+// offset, degree) from step to step, so with edge records a step is a single
+// dependent load.  With `agg`, lanes standing on the same vertex merge their
+// visit increments (match + popc) before one atomic.
+template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kThreads)
-walk_bouquet_kernel(RL rl, const uint32_t *__restrict__ nbrs, const uint32_t *__restrict__ sorted_id,
+walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ sorted_id,
                     const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr,
-                    uint32_t n_steps, uint64_t seed, Sampler smp, bool visit_start, bool checked,
+                    uint32_t n_steps, uint64_t seed, Sampler smp, bool visit_start, bool checked, bool agg,
                     uint32_t *__restrict__ visits, uint32_t *__restrict__ paths, uint32_t *status) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -131,8 +135,8 @@ walk_bouquet_kernel(RL rl, const uint32_t *__restrict__ nbrs, const uint32_t *__
     const uint64_t base = warp * 32ull * W;
     if (base >= n_valid) return;
 
-    uint32_t cur[W], id[W], amask[W];
-    uint64_t st[W], gs[W];
+    uint32_t cur[W], id[W], deg[W], amask[W];
+    uint64_t off[W], st[W], gs[W];
     bool act[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
@@ -141,14 +145,18 @@ walk_bouquet_kernel(RL rl, const uint32_t *__restrict__ nbrs, const uint32_t *__
         amask[j] = __ballot_sync(0xffffffffu, act[j]);
         id[j] = act[j] ? sorted_id[p] : 0u;
         cur[j] = act[j] ? sorted_start[p] : 0u;
+        off[j] = 0;
+        deg[j] = 0;
+        if (act[j]) start_record(offsets, cur[j], off[j], deg[j]);
         st[j] = walk_key(seed, kBatchStream, id[j]);
         gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, id[j] / smp.width) : 0ull;
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-        if (paths && act[j]) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1)] = cur[j];
-        if (visit_start && act[j]) {
-            if (AGG) {
+        if (!act[j]) continue;
+        if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1)] = cur[j];
+        if (visit_start) {
+            if (agg) {
                 const uint32_t peers = __match_any_sync(amask[j], cur[j]);
                 if (lane == (uint32_t)(__ffs(peers) - 1)) add_visits(visits, cur[j], __popc(peers), checked, status);
             } else {
@@ -157,24 +165,19 @@ walk_bouquet_kernel(RL rl, const uint32_t *__restrict__ nbrs, const uint32_t *__
         }
     }
     for (uint32_t l = 1; l <= n_steps; ++l) {
-        uint64_t off[W];
-        uint32_t d[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             st[j] += kGolden;
             if (COUPLED) gs[j] += kGolden;
-            d[j] = 0;
-            off[j] = 0;
-            if (act[j]) rl.load(cur[j], off[j], d[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            if (d[j]) cur[j] = nbrs[off[j] + choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), d[j])];
+            if (deg[j]) {
+                const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                el.next(off[j] + k, cur[j], off[j], deg[j]);
+            }
         }
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             if (!act[j]) continue;
-            if (AGG) {
+            if (agg) {
                 const uint32_t peers = __match_any_sync(amask[j], cur[j]);
                 if (lane == (uint32_t)(__ffs(peers) - 1)) add_visits(visits, cur[j], __popc(peers), checked, status);
             } else {
@@ -209,107 +212,82 @@ int launch_naive(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *sta
     return BQ_OK;
 }
 
-template <typename RL, int W>
-void launch_bouquet_w(RL rl, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst,
-                      const uint32_t *n_valid, uint64_t n_walks, uint32_t n_steps, uint64_t seed,
-                      const Sampler &smp, bool visit_start, bool checked, bool agg, uint32_t *visits,
-                      uint32_t *paths, uint32_t *status, cudaStream_t s) {
+template <typename EL, int W>
+void launch_bouquet_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+                      uint64_t n_walks, uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start,
+                      bool checked, bool agg, uint32_t *visits, uint32_t *paths, uint32_t *status, cudaStream_t s) {
     const unsigned grid = blocks_for(n_walks, (uint64_t)kThreads * W);
     ProfScope prof(kProfWalk, s);
     count_launches(1);
-#define BQ_LAUNCH(C, A)                                                                                \
-    walk_bouquet_kernel<RL, W, C, A><<<grid, kThreads, 0, s>>>(rl, g.nbrs, sid, sst, n_valid, n_steps, seed, \
-                                                               smp, visit_start, checked, visits, paths, status)
-    if (smp.kind == 1) {
-        if (agg) BQ_LAUNCH(true, true);
-        else BQ_LAUNCH(true, false);
-    } else {
-        if (agg) BQ_LAUNCH(false, true);
-        else BQ_LAUNCH(false, false);
-    }
-#undef BQ_LAUNCH
+    if (smp.kind == 1)
+        walk_bouquet_kernel<EL, W, true><<<grid, kThreads, 0, s>>>(el, g.offsets, sid, sst, n_valid, n_steps, seed,
+                                                                   smp, visit_start, checked, agg, visits, paths,
+                                                                   status);
+    else
+        walk_bouquet_kernel<EL, W, false><<<grid, kThreads, 0, s>>>(el, g.offsets, sid, sst, n_valid, n_steps, seed,
+                                                                    smp, visit_start, checked, agg, visits, paths,
+                                                                    status);
 }
 
-template <typename RL>
-int launch_bouquet(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
-                   uint32_t n_steps, const Sampler &smp, bool visit_start, bool checked, uint32_t *visits,
-                   uint32_t *paths, uint32_t *status, int lanes_w, bool agg, cudaStream_t s) {
-    // scratch: counts[n] | cursor[n + 1] | sorted_id[n_walks] | sorted_start[n_walks]
-    const size_t n = g.n;
-    const size_t bytes = sizeof(uint32_t) * (2 * n + 1 + 2 * (size_t)n_walks);
-    uint32_t *buf = nullptr;
-    int rc = scratch_alloc((void **)&buf, bytes, s);
-    if (rc) return rc;
-    uint32_t *counts = buf, *cursor = buf + n, *sid = cursor + n + 1, *sst = sid + n_walks;
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n, s);
-    if (e != cudaSuccess) {
-        scratch_free(buf, s);
-        return cuda_fail(e, "cudaMemsetAsync(counts)");
-    }
-    const unsigned grid = blocks_for(n_walks, kThreads * 4);
-    {
-        ProfScope prof(kProfGroup, s);
-        hist_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, counts, status);
-        rc = scan_u32(counts, cursor, n, s);
-        if (rc == BQ_OK) scatter_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, cursor, sid, sst);
-        count_launches(2);
-    }
-    if (rc == BQ_OK) {
-        // after the scatter cursor[v] is the end of bucket v; cursor[n] = valid walks
-        switch (lanes_w) {
-        case 1: launch_bouquet_w<RL, 1>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start,
-                                        checked, agg, visits, paths, status, s); break;
-        case 2: launch_bouquet_w<RL, 2>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start,
-                                        checked, agg, visits, paths, status, s); break;
-        case 8: launch_bouquet_w<RL, 8>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start,
-                                        checked, agg, visits, paths, status, s); break;
-        default: launch_bouquet_w<RL, 4>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start,
-                                         checked, agg, visits, paths, status, s); break;
-        }
-        e = cudaGetLastError();
-        if (e != cudaSuccess) rc = cuda_fail(e, "walk_bouquet_kernel");
-    }
-    scratch_free(buf, s);
-    return rc;
-}
-
-// The bouquet walk batch with every temporary buffer carved from a
-// caller-provided scratch region (layout of launch_bouquet, scan workspace
-// after it); used by the entry point that must not allocate.
-template <typename RL>
-int launch_bouquet_in(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
-                      uint32_t n_steps, const Sampler &smp, bool visit_start, bool checked, uint32_t *visits,
-                      uint32_t *paths, uint32_t *status, int lanes_w, bool agg, char *scratch,
-                      size_t scratch_bytes, size_t arrays_bytes, cudaStream_t s) {
-    const size_t n = g.n;
-    uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n, *sid = cursor + n + 1, *sst = sid + n_walks;
-    BQ_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n, s));
-    const unsigned grid = blocks_for(n_walks, kThreads * 4);
-    int rc;
-    {
-        ProfScope prof(kProfGroup, s);
-        hist_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, counts, status);
-        rc = scan_u32_ws(counts, cursor, n, scratch + arrays_bytes, scratch_bytes - arrays_bytes, s);
-        if (rc == BQ_OK) scatter_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, cursor, sid, sst);
-        count_launches(2);
-    }
-    if (rc) return rc;
+template <typename EL>
+void launch_bouquet_any(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst,
+                        const uint32_t *n_valid, uint64_t n_walks, uint32_t n_steps, uint64_t seed,
+                        const Sampler &smp, bool visit_start, bool checked, bool agg, uint32_t *visits,
+                        uint32_t *paths, uint32_t *status, int lanes_w, cudaStream_t s) {
     switch (lanes_w) {
-    case 1: launch_bouquet_w<RL, 1>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
-                                    agg, visits, paths, status, s); break;
-    case 2: launch_bouquet_w<RL, 2>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
-                                    agg, visits, paths, status, s); break;
-    case 8: launch_bouquet_w<RL, 8>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
-                                    agg, visits, paths, status, s); break;
-    default: launch_bouquet_w<RL, 4>(rl, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked,
+    case 1: launch_bouquet_w<EL, 1>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+                                    visits, paths, status, s); break;
+    case 2: launch_bouquet_w<EL, 2>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+                                    visits, paths, status, s); break;
+    case 8: launch_bouquet_w<EL, 8>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+                                    visits, paths, status, s); break;
+    default: launch_bouquet_w<EL, 4>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked,
                                      agg, visits, paths, status, s); break;
     }
+}
+
+// Group the walks by start vertex into (sid, sst); cursor[n] = valid walks.
+int group_by_start(const DeviceGraph &g, const uint32_t *starts, uint64_t n_walks, uint32_t *counts, uint32_t *cursor,
+                   uint32_t *sid, uint32_t *sst, uint32_t *status, void *scan_ws, size_t scan_ws_bytes,
+                   cudaStream_t s) {
+    BQ_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * g.n, s));
+    const unsigned grid = blocks_for(n_walks, kThreads * 4);
+    ProfScope prof(kProfGroup, s);
+    count_launches(2);
+    hist_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, counts, status);
+    const int rc = scan_ws ? scan_u32_ws(counts, cursor, g.n, scan_ws, scan_ws_bytes, s)
+                           : scan_u32(counts, cursor, g.n, s);
+    if (rc) return rc;
+    scatter_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, cursor, sid, sst);
     BQ_CUDA(cudaGetLastError());
     return BQ_OK;
 }
 
 size_t bouquet_arrays_bytes(uint32_t n, uint64_t n_walks) {
     return (sizeof(uint32_t) * (2 * (size_t)n + 1 + 2 * (size_t)n_walks) + 255) & ~(size_t)255;
+}
+
+// The bouquet walk batch in `scratch` (counts[n] | cursor[n + 1] | sorted
+// ids | sorted starts, then the scan workspace when scan_ws is set).
+int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks, uint32_t n_steps,
+               const Sampler &smp, bool visit_start, uint32_t *visits, uint32_t *paths, uint32_t *status,
+               char *scratch, char *scan_ws, size_t scan_ws_bytes, cudaStream_t s) {
+    const uint64_t positions = (uint64_t)n_steps + (visit_start ? 1 : 0);
+    // Below this bound a counter that starts at zero cannot wrap.
+    const bool checked = positions > 0 && n_walks > 0xffffffffull / positions;
+    const int lanes_w = tuning_walks_per_lane();
+    const bool agg = tuning_aggregate_visits();
+    const size_t n = g.n;
+    uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n, *sid = cursor + n + 1, *sst = sid + n_walks;
+    int rc = group_by_start(g, starts, n_walks, counts, cursor, sid, sst, status, scan_ws, scan_ws_bytes, s);
+    if (rc) return rc;
+    rc = with_edges(g, [&](auto el) {
+        launch_bouquet_any(el, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+                           visits, paths, status, lanes_w, s);
+        return BQ_OK;
+    });
+    BQ_CUDA(cudaGetLastError());
+    return rc;
 }
 
 }  // namespace
@@ -323,39 +301,31 @@ int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *st
                          uint32_t *status, void *scratch, size_t scratch_bytes, cudaStream_t s) {
     if (n_walks == 0) return BQ_OK;
     if (walk_batch_scratch_bytes(g.n, n_walks) > scratch_bytes) return fail(BQ_EINVAL, "scratch too small");
-    const uint64_t positions = (uint64_t)n_steps + (visit_start ? 1 : 0);
-    const bool checked = positions > 0 && n_walks > 0xffffffffull / positions;
-    const int lanes_w = tuning_walks_per_lane();
-    const bool agg = tuning_aggregate_visits();
     const size_t arrays = bouquet_arrays_bytes(g.n, n_walks);
-    if (g.compact())
-        return launch_bouquet_in(RecCompact{g.rec8}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked,
-                                 visits, paths, status, lanes_w, agg, (char *)scratch, scratch_bytes, arrays, s);
-    return launch_bouquet_in(RecWide{g.rec16}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked, visits,
-                             paths, status, lanes_w, agg, (char *)scratch, scratch_bytes, arrays, s);
+    char *base = (char *)scratch;
+    return bouquet_in(g, seed, starts, n_walks, n_steps, smp, visit_start, visits, paths, status, base, base + arrays,
+                      scratch_bytes - arrays, s);
 }
 
 int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
                       uint32_t n_steps, uint32_t mode, const Sampler &smp, bool visit_start, uint32_t *visits,
                       uint32_t *paths, uint32_t *status, cudaStream_t s) {
     if (n_walks == 0) return BQ_OK;
-    const uint64_t positions = (uint64_t)n_steps + (visit_start ? 1 : 0);
-    // Below this bound a counter that starts at zero cannot wrap.
-    const bool checked = positions > 0 && n_walks > 0xffffffffull / positions;
-    const int lanes_w = tuning_walks_per_lane();
-    const bool agg = tuning_aggregate_visits();
     if (mode == BQ_MODE_NAIVE) {
+        const uint64_t positions = (uint64_t)n_steps + (visit_start ? 1 : 0);
+        const bool checked = positions > 0 && n_walks > 0xffffffffull / positions;
         if (g.compact())
             return launch_naive(RecCompact{g.rec8}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked,
                                 visits, paths, status, s);
-        return launch_naive(RecWide{g.rec16}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked,
-                            visits, paths, status, s);
+        return launch_naive(RecWide{g.rec16}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked, visits,
+                            paths, status, s);
     }
-    if (g.compact())
-        return launch_bouquet(RecCompact{g.rec8}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked,
-                              visits, paths, status, lanes_w, agg, s);
-    return launch_bouquet(RecWide{g.rec16}, g, seed, starts, n_walks, n_steps, smp, visit_start, checked, visits,
-                          paths, status, lanes_w, agg, s);
+    char *buf = nullptr;
+    int rc = scratch_alloc((void **)&buf, bouquet_arrays_bytes(g.n, n_walks), s);
+    if (rc) return rc;
+    rc = bouquet_in(g, seed, starts, n_walks, n_steps, smp, visit_start, visits, paths, status, buf, nullptr, 0, s);
+    scratch_free(buf, s);
+    return rc;
 }
 
 }  // namespace bq

@@ -111,6 +111,70 @@ def test_tuning_never_changes_results(env):
         bq.set_tuning(**old)
 
 
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
+def test_every_graph_layout_bit_exact(env, layout):
+    bq, torch = env
+    g = gnp_connected(40, 0.15, 6)
+    uv = all_edges(g)
+    tau = (np.arange(uv.shape[0], dtype=np.uint32) % 9) + 1
+    nw = (np.arange(uv.shape[0], dtype=np.uint32) * 53) % 1500 + 1
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(layout=layout)
+        graph = bq.Graph.from_csr(g)
+        for sampler in (None, (1, 6, 32)):
+            counts, sc = bq.aesc_estimate_host(graph, 13, uv, tau, nw, sampler=sampler)
+            ocounts, osc = oracle.aesc_estimate(g, 13, uv, tau, nw, sampler=sampler)
+            assert np.array_equal(counts, ocounts) and same_bits(sc, osc), sampler
+        graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
+SCHEDULE = (2.0, 2, 64, 9.0, 32)  # tau_scale, tau_add, tau_max, n_scale, n_min (as the bench)
+
+
+def test_scheduled_plan_matches_oracle(env):
+    bq, torch = env
+    from workloads import chung_lu
+    for g in (er_with_path(1000, 5000, 1), chung_lu(20000, 10, 2.1, seed=5)):
+        graph = bq.Graph.from_csr(g)
+        uv = all_edges(g)
+        sched = bq.Schedule(SCHEDULE[0], SCHEDULE[1], SCHEDULE[2], SCHEDULE[3], SCHEDULE[4], 0)
+        tau, nw = bq.aesc_plan(graph, uv, 0.05, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+        otau, onw = oracle.plan_scheduled(g, uv, 0.05, *SCHEDULE)
+        assert np.array_equal(tau, otau) and np.array_equal(nw, onw)
+        tau2, nw2 = bq.aesc_plan(graph, None, 0.05, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+        assert np.array_equal(tau2, tau) and np.array_equal(nw2, nw)
+        graph.close()
+
+
+def test_powerlaw_full_size_sampled(env):
+    """Chung-Lu n=4M, mean degree 10, exponent 2.1, largest component: all
+    edges estimated on the GPU with the scheduled plan at eps=0.05, in the
+    launch configuration the bench times; 300 sampled edges bit-exact
+    against the oracle (a result depends only on its own edge)."""
+    bq, torch = env
+    from workloads import cached, chung_lu
+    g = cached("chunglu4m_d10_g2.1_s3", lambda: chung_lu(4_000_000, 10, 2.1, seed=3))
+    graph = bq.Graph.from_csr(g)
+    sched = bq.Schedule(SCHEDULE[0], SCHEDULE[1], SCHEDULE[2], SCHEDULE[3], SCHEDULE[4], 0)
+    tau, nw = bq.aesc_plan(graph, None, 0.05, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+    counts, sc = bq.aesc_estimate(graph, 5, None, torch.from_numpy(tau.view(np.int32)).cuda(),
+                                  torch.from_numpy(nw.view(np.int32)).cuda())
+    bq.sync()
+    counts = counts.cpu().numpy().view(np.uint32).reshape(-1, 4)
+    sc = sc.cpu().numpy()
+    assert np.isfinite(sc).all()
+    rng = np.random.default_rng(11)
+    pick = np.sort(rng.choice(tau.size, 300, replace=False))
+    uv = all_edges(g)[pick]
+    ocounts, osc = oracle.aesc_estimate(g, 5, uv, tau[pick], nw[pick])
+    assert np.array_equal(counts[pick].ravel(), ocounts)
+    assert same_bits(sc[pick], osc)
+    graph.close()
+
+
 def test_errors_nan_and_status(env):
     bq, torch = env
     g = cycle(10)

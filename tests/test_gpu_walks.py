@@ -111,6 +111,35 @@ def test_tuning_never_changes_results(env):
         bq.set_tuning(**old)
 
 
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
+def test_every_graph_layout_bit_exact(env, layout):
+    """Plain or bit-packed neighbour ids with 8- or 16-byte vertex records,
+    8- or 16-byte edge records: five ways to read a step, one result."""
+    bq, torch = env
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(layout=layout)
+        for name in ("rmat12", "isolated", "cycle10"):
+            g = GRAPHS[name]
+            graph = bq.Graph.from_csr(g)
+            rng = np.random.default_rng(layout)
+            starts = rng.integers(0, g.n, 20011).astype(np.uint32)
+            st = dev_u32(torch, starts)
+            for sampler in (None, (1, 5, 32)):
+                want_v, want_p = oracle.walk_batch(g, 41, starts, 17, sampler=sampler,
+                                                   include_start=True, want_paths=True)
+                for mode in (bq.MODE_BOUQUET, bq.MODE_NAIVE):
+                    paths = torch.zeros((starts.size, 18), dtype=torch.int32, device="cuda")
+                    vis = bq.walk_batch(graph, 41, st, 17, mode=mode, sampler=sampler,
+                                        visit_start=True, paths=paths)
+                    bq.sync()
+                    assert np.array_equal(host_u32(vis), want_v), (name, sampler, mode)
+                    assert np.array_equal(host_u32(paths), want_p), (name, sampler, mode)
+            graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
 def test_host_io_matches_device(env):
     bq, torch = env
     g = GRAPHS["gnp60"]

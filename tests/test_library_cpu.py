@@ -61,7 +61,10 @@ def test_tuning_roundtrip_and_validation(lib):
     old = bq.get_tuning()
     try:
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
-        assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8}
+        assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
+                                   "layout": old["layout"]}
+        with pytest.raises(bq.BouquetError):
+            bq.set_tuning(layout=6)
         with pytest.raises(bq.BouquetError) as ei:
             bq.set_tuning(walk_lanes=3)
         assert ei.value.code == bq.EINVAL

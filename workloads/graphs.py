@@ -59,14 +59,17 @@ def csr_from_edges(n: int, u, v, name: str = "") -> Graph:
     u, v = u[keep], v[keep]
     lo = np.minimum(u, v)
     hi = np.maximum(u, v)
-    key = np.unique(lo * n + hi)
+    key = lo * n + hi
+    key.sort()
+    if key.size:
+        key = key[np.concatenate([[True], key[1:] != key[:-1]])]
     lo = key // n
     hi = key % n
-    src = np.concatenate([lo, hi])
-    dst = np.concatenate([hi, lo])
-    order = np.argsort(src * n + dst, kind="stable")
-    src = src[order]
-    dst = dst[order]
+    # both orientations; keys are distinct, so sorting them orders the CSR
+    both = np.concatenate([key, hi * n + lo])
+    both.sort()
+    src = both // n
+    dst = both - src * n
     counts = np.bincount(src, minlength=n) if n else np.zeros(0, np.int64)
     offsets = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=offsets[1:])
