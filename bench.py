@@ -80,7 +80,7 @@ def measured_peaks():
 def walk_kernel_traffic(kernel_file: str):
     """dram bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    prof = os.path.join(ROOT, "profiles", "walk_bouquet_kernel_rmat20.md")
+    prof = os.path.join(ROOT, "profiles", "walk_hub_kernel_rmat20.md")
     src = os.path.join(ROOT, "paper_2410_14056_gb300", "csrc", kernel_file)
     if not os.path.exists(prof):
         return None
@@ -401,7 +401,8 @@ def run_ours(args):
     traffic = walk_kernel_traffic("walks.cu")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "walk_bouquet_kernel", "kernel_ms": walk_ms,
+                "kernel": "walk_hub_kernel" if bq.get_tuning()["hub_bits"] else "walk_bouquet_kernel",
+                "kernel_ms": walk_ms,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s"}

@@ -269,6 +269,16 @@ typedef struct bq_tuning {
                                      bits, several per 16-byte chunk, + 8-byte
                                      vertex records (plain CSR when packing
                                      saves nothing) */
+    uint32_t hub_bits;         /* graphs created from now on get a table of
+                                  2^hub_bits hub slots (0 = none; 10..13,
+                                  default 13): each slot holds the highest-
+                                  degree vertex hashing to it.  The bouquet
+                                  walk-batch kernel keeps the table in shared
+                                  memory (16 bytes per slot) and serves those
+                                  vertices' records and visit counters from it:
+                                  the random walk visits a vertex in proportion
+                                  to its degree */
+    uint32_t reserved[3];
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

@@ -25,6 +25,7 @@ std::atomic<int> g_walks_per_lane{4};
 std::atomic<int> g_aggregate{0};
 std::atomic<int> g_aesc_walks_per_lane{4};
 std::atomic<int> g_edge_records{1};
+std::atomic<int> g_hub_bits{13};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -139,6 +140,7 @@ int tuning_walks_per_lane() { return g_walks_per_lane.load(); }
 bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
 int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
 int tuning_layout() { return g_edge_records.load(); }
+int tuning_hub_bits() { return g_hub_bits.load(); }
 
 namespace {
 
@@ -315,6 +317,7 @@ int bq_graph_destroy(bq_graph *g) {
     cudaFree(g->d_edge8);
     cudaFree(g->d_edge16);
     cudaFree(g->d_pk);
+    cudaFree(g->d_hub_tag);
     delete g;
     return BQ_OK;
 }
@@ -629,6 +632,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->aggregate_visits = (uint32_t)g_aggregate.load();
     out->aesc_lanes = (uint32_t)g_aesc_walks_per_lane.load();
     out->layout = (uint32_t)g_edge_records.load();
+    out->hub_bits = (uint32_t)g_hub_bits.load();
     return BQ_OK;
 }
 
@@ -640,10 +644,13 @@ int bq_set_tuning(const bq_tuning *in) {
     if (a != 2 && a != 4 && a != 8) return fail(BQ_EINVAL, "aesc_lanes must be 2, 4 or 8");
     if (in->aggregate_visits > 1) return fail(BQ_EINVAL, "aggregate_visits must be 0 or 1");
     if (in->layout > 5) return fail(BQ_EINVAL, "layout must be 0 to 5");
+    if (in->hub_bits != 0 && (in->hub_bits < 10 || in->hub_bits > 13))
+        return fail(BQ_EINVAL, "hub_bits must be 0 or 10..13");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
     g_edge_records.store((int)in->layout);
+    g_hub_bits.store((int)in->hub_bits);
     return BQ_OK;
 }
 

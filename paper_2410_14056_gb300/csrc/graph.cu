@@ -301,6 +301,25 @@ __global__ void build_packed_ids_kernel(const uint32_t *__restrict__ nbrs, uint6
     }
 }
 
+// Hub table: every vertex with a neighbour bids for slot hash(v); the highest
+// degree wins (ties: the smaller id).  key = degree << 32 | (2^32 - 1 - v).
+__global__ void hub_select_kernel(const int64_t *__restrict__ off, uint32_t n, uint32_t hub_bits,
+                                  unsigned long long *__restrict__ best) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t deg = (uint64_t)(off[v + 1] - off[v]);
+        if (deg == 0) continue;
+        const uint32_t slot = ((uint32_t)v * kHubHash) >> (32 - hub_bits);
+        atomicMax(best + slot, (unsigned long long)((deg << 32) | (0xffffffffull - v)));
+    }
+}
+
+__global__ void hub_finish_kernel(const unsigned long long *__restrict__ best, uint32_t slots,
+                                  uint32_t *__restrict__ tag) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += gridDim.x * blockDim.x)
+        tag[i] = best[i] ? 0xffffffffu - (uint32_t)best[i] : kNoHub;
+}
+
 uint32_t bits_for(uint64_t max_value) {
     uint32_t b = 1;
     while (b < 64 && (max_value >> b) != 0) ++b;
@@ -517,6 +536,26 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
             }
         }
         g->layout = g->d_pk ? 5 : (g->d_edge8 ? 2 : (g->d_edge16 ? 3 : (compact ? 0 : 4)));
+        const int hub_bits = tuning_hub_bits();
+        if (hub_bits > 0 && compact && n > 0) {
+            const uint32_t slots = 1u << hub_bits;
+            unsigned long long *best = nullptr;
+            e = cudaMalloc(&best, sizeof(unsigned long long) * slots);
+            if (e == cudaSuccess) e = cudaMalloc(&g->d_hub_tag, sizeof(uint32_t) * slots);
+            if (e == cudaSuccess) e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * slots, s);
+            if (e == cudaSuccess) {
+                hub_select_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, n, (uint32_t)hub_bits, best);
+                hub_finish_kernel<<<grid_for(slots, 256), 256, 0, s>>>(best, slots, g->d_hub_tag);
+                e = cudaStreamSynchronize(s);
+            }
+            cudaFree(best);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "hub table");
+                goto done;
+            }
+            g->hub_bits = (uint32_t)hub_bits;
+            g->device_bytes += sizeof(uint32_t) * slots;
+        }
     }
 done:
     cudaFree(res);

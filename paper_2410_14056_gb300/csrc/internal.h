@@ -21,6 +21,9 @@ enum StatusBits : uint32_t {
     kStatusTimeout = 1u << 4,    // a bounded wait gave up
 };
 
+constexpr uint32_t kNoHub = 0xffffffffu;
+constexpr uint32_t kHubHash = 0x9E3779B1u;
+
 // Stream reserved for walk-batch walks; AESC walks use stream 2 * edge + side.
 constexpr uint64_t kBatchStream = 0x4000000000000000ull;
 // Top bit of the stream selects the shared key of the coupled sampler.
@@ -57,6 +60,10 @@ struct DeviceGraph {
     // never straddles a chunk and one aligned vector load reads it.
     const uint4 *pk;
     uint32_t pk_bits, pk_q, pk_mask;
+    // Hub table: slot (v * 0x9E3779B1) >> (32 - hub_bits) holds the
+    // highest-degree vertex hashing there (kNoHub when empty); null if none.
+    const uint32_t *hub_tag;
+    uint32_t hub_bits;
     bool compact() const { return rec8 != nullptr; }
 };
 
@@ -79,6 +86,8 @@ struct bq_graph {
     uint4 *d_pk = nullptr;
     uint32_t pk_bits = 0, pk_q = 0, pk_mask = 0;
     int layout = 0;  // layout chosen at creation (bq_tuning.layout values)
+    uint32_t *d_hub_tag = nullptr;
+    uint32_t hub_bits = 0;
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
     uint64_t device_bytes = 0;
@@ -109,6 +118,8 @@ struct bq_graph {
         v.pk_bits = pk_bits;
         v.pk_q = pk_q;
         v.pk_mask = pk_mask;
+        v.hub_tag = d_hub_tag;
+        v.hub_bits = hub_bits;
         return v;
     }
 };
@@ -137,7 +148,8 @@ void scratch_free(void *p, cudaStream_t s);
 int tuning_walks_per_lane();
 bool tuning_aggregate_visits();
 int tuning_aesc_walks_per_lane();
-int tuning_layout();  // graph layout built at creation (bq_tuning.layout)
+int tuning_layout();    // graph layout built at creation (bq_tuning.layout)
+int tuning_hub_bits();  // hub table size built at creation (bq_tuning.hub_bits)
 
 // Profiling (api.cu): event brackets around kernel groups while enabled, and
 // a count of every kernel launch.

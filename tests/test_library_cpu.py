@@ -62,9 +62,14 @@ def test_tuning_roundtrip_and_validation(lib):
     try:
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
-                                   "layout": old["layout"]}
+                                   "layout": old["layout"], "hub_bits": old["hub_bits"]}
         with pytest.raises(bq.BouquetError):
             bq.set_tuning(layout=6)
+        for bad in (1, 9, 14):
+            with pytest.raises(bq.BouquetError):
+                bq.set_tuning(hub_bits=bad)
+        bq.set_tuning(hub_bits=0)
+        assert bq.get_tuning()["hub_bits"] == 0
         with pytest.raises(bq.BouquetError) as ei:
             bq.set_tuning(walk_lanes=3)
         assert ei.value.code == bq.EINVAL
