@@ -278,7 +278,10 @@ typedef struct bq_tuning {
                                   vertices' records and visit counters from it:
                                   the random walk visits a vertex in proportion
                                   to its degree */
-    uint32_t reserved[3];
+    uint32_t l2_hints;         /* 1: the hub walk kernel reads the graph arrays
+                                  with an L2 evict-last policy and the grouped
+                                  walk list with evict-first (0 = plain loads) */
+    uint32_t reserved[2];
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

@@ -59,7 +59,8 @@ class Schedule(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("walk_lanes", ctypes.c_uint32), ("aggregate_visits", ctypes.c_uint32),
                 ("aesc_lanes", ctypes.c_uint32), ("layout", ctypes.c_uint32),
-                ("hub_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("hub_bits", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -346,14 +347,15 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(load_library().bq_get_tuning(ctypes.byref(t)))
     return {"walk_lanes": t.walk_lanes, "aggregate_visits": t.aggregate_visits,
-            "aesc_lanes": t.aesc_lanes, "layout": t.layout, "hub_bits": t.hub_bits}
+            "aesc_lanes": t.aesc_lanes, "layout": t.layout, "hub_bits": t.hub_bits,
+            "l2_hints": t.l2_hints}
 
 
 def set_tuning(**kw):
     cur = get_tuning()
     cur.update(kw)
     t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]),
-               int(cur["layout"]), int(cur["hub_bits"]))
+               int(cur["layout"]), int(cur["hub_bits"]), int(cur["l2_hints"]))
     _check(load_library().bq_set_tuning(ctypes.byref(t)))
 
 

@@ -26,6 +26,7 @@ std::atomic<int> g_aggregate{0};
 std::atomic<int> g_aesc_walks_per_lane{4};
 std::atomic<int> g_edge_records{1};
 std::atomic<int> g_hub_bits{13};
+std::atomic<int> g_l2_hints{0};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -141,6 +142,7 @@ bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
 int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
 int tuning_layout() { return g_edge_records.load(); }
 int tuning_hub_bits() { return g_hub_bits.load(); }
+bool tuning_l2_hints() { return g_l2_hints.load() != 0; }
 
 namespace {
 
@@ -633,6 +635,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->aesc_lanes = (uint32_t)g_aesc_walks_per_lane.load();
     out->layout = (uint32_t)g_edge_records.load();
     out->hub_bits = (uint32_t)g_hub_bits.load();
+    out->l2_hints = (uint32_t)g_l2_hints.load();
     return BQ_OK;
 }
 
@@ -646,11 +649,13 @@ int bq_set_tuning(const bq_tuning *in) {
     if (in->layout > 5) return fail(BQ_EINVAL, "layout must be 0 to 5");
     if (in->hub_bits != 0 && (in->hub_bits < 10 || in->hub_bits > 13))
         return fail(BQ_EINVAL, "hub_bits must be 0 or 10..13");
+    if (in->l2_hints > 1) return fail(BQ_EINVAL, "l2_hints must be 0 or 1");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
     g_edge_records.store((int)in->layout);
     g_hub_bits.store((int)in->hub_bits);
+    g_l2_hints.store((int)in->l2_hints);
     return BQ_OK;
 }
 

@@ -22,6 +22,47 @@
 
 namespace bq {
 
+// L2 cache policies (createpolicy) and read-only loads that carry them.  The
+// graph arrays a step reads at random are re-read all through a launch; the
+// grouped walk ids and starts are read once.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_normal() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint4 ldg_pol(const uint4 *a, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(a), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ uint2 ldg_pol(const uint2 *a, uint64_t pol) {
+    uint2 r;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(a), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ldg_pol(const uint32_t *a, uint64_t pol) {
+    uint32_t r;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(a), "l"(pol));
+    return r;
+}
+
 __device__ __forceinline__ void start_record(const int64_t *__restrict__ offsets, uint32_t v, uint64_t &off,
                                              uint32_t &deg) {
     const int64_t lo = __ldg(offsets + v);
@@ -38,18 +79,29 @@ struct EdgesPackedIds {
     const uint4 *pk;
     const uint2 *rec;
     uint32_t bits, q, mask;
-    __device__ __forceinline__ uint32_t id(uint64_t j) const {
-        const uint32_t jj = (uint32_t)j;  // built only when nnz < 2^32
-        const uint32_t c = jj / q;
-        const uint32_t bit = (jj - c * q) * bits;
-        const uint4 w = __ldg(pk + c);
+    __device__ __forceinline__ uint32_t unpack(const uint4 &w, uint32_t bit) const {
         const uint32_t wi = bit >> 5, sh = bit & 31;
         const uint32_t lo = wi == 0 ? w.x : (wi == 1 ? w.y : (wi == 2 ? w.z : w.w));
         const uint32_t hi = wi == 0 ? w.y : (wi == 1 ? w.z : w.w);
         return __funnelshift_r(lo, hi, sh) & mask;
     }
+    __device__ __forceinline__ uint32_t id(uint64_t j) const {
+        const uint32_t jj = (uint32_t)j;  // built only when nnz < 2^32
+        const uint32_t c = jj / q;
+        return unpack(__ldg(pk + c), (jj - c * q) * bits);
+    }
+    __device__ __forceinline__ uint32_t id(uint64_t j, uint64_t pol) const {
+        const uint32_t jj = (uint32_t)j;
+        const uint32_t c = jj / q;
+        return unpack(ldg_pol(pk + c, pol), (jj - c * q) * bits);
+    }
     __device__ __forceinline__ void rec_of(uint32_t v, uint64_t &off, uint32_t &deg) const {
         const uint2 r = __ldg(rec + v);
+        off = r.x;
+        deg = r.y;
+    }
+    __device__ __forceinline__ void rec_of(uint32_t v, uint64_t &off, uint32_t &deg, uint64_t pol) const {
+        const uint2 r = ldg_pol(rec + v, pol);
         off = r.x;
         deg = r.y;
     }
@@ -64,8 +116,14 @@ struct EdgesCsr8 {
     const uint32_t *nbrs;
     const uint2 *rec;
     __device__ __forceinline__ uint32_t id(uint64_t j) const { return __ldg(nbrs + j); }
+    __device__ __forceinline__ uint32_t id(uint64_t j, uint64_t pol) const { return ldg_pol(nbrs + j, pol); }
     __device__ __forceinline__ void rec_of(uint32_t v, uint64_t &off, uint32_t &deg) const {
         const uint2 r = __ldg(rec + v);
+        off = r.x;
+        deg = r.y;
+    }
+    __device__ __forceinline__ void rec_of(uint32_t v, uint64_t &off, uint32_t &deg, uint64_t pol) const {
+        const uint2 r = ldg_pol(rec + v, pol);
         off = r.x;
         deg = r.y;
     }
@@ -80,8 +138,14 @@ struct EdgesCsr16 {
     const uint32_t *nbrs;
     const uint4 *rec;
     __device__ __forceinline__ uint32_t id(uint64_t j) const { return __ldg(nbrs + j); }
+    __device__ __forceinline__ uint32_t id(uint64_t j, uint64_t pol) const { return ldg_pol(nbrs + j, pol); }
     __device__ __forceinline__ void rec_of(uint32_t v, uint64_t &off, uint32_t &deg) const {
         const uint4 r = __ldg(rec + v);
+        off = ((uint64_t)r.y << 32) | r.x;
+        deg = r.z;
+    }
+    __device__ __forceinline__ void rec_of(uint32_t v, uint64_t &off, uint32_t &deg, uint64_t pol) const {
+        const uint4 r = ldg_pol(rec + v, pol);
         off = ((uint64_t)r.y << 32) | r.x;
         deg = r.z;
     }

@@ -206,8 +206,10 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
                 const uint32_t *__restrict__ sorted_id, const uint32_t *__restrict__ sorted_start,
                 const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps, uint64_t seed, Sampler smp,
                 bool visit_start, uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
-                unsigned long long *__restrict__ next_chunk) {
+                unsigned long long *__restrict__ next_chunk, bool l2_hints) {
     extern __shared__ __align__(16) unsigned char hub_smem[];
+    const uint64_t pol_keep = l2_hints ? l2_policy_keep() : 0ull;
+    const uint64_t pol_stream = l2_hints ? l2_policy_stream() : 0ull;
     const uint32_t slots = 1u << hub_bits;
     const uint32_t shift = 32 - hub_bits;
     uint2 *s_rec = reinterpret_cast<uint2 *>(hub_smem);
@@ -246,8 +248,12 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
         for (int j = 0; j < W; ++j) {
             const uint64_t p = base + (uint64_t)j * 32 + lane;
             act[j] = p < n_valid;
-            id[j] = act[j] ? sorted_id[p] : 0u;
-            cur[j] = act[j] ? sorted_start[p] : 0u;
+            id[j] = 0u;
+            cur[j] = 0u;
+            if (act[j]) {
+                id[j] = l2_hints ? ldg_pol(sorted_id + p, pol_stream) : sorted_id[p];
+                cur[j] = l2_hints ? ldg_pol(sorted_start + p, pol_stream) : sorted_start[p];
+            }
             off[j] = 0;
             deg[j] = 0;
             if (act[j]) start_record(offsets, cur[j], off[j], deg[j]);
@@ -270,7 +276,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
                 moved[j] = deg[j] != 0;
                 if (moved[j]) {
                     const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
-                    if constexpr (EL::kSplit) cur[j] = el.id(off[j] + k);
+                    if constexpr (EL::kSplit) cur[j] = l2_hints ? el.id(off[j] + k, pol_keep) : el.id(off[j] + k);
                     else el.next(off[j] + k, cur[j], off[j], deg[j]);
                 }
             }
@@ -290,7 +296,10 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
                 } else {
                     atomicAdd(visits + cur[j], 1u);
                     if constexpr (EL::kSplit) {
-                        if (moved[j]) el.rec_of(cur[j], off[j], deg[j]);
+                        if (moved[j]) {
+                            if (l2_hints) el.rec_of(cur[j], off[j], deg[j], pol_keep);
+                            else el.rec_of(cur[j], off[j], deg[j]);
+                        }
                     }
                 }
                 if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1) + l] = cur[j];
@@ -385,7 +394,8 @@ bool launch_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32
     ProfScope prof(kProfWalk, s);
     count_launches(1);
     kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.offsets, g.hub_tag, g.hub_bits, sid, sst, n_valid, n_steps,
-                                                   seed, smp, visit_start, visits, paths, next_chunk);
+                                                   seed, smp, visit_start, visits, paths, next_chunk,
+                                                   tuning_l2_hints());
     return true;
 }
 

@@ -103,7 +103,7 @@ def test_tuning_never_changes_results(env):
     try:
         for lanes in (1, 2, 4, 8):
             for agg in (0, 1):
-                bq.set_tuning(walk_lanes=lanes, aggregate_visits=agg)
+                bq.set_tuning(walk_lanes=lanes, aggregate_visits=agg, l2_hints=agg)
                 vis = bq.walk_batch(graph, 3, st, 12)
                 bq.sync()
                 assert np.array_equal(host_u32(vis), want), (lanes, agg)

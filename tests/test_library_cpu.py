@@ -62,7 +62,8 @@ def test_tuning_roundtrip_and_validation(lib):
     try:
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
-                                   "layout": old["layout"], "hub_bits": old["hub_bits"]}
+                                   "layout": old["layout"], "hub_bits": old["hub_bits"],
+                                   "l2_hints": old["l2_hints"]}
         with pytest.raises(bq.BouquetError):
             bq.set_tuning(layout=6)
         for bad in (1, 9, 14):
