@@ -239,6 +239,51 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
                      const bq_sampler *sampler, uint32_t flags, uint32_t *counts_dev,
                      double *sc_dev, void *stream);
 
+/* ---------------------------------------------------------- AESC batches */
+/*
+ * Many AESC estimates (on one or many graphs, of uneven sizes) run as one
+ * batch: one persistent counting launch pulls bouquet tasks from all queries
+ * at once (the walk loop of Alg. 1, as bq_aesc_estimate), so small queries do
+ * not leave the GPU idle.  Each query's counters and estimates are
+ * bit-identical to what bq_aesc_estimate returns for it alone.
+ */
+typedef struct bq_aesc_query {
+    const bq_graph *graph;        /* compact graph (nnz < 2^32) */
+    uint64_t seed;
+    const uint32_t *edges_uv_dev; /* 2k vertex pairs, or NULL = all m edges (k = m) */
+    uint64_t k;
+    const uint32_t *tau_dev;      /* k */
+    const uint32_t *nwalks_dev;   /* k */
+    uint32_t *counts_dev;         /* 4k, overwritten */
+    double *sc_dev;               /* k, written */
+} bq_aesc_query;
+
+typedef struct bq_batch bq_batch;
+
+/*
+ * Prepare a batch: validates the queries (all graphs on the current device,
+ * compact), copies their descriptors to the device and allocates every
+ * buffer bq_batch_run needs (about 56 bytes per queried edge).  The device
+ * buffers named in the queries must stay valid while the batch is used; their
+ * contents may change between runs (new plans, new edge lists of the same
+ * size).  Synchronous.
+ */
+int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_sampler *sampler,
+                    bq_batch **out);
+
+/*
+ * Run the batch on `stream`: kernel launches only (no allocation, no host
+ * copy, no synchronisation), so the call can be captured into a CUDA graph
+ * and the graph replayed.  Errors (a pair that is not an edge, tau = 0,
+ * overflow) are reported by bq_sync as for bq_aesc_estimate.
+ */
+int bq_batch_run(bq_batch *batch, void *stream);
+
+/* Number of queried edges over all queries of the batch. */
+int bq_batch_size(const bq_batch *batch, uint64_t *edges);
+
+int bq_batch_destroy(bq_batch *batch);
+
 /* ---------------------------------------------------------------- tuning */
 /*
  * Process-wide performance knobs of the kernels (the choices an autotuner

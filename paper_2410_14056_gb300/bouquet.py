@@ -81,12 +81,20 @@ class Profile(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64)]
 
 
+class AescQuery(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("edges_uv_dev", ctypes.c_void_p), ("k", ctypes.c_uint64),
+                ("tau_dev", ctypes.c_void_p), ("nwalks_dev", ctypes.c_void_p),
+                ("counts_dev", ctypes.c_void_p), ("sc_dev", ctypes.c_void_p)]
+
+
 # every symbol include/bouquet.h declares
 EXPORTS = (
     "bq_graph_create", "bq_graph_destroy", "bq_graph_info", "bq_graph_set_spectrum",
     "bq_walk_batch", "bq_aesc_plan", "bq_aesc_estimate", "bq_sync", "bq_strerror",
     "bq_last_error", "bq_version", "bq_get_tuning", "bq_set_tuning", "bq_profile_enable",
-    "bq_profile_read", "bq_walk_batch_noalloc",
+    "bq_profile_read", "bq_walk_batch_noalloc", "bq_batch_create", "bq_batch_run",
+    "bq_batch_size", "bq_batch_destroy",
 )
 
 _lock = threading.Lock()
@@ -124,6 +132,10 @@ def load_library(path: str | None = None):
         L.bq_get_tuning.argtypes = [c.POINTER(Tuning)]
         L.bq_set_tuning.argtypes = [c.POINTER(Tuning)]
         L.bq_walk_batch_noalloc.argtypes = [vp, u64, vp, u64, u32, c.POINTER(Sampler), u32, vp, vp, vp]
+        L.bq_batch_create.argtypes = [c.POINTER(AescQuery), u32, c.POINTER(Sampler), c.POINTER(vp)]
+        L.bq_batch_run.argtypes = [vp, vp]
+        L.bq_batch_size.argtypes = [vp, c.POINTER(u64)]
+        L.bq_batch_destroy.argtypes = [vp]
         L.bq_profile_enable.argtypes = [i32]
         L.bq_profile_read.argtypes = [c.POINTER(Profile)]
         for name in EXPORTS:
@@ -336,6 +348,59 @@ def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.n
                               _sampler(sampler), HOST_IO, _hptr(counts, "counts", np.uint32),
                               _hptr(sc, "sc", np.float64), _stream_handle(stream)))
     return counts, sc
+
+
+class Batch:
+    """Several AESC estimates run by one persistent counting launch.
+
+    `queries` is a list of dicts with keys graph, seed, tau, nwalks (device
+    uint32 tensors) and optionally uv (device pairs; None = all edges),
+    counts, sc (outputs, allocated when absent).  run() only launches
+    kernels, so it may be captured in a CUDA graph."""
+
+    def __init__(self, queries, sampler=None):
+        import torch
+        L = load_library()
+        arr = (AescQuery * len(queries))()
+        self._keep = []
+        self.outputs = []
+        for i, q in enumerate(queries):
+            tau, nw = q["tau"], q["nwalks"]
+            k = tau.numel()
+            counts = q.get("counts")
+            sc = q.get("sc")
+            if counts is None:
+                counts = torch.empty(4 * k, dtype=torch.int32, device=tau.device)
+            if sc is None:
+                sc = torch.empty(k, dtype=torch.float64, device=tau.device)
+            uv = q.get("uv")
+            arr[i] = AescQuery(q["graph"].handle, int(q["seed"]) & (2**64 - 1),
+                               _dptr(uv, "edges") if uv is not None else None, k,
+                               _dptr(tau, "tau"), _dptr(nw, "nwalks"), _dptr(counts, "counts"),
+                               _dptr(sc, "sc", 8))
+            self._keep.append((q["graph"], uv, tau, nw, counts, sc))
+            self.outputs.append((counts, sc))
+        self._h = ctypes.c_void_p()
+        _check(L.bq_batch_create(arr, len(queries), _sampler(sampler), ctypes.byref(self._h)))
+
+    def run(self, stream=None):
+        _check(load_library().bq_batch_run(self._h, _stream_handle(stream)))
+
+    def size(self) -> int:
+        e = ctypes.c_uint64()
+        _check(load_library().bq_batch_size(self._h, ctypes.byref(e)))
+        return e.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().bq_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sync(stream=None):

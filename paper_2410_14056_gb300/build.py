@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
-UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu"]
+UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu", "batch.cu"]
 HEADERS = ["internal.h", "hash.cuh", "edges.cuh"]
 
 

@@ -345,6 +345,12 @@ int scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, cudaStream_t s) {
 
 size_t scan_u32_ws_bytes(uint64_t n) { return scan_ws_bytes_impl<uint32_t>(n); }
 
+size_t scan_u32_to_u64_ws_bytes(uint64_t n) { return scan_ws_bytes_impl<uint64_t>(n); }
+
+int scan_u32_to_u64_ws(const uint32_t *in, uint64_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
+    return scan_ws_impl<uint32_t, uint64_t>(in, out, n, (char *)ws, ws_bytes, s);
+}
+
 int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
     return scan_ws_impl<uint32_t, uint32_t>(in, out, n, (char *)ws, ws_bytes, s);
 }

@@ -189,6 +189,8 @@ int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *st
 // graph.cu: the scan with its tile sums in a caller workspace.
 size_t scan_u32_ws_bytes(uint64_t n);
 int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s);
+size_t scan_u32_to_u64_ws_bytes(uint64_t n);
+int scan_u32_to_u64_ws(const uint32_t *in, uint64_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s);
 // api.cu: the device's status word if it was already allocated (never allocates).
 int existing_status_word(int device, uint32_t **out);
 int validate_sampler(const bq_sampler *in, Sampler &out);

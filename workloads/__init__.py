@@ -30,6 +30,7 @@ from .graphs import (  # noqa: F401
     uniform_starts,
     cached,
     rmat20,
+    batched_mix,
     all_edges,
     edges_of,
 )

@@ -309,6 +309,35 @@ def rmat20() -> Graph:
     return cached("rmat20_ef16_s20", lambda: rmat(20, 16, 0.57, 0.19, 0.19, seed=20))
 
 
+def batched_mix(count: int = 256, seed: int = 4, n_min: float = 1e3, n_max: float = 1e6):
+    """The batched-AESC workload: `count` graphs with n log-uniform in
+    [n_min, n_max] and mean degree uniform in [4, 16]; a third Erdos-Renyi
+    (plus a spanning path), a third R-MAT (a, b, c = 0.57, 0.19, 0.19; scale
+    round(log2 n), edge factor d/2; largest component), a third
+    sqrt(n) x sqrt(n) grids with 10% of edges deleted (largest component).
+    Returns [(graph, eps)] with eps drawn from {0.05, 0.1, 0.2}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        d = float(rng.uniform(4.0, 16.0))
+        eps = float(rng.choice([0.05, 0.1, 0.2]))
+        kind = i % 3
+        s = int(rng.integers(0, 2**31))
+        key = f"mix{seed}_{i}_{kind}_{n}_{s}"
+        if kind == 0:
+            build = (lambda n=n, d=d, s=s: er_with_path(n, max(1, int(round(n * d / 2))), s))
+        elif kind == 1:
+            scale = max(4, int(round(np.log2(n))))
+            build = (lambda scale=scale, d=d, s=s:
+                     largest_component(rmat(scale, max(1, int(round(d / 2))), seed=s)))
+        else:
+            side = max(4, int(round(np.sqrt(n))))
+            build = (lambda side=side, s=s: grid_deleted(side, side, 0.1, s))
+        out.append((cached(key, build), eps))
+    return out
+
+
 def uniform_starts(g: Graph, n_walks: int, seed: int) -> np.ndarray:
     """uint32[n_walks] start vertices drawn uniformly over the vertices that
     have at least one neighbour (an isolated vertex has no walk to take)."""
