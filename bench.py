@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["walks", "batched", "serving"], default="walks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aesc", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -383,6 +384,10 @@ def run_ours(args):
             total_ms = float(t.item())
         return total_ms, prof
 
+    autotune = None
+    if args.walk_lanes is None:
+        best_w, w_ms = bq.autotune_walks(graph, seed, st, N_STEPS, visits)
+        autotune = {"walk_lanes": best_w, "ms_per_candidate_1_2_4": w_ms}
     with ClockSampler(local) as clocks:
         total_ms, prof = timed(bq.MODE_BOUQUET, args.steps, args.warmup)
     ms_per_step = total_ms / args.steps
@@ -448,6 +453,7 @@ def run_ours(args):
                        "n_walks_per_gpu": N_WALKS, "n_steps": N_STEPS,
                        "starts": "uniform over non-isolated vertices (seeded)",
                        "mode": "BOUQUET, independent sampler", "tuning": bq.get_tuning(),
+                       "autotune": autotune,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (each GPU its own batch)"},
             "roofline": roofline,
@@ -469,10 +475,290 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Batched AESC (256 graphs, one persistent launch captured in a CUDA
+    graph): all edges of every graph at its own eps, scheduled plan."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_14056_gb300 as bq
+    from workloads import batched_mix
+
+    mix = batched_mix()
+    sched = bq.Schedule(POWERLAW_SCHEDULE["tau_scale"], POWERLAW_SCHEDULE["tau_add"],
+                        POWERLAW_SCHEDULE["tau_max"], POWERLAW_SCHEDULE["n_scale"],
+                        POWERLAW_SCHEDULE["n_min"], 0)
+    queries, host_plans = [], []
+    steps_total = 0.0
+    for i, (g, eps) in enumerate(mix):
+        graph = bq.Graph.from_csr(g)
+        tau, nw = bq.aesc_plan(graph, None, eps, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+        steps_total += float(np.sum(2.0 * tau.astype(np.float64) * nw))
+        queries.append({"graph": graph, "seed": 1000 + i, "uv": None,
+                        "tau": torch.from_numpy(tau.view(np.int32)).cuda(),
+                        "nwalks": torch.from_numpy(nw.view(np.int32)).cuda()})
+        host_plans.append((tau, nw))
+    edges = sum(int(q["tau"].numel()) for q in queries)
+    best, tune_ms = bq.autotune_aesc(queries[::8])
+    batch = bq.Batch(queries)
+
+    # sequential baseline: one bq_aesc_estimate per graph on one stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for q, (counts, sc) in zip(queries, batch.outputs):
+        bq.aesc_estimate(q["graph"], q["seed"], None, q["tau"], q["nwalks"], counts=counts, sc=sc)
+    e1.record()
+    e1.synchronize()
+    bq.sync()
+    seq_ms = e0.elapsed_time(e1)
+
+    # kernel time of the counting launch (uncaptured run with event brackets)
+    bq.profile_read()
+    bq.profile_enable(True)
+    batch.run()
+    bq.sync()
+    prof = bq.profile_read()
+    bq.profile_enable(False)
+    kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.run()
+    torch.cuda.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=stream):
+        batch.run()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        cg.replay()
+    torch.cuda.synchronize()
+    lat = []
+    with ClockSampler(0) as clocks:
+        for k in range(args.steps):
+            flush.fill_(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            cg.replay()
+            b.record()
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+    bq.sync()
+    ms = sum(lat) / len(lat)
+
+    # end to end: plans in from pinned host memory, estimates out, per step
+    pinned = [(torch.from_numpy(t.view(np.int32)).pin_memory(), torch.from_numpy(n.view(np.int32)).pin_memory())
+              for t, n in host_plans]
+    sc_host = [torch.empty(s.numel(), dtype=torch.float64).pin_memory() for _, s in batch.outputs]
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        for q, (ht, hn) in zip(queries, pinned):
+            q["tau"].copy_(ht, non_blocking=True)
+            q["nwalks"].copy_(hn, non_blocking=True)
+        cg.replay()
+        for (_, s), hs in zip(batch.outputs, sc_host):
+            hs.copy_(s, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+
+    peak, peak_kind = measured_peaks()
+    achieved = steps_total * BYTES_PER_STEP / (kern_ms / 1e3) / 1e9
+    n_total = sum(g.n for g, _ in mix)
+    line = {
+        "metric": METRIC, "value": edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batched_mix256_aesc", "graphs": len(mix), "vertices": n_total,
+                   "edges": edges, "walk_steps_per_step": steps_total,
+                   "eps": "per graph from {0.05, 0.1, 0.2}", "plan": "scheduled",
+                   "schedule": POWERLAW_SCHEDULE, "launch": "one persistent batch, CUDA-graph replay",
+                   "autotuned_aesc_lanes": best, "autotune_ms": tune_ms,
+                   "l2": "flushed between timed steps (256 MiB write, untimed)"},
+        "walk_steps_per_s": steps_total / (ms / 1e3),
+        "p50_ms": statistics.median(lat), "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "sequential_one_call_per_graph_ms": seq_ms, "batching_speedup": seq_ms / ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "batch_count_kernel",
+                     "kernel_ms": kern_ms, "peak_source": peak_kind},
+        "e2e": {"value": edges / e2e_s, "unit": "edges/s",
+                "h2d_bytes_per_step": int(8 * edges), "d2h_bytes_per_step": int(8 * edges),
+                "ms_per_step": e2e_s * 1e3},
+        "gpu_launches_per_step": prof["kernel_launches"], "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
+SERVE_LOADS = (0.5, 0.8, 1.0)
+SERVE_SATURATION_REQUESTS = 300
+SERVE_LOAD_SECONDS = 8.0
+SERVE_SUBMITTERS = 8
+
+
+def serving_graphs(bq, torch):
+    """Eight resident graphs: two R-MAT scale 24 (edge factor 16), two
+    4096 x 4096 grids with 5% of the edges deleted, four Chung-Lu graphs
+    (n = 1M, mean degree 10, exponent 2.3, largest component)."""
+    import numpy as np
+    from workloads import cached, chung_lu
+    from workloads import device as dev
+    dgs = [dev.rmat(24, 16, seed=301), dev.rmat(24, 16, seed=302),
+           dev.grid(4096, 4096, 0.05, 303), dev.grid(4096, 4096, 0.05, 304)]
+    for s in (305, 306, 307, 308):
+        h = cached(f"chunglu1m_d10_g2.3_s{s}", lambda s=s: chung_lu(1_000_000, 10.0, 2.3, s))
+        dgs.append(dev.DeviceGraph(h.name, h.n, torch.from_numpy(np.asarray(h.offsets, np.int64)).cuda(),
+                                   torch.from_numpy(np.asarray(h.nbrs, np.uint32).view(np.int32)).cuda()))
+    torch.cuda.synchronize()
+    graphs = [bq.Graph(d.n, d.offsets, d.nbrs, bq.DEVICE_PTRS | bq.BORROW) for d in dgs]
+    return dgs, graphs
+
+
+def serving_requests(dgs, count, rng, gen):
+    """count requests: graph uniform over the eight, subset size log-uniform
+    on [1, 1e5] with edges uniform over the graph's edges, eps ~ U[0.05, 0.2],
+    a distinct seed each."""
+    import numpy as np
+    from workloads import device as dev
+    out = []
+    for _ in range(count):
+        gi = int(rng.integers(len(dgs)))
+        k = int(min(100_000, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(100_001.0)))))))
+        uv = dev.sample_edges(dgs[gi], k, gen)
+        out.append((gi, uv, float(rng.uniform(0.05, 0.2)), int(rng.integers(0, 2**63))))
+    return out
+
+
+def serve_run(srv, reqs, arrivals):
+    """Submit reqs at the given offsets (s) from a pool of submitting threads
+    (each plans on its own thread), then wait for all.  Returns the
+    latencies (arrival -> results on the host, ms) and the wall time from
+    the first arrival to the last completion."""
+    import concurrent.futures as cf
+
+    def submit(req, t_sched):
+        t_start = time.perf_counter()
+        rid = srv.submit(*req)
+        return rid, (t_start - t_sched) * 1e3
+
+    futs = []
+    with cf.ThreadPoolExecutor(SERVE_SUBMITTERS) as pool:
+        t0 = time.perf_counter()
+        for req, at in zip(reqs, arrivals):
+            t_sched = t0 + at
+            while True:
+                dt = t_sched - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(dt if dt > 2e-3 else 0)
+            futs.append(pool.submit(submit, req, t_sched))
+        lat = []
+        for f in futs:
+            rid, queued_ms = f.result()
+            _, _, server_ms = srv.wait(rid, timeout=600)
+            lat.append(queued_ms + server_ms)
+        t_end = time.perf_counter()
+    return lat, t_end - t0
+
+
+def pct(v, q):
+    s = sorted(v)
+    return s[min(len(s) - 1, int(round(q * (len(s) - 1))))]
+
+
+def run_serving(args):
+    """Serving: resident graphs, requests with Poisson arrivals at fractions
+    of the measured saturation throughput; p50/p99 latency and edges/s."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_14056_gb300 as bq
+
+    dgs, graphs = serving_graphs(bq, torch)
+    resident = sum(g.info()["device_bytes"] for g in graphs)
+    rng = np.random.default_rng(909)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(910)
+    cfg = bq.ServerConfig(device_budget_bytes=4 << 30, max_inflight=256, max_pending=65536,
+                          tasks_per_iteration=1 << 16, **POWERLAW_SCHEDULE)
+    with bq.Server(graphs, cfg) as srv:
+        # warm-up: a few requests through the whole path
+        warm = serving_requests(dgs, max(3, args.warmup) * 4, rng, gen)
+        serve_run(srv, warm, [0.0] * len(warm))
+        # saturation: every request arrives at once
+        sat_reqs = serving_requests(dgs, SERVE_SATURATION_REQUESTS, rng, gen)
+        st0 = srv.stats()
+        bq.profile_read()
+        bq.profile_enable(True)
+        with ClockSampler(0) as clocks:
+            lat, wall = serve_run(srv, sat_reqs, [0.0] * len(sat_reqs))
+        prof = bq.profile_read()
+        bq.profile_enable(False)
+        st1 = srv.stats()
+        sat_edges = sum(r[1].shape[0] for r in sat_reqs)
+        sat_rps = len(sat_reqs) / wall
+        steps = st1["walk_steps"] - st0["walk_steps"]
+        kern_ms = prof["aesc_ms"]
+        saturation = {"requests": len(sat_reqs), "edges": sat_edges, "wall_s": wall,
+                      "requests_per_s": sat_rps, "edges_per_s": sat_edges / wall,
+                      "walk_steps_per_s": steps / wall, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+                      "iterations": st1["iterations"] - st0["iterations"]}
+        loads = []
+        for f in SERVE_LOADS:
+            rate = f * sat_rps
+            count = int(min(3000, max(60, rate * SERVE_LOAD_SECONDS)))
+            reqs = serving_requests(dgs, count, rng, gen)
+            gaps = rng.exponential(1.0 / rate, count)
+            arrivals = np.cumsum(gaps) - gaps[0]
+            lat, wall = serve_run(srv, reqs, arrivals.tolist())
+            edges = sum(r[1].shape[0] for r in reqs)
+            loads.append({"offered": f, "rate_rps": rate, "requests": count, "edges": edges,
+                          "edges_per_s": edges / wall, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+                          "max_ms": max(lat)})
+        final = srv.stats()
+    peak, peak_kind = measured_peaks()
+    achieved = steps * BYTES_PER_STEP / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": saturation["edges_per_s"], "unit": "edges/s", "n_gpus": 1,
+        "steps": len(sat_reqs), "warmup": len(warm), "ms_per_step": 1e3 * wall / len(sat_reqs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "serving_8graphs_poisson",
+                   "graphs": [{"name": d.name, "n": d.n, "m": d.m} for d in dgs],
+                   "resident_graph_bytes": resident, "subset": "log-uniform [1, 1e5] edges",
+                   "eps": "U[0.05, 0.2]", "plan": "scheduled", "schedule": POWERLAW_SCHEDULE,
+                   "server": {"device_budget_bytes": cfg.device_budget_bytes, "max_inflight": cfg.max_inflight,
+                              "tasks_per_iteration": cfg.tasks_per_iteration,
+                              "submitting_threads": SERVE_SUBMITTERS},
+                   "step": "one request", "l2": "inputs (resident graphs, 2 x 1.6 GB R-MAT) larger than L2"},
+        "saturation": saturation, "loads": loads,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "serve_count_kernel", "kernel_ms": kern_ms, "peak_source": peak_kind},
+        "e2e": {"value": saturation["edges_per_s"], "unit": "edges/s",
+                "h2d_bytes_per_step": int(8 * sat_edges / len(sat_reqs)),
+                "d2h_bytes_per_step": int(8 * sat_edges / len(sat_reqs)),
+                "note": "serving is end to end: pairs in from the host, estimates back to the host"},
+        "gpu_launches": prof["kernel_launches"], "clocks": clocks.summary(),
+        "server_stats": final,
+    }
+    print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

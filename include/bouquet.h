@@ -284,6 +284,78 @@ int bq_batch_size(const bq_batch *batch, uint64_t *edges);
 
 int bq_batch_destroy(bq_batch *batch);
 
+/* --------------------------------------------------------------- serving */
+/*
+ * A serving loop for SC queries on resident graphs (the paper has no
+ * counterpart: its AESC runs once over all edges).  A worker thread owns a
+ * stream; requests (edge subset, eps, seed) are planned on the host with the
+ * scheduled plan and admitted while the device memory they need and the
+ * number of requests on the GPU stay within the configured limits.  Every
+ * iteration launches one persistent counting kernel over a window of tasks
+ * (bouquets of walks) of every admitted request, so a request that arrives
+ * while others run joins the next iteration instead of waiting for them
+ * (continuous batching).  A request's counters are the sums over the same
+ * walks however its tasks are spread over iterations, so its result is
+ * bit-identical to bq_aesc_estimate with the same plan and seed.
+ */
+typedef struct bq_server bq_server;
+
+typedef struct bq_server_config {
+    uint64_t device_budget_bytes; /* device memory of admitted requests (0: 1 GiB);
+                                     about 92 bytes per queried edge */
+    uint32_t max_inflight;        /* requests on the GPU at once (0: 256) */
+    uint32_t max_pending;         /* queued requests before submit says BQ_EBUSY (0: 65536) */
+    uint64_t tasks_per_iteration; /* bouquet tasks per iteration launch, shared by the
+                                     admitted requests (0: 2^16) */
+    double tau_scale;             /* scheduled plan of every request (bq_schedule) */
+    uint32_t tau_add;
+    uint32_t tau_max;
+    double n_scale;
+    uint32_t n_min;
+    uint32_t reserved;
+} bq_server_config;
+
+typedef struct bq_server_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t edges_completed;
+    uint64_t iterations;
+    double walk_steps;    /* sum of 2 N tau over completed requests */
+    double p50_ms, p99_ms; /* latency submit -> result ready, completed requests */
+    double uptime_s;
+    uint32_t inflight, pending;
+} bq_server_stats;
+
+/* Start a server over graphs (all on the current device, nnz < 2^32; they
+ * must outlive the server).  cfg NULL = defaults with the schedule
+ * tau_scale 2, tau_add 2, tau_max 64, n_scale 9, n_min 32. */
+int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server_config *cfg, bq_server **out);
+
+/* Plan and queue a request: k vertex pairs (host, copied) of graph `graph`,
+ * absolute error eps, walks keyed by seed.  The scheduled plan is computed on
+ * the calling thread (host work of roughly 0.1 us per edge; several threads
+ * may submit at once), then the call returns with *request_id without
+ * waiting for the GPU.  Errors: BQ_ENOEDGE (a pair is not an edge),
+ * BQ_EOVERFLOW (2 N tau >= 2^32 for an edge), BQ_EBUSY (max_pending requests
+ * already queued), BQ_EINVAL (bad arguments, server stopping); no request is
+ * created then. */
+int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, uint64_t k, double eps,
+                     uint64_t seed, uint64_t *request_id);
+
+/* Wait up to timeout_s for a request, then copy its estimates (sc, k
+ * doubles) and, if not NULL, counters (4k, layout of bq_aesc_estimate) and
+ * latency (submit call -> results on the host, ms).  Returns the request's
+ * status: BQ_OK, BQ_ENOMEM (it alone needs more than the device budget, or
+ * the allocation failed), BQ_ECUDA; or BQ_ETIMEOUT (the request is still
+ * running or queued: wait again).  Each request is returned once; waiting
+ * for an unknown or already returned id is BQ_EINVAL. */
+int bq_server_wait(bq_server *srv, uint64_t request_id, double timeout_s, double *sc, uint32_t *counts,
+                   double *latency_ms);
+
+int bq_server_stats_get(bq_server *srv, bq_server_stats *out);
+
+/* Finish every queued request, then stop the worker and free the server. */
+int bq_server_destroy(bq_server *srv);
+
 /* ---------------------------------------------------------------- tuning */
 /*
  * Process-wide performance knobs of the kernels (the choices an autotuner
@@ -331,6 +403,21 @@ typedef struct bq_tuning {
 
 int bq_get_tuning(bq_tuning *out);
 int bq_set_tuning(const bq_tuning *in);
+
+/*
+ * Autotuners (the paper has no counterpart: it fixes B = 8 AVX2 lanes).  Each
+ * times the caller's own workload on `stream` with CUDA events, once per
+ * candidate after one warm-up run, keeps the fastest candidate in the
+ * process-wide tuning and returns it; ms (nullable, 3 floats) receives the
+ * time of each candidate in the order listed.  Results never depend on the
+ * choice.  Both synchronise the stream; the walk tuner overwrites visits_dev.
+ *   bq_autotune_walks: walk_lanes in {1, 2, 4} for bq_walk_batch BOUQUET.
+ *   bq_autotune_aesc:  aesc_lanes in {2, 4, 8} for a batch of these queries.
+ */
+int bq_autotune_walks(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, uint64_t n_walks,
+                      uint32_t n_steps, uint32_t *visits_dev, void *stream, uint32_t *best, float *ms);
+int bq_autotune_aesc(const bq_aesc_query *queries, uint32_t n_queries, const bq_sampler *sampler,
+                     void *stream, uint32_t *best, float *ms);
 
 /* ------------------------------------------------------------- profiling */
 /*

@@ -88,13 +88,32 @@ class AescQuery(ctypes.Structure):
                 ("counts_dev", ctypes.c_void_p), ("sc_dev", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_pending", ctypes.c_uint32), ("tasks_per_iteration", ctypes.c_uint64),
+                ("tau_scale", ctypes.c_double), ("tau_add", ctypes.c_uint32),
+                ("tau_max", ctypes.c_uint32), ("n_scale", ctypes.c_double),
+                ("n_min", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("edges_completed", ctypes.c_uint64),
+                ("iterations", ctypes.c_uint64), ("walk_steps", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("uptime_s", ctypes.c_double), ("inflight", ctypes.c_uint32),
+                ("pending", ctypes.c_uint32)]
+
+
 # every symbol include/bouquet.h declares
 EXPORTS = (
     "bq_graph_create", "bq_graph_destroy", "bq_graph_info", "bq_graph_set_spectrum",
     "bq_walk_batch", "bq_aesc_plan", "bq_aesc_estimate", "bq_sync", "bq_strerror",
     "bq_last_error", "bq_version", "bq_get_tuning", "bq_set_tuning", "bq_profile_enable",
     "bq_profile_read", "bq_walk_batch_noalloc", "bq_batch_create", "bq_batch_run",
-    "bq_batch_size", "bq_batch_destroy",
+    "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
+    "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
+    "bq_server_destroy",
 )
 
 _lock = threading.Lock()
@@ -136,6 +155,15 @@ def load_library(path: str | None = None):
         L.bq_batch_run.argtypes = [vp, vp]
         L.bq_batch_size.argtypes = [vp, c.POINTER(u64)]
         L.bq_batch_destroy.argtypes = [vp]
+        f32p = c.POINTER(c.c_float)
+        L.bq_autotune_walks.argtypes = [vp, u64, vp, u64, u32, vp, vp, c.POINTER(u32), f32p]
+        L.bq_autotune_aesc.argtypes = [c.POINTER(AescQuery), u32, c.POINTER(Sampler), vp,
+                                       c.POINTER(u32), f32p]
+        L.bq_server_create.argtypes = [vp, u32, c.POINTER(ServerConfig), c.POINTER(vp)]
+        L.bq_server_submit.argtypes = [vp, u32, vp, u64, f64, u64, c.POINTER(u64)]
+        L.bq_server_wait.argtypes = [vp, u64, f64, vp, vp, c.POINTER(f64)]
+        L.bq_server_stats_get.argtypes = [vp, c.POINTER(ServerStats)]
+        L.bq_server_destroy.argtypes = [vp]
         L.bq_profile_enable.argtypes = [i32]
         L.bq_profile_read.argtypes = [c.POINTER(Profile)]
         for name in EXPORTS:
@@ -350,6 +378,57 @@ def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.n
     return counts, sc
 
 
+def _query_array(queries):
+    """bq_aesc_query array for a list of query dicts (outputs allocated when
+    absent); returns (array, objects to keep alive, [(counts, sc)])."""
+    import torch
+    arr = (AescQuery * len(queries))()
+    keep, outputs = [], []
+    for i, q in enumerate(queries):
+        tau, nw = q["tau"], q["nwalks"]
+        k = tau.numel()
+        counts = q.get("counts")
+        sc = q.get("sc")
+        if counts is None:
+            counts = torch.empty(4 * k, dtype=torch.int32, device=tau.device)
+        if sc is None:
+            sc = torch.empty(k, dtype=torch.float64, device=tau.device)
+        uv = q.get("uv")
+        arr[i] = AescQuery(q["graph"].handle, int(q["seed"]) & (2**64 - 1),
+                           _dptr(uv, "edges") if uv is not None else None, k,
+                           _dptr(tau, "tau"), _dptr(nw, "nwalks"), _dptr(counts, "counts"),
+                           _dptr(sc, "sc", 8))
+        keep.append((q["graph"], uv, tau, nw, counts, sc))
+        outputs.append((counts, sc))
+    return arr, keep, outputs
+
+
+def autotune_walks(graph: Graph, seed: int, starts, n_steps: int, visits=None, stream=None):
+    """Time walk_lanes 1, 2, 4 on this walk batch; keep the fastest.
+    Returns (best, [ms per candidate])."""
+    import torch
+    if visits is None:
+        visits = torch.zeros(graph.n, dtype=torch.int32, device=starts.device)
+    best = ctypes.c_uint32()
+    ms = (ctypes.c_float * 3)()
+    _check(load_library().bq_autotune_walks(graph.handle, int(seed) & (2**64 - 1), _dptr(starts, "starts"),
+                                            starts.numel(), int(n_steps), _dptr(visits, "visits"),
+                                            _stream_handle(stream), ctypes.byref(best), ms))
+    return best.value, list(ms)
+
+
+def autotune_aesc(queries, sampler=None, stream=None):
+    """Time aesc_lanes 2, 4, 8 on a batch of these queries; keep the fastest.
+    Returns (best, [ms per candidate])."""
+    arr, keep, _ = _query_array(queries)
+    best = ctypes.c_uint32()
+    ms = (ctypes.c_float * 3)()
+    _check(load_library().bq_autotune_aesc(arr, len(queries), _sampler(sampler), _stream_handle(stream),
+                                           ctypes.byref(best), ms))
+    del keep
+    return best.value, list(ms)
+
+
 class Batch:
     """Several AESC estimates run by one persistent counting launch.
 
@@ -359,27 +438,8 @@ class Batch:
     kernels, so it may be captured in a CUDA graph."""
 
     def __init__(self, queries, sampler=None):
-        import torch
         L = load_library()
-        arr = (AescQuery * len(queries))()
-        self._keep = []
-        self.outputs = []
-        for i, q in enumerate(queries):
-            tau, nw = q["tau"], q["nwalks"]
-            k = tau.numel()
-            counts = q.get("counts")
-            sc = q.get("sc")
-            if counts is None:
-                counts = torch.empty(4 * k, dtype=torch.int32, device=tau.device)
-            if sc is None:
-                sc = torch.empty(k, dtype=torch.float64, device=tau.device)
-            uv = q.get("uv")
-            arr[i] = AescQuery(q["graph"].handle, int(q["seed"]) & (2**64 - 1),
-                               _dptr(uv, "edges") if uv is not None else None, k,
-                               _dptr(tau, "tau"), _dptr(nw, "nwalks"), _dptr(counts, "counts"),
-                               _dptr(sc, "sc", 8))
-            self._keep.append((q["graph"], uv, tau, nw, counts, sc))
-            self.outputs.append((counts, sc))
+        arr, self._keep, self.outputs = _query_array(queries)
         self._h = ctypes.c_void_p()
         _check(L.bq_batch_create(arr, len(queries), _sampler(sampler), ctypes.byref(self._h)))
 
@@ -395,6 +455,76 @@ class Batch:
         if getattr(self, "_h", None):
             load_library().bq_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """SC queries on resident graphs, served with continuous batching.
+
+    Requests (edge subset of one graph, eps, seed) are planned with the
+    scheduled plan of `config` and counted by iterations that each launch one
+    persistent kernel over tasks of every admitted request.  A request's
+    estimates equal aesc_estimate() with the same plan and seed."""
+
+    def __init__(self, graphs, config: ServerConfig | None = None, **kw):
+        L = load_library()
+        self._graphs = list(graphs)  # the server reads them: keep them alive
+        arr = (ctypes.c_void_p * len(self._graphs))(*[g.handle.value for g in self._graphs])
+        cfg = config
+        if cfg is None and kw:
+            cfg = ServerConfig(tau_scale=2.0, tau_add=2, tau_max=64, n_scale=9.0, n_min=32)
+        if cfg is not None:
+            for key, val in kw.items():
+                setattr(cfg, key, val)
+        self._h = ctypes.c_void_p()
+        _check(L.bq_server_create(arr, len(self._graphs),
+                                  ctypes.byref(cfg) if cfg is not None else None,
+                                  ctypes.byref(self._h)))
+        self._k = {}
+
+    def submit(self, graph: int, uv, eps: float, seed: int) -> int:
+        uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+        rid = ctypes.c_uint64()
+        _check(load_library().bq_server_submit(self._h, int(graph), _hptr(uv, "edges", np.uint32),
+                                               uv.shape[0], float(eps), int(seed), ctypes.byref(rid)))
+        self._k[rid.value] = uv.shape[0]
+        return rid.value
+
+    def wait(self, request_id: int, timeout: float = 60.0, counts: bool = False):
+        """(sc, counts or None, latency_ms); raises BouquetError on failure."""
+        k = self._k.get(request_id, 0)
+        sc = np.zeros(k, np.float64)
+        cn = np.zeros(4 * k, np.uint32) if counts else None
+        lat = ctypes.c_double()
+        rc = load_library().bq_server_wait(self._h, int(request_id), float(timeout),
+                                           _hptr(sc, "sc", np.float64),
+                                           _hptr(cn, "counts", np.uint32) if counts else None,
+                                           ctypes.byref(lat))
+        if rc != ETIMEOUT:
+            self._k.pop(request_id, None)  # each request is returned once
+        _check(rc)
+        return sc, (cn.reshape(-1, 4) if counts else None), lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load_library().bq_server_stats_get(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().bq_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
-UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu", "batch.cu"]
+UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu", "batch.cu", "tune.cu", "serve.cu"]
 HEADERS = ["internal.h", "hash.cuh", "edges.cuh"]
 
 
@@ -64,7 +64,7 @@ def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
         cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
-            ["-Xlinker", "-rpath=" + cuda_lib]
+            ["-Xlinker", "-rpath=" + cuda_lib, "-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

@@ -97,15 +97,10 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
     }
 }
 
+// Last q with begin[q] <= t.  begin has k + 1 entries (begin[k] = total) and
+// is followed in memory by its coarse index (every kTaskStride-th entry).
 __device__ __forceinline__ uint64_t find_query(const uint64_t *__restrict__ begin, uint64_t k, uint64_t t) {
-    // last q with begin[q] <= t (begin has k + 1 entries, begin[k] = total)
-    uint64_t lo = 0, hi = k;
-    while (hi - lo > 1) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (begin[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
+    return task_edge(begin, begin + k + 1, k, t);
 }
 
 // Persistent counting kernel.  Task t -> query q, side = local & 1, chunk =
@@ -262,9 +257,10 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
     int w = tuning_aesc_walks_per_lane();
     if (w != 2 && w != 4 && w != 8) w = 4;
     const uint32_t bouquet = 32u * (uint32_t)w;
-    // scratch: info[k] | begin[k + 1] | tasks[k] | next_task | (edges[2k] if all-edges)
+    // scratch: info[k] | begin[k + 1] coarse[ceil(k / stride)] | tasks[k] |
+    // next_task | (edges[2k] if all-edges)
     const size_t info_bytes = sizeof(QueryInfo) * k;
-    const size_t begin_bytes = sizeof(uint64_t) * (k + 1);
+    const size_t begin_bytes = sizeof(uint64_t) * (k + 1 + coarse_count(k));
     const size_t task_bytes = sizeof(uint32_t) * ((k + 1) & ~1ull);
     const size_t edge_bytes = edges_uv ? 0 : sizeof(uint32_t) * 2 * k;
     const size_t bytes = info_bytes + begin_bytes + task_bytes + 16 + edge_bytes;
@@ -294,6 +290,10 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
         prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, info, tasks,
                                                                     sc, status);
         rc = scan_u32_to_u64(tasks, begin, k, s);
+        if (rc == BQ_OK) {
+            count_launches(1);
+            build_coarse_kernel<<<blocks_for(coarse_count(k), kThreads), kThreads, 0, s>>>(begin, k, begin + k + 1);
+        }
     }
     if (rc == BQ_OK) {
         ProfScope prof(kProfAesc, s);

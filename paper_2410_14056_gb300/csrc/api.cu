@@ -37,6 +37,8 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+void clear_error() { g_last_error[0] = 0; }
+
 int cuda_fail(cudaError_t err, const char *what) {
     return fail(BQ_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(err), cudaGetErrorName(err));
 }

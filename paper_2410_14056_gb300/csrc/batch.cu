@@ -21,35 +21,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-struct GraphDesc {
-    const int64_t *offsets;
-    const uint32_t *nbrs;
-    const uint2 *rec8;
-    const uint64_t *upper_before;
-    const uint4 *pk;
-    const uint64_t *edge8;
-    uint64_t mask_off;
-    uint32_t n, pk_bits, pk_q, pk_mask, sh_off, sh_deg, mask_id, pad;
-};
-
-struct QueryDesc {
-    GraphDesc g;
-    uint64_t seed;
-    const uint32_t *uv;
-    const uint32_t *tau;
-    const uint32_t *nwalks;
-    uint32_t *counts;
-    double *sc;
-    uint64_t k;
-    uint64_t ebase;  // first global edge index of this query
-};
-
-struct BInfo {
-    uint32_t u, v;
-    uint64_t edge;
-    uint32_t du, dv, tau, nwalks, valid, query;
-};
-
 // The step of any compact layout (edge records, packed ids or plain CSR),
 // chosen per query; the branch is uniform within a task.
 __device__ __forceinline__ void gd_next(const GraphDesc &g, uint64_t j, uint32_t &cur, uint64_t &off,
@@ -141,13 +112,83 @@ __global__ void batch_prepare_kernel(const QueryDesc *__restrict__ qd, const uin
     }
 }
 
-// Persistent counting kernel over the tasks of all queries (same walks and
-// counters as aesc_count_kernel).
+// One bouquet task: 32*W walks of one side of one queried edge (`local` =
+// task index within the edge: side = local & 1, chunk = local >> 1), the walks
+// and counters of aesc_count_kernel; adds the warp's weighted hits to
+// d.counts[4 i + 2 side + {0, 1}] (i = the edge's index within its query).
+template <int W, bool COUPLED>
+__device__ __forceinline__ void run_bouquet_task(const QueryDesc &d, const BInfo &bi, uint64_t i, uint64_t local,
+                                                 const Sampler &smp, uint32_t lane) {
+    const GraphDesc g = d.g;
+    const uint64_t seed = d.seed;
+    const uint32_t side = (uint32_t)(local & 1);
+    const uint64_t k0 = (local >> 1) * 32ull * W;
+    const uint64_t stream = 2 * bi.edge + side;
+    const uint32_t start = side ? bi.v : bi.u;
+
+    uint64_t st[W], gs[W], off[W];
+    uint32_t cur[W], deg[W];
+    bool act[W];
+    if (!COUPLED && (W % 2 == 0)) {
+#pragma unroll
+        for (int j = 0; j < W; j += 2) {
+            const uint64_t kk = k0 + (uint64_t)lane * W + j;
+            walk_key_pair(seed, stream, kk >> 1, st[j], st[j + 1]);
+            act[j] = kk < bi.nwalks;
+            act[j + 1] = kk + 1 < bi.nwalks;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint64_t kk = COUPLED ? k0 + (uint64_t)j * 32 + lane : k0 + (uint64_t)lane * W + j;
+            st[j] = walk_key(seed, stream, kk);
+            if (COUPLED) gs[j] = walk_key(seed, stream | kGroupBit, kk / smp.width);
+            act[j] = kk < bi.nwalks;
+        }
+    }
+    uint64_t off0;
+    uint32_t deg0;
+    start_record(g.offsets, start, off0, deg0);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        cur[j] = start;
+        off[j] = off0;
+        deg[j] = act[j] ? deg0 : 0u;
+        if (!COUPLED) gs[j] = 0;
+    }
+    uint32_t hit_u = 0, hit_v = 0;
+    for (uint32_t l = 1; l <= bi.tau; ++l) {
+        const uint32_t weight = l < bi.tau ? 2u : 1u;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            st[j] += kGolden;
+            if (COUPLED) gs[j] += kGolden;
+            if (deg[j]) {
+                const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                gd_next(g, off[j] + kk, cur[j], off[j], deg[j]);
+                hit_u += cur[j] == bi.u ? weight : 0u;
+                hit_v += cur[j] == bi.v ? weight : 0u;
+            }
+        }
+    }
+#pragma unroll
+    for (int dd = 16; dd > 0; dd >>= 1) {
+        hit_u += __shfl_down_sync(0xffffffffu, hit_u, dd);
+        hit_v += __shfl_down_sync(0xffffffffu, hit_v, dd);
+    }
+    if (lane == 0) {
+        uint32_t *c = d.counts + 4 * i + 2 * side;
+        if (hit_u) atomicAdd(c + 0, hit_u);
+        if (hit_v) atomicAdd(c + 1, hit_v);
+    }
+}
+
+// Persistent counting kernel over the tasks of all queries of a batch.
 template <int W, bool COUPLED>
 __global__ void __launch_bounds__(kThreads)
 batch_count_kernel(const QueryDesc *__restrict__ qd, const BInfo *__restrict__ info,
-                   const uint64_t *__restrict__ begin, uint64_t total_edges, Sampler smp,
-                   unsigned long long *__restrict__ next_task) {
+                   const uint64_t *__restrict__ begin, const uint64_t *__restrict__ coarse, uint64_t total_edges,
+                   Sampler smp, unsigned long long *__restrict__ next_task) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t total = begin[total_edges];
     while (true) {
@@ -155,72 +196,36 @@ batch_count_kernel(const QueryDesc *__restrict__ qd, const BInfo *__restrict__ i
         if (lane == 0) t = atomicAdd(next_task, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= total) break;
-        const uint64_t e = last_le(begin, total_edges, t);
+        const uint64_t e = task_edge(begin, coarse, total_edges, t);
         const BInfo bi = info[e];
         const QueryDesc &d = qd[bi.query];
-        const GraphDesc g = d.g;
-        const uint64_t seed = d.seed;
-        const uint64_t local = t - begin[e];
-        const uint32_t side = (uint32_t)(local & 1);
-        const uint64_t k0 = (local >> 1) * 32ull * W;
-        const uint64_t stream = 2 * bi.edge + side;
-        const uint32_t start = side ? bi.v : bi.u;
+        run_bouquet_task<W, COUPLED>(d, bi, e - d.ebase, t - begin[e], smp, lane);
+    }
+}
 
-        uint64_t st[W], gs[W], off[W];
-        uint32_t cur[W], deg[W];
-        bool act[W];
-        if (!COUPLED && (W % 2 == 0)) {
-#pragma unroll
-            for (int j = 0; j < W; j += 2) {
-                const uint64_t kk = k0 + (uint64_t)lane * W + j;
-                walk_key_pair(seed, stream, kk >> 1, st[j], st[j + 1]);
-                act[j] = kk < bi.nwalks;
-                act[j + 1] = kk + 1 < bi.nwalks;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                const uint64_t kk = COUPLED ? k0 + (uint64_t)j * 32 + lane : k0 + (uint64_t)lane * W + j;
-                st[j] = walk_key(seed, stream, kk);
-                if (COUPLED) gs[j] = walk_key(seed, stream | kGroupBit, kk / smp.width);
-                act[j] = kk < bi.nwalks;
-            }
+// The server's iteration: windows of several requests' tasks.  Item t ->
+// request (items[].item_base) -> its task -> its edge.
+template <int W, bool COUPLED>
+__global__ void __launch_bounds__(kThreads)
+serve_count_kernel(const ServeItem *__restrict__ items, uint32_t n_items, uint64_t total_items, Sampler smp,
+                   unsigned long long *__restrict__ next_item) {
+    const uint32_t lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(next_item, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total_items) break;
+        uint32_t lo = 0, hi = n_items;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (items[mid].item_base <= t) lo = mid;
+            else hi = mid;
         }
-        uint64_t off0;
-        uint32_t deg0;
-        start_record(g.offsets, start, off0, deg0);
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            cur[j] = start;
-            off[j] = off0;
-            deg[j] = act[j] ? deg0 : 0u;
-            if (!COUPLED) gs[j] = 0;
-        }
-        uint32_t hit_u = 0, hit_v = 0;
-        for (uint32_t l = 1; l <= bi.tau; ++l) {
-            const uint32_t weight = l < bi.tau ? 2u : 1u;
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                st[j] += kGolden;
-                if (COUPLED) gs[j] += kGolden;
-                if (deg[j]) {
-                    const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
-                    gd_next(g, off[j] + kk, cur[j], off[j], deg[j]);
-                    hit_u += cur[j] == bi.u ? weight : 0u;
-                    hit_v += cur[j] == bi.v ? weight : 0u;
-                }
-            }
-        }
-#pragma unroll
-        for (int dd = 16; dd > 0; dd >>= 1) {
-            hit_u += __shfl_down_sync(0xffffffffu, hit_u, dd);
-            hit_v += __shfl_down_sync(0xffffffffu, hit_v, dd);
-        }
-        if (lane == 0) {
-            uint32_t *c = d.counts + 4 * (e - d.ebase) + 2 * side;
-            if (hit_u) atomicAdd(c + 0, hit_u);
-            if (hit_v) atomicAdd(c + 1, hit_v);
-        }
+        const ServeItem it = items[lo];
+        const uint64_t task = it.task_lo + (t - it.item_base);
+        const uint64_t e = last_le_u64(it.begin, 0, it.k, task);
+        const BInfo bi = it.info[e];
+        run_bouquet_task<W, COUPLED>(*it.qd, bi, e, task - it.begin[e], smp, lane);
     }
 }
 
@@ -264,6 +269,7 @@ struct bq_batch {
     bq::BInfo *d_info = nullptr;
     uint32_t *d_tasks = nullptr;
     uint64_t *d_begin = nullptr;
+    uint64_t *d_coarse = nullptr;
     unsigned long long *d_next = nullptr;
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
@@ -287,11 +293,11 @@ int batch_occupancy(int *grid) {
 template <int W>
 void launch_batch_count(const bq_batch *b, cudaStream_t s) {
     if (b->smp.kind == 1)
-        batch_count_kernel<W, true><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->edges, b->smp,
-                                                                 b->d_next);
+        batch_count_kernel<W, true><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->d_coarse,
+                                                                 b->edges, b->smp, b->d_next);
     else
-        batch_count_kernel<W, false><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->edges, b->smp,
-                                                                  b->d_next);
+        batch_count_kernel<W, false><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->d_coarse,
+                                                                  b->edges, b->smp, b->d_next);
 }
 
 void free_batch(bq_batch *b) {
@@ -301,6 +307,7 @@ void free_batch(bq_batch *b) {
     cudaFree(b->d_info);
     cudaFree(b->d_tasks);
     cudaFree(b->d_begin);
+    cudaFree(b->d_coarse);
     cudaFree(b->d_next);
     cudaFree(b->d_ws);
     delete b;
@@ -380,6 +387,7 @@ int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_s
     if (e == cudaSuccess) e = cudaMalloc(&b->d_info, sizeof(BInfo) * (total ? total : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tasks, sizeof(uint32_t) * (total ? total : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_begin, sizeof(uint64_t) * (total + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_coarse, sizeof(uint64_t) * (coarse_count(total) + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned long long));
     if (e == cudaSuccess && b->ws_bytes) e = cudaMalloc(&b->d_ws, b->ws_bytes);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_qd, qd.data(), sizeof(QueryDesc) * n_queries, cudaMemcpyHostToDevice);
@@ -419,6 +427,11 @@ int bq_batch_run(bq_batch *b, void *stream) {
         batch_prepare_kernel<<<blocks_for(b->edges, kThreads), kThreads, 0, s>>>(
             b->d_qd, b->d_ebase, b->nq, b->edges, bouquet, b->d_info, b->d_tasks, b->status);
         rc = scan_u32_to_u64_ws(b->d_tasks, b->d_begin, b->edges, b->d_ws, b->ws_bytes, s);
+        if (rc == BQ_OK) {
+            count_launches(1);
+            build_coarse_kernel<<<blocks_for(coarse_count(b->edges), kThreads), kThreads, 0, s>>>(
+                b->d_begin, b->edges, b->d_coarse);
+        }
     }
     if (rc == BQ_OK) {
         ProfScope prof(kProfAesc, s);
@@ -458,3 +471,86 @@ int bq_batch_destroy(bq_batch *b) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ server hooks
+
+namespace bq {
+
+GraphDesc graph_desc(const bq_graph *g) {
+    const DeviceGraph v = g->view();
+    GraphDesc d;
+    d.offsets = v.offsets;
+    d.nbrs = v.nbrs;
+    d.rec8 = v.rec8;
+    d.upper_before = v.upper_before;
+    d.pk = v.pk;
+    d.edge8 = v.edge8;
+    d.mask_off = v.mask_off;
+    d.n = v.n;
+    d.pk_bits = v.pk_bits;
+    d.pk_q = v.pk_q;
+    d.pk_mask = v.pk_mask;
+    d.sh_off = v.sh_off;
+    d.sh_deg = v.sh_deg;
+    d.mask_id = v.mask_id;
+    d.pad = 0;
+    return d;
+}
+
+size_t serve_scan_ws_bytes(uint64_t k) { return scan_u32_to_u64_ws_bytes(k); }
+
+// One request (a single-query descriptor with ebase 0): edge info, task counts
+// and their prefix.
+int serve_prepare(const QueryDesc *d_qd, uint64_t k, uint32_t bouquet, BInfo *info, uint32_t *tasks,
+                  uint64_t *begin, void *ws, size_t ws_bytes, uint32_t *status, cudaStream_t s) {
+    if (k == 0) return BQ_OK;
+    count_launches(1);
+    // with one query the query index is 0 and the ebase array is not read
+    batch_prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(d_qd, begin, 1, k, bouquet, info, tasks,
+                                                                      status);
+    BQ_CUDA(cudaGetLastError());
+    return scan_u32_to_u64_ws(tasks, begin, k, ws, ws_bytes, s);
+}
+
+int serve_iterate(const ServeItem *d_items, uint32_t n_items, uint64_t total_items, int lanes, const Sampler &smp,
+                  unsigned long long *counter, cudaStream_t s) {
+    if (total_items == 0) return BQ_OK;
+    BQ_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    int dev = 0, sms = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const bool c = smp.kind == 1;
+    int per_sm = 0;
+#define BQ_SERVE(WW)                                                                                             \
+    do {                                                                                                         \
+        if (c) {                                                                                                 \
+            BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_count_kernel<WW, true>, kThreads, \
+                                                                  0));                                           \
+            serve_count_kernel<WW, true><<<sms * (per_sm < 1 ? 1 : per_sm), kThreads, 0, s>>>(                    \
+                d_items, n_items, total_items, smp, counter);                                                    \
+        } else {                                                                                                 \
+            BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_count_kernel<WW, false>,         \
+                                                                  kThreads, 0));                                 \
+            serve_count_kernel<WW, false><<<sms * (per_sm < 1 ? 1 : per_sm), kThreads, 0, s>>>(                   \
+                d_items, n_items, total_items, smp, counter);                                                    \
+        }                                                                                                        \
+    } while (0)
+    ProfScope prof(kProfAesc, s);
+    count_launches(1);
+    if (lanes == 2) BQ_SERVE(2);
+    else if (lanes == 8) BQ_SERVE(8);
+    else BQ_SERVE(4);
+#undef BQ_SERVE
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+int serve_finalize(const QueryDesc *d_qd, const BInfo *info, uint64_t k, cudaStream_t s) {
+    if (k == 0) return BQ_OK;
+    count_launches(1);
+    batch_finalize_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(d_qd, info, k);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+}  // namespace bq

@@ -179,6 +179,45 @@ struct EdgesWide {
     }
 };
 
+// Task -> edge lookup.  `begin` is the exclusive prefix of per-edge task
+// counts (count + 1 entries); `coarse[i] = begin[i * kTaskStride]`.  The
+// search runs over the coarse array (small enough to stay in L2), then over
+// at most kTaskStride contiguous entries of `begin`, instead of a binary search
+// whose lower levels touch random lines of a large array.
+constexpr uint32_t kTaskStride = 64;
+
+__device__ __forceinline__ uint64_t last_le_u64(const uint64_t *__restrict__ a, uint64_t lo, uint64_t hi,
+                                                uint64_t x) {
+    // largest i in [lo, hi) with a[i] <= x, given a[lo] <= x
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t task_edge(const uint64_t *__restrict__ begin, const uint64_t *__restrict__ coarse,
+                                              uint64_t count, uint64_t t) {
+    const uint64_t n_coarse = (count + kTaskStride - 1) / kTaskStride;
+    const uint64_t c = last_le_u64(coarse, 0, n_coarse, t);
+    const uint64_t lo = c * kTaskStride;
+    const uint64_t hi = lo + kTaskStride < count ? lo + kTaskStride : count;
+    return last_le_u64(begin, lo, hi, t);
+}
+
+// coarse[i] = begin[i * kTaskStride] for i < ceil(count / kTaskStride).
+// (A template so that each translation unit gets its own instance.)
+template <int kUnused = 0>
+__global__ void build_coarse_kernel(const uint64_t *__restrict__ begin, uint64_t count, uint64_t *__restrict__ coarse) {
+    const uint64_t n_coarse = (count + kTaskStride - 1) / kTaskStride;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_coarse;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        coarse[i] = begin[i * kTaskStride];
+}
+
+inline uint64_t coarse_count(uint64_t count) { return (count + kTaskStride - 1) / kTaskStride; }
+
 // Call f with the layout the graph was built with.
 template <typename F>
 int with_edges(const DeviceGraph &g, F &&f) {

@@ -67,6 +67,49 @@ struct DeviceGraph {
     bool compact() const { return rec8 != nullptr; }
 };
 
+// Device descriptors of AESC queries run as batches (batch.cu) or by the
+// server (serve.cu).
+struct GraphDesc {
+    const int64_t *offsets;
+    const uint32_t *nbrs;
+    const uint2 *rec8;
+    const uint64_t *upper_before;
+    const uint4 *pk;
+    const uint64_t *edge8;
+    uint64_t mask_off;
+    uint32_t n, pk_bits, pk_q, pk_mask, sh_off, sh_deg, mask_id, pad;
+};
+
+struct QueryDesc {
+    GraphDesc g;
+    uint64_t seed;
+    const uint32_t *uv;
+    const uint32_t *tau;
+    const uint32_t *nwalks;
+    uint32_t *counts;
+    double *sc;
+    uint64_t k;
+    uint64_t ebase;  // first global edge index of this query
+};
+
+// Per queried edge: normalised endpoints, canonical id, degrees, plan.
+struct BInfo {
+    uint32_t u, v;
+    uint64_t edge;
+    uint32_t du, dv, tau, nwalks, valid, query;
+};
+
+// One in-flight request in a server iteration: its tasks [task_lo, task_lo +
+// count) are work items [item_base, item_base + count) of the launch.
+struct ServeItem {
+    const QueryDesc *qd;
+    const BInfo *info;
+    const uint64_t *begin;
+    uint64_t k;
+    uint64_t task_lo;
+    uint64_t item_base;
+};
+
 }  // namespace bq
 
 struct bq_graph {
@@ -129,6 +172,7 @@ namespace bq {
 // ---- error plumbing (api.cu)
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t err, const char *what);
+void clear_error();  // empties this thread's bq_last_error() message
 #define BQ_CUDA(call)                                            \
     do {                                                         \
         cudaError_t _e = (call);                                 \
@@ -194,6 +238,16 @@ int scan_u32_to_u64_ws(const uint32_t *in, uint64_t *out, uint64_t n, void *ws, 
 // api.cu: the device's status word if it was already allocated (never allocates).
 int existing_status_word(int device, uint32_t **out);
 int validate_sampler(const bq_sampler *in, Sampler &out);
+
+// ---- batch.cu, used by the server: one query's edges (prepare + task scan),
+// an iteration over windows of several queries' tasks, and the finalize.
+GraphDesc graph_desc(const bq_graph *g);
+size_t serve_scan_ws_bytes(uint64_t k);
+int serve_prepare(const QueryDesc *d_qd, uint64_t k, uint32_t bouquet, BInfo *info, uint32_t *tasks,
+                  uint64_t *begin, void *ws, size_t ws_bytes, uint32_t *status, cudaStream_t s);
+int serve_iterate(const ServeItem *d_items, uint32_t n_items, uint64_t total_items, int lanes, const Sampler &smp,
+                  unsigned long long *counter, cudaStream_t s);
+int serve_finalize(const QueryDesc *d_qd, const BInfo *info, uint64_t k, cudaStream_t s);
 
 // ---- aesc.cu
 int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,

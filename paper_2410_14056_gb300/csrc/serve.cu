@@ -1,0 +1,566 @@
+// Serving loop: SC queries on resident graphs with continuous batching.
+//
+// A request is planned on the submitting thread (scheduled plan, host) and
+// queued.  A worker thread owns a non-blocking stream; it admits queued
+// requests while the device memory they need and the number of requests on
+// the GPU fit the configured limits (uploading each and preparing its edges),
+// then runs iterations: each iteration is one persistent counting launch over
+// a window of tasks of every admitted request.  A request whose last tasks
+// were launched is finalized and its results copied back on a second stream;
+// the worker sees completion through an event, releases its memory and wakes
+// its waiter.  Newly submitted requests join at the next iteration.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "internal.h"
+
+namespace bq {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t id = 0;
+    uint32_t graph = 0;
+    std::vector<uint32_t> uv;
+    uint64_t k = 0;
+    double eps = 0.1;
+    uint64_t seed = 0;
+    Clock::time_point t_submit, t_done;
+    int status = BQ_OK;
+    std::string error;  // message of a failed request
+    // plan (host)
+    std::vector<uint32_t> tau, nwalks;
+    double walk_steps = 0;
+    uint64_t tasks_total = 0, tasks_launched = 0;
+    // device
+    char *dbuf = nullptr;
+    size_t dbytes = 0;
+    QueryDesc *d_qd = nullptr;
+    BInfo *d_info = nullptr;
+    uint64_t *d_begin = nullptr;
+    uint32_t *d_counts = nullptr;
+    double *d_sc = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    bool finalizing = false;
+    // results (host)
+    std::vector<double> sc;
+    std::vector<uint32_t> counts;
+};
+
+using RequestPtr = std::shared_ptr<Request>;
+
+// Device bytes of a request with k edges (the layout carved in admit()).
+size_t request_bytes(uint64_t k) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return up(sizeof(QueryDesc)) + up(8 * k) + up(4 * k) + up(4 * k) + up(16 * k) + up(8 * k) +
+           up(sizeof(BInfo) * k) + up(4 * k) + up(8 * (k + 1)) + up(serve_scan_ws_bytes(k)) + 256;
+}
+
+}  // namespace
+}  // namespace bq
+
+struct bq_server {
+    std::vector<bq_graph *> graphs;
+    bq_server_config cfg;
+    bq::Sampler smp{0, 0, 1};
+    int device = 0;
+    int lanes = 4;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    // iteration descriptors: pinned host ring and device ring
+    static constexpr int kRing = 2;
+    bq::ServeItem *h_items[kRing] = {nullptr, nullptr};
+    bq::ServeItem *d_items[kRing] = {nullptr, nullptr};
+    unsigned long long *d_counter = nullptr;
+    cudaEvent_t ring_ev[kRing] = {nullptr, nullptr};
+    bool ring_used[kRing] = {false, false};
+    int ring_next = 0;
+    uint32_t *status = nullptr;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<bq::RequestPtr> pending;
+    std::vector<bq::RequestPtr> inflight;
+    std::unordered_map<uint64_t, bq::RequestPtr> done;
+    std::unordered_set<uint64_t> live;  // submitted and not yet returned by bq_server_wait
+    uint64_t next_id = 1;
+    uint64_t held_bytes = 0;
+    bool stop = false;
+    std::thread worker;
+
+    // statistics
+    bq::Clock::time_point t_start;
+    uint64_t submitted = 0, completed = 0, failed = 0, edges_completed = 0, iterations = 0;
+    double walk_steps = 0;
+    std::vector<double> latencies_ms;
+};
+
+namespace bq {
+namespace {
+
+uint32_t bouquet_of(const bq_server *srv) { return 32u * (uint32_t)srv->lanes; }
+
+// Plan one request on the host (the submitting thread, no lock): tau and N
+// per edge, the number of bouquet tasks and of walk steps.
+int plan_request(bq_server *srv, Request &r) {
+    bq_graph *g = srv->graphs[r.graph];
+    r.tau.assign(r.k, 0);
+    r.nwalks.assign(r.k, 0);
+    if (r.k) {
+        bq_schedule sched{srv->cfg.tau_scale, srv->cfg.tau_add, srv->cfg.tau_max, srv->cfg.n_scale, srv->cfg.n_min, 0};
+        const int rc = bq_aesc_plan(g, r.uv.data(), r.k, r.eps, 0.01, BQ_PLAN_SCHEDULED, &sched, r.tau.data(),
+                                    r.nwalks.data());
+        if (rc) return rc;
+    }
+    const uint32_t bouquet = bouquet_of(srv);
+    r.tasks_total = 0;
+    r.walk_steps = 0;
+    for (uint64_t i = 0; i < r.k; ++i) {
+        if (2ull * r.nwalks[i] * r.tau[i] >= (1ull << 32))
+            return fail(BQ_EOVERFLOW, "server: edge %llu: 2 N tau = %llu does not fit a uint32 counter",
+                        (unsigned long long)i, 2ull * r.nwalks[i] * r.tau[i]);
+        r.tasks_total += 2ull * ((r.nwalks[i] + bouquet - 1) / bouquet);
+        r.walk_steps += 2.0 * (double)r.nwalks[i] * (double)r.tau[i];
+    }
+    return BQ_OK;
+}
+
+// Allocate, upload and prepare one planned request (worker thread, no lock).
+int admit(bq_server *srv, Request &r) {
+    bq_graph *g = srv->graphs[r.graph];
+    const uint32_t bouquet = bouquet_of(srv);
+    cudaStream_t s = srv->stream;
+    cudaError_t e = cudaMallocAsync((void **)&r.dbuf, r.dbytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BQ_ENOMEM, "server: cannot allocate %zu bytes for a request", r.dbytes);
+    }
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char *p = r.dbuf;
+    r.d_qd = (QueryDesc *)p;
+    p += up(sizeof(QueryDesc));
+    uint32_t *d_uv = (uint32_t *)p;
+    p += up(8 * r.k);
+    uint32_t *d_tau = (uint32_t *)p;
+    p += up(4 * r.k);
+    uint32_t *d_nw = (uint32_t *)p;
+    p += up(4 * r.k);
+    r.d_counts = (uint32_t *)p;
+    p += up(16 * r.k);
+    r.d_sc = (double *)p;
+    p += up(8 * r.k);
+    r.d_info = (BInfo *)p;
+    p += up(sizeof(BInfo) * r.k);
+    uint32_t *d_tasks = (uint32_t *)p;
+    p += up(4 * r.k);
+    r.d_begin = (uint64_t *)p;
+    p += up(8 * (r.k + 1));
+    void *ws = p;
+    const size_t ws_bytes = serve_scan_ws_bytes(r.k);
+
+    QueryDesc qd;
+    qd.g = graph_desc(g);
+    qd.seed = r.seed;
+    qd.uv = d_uv;
+    qd.tau = d_tau;
+    qd.nwalks = d_nw;
+    qd.counts = r.d_counts;
+    qd.sc = r.d_sc;
+    qd.k = r.k;
+    qd.ebase = 0;
+    e = cudaMemcpyAsync(r.d_qd, &qd, sizeof(qd), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && r.k) e = cudaMemcpyAsync(d_uv, r.uv.data(), 8 * r.k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && r.k) e = cudaMemcpyAsync(d_tau, r.tau.data(), 4 * r.k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && r.k) e = cudaMemcpyAsync(d_nw, r.nwalks.data(), 4 * r.k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "server: request upload");
+    return serve_prepare(r.d_qd, r.k, bouquet, r.d_info, d_tasks, r.d_begin, ws, ws_bytes, srv->status, s);
+}
+
+void start_finalize(bq_server *srv, Request &r) {
+    serve_finalize(r.d_qd, r.d_info, r.k, srv->stream);
+    cudaEventRecord(r.done_ev, srv->stream);
+    r.finalizing = true;
+}
+
+// One iteration: a window of tasks of every admitted request, one launch.
+// Returns false when no request has tasks left to launch.
+bool iterate(bq_server *srv) {
+    std::vector<Request *> active;
+    for (auto &r : srv->inflight)
+        if (!r->finalizing && r->tasks_launched < r->tasks_total) active.push_back(r.get());
+    if (active.empty()) return false;
+    const uint64_t budget = srv->cfg.tasks_per_iteration;
+    std::vector<uint64_t> take(active.size(), 0);
+    uint64_t used = 0;
+    // fair share, then hand what is left to requests that still have tasks
+    for (int pass = 0; pass < 2 && used < budget; ++pass) {
+        uint64_t open = 0;
+        for (size_t i = 0; i < active.size(); ++i)
+            if (active[i]->tasks_total - active[i]->tasks_launched > take[i]) ++open;
+        if (!open) break;
+        const uint64_t share = std::max<uint64_t>(1, (budget - used) / open);
+        for (size_t i = 0; i < active.size() && used < budget; ++i) {
+            const uint64_t left = active[i]->tasks_total - active[i]->tasks_launched - take[i];
+            const uint64_t w = std::min(std::min(left, share), budget - used);
+            take[i] += w;
+            used += w;
+        }
+    }
+    const int slot = srv->ring_next;
+    if (srv->ring_used[slot]) cudaEventSynchronize(srv->ring_ev[slot]);
+    ServeItem *items = srv->h_items[slot];
+    uint32_t n = 0;
+    uint64_t base = 0;
+    for (size_t i = 0; i < active.size(); ++i) {
+        if (!take[i]) continue;
+        Request &r = *active[i];
+        items[n].qd = r.d_qd;
+        items[n].info = r.d_info;
+        items[n].begin = r.d_begin;
+        items[n].k = r.k;
+        items[n].task_lo = r.tasks_launched;
+        items[n].item_base = base;
+        base += take[i];
+        r.tasks_launched += take[i];
+        ++n;
+    }
+    cudaMemcpyAsync(srv->d_items[slot], items, sizeof(ServeItem) * n, cudaMemcpyHostToDevice, srv->stream);
+    serve_iterate(srv->d_items[slot], n, base, srv->lanes, srv->smp, srv->d_counter, srv->stream);
+    cudaEventRecord(srv->ring_ev[slot], srv->stream);
+    srv->ring_used[slot] = true;
+    srv->ring_next = (slot + 1) % bq_server::kRing;
+    for (Request *r : active)
+        if (r->tasks_launched == r->tasks_total) start_finalize(srv, *r);
+    ++srv->iterations;
+    return true;
+}
+
+// Hand finished requests to their waiters.  With `block`, wait for the
+// oldest finalizing request first (nothing else to launch meanwhile).
+void poll_completions(bq_server *srv, bool block) {
+    std::vector<RequestPtr> finished;
+    for (auto &r : srv->inflight) {
+        if (!r->finalizing) continue;
+        cudaError_t q = block && finished.empty() ? cudaEventSynchronize(r->done_ev) : cudaEventQuery(r->done_ev);
+        if (q == cudaErrorNotReady) continue;
+        r->sc.resize(r->k);
+        r->counts.resize(4 * r->k);
+        if (r->k) {
+            cudaMemcpyAsync(r->sc.data(), r->d_sc, 8 * r->k, cudaMemcpyDeviceToHost, srv->copy_stream);
+            cudaMemcpyAsync(r->counts.data(), r->d_counts, 16 * r->k, cudaMemcpyDeviceToHost, srv->copy_stream);
+        }
+        cudaStreamSynchronize(srv->copy_stream);
+        r->status = q == cudaSuccess ? BQ_OK : BQ_ECUDA;
+        finished.push_back(r);
+    }
+    if (finished.empty()) return;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const auto now = Clock::now();
+    for (auto &r : finished) {
+        cudaFreeAsync(r->dbuf, srv->copy_stream);
+        r->dbuf = nullptr;
+        cudaEventDestroy(r->done_ev);
+        r->done_ev = nullptr;
+        srv->held_bytes -= r->dbytes;
+        r->t_done = now;
+        ++srv->completed;
+        srv->edges_completed += r->k;
+        srv->walk_steps += r->walk_steps;
+        srv->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+        srv->inflight.erase(std::find(srv->inflight.begin(), srv->inflight.end(), r));
+        srv->done[r->id] = r;
+    }
+    srv->cv_done.notify_all();
+}
+
+}  // namespace
+}  // namespace bq
+
+namespace bq {
+namespace {
+
+// A request that could not be planned or admitted completes at once with its
+// error status (its memory, if any, is released).
+void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
+    if (r->dbuf) {
+        cudaFreeAsync(r->dbuf, srv->stream);
+        r->dbuf = nullptr;
+    }
+    if (r->done_ev) {
+        cudaEventDestroy(r->done_ev);
+        r->done_ev = nullptr;
+    }
+    const char *msg = bq_last_error();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    r->status = status;
+    r->error = msg ? msg : "";
+    r->t_done = Clock::now();
+    if (r->dbytes) srv->held_bytes -= r->dbytes;
+    r->dbytes = 0;
+    ++srv->failed;
+    srv->done[r->id] = r;
+    srv->cv_done.notify_all();
+}
+
+void worker_main(bq_server *srv) {
+    cudaSetDevice(srv->device);
+    const uint64_t budget = srv->cfg.device_budget_bytes;
+    for (;;) {
+        // admission: FIFO, while slots and device memory allow
+        std::vector<RequestPtr> admitted;
+        bool idle = false;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            for (;;) {
+                if (srv->pending.empty()) break;
+                RequestPtr r = srv->pending.front();
+                const size_t bytes = request_bytes(r->k);
+                if (bytes > budget) {
+                    srv->pending.pop_front();
+                    lk.unlock();
+                    fail(BQ_ENOMEM, "server: a request of %llu edges needs %zu bytes, over the budget",
+                         (unsigned long long)r->k, bytes);
+                    complete_failed(srv, r, BQ_ENOMEM);
+                    lk.lock();
+                    continue;
+                }
+                if (srv->inflight.size() + admitted.size() >= srv->cfg.max_inflight ||
+                    srv->held_bytes + bytes > budget)
+                    break;
+                srv->pending.pop_front();
+                r->dbytes = bytes;
+                srv->held_bytes += bytes;
+                admitted.push_back(r);
+            }
+            idle = admitted.empty() && srv->inflight.empty();
+            if (idle) {
+                if (srv->stop && srv->pending.empty()) return;
+                srv->cv_work.wait(lk, [srv] { return srv->stop || !srv->pending.empty(); });
+                continue;
+            }
+        }
+        for (auto &r : admitted) {
+            const int rc = admit(srv, *r);
+            if (rc != BQ_OK) {
+                complete_failed(srv, r, rc);
+                continue;
+            }
+            std::lock_guard<std::mutex> lk(srv->mu);
+            srv->inflight.push_back(r);
+        }
+        // requests with nothing to count go straight to finalization
+        for (auto &r : srv->inflight)
+            if (!r->finalizing && r->tasks_total == 0) start_finalize(srv, *r);
+        const bool launched = iterate(srv);
+        poll_completions(srv, !launched);
+    }
+}
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = lo + 1 < v.size() ? lo + 1 : lo;
+    return v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+}
+
+}  // namespace
+}  // namespace bq
+
+using namespace bq;
+
+namespace {
+
+void server_free(bq_server *srv) {
+    for (int i = 0; i < bq_server::kRing; ++i) {
+        if (srv->ring_ev[i]) cudaEventDestroy(srv->ring_ev[i]);
+        if (srv->h_items[i]) cudaFreeHost(srv->h_items[i]);
+        if (srv->d_items[i]) cudaFree(srv->d_items[i]);
+    }
+    if (srv->d_counter) cudaFree(srv->d_counter);
+    if (srv->status) cudaFree(srv->status);
+    if (srv->stream) cudaStreamDestroy(srv->stream);
+    if (srv->copy_stream) cudaStreamDestroy(srv->copy_stream);
+    delete srv;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server_config *cfg, bq_server **out) {
+    clear_error();
+    if (!out) return fail(BQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!graphs || n_graphs == 0) return fail(BQ_EINVAL, "a server needs at least one graph");
+    int dev = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    for (uint32_t i = 0; i < n_graphs; ++i) {
+        if (!graphs[i]) return fail(BQ_EINVAL, "graph %u is NULL", i);
+        if (graphs[i]->device != dev)
+            return fail(BQ_EINVAL, "graph %u lives on device %d, not %d", i, graphs[i]->device, dev);
+        if (!graphs[i]->d_rec8) return fail(BQ_EINVAL, "graph %u: the server needs nnz < 2^32", i);
+    }
+    bq_server_config c{};
+    if (cfg) c = *cfg;
+    else {
+        c.tau_scale = 2.0;
+        c.tau_add = 2;
+        c.tau_max = 64;
+        c.n_scale = 9.0;
+        c.n_min = 32;
+    }
+    if (!c.device_budget_bytes) c.device_budget_bytes = 1ull << 30;
+    if (!c.max_inflight) c.max_inflight = 256;
+    if (!c.max_pending) c.max_pending = 65536;
+    if (!c.tasks_per_iteration) c.tasks_per_iteration = 1ull << 16;
+    if (c.max_inflight > (1u << 20)) return fail(BQ_EINVAL, "max_inflight %u is above 2^20", c.max_inflight);
+    if (c.tau_max < 1 || !(c.tau_scale >= 0.0) || !(c.n_scale >= 0.0)) return fail(BQ_EINVAL, "bad schedule");
+    // the planner reads host copies of the graphs: take them now, before the
+    // worker thread exists
+    for (uint32_t i = 0; i < n_graphs; ++i) {
+        const int rc = graph_fetch_host(graphs[i]);
+        if (rc) return rc;
+    }
+    bq_server *srv = new bq_server();
+    srv->graphs.assign(graphs, graphs + n_graphs);
+    srv->cfg = c;
+    srv->device = dev;
+    srv->lanes = tuning_aesc_walks_per_lane();
+    cudaError_t e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&srv->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < bq_server::kRing && e == cudaSuccess; ++i) {
+        e = cudaMallocHost((void **)&srv->h_items[i], sizeof(ServeItem) * c.max_inflight);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&srv->d_items[i], sizeof(ServeItem) * c.max_inflight);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->ring_ev[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&srv->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&srv->status, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(srv->status, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(e, "bq_server_create");
+        server_free(srv);
+        return rc;
+    }
+    srv->t_start = Clock::now();
+    srv->worker = std::thread(worker_main, srv);
+    *out = srv;
+    return BQ_OK;
+}
+
+int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, uint64_t k, double eps,
+                     uint64_t seed, uint64_t *request_id) {
+    clear_error();
+    if (!srv || !request_id) return fail(BQ_EINVAL, "server or request_id is NULL");
+    if (graph >= srv->graphs.size()) return fail(BQ_EINVAL, "graph %u of %zu", graph, srv->graphs.size());
+    if (k && !edges_uv) return fail(BQ_EINVAL, "edges_uv is NULL");
+    if (!(eps > 0.0) || !(eps < 1e6)) return fail(BQ_EINVAL, "eps = %g must be positive", eps);
+    if (k >= (1ull << 32)) return fail(BQ_EINVAL, "k = %llu edges in one request", (unsigned long long)k);
+    auto r = std::make_shared<Request>();
+    r->t_submit = Clock::now();
+    r->graph = graph;
+    r->uv.assign(edges_uv, edges_uv + 2 * k);
+    r->k = k;
+    r->eps = eps;
+    r->seed = seed;
+    const int rc = plan_request(srv, *r);
+    if (rc != BQ_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) return fail(BQ_EINVAL, "server is stopping");
+        if (srv->pending.size() >= srv->cfg.max_pending)
+            return fail(BQ_EBUSY, "server queue is full (%u requests)", srv->cfg.max_pending);
+        r->id = srv->next_id++;
+        srv->pending.push_back(r);
+        srv->live.insert(r->id);
+        ++srv->submitted;
+        *request_id = r->id;
+    }
+    srv->cv_work.notify_one();
+    return BQ_OK;
+}
+
+int bq_server_wait(bq_server *srv, uint64_t request_id, double timeout_s, double *sc, uint32_t *counts,
+                   double *latency_ms) {
+    clear_error();
+    if (!srv) return fail(BQ_EINVAL, "server is NULL");
+    if (!(timeout_s >= 0.0)) return fail(BQ_EINVAL, "timeout %g", timeout_s);
+    RequestPtr r;
+    {
+        std::unique_lock<std::mutex> lk(srv->mu);
+        if (!srv->live.count(request_id))
+            return fail(BQ_EINVAL, "request %llu is unknown or was already returned", (unsigned long long)request_id);
+        const auto deadline =
+            Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(
+                               timeout_s > 1e7 ? 1e7 : timeout_s));
+        const bool ok = srv->cv_done.wait_until(lk, deadline, [&] { return srv->done.count(request_id) > 0; });
+        if (!ok) return fail(BQ_ETIMEOUT, "request %llu is not done", (unsigned long long)request_id);
+        auto it = srv->done.find(request_id);
+        r = it->second;
+        srv->done.erase(it);
+        srv->live.erase(request_id);
+    }
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    if (r->status != BQ_OK)
+        return fail(r->status, "request %llu: %s", (unsigned long long)request_id,
+                    r->error.empty() ? bq_strerror(r->status) : r->error.c_str());
+    if (sc && r->k) std::copy(r->sc.begin(), r->sc.end(), sc);
+    if (counts && r->k) std::copy(r->counts.begin(), r->counts.end(), counts);
+    return BQ_OK;
+}
+
+int bq_server_stats_get(bq_server *srv, bq_server_stats *out) {
+    clear_error();
+    if (!srv || !out) return fail(BQ_EINVAL, "server or out is NULL");
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        out->submitted = srv->submitted;
+        out->completed = srv->completed;
+        out->failed = srv->failed;
+        out->edges_completed = srv->edges_completed;
+        out->iterations = srv->iterations;
+        out->walk_steps = srv->walk_steps;
+        out->inflight = (uint32_t)srv->inflight.size();
+        out->pending = (uint32_t)srv->pending.size();
+        lat = srv->latencies_ms;
+    }
+    out->p50_ms = percentile(lat, 0.50);
+    out->p99_ms = percentile(lat, 0.99);
+    out->uptime_s = std::chrono::duration<double>(Clock::now() - srv->t_start).count();
+    return BQ_OK;
+}
+
+int bq_server_destroy(bq_server *srv) {
+    clear_error();
+    if (!srv) return BQ_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(srv->device);
+    cudaStreamSynchronize(srv->stream);
+    cudaStreamSynchronize(srv->copy_stream);
+    server_free(srv);
+    cudaSetDevice(prev);
+    return BQ_OK;
+}
+
+}  // extern "C"

@@ -123,6 +123,36 @@ def test_batch_cuda_graph_capture_and_replay(env):
     batch.close()
 
 
+def test_autotuners_pick_a_candidate_and_change_nothing(env):
+    bq, torch = env
+    from workloads import uniform_starts
+    old = bq.get_tuning()
+    try:
+        g = rmat(12, 8, seed=2)
+        graph = bq.Graph.from_csr(g)
+        starts = uniform_starts(g, 50000, 1)
+        st = u32(torch, starts)
+        best, ms = bq.autotune_walks(graph, 4, st, 16)
+        assert best in (1, 2, 4) and len(ms) == 3 and min(ms) > 0
+        assert bq.get_tuning()["walk_lanes"] == best
+        vis = bq.walk_batch(graph, 4, st, 16)
+        bq.sync()
+        assert np.array_equal(vis.cpu().numpy().view(np.uint32), oracle.walk_batch(g, 4, starts, 16))
+        rng = np.random.default_rng(5)
+        graphs, queries, host = make_queries(bq, torch, rng)
+        best, ms = bq.autotune_aesc(queries)
+        assert best in (2, 4, 8) and bq.get_tuning()["aesc_lanes"] == best
+        batch = bq.Batch(queries)
+        batch.run()
+        bq.sync()
+        for (counts, _), (hg, seed, uv, tau, nw) in zip(batch.outputs, host):
+            oc, _ = oracle.aesc_estimate(hg, seed, uv, tau, nw)
+            assert np.array_equal(counts.cpu().numpy().view(np.uint32), oc)
+        batch.close()
+    finally:
+        bq.set_tuning(**old)
+
+
 def test_batch_invalid_pairs(env):
     bq, torch = env
     from workloads import cycle

@@ -57,6 +57,18 @@ def test_argument_errors_without_device(lib):
     assert lib.bq_graph_destroy(None) == bq.OK
 
 
+def test_server_argument_errors_without_device(lib):
+    out = ctypes.c_void_p()
+    assert lib.bq_server_create(None, 0, None, ctypes.byref(out)) == bq.EINVAL
+    assert out.value is None
+    assert lib.bq_server_create(None, 1, None, None) == bq.EINVAL
+    rid = ctypes.c_uint64()
+    assert lib.bq_server_submit(None, 0, None, 0, 0.1, 0, ctypes.byref(rid)) == bq.EINVAL
+    assert lib.bq_server_wait(None, 1, 0.0, None, None, None) == bq.EINVAL
+    assert lib.bq_server_stats_get(None, None) == bq.EINVAL
+    assert lib.bq_server_destroy(None) == bq.OK
+
+
 def test_tuning_roundtrip_and_validation(lib):
     old = bq.get_tuning()
     try:
