@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aesc", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mix-count", type=int, default=256,
+                    help="batched workload: use the first N graphs of the 256-graph mix")
     ap.add_argument("--walk-lanes", type=int, default=None)
     ap.add_argument("--aggregate", type=int, default=None)
     return ap.parse_args()
@@ -67,6 +69,27 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def rank_seeds(rank: int):
+    """(walk seed, start-vertex seed) of a rank's own batch: every rank walks
+    a distinct batch of the same size (weak scaling, no data-path exchange)."""
+    return 2024 + rank, 21 + rank
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """The slowest rank's time (the job's time); x itself on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / seconds
 
 
 def measured_peaks():
@@ -343,8 +366,8 @@ def run_ours(args):
                       aggregate_visits=t["aggregate_visits"] if args.aggregate is None else args.aggregate)
 
     g = rmat20()
-    seed = 2024 + rank
-    starts = uniform_starts(g, N_WALKS, 21 + rank)
+    seed, start_seed = rank_seeds(rank)
+    starts = uniform_starts(g, N_WALKS, start_seed)
     graph = bq.Graph.from_csr(g)
     st = torch.from_numpy(starts.view(np.int32)).cuda()
     visits = torch.zeros(g.n, dtype=torch.int32, device="cuda")
@@ -377,11 +400,7 @@ def run_ours(args):
             dist.barrier()
         prof = bq.profile_read()
         bq.profile_enable(False)
-        total_ms = sum(a.elapsed_time(b) for a, b in evs)
-        if dist:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in evs), "cuda")
         return total_ms, prof
 
     autotune = None
@@ -392,7 +411,7 @@ def run_ours(args):
         total_ms, prof = timed(bq.MODE_BOUQUET, args.steps, args.warmup)
     ms_per_step = total_ms / args.steps
     steps_per_batch = N_WALKS * N_STEPS
-    value = world * steps_per_batch / (ms_per_step / 1e3)
+    value = whole_job_rate(world, steps_per_batch, ms_per_step / 1e3)
     walk_ms = prof["walk_ms"] / max(prof["walk_launches"], 1)
     group_ms = prof["group_ms"] / max(prof["group_launches"], 1)
     launches = prof["kernel_launches"]
@@ -424,12 +443,8 @@ def run_ours(args):
         for _ in range(args.steps):
             host_visits[:] = 0
             bq.walk_batch_host(graph, seed, host_starts, N_STEPS, visits=host_visits)
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * steps_per_batch / e2e_s, "unit": "walk-steps/s",
+        e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / args.steps, "cuda")
+        e2e = {"value": whole_job_rate(world, steps_per_batch, e2e_s), "unit": "walk-steps/s",
                "h2d_bytes_per_step": int(starts.nbytes + 4 * g.n),
                "d2h_bytes_per_step": int(4 * g.n), "ms_per_step": e2e_s * 1e3,
                "api": "bq_walk_batch with BQ_HOST_IO (pinned host buffers)"}
@@ -463,7 +478,7 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps,
             "clocks": clocks.summary(),
             "grouping_ms_per_step": group_ms,
-            "naive": {"value": world * steps_per_batch / (naive_ms / 1e3), "unit": "walk-steps/s",
+            "naive": {"value": whole_job_rate(world, steps_per_batch, naive_ms / 1e3), "unit": "walk-steps/s",
                       "ms_per_step": naive_ms,
                       "bouquet_speedup": naive_ms / ms_per_step},
             "aesc": aesc,
@@ -487,7 +502,7 @@ def run_batched(args):
     import paper_2410_14056_gb300 as bq
     from workloads import batched_mix
 
-    mix = batched_mix()
+    mix = batched_mix(count=max(1, args.mix_count))
     sched = bq.Schedule(POWERLAW_SCHEDULE["tau_scale"], POWERLAW_SCHEDULE["tau_add"],
                         POWERLAW_SCHEDULE["tau_max"], POWERLAW_SCHEDULE["n_scale"],
                         POWERLAW_SCHEDULE["n_min"], 0)
@@ -570,7 +585,7 @@ def run_batched(args):
         "metric": METRIC, "value": edges / (ms / 1e3), "unit": "edges/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batched_mix256_aesc", "graphs": len(mix), "vertices": n_total,
+        "config": {"workload": f"batched_mix{len(mix)}_aesc", "graphs": len(mix), "vertices": n_total,
                    "edges": edges, "walk_steps_per_step": steps_total,
                    "eps": "per graph from {0.05, 0.1, 0.2}", "plan": "scheduled",
                    "schedule": POWERLAW_SCHEDULE, "launch": "one persistent batch, CUDA-graph replay",
@@ -592,8 +607,8 @@ def run_batched(args):
 
 
 SERVE_LOADS = (0.5, 0.8, 1.0)
-SERVE_SATURATION_REQUESTS = 300
-SERVE_LOAD_SECONDS = 8.0
+SERVE_SATURATION_REQUESTS = 2000
+SERVE_LOAD_SECONDS = 3.0
 SERVE_SUBMITTERS = 8
 
 
@@ -710,7 +725,7 @@ def run_serving(args):
         loads = []
         for f in SERVE_LOADS:
             rate = f * sat_rps
-            count = int(min(3000, max(60, rate * SERVE_LOAD_SECONDS)))
+            count = int(min(20000, max(200, rate * SERVE_LOAD_SECONDS)))
             reqs = serving_requests(dgs, count, rng, gen)
             gaps = rng.exponential(1.0 / rate, count)
             arrivals = np.cumsum(gaps) - gaps[0]

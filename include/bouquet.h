@@ -331,21 +331,23 @@ typedef struct bq_server_stats {
 int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server_config *cfg, bq_server **out);
 
 /* Plan and queue a request: k vertex pairs (host, copied) of graph `graph`,
- * absolute error eps, walks keyed by seed.  The scheduled plan is computed on
- * the calling thread (host work of roughly 0.1 us per edge; several threads
- * may submit at once), then the call returns with *request_id without
- * waiting for the GPU.  Errors: BQ_ENOEDGE (a pair is not an edge),
- * BQ_EOVERFLOW (2 N tau >= 2^32 for an edge), BQ_EBUSY (max_pending requests
- * already queued), BQ_EINVAL (bad arguments, server stopping); no request is
- * created then. */
+ * absolute error eps, walks keyed by seed.  The scheduled plan (from the
+ * endpoint degrees) is computed on the calling thread, so several threads
+ * may submit at once; the call then returns with *request_id without waiting
+ * for the GPU.  Errors, with no request created: BQ_ENOEDGE (an id >= n,
+ * equal endpoints, or an endpoint without neighbours), BQ_EOVERFLOW (2 N tau
+ * >= 2^32 for an edge), BQ_EBUSY (max_pending requests already queued),
+ * BQ_EINVAL (bad arguments, server stopping).  Whether each pair is an edge
+ * is checked on the GPU; bq_server_wait reports a pair that is not. */
 int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, uint64_t k, double eps,
                      uint64_t seed, uint64_t *request_id);
 
 /* Wait up to timeout_s for a request, then copy its estimates (sc, k
  * doubles) and, if not NULL, counters (4k, layout of bq_aesc_estimate) and
  * latency (submit call -> results on the host, ms).  Returns the request's
- * status: BQ_OK, BQ_ENOMEM (it alone needs more than the device budget, or
- * the allocation failed), BQ_ECUDA; or BQ_ETIMEOUT (the request is still
+ * status: BQ_OK, BQ_ENOEDGE (a pair is not an edge; nothing is copied),
+ * BQ_ENOMEM (it alone needs more than the device budget, or the allocation
+ * failed), BQ_ECUDA; or BQ_ETIMEOUT (the request is still
  * running or queued: wait again).  Each request is returned once; waiting
  * for an unknown or already returned id is BQ_EINVAL. */
 int bq_server_wait(bq_server *srv, uint64_t request_id, double timeout_s, double *sc, uint32_t *counts,

@@ -97,12 +97,6 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
     }
 }
 
-// Last q with begin[q] <= t.  begin has k + 1 entries (begin[k] = total) and
-// is followed in memory by its coarse index (every kTaskStride-th entry).
-__device__ __forceinline__ uint64_t find_query(const uint64_t *__restrict__ begin, uint64_t k, uint64_t t) {
-    return task_edge(begin, begin + k + 1, k, t);
-}
-
 // Persistent counting kernel.  Task t -> query q, side = local & 1, chunk =
 // local >> 1; the chunk's walks are [chunk*32W, min(N, (chunk+1)*32W)).
 // Independent sampler: lane l takes the W consecutive walks chunk*32W + l*W +
@@ -112,16 +106,18 @@ __device__ __forceinline__ uint64_t find_query(const uint64_t *__restrict__ begi
 template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kThreads)
 aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *__restrict__ info,
-                  const uint64_t *__restrict__ begin, uint64_t k, uint64_t seed, Sampler smp,
-                  unsigned long long *__restrict__ next_task, uint32_t *__restrict__ counts) {
+                  const uint64_t *__restrict__ begin, const uint32_t *__restrict__ bucket, uint64_t k,
+                  uint64_t seed, Sampler smp, unsigned long long *__restrict__ next_task,
+                  uint32_t *__restrict__ counts) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t total = begin[k];
+    const uint32_t shift = bucket_shift(total, k);
     while (true) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(next_task, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= total) break;
-        const uint64_t q = find_query(begin, k, t);
+        const uint64_t q = task_edge(begin, bucket, k, total, shift, t);
         const QueryInfo qi = info[q];
         const uint64_t local = t - begin[q];
         const uint32_t side = (uint32_t)(local & 1);
@@ -224,7 +220,9 @@ int launch_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint6
     BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aesc_count_kernel<EL, W, COUPLED>, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
-    aesc_count_kernel<EL, W, COUPLED><<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, info, begin, k, seed, smp,
+    // the bucket table follows begin[k + 1] in the scratch buffer
+    const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
+    aesc_count_kernel<EL, W, COUPLED><<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, info, begin, bucket, k, seed, smp,
                                                                          next_task, counts);
     BQ_CUDA(cudaGetLastError());
     return BQ_OK;
@@ -257,10 +255,11 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
     int w = tuning_aesc_walks_per_lane();
     if (w != 2 && w != 4 && w != 8) w = 4;
     const uint32_t bouquet = 32u * (uint32_t)w;
-    // scratch: info[k] | begin[k + 1] coarse[ceil(k / stride)] | tasks[k] |
-    // next_task | (edges[2k] if all-edges)
+    if (k >= kMaxBucketEdges) return fail(BQ_EINVAL, "k = %llu edges in one estimate", (unsigned long long)k);
+    // scratch: info[k] | begin[k + 1] bucket[k + 1] | tasks[k] | next_task |
+    // (edges[2k] if all-edges)
     const size_t info_bytes = sizeof(QueryInfo) * k;
-    const size_t begin_bytes = sizeof(uint64_t) * (k + 1 + coarse_count(k));
+    const size_t begin_bytes = sizeof(uint64_t) * (k + 1) + ((sizeof(uint32_t) * bucket_count(k) + 7) & ~(size_t)7);
     const size_t task_bytes = sizeof(uint32_t) * ((k + 1) & ~1ull);
     const size_t edge_bytes = edges_uv ? 0 : sizeof(uint32_t) * 2 * k;
     const size_t bytes = info_bytes + begin_bytes + task_bytes + 16 + edge_bytes;
@@ -292,7 +291,8 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
         rc = scan_u32_to_u64(tasks, begin, k, s);
         if (rc == BQ_OK) {
             count_launches(1);
-            build_coarse_kernel<<<blocks_for(coarse_count(k), kThreads), kThreads, 0, s>>>(begin, k, begin + k + 1);
+            build_bucket_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(
+                begin, k, reinterpret_cast<uint32_t *>(begin + k + 1));
         }
     }
     if (rc == BQ_OK) {

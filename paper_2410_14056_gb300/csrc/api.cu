@@ -441,6 +441,28 @@ int64_t find_in_row(const bq_graph *g, uint32_t u, uint32_t v) {
 
 }  // namespace
 
+}  // extern "C"
+
+namespace bq {
+
+// Scheduled plan of one edge (s_e = 1/d_u + 1/d_v): tau = clamp(ceil(c ln(s_e /
+// eps)) + a, 1, tau_max) with the log term only when s_e > eps, N =
+// max(N_min, ceil(k s_e^2 / eps^2)).
+void plan_scheduled_edge(double s_e, double eps, const bq_schedule &sched, uint32_t &tau, double &nw) {
+    const double ratio = s_e / eps;
+    double tt = ratio > 1.0 ? ceil(sched.tau_scale * log(ratio)) : 0.0;
+    tt += (double)sched.tau_add;
+    if (tt < 1.0) tt = 1.0;
+    if (tt > (double)sched.tau_max) tt = (double)sched.tau_max;
+    tau = (uint32_t)tt;
+    nw = ceil(sched.n_scale * s_e * s_e / (eps * eps));
+    if (nw < (double)sched.n_min) nw = (double)sched.n_min;
+}
+
+}  // namespace bq
+
+extern "C" {
+
 int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, double delta, uint32_t plan_mode,
                  const bq_schedule *sched, uint32_t *tau, uint32_t *nwalks) {
     g_last_error[0] = 0;
@@ -498,14 +520,7 @@ int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, 
             const double half = (double)t - 0.5;
             nw = ceil(8.0 * half * half * s_e * s_e * log_term / (eps * eps));
         } else {
-            const double ratio = s_e / eps;
-            double tt = ratio > 1.0 ? ceil(sched->tau_scale * log(ratio)) : 0.0;
-            tt += (double)sched->tau_add;
-            if (tt < 1.0) tt = 1.0;
-            if (tt > (double)sched->tau_max) tt = (double)sched->tau_max;
-            t = (uint32_t)tt;
-            nw = ceil(sched->n_scale * s_e * s_e / (eps * eps));
-            if (nw < (double)sched->n_min) nw = (double)sched->n_min;
+            plan_scheduled_edge(s_e, eps, *sched, t, nw);
         }
         if (nw < 1.0) nw = 1.0;
         if (nw * 2.0 * (double)t >= 4294967296.0)

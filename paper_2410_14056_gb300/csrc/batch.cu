@@ -21,17 +21,11 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// The step of any compact layout (edge records, packed ids or plain CSR),
-// chosen per query; the branch is uniform within a task.
-__device__ __forceinline__ void gd_next(const GraphDesc &g, uint64_t j, uint32_t &cur, uint64_t &off,
-                                        uint32_t &deg) {
-    if (g.edge8) {
-        EdgesPacked{g.edge8, g.sh_off, g.sh_deg, g.mask_id, g.mask_off}.next(j, cur, off, deg);
-    } else if (g.pk) {
-        EdgesPackedIds{g.pk, g.rec8, g.pk_bits, g.pk_q, g.pk_mask}.next(j, cur, off, deg);
-    } else {
-        EdgesCsr8{g.nbrs, g.rec8}.next(j, cur, off, deg);
-    }
+// Resident blocks a counting kernel is compiled for: the gathers are latency
+// bound, so the common shapes keep 40 warps per SM (<= 48 registers).
+template <int W, bool COUPLED>
+constexpr int count_min_blocks() {
+    return (!COUPLED && W <= 4) ? 5 : 1;
 }
 
 __device__ __forceinline__ int64_t lower_bound_row(const uint32_t *__restrict__ nbrs, int64_t lo, int64_t hi,
@@ -116,10 +110,10 @@ __global__ void batch_prepare_kernel(const QueryDesc *__restrict__ qd, const uin
 // task index within the edge: side = local & 1, chunk = local >> 1), the walks
 // and counters of aesc_count_kernel; adds the warp's weighted hits to
 // d.counts[4 i + 2 side + {0, 1}] (i = the edge's index within its query).
-template <int W, bool COUPLED>
-__device__ __forceinline__ void run_bouquet_task(const QueryDesc &d, const BInfo &bi, uint64_t i, uint64_t local,
-                                                 const Sampler &smp, uint32_t lane) {
-    const GraphDesc g = d.g;
+template <typename EL, int W, bool COUPLED>
+__device__ __forceinline__ void run_bouquet_task_el(const EL &el, const int64_t *__restrict__ offsets,
+                                                    const QueryDesc &d, const BInfo &bi, uint64_t i,
+                                                    uint64_t local, const Sampler &smp, uint32_t lane) {
     const uint64_t seed = d.seed;
     const uint32_t side = (uint32_t)(local & 1);
     const uint64_t k0 = (local >> 1) * 32ull * W;
@@ -148,7 +142,7 @@ __device__ __forceinline__ void run_bouquet_task(const QueryDesc &d, const BInfo
     }
     uint64_t off0;
     uint32_t deg0;
-    start_record(g.offsets, start, off0, deg0);
+    start_record(offsets, start, off0, deg0);
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         cur[j] = start;
@@ -165,7 +159,7 @@ __device__ __forceinline__ void run_bouquet_task(const QueryDesc &d, const BInfo
             if (COUPLED) gs[j] += kGolden;
             if (deg[j]) {
                 const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
-                gd_next(g, off[j] + kk, cur[j], off[j], deg[j]);
+                el.next(off[j] + kk, cur[j], off[j], deg[j]);
                 hit_u += cur[j] == bi.u ? weight : 0u;
                 hit_v += cur[j] == bi.v ? weight : 0u;
             }
@@ -183,20 +177,39 @@ __device__ __forceinline__ void run_bouquet_task(const QueryDesc &d, const BInfo
     }
 }
 
+// The query's layout is chosen once per task, so each step loop is
+// specialised for one layout.
+template <int W, bool COUPLED>
+__device__ __forceinline__ void run_bouquet_task(const QueryDesc &d, const BInfo &bi, uint64_t i, uint64_t local,
+                                                 const Sampler &smp, uint32_t lane) {
+    const GraphDesc &g = d.g;
+    if (g.edge8) {
+        const EdgesPacked el{g.edge8, g.sh_off, g.sh_deg, g.mask_id, g.mask_off};
+        run_bouquet_task_el<EdgesPacked, W, COUPLED>(el, g.offsets, d, bi, i, local, smp, lane);
+    } else if (g.pk) {
+        const EdgesPackedIds el{g.pk, g.rec8, g.pk_bits, g.pk_q, g.pk_mask};
+        run_bouquet_task_el<EdgesPackedIds, W, COUPLED>(el, g.offsets, d, bi, i, local, smp, lane);
+    } else {
+        const EdgesCsr8 el{g.nbrs, g.rec8};
+        run_bouquet_task_el<EdgesCsr8, W, COUPLED>(el, g.offsets, d, bi, i, local, smp, lane);
+    }
+}
+
 // Persistent counting kernel over the tasks of all queries of a batch.
 template <int W, bool COUPLED>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, count_min_blocks<W, COUPLED>())
 batch_count_kernel(const QueryDesc *__restrict__ qd, const BInfo *__restrict__ info,
-                   const uint64_t *__restrict__ begin, const uint64_t *__restrict__ coarse, uint64_t total_edges,
+                   const uint64_t *__restrict__ begin, const uint32_t *__restrict__ bucket, uint64_t total_edges,
                    Sampler smp, unsigned long long *__restrict__ next_task) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t total = begin[total_edges];
+    const uint32_t shift = bucket_shift(total, total_edges);
     while (true) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(next_task, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= total) break;
-        const uint64_t e = task_edge(begin, coarse, total_edges, t);
+        const uint64_t e = task_edge(begin, bucket, total_edges, total, shift, t);
         const BInfo bi = info[e];
         const QueryDesc &d = qd[bi.query];
         run_bouquet_task<W, COUPLED>(d, bi, e - d.ebase, t - begin[e], smp, lane);
@@ -206,7 +219,7 @@ batch_count_kernel(const QueryDesc *__restrict__ qd, const BInfo *__restrict__ i
 // The server's iteration: windows of several requests' tasks.  Item t ->
 // request (items[].item_base) -> its task -> its edge.
 template <int W, bool COUPLED>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, count_min_blocks<W, COUPLED>())
 serve_count_kernel(const ServeItem *__restrict__ items, uint32_t n_items, uint64_t total_items, Sampler smp,
                    unsigned long long *__restrict__ next_item) {
     const uint32_t lane = threadIdx.x & 31;
@@ -269,7 +282,7 @@ struct bq_batch {
     bq::BInfo *d_info = nullptr;
     uint32_t *d_tasks = nullptr;
     uint64_t *d_begin = nullptr;
-    uint64_t *d_coarse = nullptr;
+    uint32_t *d_bucket = nullptr;
     unsigned long long *d_next = nullptr;
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
@@ -293,10 +306,10 @@ int batch_occupancy(int *grid) {
 template <int W>
 void launch_batch_count(const bq_batch *b, cudaStream_t s) {
     if (b->smp.kind == 1)
-        batch_count_kernel<W, true><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->d_coarse,
+        batch_count_kernel<W, true><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->d_bucket,
                                                                  b->edges, b->smp, b->d_next);
     else
-        batch_count_kernel<W, false><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->d_coarse,
+        batch_count_kernel<W, false><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_info, b->d_begin, b->d_bucket,
                                                                   b->edges, b->smp, b->d_next);
 }
 
@@ -307,7 +320,7 @@ void free_batch(bq_batch *b) {
     cudaFree(b->d_info);
     cudaFree(b->d_tasks);
     cudaFree(b->d_begin);
-    cudaFree(b->d_coarse);
+    cudaFree(b->d_bucket);
     cudaFree(b->d_next);
     cudaFree(b->d_ws);
     delete b;
@@ -379,6 +392,10 @@ int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_s
     b->edges = total;
     b->smp = smp;
     b->status = status;
+    if (total >= kMaxBucketEdges) {
+        delete b;
+        return fail(BQ_EINVAL, "a batch of %llu edges (at most 2^32 - 2)", (unsigned long long)total);
+    }
     b->lanes = tuning_aesc_walks_per_lane();
     if (b->lanes != 2 && b->lanes != 8) b->lanes = 4;
     b->ws_bytes = scan_u32_to_u64_ws_bytes(total);
@@ -387,7 +404,7 @@ int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_s
     if (e == cudaSuccess) e = cudaMalloc(&b->d_info, sizeof(BInfo) * (total ? total : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tasks, sizeof(uint32_t) * (total ? total : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_begin, sizeof(uint64_t) * (total + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_coarse, sizeof(uint64_t) * (coarse_count(total) + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bucket, sizeof(uint32_t) * bucket_count(total));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned long long));
     if (e == cudaSuccess && b->ws_bytes) e = cudaMalloc(&b->d_ws, b->ws_bytes);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_qd, qd.data(), sizeof(QueryDesc) * n_queries, cudaMemcpyHostToDevice);
@@ -429,8 +446,8 @@ int bq_batch_run(bq_batch *b, void *stream) {
         rc = scan_u32_to_u64_ws(b->d_tasks, b->d_begin, b->edges, b->d_ws, b->ws_bytes, s);
         if (rc == BQ_OK) {
             count_launches(1);
-            build_coarse_kernel<<<blocks_for(coarse_count(b->edges), kThreads), kThreads, 0, s>>>(
-                b->d_begin, b->edges, b->d_coarse);
+            build_bucket_kernel<<<blocks_for(b->edges, kThreads), kThreads, 0, s>>>(b->d_begin, b->edges,
+                                                                                   b->d_bucket);
         }
     }
     if (rc == BQ_OK) {

@@ -180,12 +180,14 @@ struct EdgesWide {
 };
 
 // Task -> edge lookup.  `begin` is the exclusive prefix of per-edge task
-// counts (count + 1 entries); `coarse[i] = begin[i * kTaskStride]`.  The
-// search runs over the coarse array (small enough to stay in L2), then over
-// at most kTaskStride contiguous entries of `begin`, instead of a binary search
-// whose lower levels touch random lines of a large array.
-constexpr uint32_t kTaskStride = 64;
-
+// counts (count + 1 entries, begin[count] = total tasks).  A direct-mapped
+// bucket table indexed by task number replaces a binary search over the whole
+// prefix (whose ~log2(count) dependent loads cost more than a short task's
+// walks): with shift s = the least s such that (total >> s) <= count,
+// bucket[b] = the edge holding task b << s, for the b with b << s < total (at
+// most count + 1 entries).  Task t lies in an edge between bucket[t >> s] and
+// bucket[(t >> s) + 1], a range that is about one edge on average, searched
+// over contiguous entries of `begin`.
 __device__ __forceinline__ uint64_t last_le_u64(const uint64_t *__restrict__ a, uint64_t lo, uint64_t hi,
                                                 uint64_t x) {
     // largest i in [lo, hi) with a[i] <= x, given a[lo] <= x
@@ -197,26 +199,41 @@ __device__ __forceinline__ uint64_t last_le_u64(const uint64_t *__restrict__ a, 
     return lo;
 }
 
-__device__ __forceinline__ uint64_t task_edge(const uint64_t *__restrict__ begin, const uint64_t *__restrict__ coarse,
-                                              uint64_t count, uint64_t t) {
-    const uint64_t n_coarse = (count + kTaskStride - 1) / kTaskStride;
-    const uint64_t c = last_le_u64(coarse, 0, n_coarse, t);
-    const uint64_t lo = c * kTaskStride;
-    const uint64_t hi = lo + kTaskStride < count ? lo + kTaskStride : count;
+__host__ __device__ __forceinline__ uint32_t bucket_shift(uint64_t total, uint64_t count) {
+    // least s with (total >> s) <= count: 2^s > total / (count + 1), i.e.
+    // s = ceil(log2(q + 1)) for q = floor(total / (count + 1))
+    const uint64_t q = total / (count + 1);
+    uint32_t s = 0;
+    while ((q >> s) != 0) ++s;
+    return s;
+}
+
+__device__ __forceinline__ uint64_t task_edge(const uint64_t *__restrict__ begin, const uint32_t *__restrict__ bucket,
+                                              uint64_t count, uint64_t total, uint32_t shift, uint64_t t) {
+    const uint64_t b = t >> shift;
+    const uint64_t lo = bucket[b];
+    const uint64_t hi = ((b + 1) << shift) < total ? (uint64_t)bucket[b + 1] + 1 : count;
     return last_le_u64(begin, lo, hi, t);
 }
 
-// coarse[i] = begin[i * kTaskStride] for i < ceil(count / kTaskStride).
+// bucket[b] = e for every b with b << shift in [begin[e], begin[e + 1]).
 // (A template so that each translation unit gets its own instance.)
 template <int kUnused = 0>
-__global__ void build_coarse_kernel(const uint64_t *__restrict__ begin, uint64_t count, uint64_t *__restrict__ coarse) {
-    const uint64_t n_coarse = (count + kTaskStride - 1) / kTaskStride;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_coarse;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        coarse[i] = begin[i * kTaskStride];
+__global__ void build_bucket_kernel(const uint64_t *__restrict__ begin, uint64_t count, uint32_t *__restrict__ bucket) {
+    const uint64_t total = begin[count];
+    const uint32_t shift = bucket_shift(total, count);
+    const uint64_t step = 1ull << shift;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < count;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t lo = begin[e], hi = begin[e + 1];
+        if (lo == hi) continue;
+        for (uint64_t b = (lo + step - 1) >> shift; b <= ((hi - 1) >> shift); ++b) bucket[b] = (uint32_t)e;
+    }
 }
 
-inline uint64_t coarse_count(uint64_t count) { return (count + kTaskStride - 1) / kTaskStride; }
+// Entries of the bucket table for `count` edges; edge indices are 32-bit.
+inline uint64_t bucket_count(uint64_t count) { return count + 1; }
+constexpr uint64_t kMaxBucketEdges = 0xffffffffull;
 
 // Call f with the layout the graph was built with.
 template <typename F>

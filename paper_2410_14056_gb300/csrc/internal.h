@@ -173,6 +173,8 @@ namespace bq {
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t err, const char *what);
 void clear_error();  // empties this thread's bq_last_error() message
+// scheduled plan of one edge (api.cu; shared by bq_aesc_plan and the server)
+void plan_scheduled_edge(double s_e, double eps, const bq_schedule &sched, uint32_t &tau, double &nw);
 #define BQ_CUDA(call)                                            \
     do {                                                         \
         cudaError_t _e = (call);                                 \

@@ -10,6 +10,7 @@
 // the worker sees completion through an event, releases its memory and wakes
 // its waiter.  Newly submitted requests join at the next iteration.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -30,43 +31,82 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Device layout of a request with k edges (byte offsets; 256-aligned
+// sections).  Inputs, uploaded by one copy: descriptor | uv[2k] | tau[k] |
+// nwalks[k].  Work: info[k] | tasks[k] | begin[k + 1] | scan workspace.
+// Outputs, read back by one copy: status word (16 B) | counts[4k] | sc[k].
+struct Layout {
+    size_t qd, uv, tau, nw, in_bytes;
+    size_t info, tasks, begin, ws, ws_bytes;
+    size_t out, counts, sc, out_bytes;
+    size_t total;
+};
+
+Layout layout_of(uint64_t k) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    Layout L;
+    size_t p = 0;
+    L.qd = p;
+    p += up(sizeof(QueryDesc));
+    L.uv = p;
+    p += up(8 * k);
+    L.tau = p;
+    p += up(4 * k);
+    L.nw = p;
+    p += up(4 * k);
+    L.in_bytes = p;
+    L.info = p;
+    p += up(sizeof(BInfo) * k);
+    L.tasks = p;
+    p += up(4 * k);
+    L.begin = p;
+    p += up(8 * (k + 1));
+    L.ws = p;
+    L.ws_bytes = serve_scan_ws_bytes(k);
+    p += up(L.ws_bytes);
+    L.out = p;
+    L.counts = p + 16;
+    L.sc = L.counts + 16 * k;
+    L.out_bytes = 16 + 24 * k;
+    p += up(L.out_bytes);
+    L.total = p;
+    return L;
+}
+
 struct Request {
     uint64_t id = 0;
     uint32_t graph = 0;
-    std::vector<uint32_t> uv;
     uint64_t k = 0;
     double eps = 0.1;
     uint64_t seed = 0;
+    Layout L;
     Clock::time_point t_submit, t_done;
     int status = BQ_OK;
     std::string error;  // message of a failed request
-    // plan (host)
-    std::vector<uint32_t> tau, nwalks;
+    // host image of the input sections (pairs and plan, filled on the
+    // submitting thread; the descriptor is written at admission)
+    std::vector<char> in;
     double walk_steps = 0;
     uint64_t tasks_total = 0, tasks_launched = 0;
     // device
     char *dbuf = nullptr;
     size_t dbytes = 0;
-    QueryDesc *d_qd = nullptr;
-    BInfo *d_info = nullptr;
-    uint64_t *d_begin = nullptr;
-    uint32_t *d_counts = nullptr;
-    double *d_sc = nullptr;
     cudaEvent_t done_ev = nullptr;
     bool finalizing = false;
-    // results (host)
-    std::vector<double> sc;
-    std::vector<uint32_t> counts;
+    // host image of the output sections
+    std::vector<char> out;
+
+    QueryDesc *d_qd() const { return reinterpret_cast<QueryDesc *>(dbuf + L.qd); }
+    BInfo *d_info() const { return reinterpret_cast<BInfo *>(dbuf + L.info); }
+    uint64_t *d_begin() const { return reinterpret_cast<uint64_t *>(dbuf + L.begin); }
+    uint32_t *h_uv() { return reinterpret_cast<uint32_t *>(in.data() + L.uv); }
+    uint32_t *h_tau() { return reinterpret_cast<uint32_t *>(in.data() + L.tau); }
+    uint32_t *h_nw() { return reinterpret_cast<uint32_t *>(in.data() + L.nw); }
 };
 
 using RequestPtr = std::shared_ptr<Request>;
 
-// Device bytes of a request with k edges (the layout carved in admit()).
-size_t request_bytes(uint64_t k) {
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return up(sizeof(QueryDesc)) + up(8 * k) + up(4 * k) + up(4 * k) + up(16 * k) + up(8 * k) +
-           up(sizeof(BInfo) * k) + up(4 * k) + up(8 * (k + 1)) + up(serve_scan_ws_bytes(k)) + 256;
-}
+size_t request_bytes(uint64_t k) { return layout_of(k).total; }
 
 }  // namespace
 }  // namespace bq
@@ -111,85 +151,82 @@ namespace {
 
 uint32_t bouquet_of(const bq_server *srv) { return 32u * (uint32_t)srv->lanes; }
 
-// Plan one request on the host (the submitting thread, no lock): tau and N
-// per edge, the number of bouquet tasks and of walk steps.
-int plan_request(bq_server *srv, Request &r) {
-    bq_graph *g = srv->graphs[r.graph];
-    r.tau.assign(r.k, 0);
-    r.nwalks.assign(r.k, 0);
-    if (r.k) {
-        bq_schedule sched{srv->cfg.tau_scale, srv->cfg.tau_add, srv->cfg.tau_max, srv->cfg.n_scale, srv->cfg.n_min, 0};
-        const int rc = bq_aesc_plan(g, r.uv.data(), r.k, r.eps, 0.01, BQ_PLAN_SCHEDULED, &sched, r.tau.data(),
-                                    r.nwalks.data());
-        if (rc) return rc;
-    }
+// Plan one request on the host (the submitting thread, no lock): copy the
+// pairs into the request's input image and fill tau and N per edge from the
+// endpoint degrees (the scheduled plan), count its bouquet tasks and walk
+// steps.  Pairs with an id out of range, equal endpoints or an endpoint of
+// degree 0 are rejected here; whether a pair is an edge is checked on the
+// GPU (the prepare kernel's row search), whose status comes back with the
+// results.
+int plan_request(bq_server *srv, Request &r, const uint32_t *edges_uv) {
+    const bq_graph *g = srv->graphs[r.graph];
+    r.L = layout_of(r.k);
+    r.in.assign(r.L.in_bytes, 0);
+    if (r.k) memcpy(r.h_uv(), edges_uv, 8 * r.k);
+    const bq_schedule sched{srv->cfg.tau_scale, srv->cfg.tau_add, srv->cfg.tau_max,
+                            srv->cfg.n_scale,   srv->cfg.n_min,   0};
+    const int64_t *off = g->h_offsets.data();
     const uint32_t bouquet = bouquet_of(srv);
+    uint32_t *tau = r.h_tau(), *nw = r.h_nw();
     r.tasks_total = 0;
     r.walk_steps = 0;
     for (uint64_t i = 0; i < r.k; ++i) {
-        if (2ull * r.nwalks[i] * r.tau[i] >= (1ull << 32))
-            return fail(BQ_EOVERFLOW, "server: edge %llu: 2 N tau = %llu does not fit a uint32 counter",
-                        (unsigned long long)i, 2ull * r.nwalks[i] * r.tau[i]);
-        r.tasks_total += 2ull * ((r.nwalks[i] + bouquet - 1) / bouquet);
-        r.walk_steps += 2.0 * (double)r.nwalks[i] * (double)r.tau[i];
+        const uint32_t a = edges_uv[2 * i], b = edges_uv[2 * i + 1];
+        if (a >= g->n || b >= g->n || a == b)
+            return fail(BQ_ENOEDGE, "pair %llu: (%u, %u) is not an edge", (unsigned long long)i, a, b);
+        const int64_t da = off[a + 1] - off[a], db = off[b + 1] - off[b];
+        if (da == 0 || db == 0)
+            return fail(BQ_ENOEDGE, "pair %llu: (%u, %u) is not an edge", (unsigned long long)i, a, b);
+        const double s_e = 1.0 / (double)da + 1.0 / (double)db;
+        uint32_t t = 1;
+        double n = 0.0;
+        plan_scheduled_edge(s_e, r.eps, sched, t, n);
+        if (n < 1.0) n = 1.0;
+        if (n * 2.0 * (double)t >= 4294967296.0)
+            return fail(BQ_EOVERFLOW, "pair %llu: 2 N tau = %.3g reaches 2^32", (unsigned long long)i,
+                        n * 2.0 * (double)t);
+        tau[i] = t;
+        nw[i] = (uint32_t)n;
+        r.tasks_total += 2ull * ((nw[i] + bouquet - 1) / bouquet);
+        r.walk_steps += 2.0 * (double)nw[i] * (double)t;
     }
     return BQ_OK;
 }
 
 // Allocate, upload and prepare one planned request (worker thread, no lock).
 int admit(bq_server *srv, Request &r) {
-    bq_graph *g = srv->graphs[r.graph];
-    const uint32_t bouquet = bouquet_of(srv);
+    const bq_graph *g = srv->graphs[r.graph];
     cudaStream_t s = srv->stream;
     cudaError_t e = cudaMallocAsync((void **)&r.dbuf, r.dbytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        r.dbuf = nullptr;
         return fail(BQ_ENOMEM, "server: cannot allocate %zu bytes for a request", r.dbytes);
     }
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    char *p = r.dbuf;
-    r.d_qd = (QueryDesc *)p;
-    p += up(sizeof(QueryDesc));
-    uint32_t *d_uv = (uint32_t *)p;
-    p += up(8 * r.k);
-    uint32_t *d_tau = (uint32_t *)p;
-    p += up(4 * r.k);
-    uint32_t *d_nw = (uint32_t *)p;
-    p += up(4 * r.k);
-    r.d_counts = (uint32_t *)p;
-    p += up(16 * r.k);
-    r.d_sc = (double *)p;
-    p += up(8 * r.k);
-    r.d_info = (BInfo *)p;
-    p += up(sizeof(BInfo) * r.k);
-    uint32_t *d_tasks = (uint32_t *)p;
-    p += up(4 * r.k);
-    r.d_begin = (uint64_t *)p;
-    p += up(8 * (r.k + 1));
-    void *ws = p;
-    const size_t ws_bytes = serve_scan_ws_bytes(r.k);
-
     QueryDesc qd;
     qd.g = graph_desc(g);
     qd.seed = r.seed;
-    qd.uv = d_uv;
-    qd.tau = d_tau;
-    qd.nwalks = d_nw;
-    qd.counts = r.d_counts;
-    qd.sc = r.d_sc;
+    qd.uv = reinterpret_cast<const uint32_t *>(r.dbuf + r.L.uv);
+    qd.tau = reinterpret_cast<const uint32_t *>(r.dbuf + r.L.tau);
+    qd.nwalks = reinterpret_cast<const uint32_t *>(r.dbuf + r.L.nw);
+    qd.counts = reinterpret_cast<uint32_t *>(r.dbuf + r.L.counts);
+    qd.sc = reinterpret_cast<double *>(r.dbuf + r.L.sc);
     qd.k = r.k;
     qd.ebase = 0;
-    e = cudaMemcpyAsync(r.d_qd, &qd, sizeof(qd), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && r.k) e = cudaMemcpyAsync(d_uv, r.uv.data(), 8 * r.k, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && r.k) e = cudaMemcpyAsync(d_tau, r.tau.data(), 4 * r.k, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && r.k) e = cudaMemcpyAsync(d_nw, r.nwalks.data(), 4 * r.k, cudaMemcpyHostToDevice, s);
+    memcpy(r.in.data() + r.L.qd, &qd, sizeof(qd));
+    // pageable source: the call returns once the image is staged
+    e = cudaMemcpyAsync(r.dbuf, r.in.data(), r.L.in_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r.dbuf + r.L.out, 0, 16, s);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "server: request upload");
-    return serve_prepare(r.d_qd, r.k, bouquet, r.d_info, d_tasks, r.d_begin, ws, ws_bytes, srv->status, s);
+    std::vector<char>().swap(r.in);
+    return serve_prepare(r.d_qd(), r.k, bouquet_of(srv), r.d_info(), reinterpret_cast<uint32_t *>(r.dbuf + r.L.tasks),
+                         r.d_begin(), r.dbuf + r.L.ws, r.L.ws_bytes, reinterpret_cast<uint32_t *>(r.dbuf + r.L.out),
+                         s);
 }
 
 void start_finalize(bq_server *srv, Request &r) {
-    serve_finalize(r.d_qd, r.d_info, r.k, srv->stream);
+    serve_finalize(r.d_qd(), r.d_info(), r.k, srv->stream);
     cudaEventRecord(r.done_ev, srv->stream);
     r.finalizing = true;
 }
@@ -226,9 +263,9 @@ bool iterate(bq_server *srv) {
     for (size_t i = 0; i < active.size(); ++i) {
         if (!take[i]) continue;
         Request &r = *active[i];
-        items[n].qd = r.d_qd;
-        items[n].info = r.d_info;
-        items[n].begin = r.d_begin;
+        items[n].qd = r.d_qd();
+        items[n].info = r.d_info();
+        items[n].begin = r.d_begin();
         items[n].k = r.k;
         items[n].task_lo = r.tasks_launched;
         items[n].item_base = base;
@@ -255,14 +292,24 @@ void poll_completions(bq_server *srv, bool block) {
         if (!r->finalizing) continue;
         cudaError_t q = block && finished.empty() ? cudaEventSynchronize(r->done_ev) : cudaEventQuery(r->done_ev);
         if (q == cudaErrorNotReady) continue;
-        r->sc.resize(r->k);
-        r->counts.resize(4 * r->k);
-        if (r->k) {
-            cudaMemcpyAsync(r->sc.data(), r->d_sc, 8 * r->k, cudaMemcpyDeviceToHost, srv->copy_stream);
-            cudaMemcpyAsync(r->counts.data(), r->d_counts, 16 * r->k, cudaMemcpyDeviceToHost, srv->copy_stream);
+        r->out.resize(r->L.out_bytes);
+        cudaError_t e = q;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->out.data(), r->dbuf + r->L.out, r->L.out_bytes, cudaMemcpyDeviceToHost,
+                                srv->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(srv->copy_stream);
+        uint32_t bits = 0;
+        if (e == cudaSuccess) memcpy(&bits, r->out.data(), sizeof(bits));
+        if (e != cudaSuccess) {
+            r->status = BQ_ECUDA;
+            r->error = cudaGetErrorString(e);
+        } else if (bits & kStatusNoEdge) {
+            r->status = BQ_ENOEDGE;
+            r->error = "a queried pair is not an edge";
+        } else if (bits) {
+            r->status = BQ_EOVERFLOW;
+            r->error = "a plan entry is out of range";
         }
-        cudaStreamSynchronize(srv->copy_stream);
-        r->status = q == cudaSuccess ? BQ_OK : BQ_ECUDA;
         finished.push_back(r);
     }
     if (finished.empty()) return;
@@ -275,9 +322,13 @@ void poll_completions(bq_server *srv, bool block) {
         r->done_ev = nullptr;
         srv->held_bytes -= r->dbytes;
         r->t_done = now;
-        ++srv->completed;
-        srv->edges_completed += r->k;
-        srv->walk_steps += r->walk_steps;
+        if (r->status != BQ_OK) {
+            ++srv->failed;
+        } else {
+            ++srv->completed;
+            srv->edges_completed += r->k;
+            srv->walk_steps += r->walk_steps;
+        }
         srv->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
         srv->inflight.erase(std::find(srv->inflight.begin(), srv->inflight.end(), r));
         srv->done[r->id] = r;
@@ -472,11 +523,10 @@ int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, u
     auto r = std::make_shared<Request>();
     r->t_submit = Clock::now();
     r->graph = graph;
-    r->uv.assign(edges_uv, edges_uv + 2 * k);
     r->k = k;
     r->eps = eps;
     r->seed = seed;
-    const int rc = plan_request(srv, *r);
+    const int rc = plan_request(srv, *r, edges_uv);
     if (rc != BQ_OK) return rc;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
@@ -517,8 +567,8 @@ int bq_server_wait(bq_server *srv, uint64_t request_id, double timeout_s, double
     if (r->status != BQ_OK)
         return fail(r->status, "request %llu: %s", (unsigned long long)request_id,
                     r->error.empty() ? bq_strerror(r->status) : r->error.c_str());
-    if (sc && r->k) std::copy(r->sc.begin(), r->sc.end(), sc);
-    if (counts && r->k) std::copy(r->counts.begin(), r->counts.end(), counts);
+    if (sc && r->k) memcpy(sc, r->out.data() + (r->L.sc - r->L.out), 8 * r->k);
+    if (counts && r->k) memcpy(counts, r->out.data() + (r->L.counts - r->L.out), 16 * r->k);
     return BQ_OK;
 }
 

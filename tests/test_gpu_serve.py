@@ -105,20 +105,25 @@ def test_empty_and_failed_requests(env):
         g0 = hosts[0]
         row0 = set(g0.nbrs[g0.offsets[0]:g0.offsets[1]].tolist())
         non_nbr = next(x for x in range(1, g0.n) if x not in row0)
-        for bad in ([[0, 0]], [[0, 1], [g0.n, 1]], [uv_ok[0].tolist(), [0, non_nbr]]):
+        for bad in ([[0, 0]], [[0, 1], [g0.n, 1]]):
             with pytest.raises(bq.BouquetError) as ei:
                 srv.submit(0, np.array(bad, np.uint32), 0.1, 1)
             assert ei.value.code == bq.ENOEDGE
+        # a pair of vertices with neighbours that is not an edge: found on the GPU
+        not_edge = srv.submit(0, np.array([uv_ok[0].tolist(), [0, non_nbr]], np.uint32), 0.1, 1)
         ok = srv.submit(0, uv_ok, 0.2, 3)
         sc, _, _ = srv.wait(empty, timeout=60)
         assert sc.size == 0
+        with pytest.raises(bq.BouquetError) as ei:
+            srv.wait(not_edge, timeout=60)
+        assert ei.value.code == bq.ENOEDGE
         sc, counts, _ = srv.wait(ok, timeout=60, counts=True)
         check_against_oracle(hosts, (0, uv_ok, 0.2, 3), sc, counts)
         with pytest.raises(bq.BouquetError) as ei:
             srv.wait(ok, timeout=0)  # each request is returned once
         assert ei.value.code == bq.EINVAL
         st = srv.stats()
-        assert st["completed"] == 2 and st["failed"] == 0 and st["submitted"] == 2
+        assert st["completed"] == 2 and st["failed"] == 1 and st["submitted"] == 3
         for args in [(7, uv_ok, 0.1, 0), (0, uv_ok, 0.0, 0), (0, uv_ok, float("nan"), 0)]:
             with pytest.raises(bq.BouquetError) as ei:
                 srv.submit(*args)
