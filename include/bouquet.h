@@ -400,7 +400,14 @@ typedef struct bq_tuning {
     uint32_t l2_hints;         /* 1: the hub walk kernel reads the graph arrays
                                   with an L2 evict-last policy and the grouped
                                   walk list with evict-first (0 = plain loads) */
-    uint32_t reserved[2];
+    uint32_t aesc_hub;         /* 1: AESC estimates on graphs with a hub table
+                                  and a layout with separate vertex records
+                                  serve the hubs' records from shared memory
+                                  (12 bytes per slot); 0 (default): plain
+                                  kernel, which measured faster (the table's
+                                  shared memory takes the L1 capacity that a
+                                  bouquet's walks reuse) */
+    uint32_t reserved;
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

@@ -103,12 +103,53 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
 // j, so walk pairs (2i, 2i+1) share one Philox block.  Coupled sampler: slot
 // j of lane l is walk chunk*32W + j*32 + l, so a coupling group of 32 fills
 // one lockstep slot.
-template <typename EL, int W, bool COUPLED>
-__global__ void __launch_bounds__(kThreads)
+//
+// HUB: the graph's hub table (the highest-degree vertex of each of 2^hub_bits
+// hash slots) is copied into shared memory with the hubs' vertex records, and
+// a step that lands on a hub reads the record there instead of from L2/HBM.
+// The grid is then 2 blocks of kHubAescThreads per SM (40 warps, the same as
+// the plain kernel), each block with its own 12 B-per-slot copy of the table.
+constexpr int kHubAescThreads = 640;
+
+template <bool HUB>
+constexpr int count_threads() {
+    return HUB ? kHubAescThreads : kThreads;
+}
+
+// Resident blocks per SM the common shapes are compiled for: 40 warps
+// (<= 48 registers) for both variants; the wider and coupled shapes keep
+// their registers instead.
+template <int W, bool COUPLED, bool HUB>
+constexpr int count_min_blocks() {
+    return (!COUPLED && W <= 4) ? (HUB ? 2 : 5) : 1;
+}
+
+template <typename EL, int W, bool COUPLED, bool HUB>
+__global__ void __launch_bounds__(count_threads<HUB>(), count_min_blocks<W, COUPLED, HUB>())
 aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *__restrict__ info,
                   const uint64_t *__restrict__ begin, const uint32_t *__restrict__ bucket, uint64_t k,
                   uint64_t seed, Sampler smp, unsigned long long *__restrict__ next_task,
-                  uint32_t *__restrict__ counts) {
+                  uint32_t *__restrict__ counts, const uint32_t *__restrict__ hub_tag, uint32_t hub_bits) {
+    extern __shared__ __align__(16) unsigned char hub_smem[];
+    uint2 *s_rec = reinterpret_cast<uint2 *>(hub_smem);
+    const uint32_t slots = HUB ? (1u << hub_bits) : 0u;
+    uint32_t *s_tag = reinterpret_cast<uint32_t *>(s_rec + slots);
+    const uint32_t hub_shift = 32 - hub_bits;
+    if constexpr (HUB) {
+        for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+            const uint32_t t = hub_tag[i];
+            uint2 r = make_uint2(0u, 0u);
+            if (t != kNoHub) {
+                uint64_t o;
+                uint32_t d;
+                el.rec_of(t, o, d);
+                r = make_uint2((uint32_t)o, d);
+            }
+            s_tag[i] = t;
+            s_rec[i] = r;
+        }
+        __syncthreads();
+    }
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t total = begin[k];
     const uint32_t shift = bucket_shift(total, k);
@@ -161,15 +202,52 @@ aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *_
         uint32_t hit_u = 0, hit_v = 0;
         for (uint32_t l = 1; l <= qi.tau; ++l) {
             const uint32_t weight = l < qi.tau ? 2u : 1u;
+            if constexpr (HUB) {
+                // the W walks' id loads, then their record loads, each issued
+                // back to back so that a lane keeps W gathers in flight
+                bool mv[W], hub[W];
+                uint32_t slot[W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                st[j] += kGolden;
-                if (COUPLED) gs[j] += kGolden;
-                if (deg[j]) {
-                    const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
-                    el.next(off[j] + kk, cur[j], off[j], deg[j]);
-                    hit_u += cur[j] == qi.u ? weight : 0u;
-                    hit_v += cur[j] == qi.v ? weight : 0u;
+                for (int j = 0; j < W; ++j) {
+                    st[j] += kGolden;
+                    if (COUPLED) gs[j] += kGolden;
+                    mv[j] = deg[j] != 0;
+                    if (mv[j]) {
+                        const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                        cur[j] = el.id(off[j] + kk);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    slot[j] = (cur[j] * kHubHash) >> hub_shift;
+                    hub[j] = mv[j] && s_tag[slot[j]] == cur[j];
+                }
+#pragma unroll
+                for (int j = 0; j < W; ++j)
+                    if (mv[j] && !hub[j]) el.rec_of(cur[j], off[j], deg[j]);
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    if (hub[j]) {
+                        const uint2 r = s_rec[slot[j]];
+                        off[j] = r.x;
+                        deg[j] = r.y;
+                    }
+                    if (mv[j]) {
+                        hit_u += cur[j] == qi.u ? weight : 0u;
+                        hit_v += cur[j] == qi.v ? weight : 0u;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    st[j] += kGolden;
+                    if (COUPLED) gs[j] += kGolden;
+                    if (deg[j]) {
+                        const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                        el.next(off[j] + kk, cur[j], off[j], deg[j]);
+                        hit_u += cur[j] == qi.u ? weight : 0u;
+                        hit_v += cur[j] == qi.v ? weight : 0u;
+                    }
                 }
             }
         }
@@ -211,6 +289,9 @@ unsigned blocks_for(uint64_t items, uint64_t per_block) {
     return (unsigned)b;
 }
 
+// The hub variant when the graph has a hub table and a split layout (a
+// separate vertex-record load per step) and the table fits; else the plain
+// kernel.
 template <typename EL, int W, bool COUPLED>
 int launch_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
                  uint64_t seed, const Sampler &smp, unsigned long long *next_task, uint32_t *counts,
@@ -218,12 +299,28 @@ int launch_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint6
     int dev = 0, sms = 0, per_sm = 0;
     BQ_CUDA(cudaGetDevice(&dev));
     BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aesc_count_kernel<EL, W, COUPLED>, kThreads, 0));
-    if (per_sm < 1) per_sm = 1;
     // the bucket table follows begin[k + 1] in the scratch buffer
     const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
-    aesc_count_kernel<EL, W, COUPLED><<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, info, begin, bucket, k, seed, smp,
-                                                                         next_task, counts);
+    if constexpr (EL::kSplit) {
+        if (g.hub_tag && g.rec8 && tuning_aesc_hub()) {
+            const size_t smem = (size_t)12 << g.hub_bits;
+            auto kernel = aesc_count_kernel<EL, W, COUPLED, true>;
+            if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kHubAescThreads, smem) == cudaSuccess &&
+                per_sm >= 1) {
+                kernel<<<sms * per_sm, kHubAescThreads, smem, s>>>(el, g.offsets, info, begin, bucket, k, seed, smp,
+                                                                  next_task, counts, g.hub_tag, g.hub_bits);
+                BQ_CUDA(cudaGetLastError());
+                return BQ_OK;
+            }
+            cudaGetLastError();
+        }
+    }
+    auto kernel = aesc_count_kernel<EL, W, COUPLED, false>;
+    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, info, begin, bucket, k, seed, smp, next_task, counts,
+                                             nullptr, 0);
     BQ_CUDA(cudaGetLastError());
     return BQ_OK;
 }

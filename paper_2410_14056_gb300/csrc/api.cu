@@ -27,6 +27,7 @@ std::atomic<int> g_aesc_walks_per_lane{4};
 std::atomic<int> g_edge_records{1};
 std::atomic<int> g_hub_bits{13};
 std::atomic<int> g_l2_hints{0};
+std::atomic<int> g_aesc_hub{0};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -145,6 +146,7 @@ int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
 int tuning_layout() { return g_edge_records.load(); }
 int tuning_hub_bits() { return g_hub_bits.load(); }
 bool tuning_l2_hints() { return g_l2_hints.load() != 0; }
+bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
 
 namespace {
 
@@ -653,6 +655,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->layout = (uint32_t)g_edge_records.load();
     out->hub_bits = (uint32_t)g_hub_bits.load();
     out->l2_hints = (uint32_t)g_l2_hints.load();
+    out->aesc_hub = (uint32_t)g_aesc_hub.load();
     return BQ_OK;
 }
 
@@ -667,12 +670,14 @@ int bq_set_tuning(const bq_tuning *in) {
     if (in->hub_bits != 0 && (in->hub_bits < 10 || in->hub_bits > 13))
         return fail(BQ_EINVAL, "hub_bits must be 0 or 10..13");
     if (in->l2_hints > 1) return fail(BQ_EINVAL, "l2_hints must be 0 or 1");
+    if (in->aesc_hub > 1) return fail(BQ_EINVAL, "aesc_hub must be 0 or 1");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
     g_edge_records.store((int)in->layout);
     g_hub_bits.store((int)in->hub_bits);
     g_l2_hints.store((int)in->l2_hints);
+    g_aesc_hub.store((int)in->aesc_hub);
     return BQ_OK;
 }
 

@@ -197,6 +197,7 @@ int tuning_aesc_walks_per_lane();
 int tuning_layout();    // graph layout built at creation (bq_tuning.layout)
 int tuning_hub_bits();  // hub table size built at creation (bq_tuning.hub_bits)
 bool tuning_l2_hints(); // L2 eviction policies on the walk kernel's loads
+bool tuning_aesc_hub();  // AESC counting reads hub records from shared memory
 
 // Profiling (api.cu): event brackets around kernel groups while enabled, and
 // a count of every kernel launch.

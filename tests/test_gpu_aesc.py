@@ -131,6 +131,36 @@ def test_every_graph_layout_bit_exact(env, layout):
         bq.set_tuning(**old)
 
 
+@pytest.mark.parametrize("layout", [0, 5, 2])
+def test_hub_table_never_changes_results(env, layout):
+    """The hub variant of the counting kernel (hub records from shared
+    memory) on a skewed graph where only part of the steps land on hubs, for
+    several table sizes, both samplers, equal to the oracle and to the plain
+    kernel."""
+    bq, torch = env
+    from workloads import rmat
+    g = rmat(12, 8, seed=5)
+    rng = np.random.default_rng(8)
+    uv_all = all_edges(g)
+    uv = uv_all[rng.choice(uv_all.shape[0], 700, replace=False)]
+    tau = rng.integers(1, 12, uv.shape[0]).astype(np.uint32)
+    nw = rng.integers(1, 900, uv.shape[0]).astype(np.uint32)
+    old = bq.get_tuning()
+    try:
+        for hub_bits in (0, 10, 13):
+            bq.set_tuning(layout=layout, hub_bits=hub_bits)
+            graph = bq.Graph.from_csr(g)
+            for sampler in (None, (1, 4, 32)):
+                want = oracle.aesc_estimate(g, 21, uv, tau, nw, sampler=sampler)
+                for hub in (1, 0):
+                    bq.set_tuning(aesc_hub=hub)
+                    counts, sc = bq.aesc_estimate_host(graph, 21, uv, tau, nw, sampler=sampler)
+                    assert np.array_equal(counts, want[0]) and same_bits(sc, want[1]), (hub_bits, sampler, hub)
+            graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
 SCHEDULE = (2.0, 2, 64, 9.0, 32)  # tau_scale, tau_add, tau_max, n_scale, n_min (as the bench)
 
 

@@ -75,7 +75,12 @@ def test_tuning_roundtrip_and_validation(lib):
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
                                    "layout": old["layout"], "hub_bits": old["hub_bits"],
-                                   "l2_hints": old["l2_hints"]}
+                                   "l2_hints": old["l2_hints"], "aesc_hub": old["aesc_hub"]}
+        assert old["aesc_hub"] == 0  # off by default
+        bq.set_tuning(aesc_hub=1)
+        assert bq.get_tuning()["aesc_hub"] == 1
+        with pytest.raises(bq.BouquetError):
+            bq.set_tuning(aesc_hub=2)
         with pytest.raises(bq.BouquetError):
             bq.set_tuning(layout=6)
         for bad in (1, 9, 14):
