@@ -297,7 +297,29 @@ def aesc_measure(bq, torch, steps, warmup):
 POWERLAW_SCHEDULE = dict(tau_scale=2.0, tau_add=2, tau_max=64, n_scale=9.0, n_min=32)
 
 
-def aesc_powerlaw(bq, torch, steps, warmup):
+def aesc_cpu_baseline(g, seed, uv, tau, nw, n_edges=100_000):
+    """The C oracle's AESC counters on a seeded sample of the edges, one
+    contiguous slice per host core (the oracle call releases the GIL)."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(11)
+    pick = np.sort(rng.choice(uv.shape[0], min(n_edges, uv.shape[0]), replace=False))
+    cores = os.cpu_count() or 1
+    parts = np.array_split(pick, cores)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(cores) as pool:
+        list(pool.map(lambda p: oracle.aesc_counts(g, seed, uv[p], tau[p], nw[p]), parts))
+    dt = time.perf_counter() - t0
+    steps = float(np.sum(2.0 * tau[pick].astype(np.float64) * nw[pick]))
+    return {"value": pick.size / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "sample": f"{pick.size} edges drawn uniformly (seed 11) with their plan, {steps:.3g} walk steps, "
+                      f"C oracle counters on {cores} threads, {dt:.1f} s"}
+
+
+def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     """AESC on the power-law graph (Chung-Lu n = 4M, mean degree 10,
     exponent 2.1, largest component), all edges at eps = 0.05 with the
     scheduled (uncertified) plan.  Accuracy checks: Foster residual
@@ -347,7 +369,9 @@ def aesc_powerlaw(bq, torch, steps, warmup):
     _, ref = bq.aesc_estimate_host(graph, 99, uv, t2, n2)
     diff = np.abs(est[pick] - ref)
     graph.close()
+    cpu_line = aesc_cpu_baseline(g, 5, all_edges(g), tau, nw) if cpu else None
     return {
+        "cpu_baseline": cpu_line,
         "workload": f"chung-lu n=4M d=10 gamma=2.1 LCC (n={g.n}, m={g.m}), all edges, eps={eps}, "
                     "scheduled plan (uncertified)",
         "schedule": POWERLAW_SCHEDULE,
@@ -472,7 +496,7 @@ def run_ours(args):
     aesc = aesc_pl = None
     if not args.no_aesc and rank == 0:
         aesc = aesc_measure(bq, torch, max(5, args.steps), args.warmup)
-        aesc_pl = aesc_powerlaw(bq, torch, 3, 1)
+        aesc_pl = aesc_powerlaw(bq, torch, 3, 1, cpu=not args.no_cpu_baseline)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:

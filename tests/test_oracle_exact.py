@@ -11,7 +11,7 @@ import pytest
 from oracle import exact
 from tests.conftest import golden_rows
 from workloads import (all_edges, complete, cycle, diamond, edges_of, er_with_path,
-                       gnp_connected, path, prufer_tree)
+                       gnp_connected, grid_deleted, path, prufer_tree)
 
 
 def edge_list(g):
@@ -141,3 +141,27 @@ def test_expected_distinct_ratio_brute_force():
 def test_path_graph_sc_is_one():
     g = path(6)
     assert np.allclose(exact.sc_pinv(g, all_edges(g)), 1.0)
+
+
+def test_grid_interior_edges_tend_to_one_half():
+    """On the infinite square lattice the effective resistance between
+    neighbours is 1/2 (each of the 4 unit currents that enter a node splits
+    symmetrically).  The central edge of an s x s grid approaches it from above,
+    the gap shrinking like 1/s^2; a corner edge stays far from it."""
+    gaps = []
+    for side in (21, 31, 41):
+        g = grid_deleted(side, side, 0.0, 1)
+        c = side // 2
+        v0 = c * side + c
+        sc = exact.sc_pinv(g, np.array([[v0, v0 + 1], [v0, v0 + side], [0, 1]]))
+        assert abs(sc[0] - sc[1]) < 1e-12  # horizontal = vertical by symmetry
+        gaps.append(sc[0] - 0.5)
+        assert sc[2] > 0.6
+    assert 0 < gaps[2] < gaps[1] < gaps[0] < 2e-3
+    assert gaps[1] / gaps[0] == pytest.approx((21 / 31) ** 2, rel=0.1)
+    # the half-weighted walk series of the central edge heads there too
+    g = grid_deleted(21, 21, 0.0, 1)
+    v0 = 10 * 21 + 10
+    t64 = exact.truncated_series(g, v0, v0 + 1, 64)
+    t400 = exact.truncated_series(g, v0, v0 + 1, 400)
+    assert abs(t400 - 0.5) < abs(t64 - 0.5) < 0.05
