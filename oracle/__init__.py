@@ -89,6 +89,13 @@ def lib():
             L.orc_aesc_counts.restype = c.c_int
             L.orc_aesc_finalize.argtypes = [c.c_uint32, i64p, c.c_uint64, u32p, u32p, u32p, f64p]
             L.orc_aesc_finalize.restype = c.c_int
+            L.orc_aesc_push_counts.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, c.c_uint64, u32p, u32p, u32p,
+                c.c_uint32, u32p, u64p]
+            L.orc_aesc_push_counts.restype = c.c_int
+            L.orc_aesc_push_finalize.argtypes = [
+                c.c_uint32, i64p, c.c_uint64, u32p, u32p, u32p, u32p, u64p, f64p]
+            L.orc_aesc_push_finalize.restype = c.c_int
             L.orc_trunc_bound.argtypes = [c.c_double, c.c_double, c.c_double, c.c_uint32]
             L.orc_trunc_bound.restype = c.c_double
             L.orc_plan_certified.argtypes = [
@@ -275,3 +282,48 @@ def aesc_estimate(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndar
                   sampler=None):
     counts = aesc_counts(g, seed, uv, tau, nwalks, sampler)
     return counts, aesc_finalize(g, uv, nwalks, counts)
+
+
+# ------------------------------------------------ AESC with a push phase
+
+PUSH_Q = 1 << 30  # fixed-point scale of the pushed values
+
+
+def aesc_push_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
+                     push_max: int = 1):
+    """(depth uint32[k], acc uint64[4k]): push depth per edge and the
+    fixed-point accumulators A_uu, A_uv, A_vu, A_vv (Alg. 1, depth 0 or 1)."""
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    depth = np.zeros(q.shape[0], np.uint32)
+    acc = np.zeros(4 * q.shape[0], np.uint64)
+    rc = lib().orc_aesc_push_counts(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed, q.shape[0],
+        _p(q, ctypes.c_uint32), _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
+        int(push_max), _p(depth, ctypes.c_uint32), _p(acc, ctypes.c_uint64))
+    _check(rc, "aesc_push_counts")
+    return depth, acc
+
+
+def aesc_push_finalize(g, uv, tau, nwalks, depth, acc) -> np.ndarray:
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    dp = np.ascontiguousarray(depth, dtype=np.uint32)
+    ac = np.ascontiguousarray(acc, dtype=np.uint64)
+    sc = np.zeros(q.shape[0], np.float64)
+    rc = lib().orc_aesc_push_finalize(g.n, _p(off, ctypes.c_int64), q.shape[0], _p(q, ctypes.c_uint32),
+                                      _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
+                                      _p(dp, ctypes.c_uint32), _p(ac, ctypes.c_uint64),
+                                      _p(sc, ctypes.c_double))
+    _check(rc, "aesc_push_finalize")
+    return sc
+
+
+def aesc_push_estimate(g, seed: int, uv, tau, nwalks, push_max: int = 1):
+    """(depth, acc, sc) of the push-phase estimator."""
+    depth, acc = aesc_push_counts(g, seed, uv, tau, nwalks, push_max)
+    return depth, acc, aesc_push_finalize(g, uv, tau, nwalks, depth, acc)

@@ -409,6 +409,145 @@ int orc_aesc_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
 
 /* ------------------------------------------------------------------ plan */
 
+/* ------------------------------------------------ AESC with a push phase */
+
+/* Alg. 1 splits each walk term at push depth tau~: the first tau~ levels of
+ * p_l(., v_i) are pushed exactly, and walks of tau - tau~ steps carry the
+ * rest, each position y adding p_tau~(y -> x) for target x.  Here tau~ is
+ * 0 or 1, in fixed point with Q = 2^30:
+ *   r_x(y) = Q * [y == x]                         (tau~ = 0)
+ *   r_x(y) = floor(Q / d(y)) if y is a neighbour of x, else 0   (tau~ = 1)
+ * (a walk from y stands on x one step later with probability 1/d(y) exactly
+ * when y is adjacent to x).  tau~ = 1 is taken, as in TGT+'s while loop,
+ * when the push volume d(u) + d(v) is below the 2 N walks it replaces, the
+ * edge has tau >= 1 and push_max >= 1. */
+#define ORC_PUSH_Q 1073741824u
+
+static uint32_t push_depth_of(const int64_t *offsets, uint32_t u, uint32_t v,
+                              uint32_t tau, uint32_t nwalks, uint32_t push_max)
+{
+    uint64_t vol = (uint64_t)(offsets[u + 1] - offsets[u]) + (uint64_t)(offsets[v + 1] - offsets[v]);
+    return (push_max >= 1 && tau >= 1 && vol < 2ull * nwalks) ? 1u : 0u;
+}
+
+static uint64_t push_value(const int64_t *offsets, const uint32_t *nbrs, uint32_t x,
+                           uint32_t y, uint32_t depth)
+{
+    int64_t j;
+    if (depth == 0)
+        return y == x ? ORC_PUSH_Q : 0u;
+    for (j = offsets[x]; j < offsets[x + 1]; j++)
+        if (nbrs[j] == y)
+            return ORC_PUSH_Q / (uint32_t)(offsets[y + 1] - offsets[y]);
+    return 0u;
+}
+
+/* Accumulators for query edge q = {u, v}, u < v: the walks of the plain
+ * counters (streams 2e + side, walk index w < nwalks[q]) but tau[q] - tau~
+ * steps long; at step l the walk adds w * r_u(cur) and w * r_v(cur) with
+ * w = 2 if l + tau~ < tau else 1:
+ *   acc[4q + 0..3] = A_uu, A_uv (walks from u), A_vu, A_vv (walks from v).
+ * depth[q] (may be NULL) receives tau~. */
+int orc_aesc_push_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                         uint64_t seed, uint64_t k, const uint32_t *uv,
+                         const uint32_t *tau, const uint32_t *nwalks,
+                         uint32_t push_max, uint32_t *depth, uint64_t *acc)
+{
+    orc_sampler smp;
+    uint64_t *ub;
+    uint64_t q;
+    smp.kind = 0;
+    smp.t = 0;
+    smp.width = 1;
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub)
+        return ORC_EINVAL;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b;
+        uint32_t v = a < b ? b : a;
+        uint64_t e, c[4] = {0, 0, 0, 0};
+        uint32_t side, dep;
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &e) != ORC_OK) {
+            free(ub);
+            return ORC_ENOEDGE;
+        }
+        if (tau[q] == 0 || nwalks[q] == 0 || 2ull * nwalks[q] * tau[q] >= 4294967296ull) {
+            free(ub);
+            return ORC_EOVERFLOW;
+        }
+        dep = push_depth_of(offsets, u, v, tau[q], nwalks[q], push_max);
+        if (depth)
+            depth[q] = dep;
+        for (side = 0; side < 2; side++) {
+            uint64_t stream = 2 * e + side;
+            uint64_t w;
+            for (w = 0; w < nwalks[q]; w++) {
+                uint64_t kw = orc_walk_key(seed, stream, w);
+                uint32_t cur = side == 0 ? u : v;
+                uint32_t l;
+                for (l = 1; l + dep <= tau[q]; l++) {
+                    int64_t lo = offsets[cur];
+                    uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
+                    uint64_t weight = l + dep < tau[q] ? 2u : 1u;
+                    cur = nbrs[lo + orc_choose(sample_word(&smp, kw, 0, l, cur), d)];
+                    c[2 * side + 0] += weight * push_value(offsets, nbrs, u, cur, dep);
+                    c[2 * side + 1] += weight * push_value(offsets, nbrs, v, cur, dep);
+                }
+            }
+        }
+        acc[4 * q + 0] = c[0];
+        acc[4 * q + 1] = c[1];
+        acc[4 * q + 2] = c[2];
+        acc[4 * q + 3] = c[3];
+    }
+    free(ub);
+    return ORC_OK;
+}
+
+/* Estimate of query edge q from its accumulators:
+ *   g(u, v) = (X_u + (A_uu - A_vu) / N) / (2 Q d_u),
+ *   X_u = 2Q                                 (tau~ = 0: the l = 0 term),
+ *   X_u = 2Q - w_1 floor(Q / d_v)            (tau~ = 1: the l = 0 term and
+ *         the l = 1 term of the walks' fixed start, r_u(u) = 0, r_u(v) = Q/d_v)
+ * with w_1 = 2 if tau > 1 else 1; g(v, u) likewise; SC = g(u, v) + g(v, u).
+ * Each operation rounds once, in this order. */
+int orc_aesc_push_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
+                           const uint32_t *uv, const uint32_t *tau, const uint32_t *nwalks,
+                           const uint32_t *depth, const uint64_t *acc, double *sc)
+{
+    uint64_t q;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b;
+        uint32_t v = a < b ? b : a;
+        uint32_t du_i, dv_i;
+        int64_t xu, xv;
+        double du, dv, nw, gu, gv;
+        if (u >= n || v >= n)
+            return ORC_EINVAL;
+        du_i = (uint32_t)(offsets[u + 1] - offsets[u]);
+        dv_i = (uint32_t)(offsets[v + 1] - offsets[v]);
+        xu = 2 * (int64_t)ORC_PUSH_Q;
+        xv = 2 * (int64_t)ORC_PUSH_Q;
+        if (depth[q] == 1) {
+            int64_t w1 = tau[q] > 1 ? 2 : 1;
+            xu -= w1 * (int64_t)(ORC_PUSH_Q / dv_i);
+            xv -= w1 * (int64_t)(ORC_PUSH_Q / du_i);
+        }
+        du = (double)du_i;
+        dv = (double)dv_i;
+        nw = (double)nwalks[q];
+        gu = ((double)xu + (double)(int64_t)(acc[4 * q + 0] - acc[4 * q + 2]) / nw) /
+             (2.0 * (double)ORC_PUSH_Q * du);
+        gv = ((double)xv + (double)(int64_t)(acc[4 * q + 3] - acc[4 * q + 1]) / nw) /
+             (2.0 * (double)ORC_PUSH_Q * dv);
+        sc[q] = gu + gv;
+    }
+    return ORC_OK;
+}
+
+
 /* Worst-case truncation error factor of the half-weighted series after tau
  * terms for eigenvalues in (0, lambda2] (P) and [lambda_neg, 0) (Q), where
  * the error of one eigen-component lambda is lambda^tau (1 + lambda) /
