@@ -368,9 +368,35 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     n2 = np.minimum(16 * nw[pick].astype(np.uint64), (2**32 - 1) // (2 * t2.astype(np.uint64) + 2)).astype(np.uint32)
     _, ref = bq.aesc_estimate_host(graph, 99, uv, t2, n2)
     diff = np.abs(est[pick] - ref)
+    # the same estimate with the push phase (depth 1 where d(u) + d(v) < 2N)
+    depth = torch.zeros(tau.size, dtype=torch.int32, device="cuda")
+    acc = torch.zeros(4 * tau.size, dtype=torch.int64, device="cuda")
+    bq.aesc_estimate_push(graph, 5, None, dtau, dnw, 1, depth=depth, acc=acc, sc=sc)
+    bq.sync()
+    plat = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bq.aesc_estimate_push(graph, 5, None, dtau, dnw, 1, depth=depth, acc=acc, sc=sc)
+        e1.record()
+        e1.synchronize()
+        plat.append(e0.elapsed_time(e1))
+    bq.sync()
+    pms = sum(plat) / len(plat)
+    pest = sc.cpu().numpy()
+    dep = depth.cpu().numpy()
+    pwork = float(np.sum(2.0 * (tau.astype(np.float64) - dep) * nw))
+    pdiff = np.abs(pest[pick] - ref)
+    push = {"edges_per_s": tau.size / (pms / 1e3), "ms_per_estimate": pms, "walk_steps_per_call": pwork,
+            "frac_edges_depth1": float(dep.mean()),
+            "foster_residual": abs(float(pest.sum()) - (g.n - 1)) / (g.n - 1),
+            "subset_1000_max_abs_diff_vs_16N_2tau": float(pdiff.max()),
+            "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(pdiff ** 2))),
+            "plain_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(diff ** 2)))}
     graph.close()
     cpu_line = aesc_cpu_baseline(g, 5, all_edges(g), tau, nw) if cpu else None
     return {
+        "push_phase": push,
         "cpu_baseline": cpu_line,
         "workload": f"chung-lu n=4M d=10 gamma=2.1 LCC (n={g.n}, m={g.m}), all edges, eps={eps}, "
                     "scheduled plan (uncertified)",
@@ -469,7 +495,7 @@ def run_ours(args):
     traffic = walk_kernel_traffic("walks.cu")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "walk_hub_kernel" if bq.get_tuning()["hub_bits"] else "walk_bouquet_kernel",
+                "kernel": "walk_hub_kernel" if bq.get_tuning()["hub_slots"] else "walk_bouquet_kernel",
                 "kernel_ms": walk_ms,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"

@@ -239,6 +239,37 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
                      const bq_sampler *sampler, uint32_t flags, uint32_t *counts_dev,
                      double *sc_dev, void *stream);
 
+/* ------------------------------------------------- bq_aesc_estimate_push */
+/*
+ * AESC with a push phase (Alg. 1: p_l(., v_i) pushed exactly for the first
+ * tau~ levels, walks of tau - tau~ steps weighted by p_tau~(x, v_i) instead
+ * of hit indicators), for push depth tau~ in {0, 1}.  Depth 1 is taken per
+ * edge when push_max = 1, tau >= 1 and d(u) + d(v) < 2 N (TGT+'s test:
+ * push while the pushed volume is below the walks it replaces); push_max =
+ * 0 keeps depth 0 everywhere.  In fixed point with Q = 2^30:
+ *   r_x(y) = Q [y == x] (depth 0), floor(Q / d(y)) if y ~ x else 0 (depth 1);
+ * the walks are those of bq_aesc_estimate (streams 2 id + side, walk index,
+ * independent sampler), tau - depth steps long; at step l a walk adds
+ * w r_u(cur) and w r_v(cur), w = 2 if l + depth < tau else 1, to
+ *   acc[4q + 0..3] = A_uu, A_uv (walks from u), A_vu, A_vv (walks from v)
+ * (uint64; 2 N tau < 2^32 keeps them below 2^62), and
+ *   SC = g(u, v) + g(v, u),  g(u, v) = (X_u + (A_uu - A_vu) / N) / (2 Q d_u),
+ *   X_u = 2Q at depth 0, 2Q - w_1 floor(Q / d_v) at depth 1 (w_1 = 2 if
+ *   tau > 1 else 1), each FP64 operation rounded once in this order.
+ * Its expectation is the same half-weighted series as bq_aesc_estimate's;
+ * depth 1 lowers the variance (a step adds 1/d(y) on every neighbour of u
+ * instead of only on u) and saves one step per walk.
+ *
+ * Arguments as bq_aesc_estimate (edges_uv_dev NULL = all edges; BQ_HOST_IO
+ * for host buffers), plus depth_dev (k uint32, may be NULL): the depth
+ * taken per edge; acc_dev: 4k uint64, overwritten.  Errors: BQ_EINVAL
+ * (push_max > 1, NULL buffers), and at bq_sync those of bq_aesc_estimate.
+ */
+int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev,
+                          uint64_t k, const uint32_t *tau_dev, const uint32_t *nwalks_dev,
+                          uint32_t push_max, uint32_t flags, uint32_t *depth_dev,
+                          uint64_t *acc_dev, double *sc_dev, void *stream);
+
 /* ---------------------------------------------------------- AESC batches */
 /*
  * Many AESC estimates (on one or many graphs, of uneven sizes) run as one
@@ -388,10 +419,11 @@ typedef struct bq_tuning {
                                      bits, several per 16-byte chunk, + 8-byte
                                      vertex records (plain CSR when packing
                                      saves nothing) */
-    uint32_t hub_bits;         /* graphs created from now on get a table of
-                                  2^hub_bits hub slots (0 = none; 10..13,
-                                  default 13): each slot holds the highest-
-                                  degree vertex hashing to it.  The bouquet
+    uint32_t hub_slots;        /* graphs created from now on get a table of
+                                  hub_slots slots (0 = none; 1024..13312,
+                                  default 8192): each slot holds the highest-
+                                  degree vertex hashing to it (slot = high
+                                  half of (v * 0x9E3779B1 mod 2^32) * slots).  The bouquet
                                   walk-batch kernel keeps the table in shared
                                   memory (16 bytes per slot) and serves those
                                   vertices' records and visit counters from it:

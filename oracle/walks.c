@@ -131,7 +131,11 @@ uint32_t orc_choose(uint32_t r, uint32_t d)
 
 /* Sampler: kind 0 = independent walks; kind 1 = coupled bouquets: walks
  * k with the same floor(k / width) share the top t bits of their random word
- * at the same (length, vertex). */
+ * at the same (length, vertex); kind 2 = the paper's SABA word taken
+ * literally (Eq. select-proposed): r = X_W xor h(cur, l), with X_W the low
+ * 32 bits of the walk's key (its seed, fixed for the whole walk) and h one
+ * hash of (vertex, length) shared by the batch (the group key of walk 0);
+ * walk batches only. */
 typedef struct {
     uint32_t kind;
     uint32_t t;
@@ -141,7 +145,10 @@ typedef struct {
 static uint32_t sample_word(const orc_sampler *smp, uint64_t kw, uint64_t kg,
                             uint32_t l, uint32_t cur)
 {
-    uint32_t own = orc_step_hash(kw, l, cur);
+    uint32_t own;
+    if (smp->kind == 2)
+        return orc_step_hash(kg, l, cur) ^ (uint32_t)kw;
+    own = orc_step_hash(kw, l, cur);
     if (smp->kind == 0)
         return own;
     {
@@ -154,6 +161,8 @@ static uint32_t sample_word(const orc_sampler *smp, uint64_t kw, uint64_t kg,
 static int sampler_ok(const orc_sampler *smp)
 {
     if (smp->kind == 0)
+        return 1;
+    if (smp->kind == 2)
         return 1;
     return smp->kind == 1 && smp->width >= 1 && smp->t <= 32;
 }
@@ -187,6 +196,8 @@ int orc_walk_batch(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
         kw = orc_walk_key(seed, ORC_BATCH_STREAM, i);
         if (kind == 1)
             kg = orc_walk_key(seed, ORC_BATCH_STREAM | ORC_GROUP_BIT, i / width);
+        if (kind == 2)
+            kg = orc_walk_key(seed, ORC_BATCH_STREAM | ORC_GROUP_BIT, 0);
         if (paths)
             paths[i * ((uint64_t)n_steps + 1)] = cur;
         if (include_start) {
@@ -235,6 +246,8 @@ int orc_walk_paths_by_id(uint32_t n, const int64_t *offsets, const uint32_t *nbr
         kw = orc_walk_key(seed, ORC_BATCH_STREAM, ids[q]);
         if (kind == 1)
             kg = orc_walk_key(seed, ORC_BATCH_STREAM | ORC_GROUP_BIT, ids[q] / width);
+        if (kind == 2)
+            kg = orc_walk_key(seed, ORC_BATCH_STREAM | ORC_GROUP_BIT, 0);
         paths[q * ((uint64_t)n_steps + 1)] = cur;
         for (l = 1; l <= n_steps; l++) {
             int64_t lo = offsets[cur];
@@ -327,7 +340,7 @@ int orc_aesc_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
     smp.kind = kind;
     smp.t = t;
     smp.width = width;
-    if (!sampler_ok(&smp))
+    if (!sampler_ok(&smp) || kind == 2)  /* the literal SABA word is biased */
         return ORC_EINVAL;
     ub = count_upper(n, offsets, nbrs);
     if (!ub)

@@ -59,7 +59,7 @@ class Schedule(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("walk_lanes", ctypes.c_uint32), ("aggregate_visits", ctypes.c_uint32),
                 ("aesc_lanes", ctypes.c_uint32), ("layout", ctypes.c_uint32),
-                ("hub_bits", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
+                ("hub_slots", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
                 ("aesc_hub", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
@@ -113,7 +113,7 @@ EXPORTS = (
     "bq_profile_read", "bq_walk_batch_noalloc", "bq_batch_create", "bq_batch_run",
     "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
     "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
-    "bq_server_destroy",
+    "bq_server_destroy", "bq_aesc_estimate_push",
 )
 
 _lock = threading.Lock()
@@ -142,6 +142,7 @@ def load_library(path: str | None = None):
         L.bq_walk_batch.argtypes = [vp, u64, vp, u64, u32, u32, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_aesc_plan.argtypes = [vp, vp, u64, f64, f64, u32, c.POINTER(Schedule), vp, vp]
         L.bq_aesc_estimate.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp, vp]
+        L.bq_aesc_estimate_push.argtypes = [vp, u64, vp, u64, vp, vp, u32, u32, vp, vp, vp, vp]
         L.bq_sync.argtypes = [vp]
         L.bq_strerror.argtypes = [i32]
         L.bq_strerror.restype = c.c_char_p
@@ -378,6 +379,48 @@ def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.n
     return counts, sc
 
 
+def aesc_estimate_push(graph: Graph, seed: int, uv, tau, nwalks, push_max: int = 1,
+                       depth=None, acc=None, sc=None, stream=None):
+    """Push-phase AESC on device tensors (uv None = all edges); returns
+    (depth, acc, sc) with acc the 4k uint64 fixed-point accumulators."""
+    import torch
+    L = load_library()
+    k = tau.numel()
+    dev = tau.device
+    if depth is None:
+        depth = torch.zeros(k, dtype=torch.int32, device=dev)
+    if acc is None:
+        acc = torch.zeros(4 * k, dtype=torch.int64, device=dev)
+    if sc is None:
+        sc = torch.empty(k, dtype=torch.float64, device=dev)
+    _check(L.bq_aesc_estimate_push(graph.handle, int(seed) & (2**64 - 1), _dptr(uv, "uv"), k,
+                                   _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), int(push_max), 0,
+                                   _dptr(depth, "depth"), _dptr(acc, "acc", 8), _dptr(sc, "sc", 8),
+                                   _stream_handle(stream)))
+    return depth, acc, sc
+
+
+def aesc_estimate_push_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.ndarray,
+                            nwalks: np.ndarray, push_max: int = 1):
+    """Push-phase AESC through host buffers (BQ_HOST_IO); synchronous."""
+    L = load_library()
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    k = ta.size
+    puv = None
+    if uv is not None:
+        uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+        puv = _hptr(uv, "edges", np.uint32)
+    depth = np.zeros(k, np.uint32)
+    acc = np.zeros(4 * k, np.uint64)
+    sc = np.zeros(k, np.float64)
+    _check(L.bq_aesc_estimate_push(graph.handle, int(seed) & (2**64 - 1), puv, k, _hptr(ta, "tau", np.uint32),
+                                   _hptr(nw, "nwalks", np.uint32), int(push_max), HOST_IO,
+                                   _hptr(depth, "depth", np.uint32), _hptr(acc, "acc", np.uint64),
+                                   _hptr(sc, "sc", np.float64), None))
+    return depth, acc, sc
+
+
 def _query_array(queries):
     """bq_aesc_query array for a list of query dicts (outputs allocated when
     absent); returns (array, objects to keep alive, [(counts, sc)])."""
@@ -542,7 +585,7 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(load_library().bq_get_tuning(ctypes.byref(t)))
     return {"walk_lanes": t.walk_lanes, "aggregate_visits": t.aggregate_visits,
-            "aesc_lanes": t.aesc_lanes, "layout": t.layout, "hub_bits": t.hub_bits,
+            "aesc_lanes": t.aesc_lanes, "layout": t.layout, "hub_slots": t.hub_slots,
             "l2_hints": t.l2_hints, "aesc_hub": t.aesc_hub}
 
 
@@ -550,7 +593,7 @@ def set_tuning(**kw):
     cur = get_tuning()
     cur.update(kw)
     t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]),
-               int(cur["layout"]), int(cur["hub_bits"]), int(cur["l2_hints"]), int(cur["aesc_hub"]))
+               int(cur["layout"]), int(cur["hub_slots"]), int(cur["l2_hints"]), int(cur["aesc_hub"]))
     _check(load_library().bq_set_tuning(ctypes.byref(t)))
 
 

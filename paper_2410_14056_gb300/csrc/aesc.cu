@@ -24,7 +24,7 @@ struct QueryInfo {
     uint32_t du, dv;  // degrees
     uint32_t tau, nwalks;
     uint32_t valid;
-    uint32_t pad;
+    uint32_t depth;   // push depth (0 for the plain estimator)
 };
 
 // first index in [lo, hi) whose entry is >= key
@@ -56,9 +56,13 @@ __global__ void canonical_edges_kernel(DeviceGraph g, uint32_t *__restrict__ uv)
     }
 }
 
+// push_max 0: the plain estimator.  push_max 1: push depth 1 where the push
+// volume d(u) + d(v) is below the 2N walks it replaces (and tau >= 1); such
+// an edge's walks are tau - 1 steps long, and none are run when that is 0.
 __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, uint64_t k,
                                const uint32_t *__restrict__ tau, const uint32_t *__restrict__ nwalks,
-                               uint32_t bouquet, QueryInfo *__restrict__ info, uint32_t *__restrict__ tasks,
+                               uint32_t bouquet, uint32_t push_max, QueryInfo *__restrict__ info,
+                               uint32_t *__restrict__ tasks, uint32_t *__restrict__ depth_out,
                                double *__restrict__ sc, uint32_t *status) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
          q += (uint64_t)gridDim.x * blockDim.x) {
@@ -71,7 +75,7 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
         qi.valid = 0;
         qi.edge = 0;
         qi.du = qi.dv = 0;
-        qi.pad = 0;
+        qi.depth = 0;
         uint32_t status_bits = 0;
         if (a >= g.n || b >= g.n || a == b) {
             status_bits = kStatusNoEdge;
@@ -88,11 +92,13 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
                 if (qi.tau == 0 || qi.nwalks == 0) status_bits = kStatusBadIndex;
                 else if (2ull * qi.nwalks * qi.tau >= (1ull << 32)) status_bits = kStatusOverflow;
                 else qi.valid = 1;
+                if (qi.valid && push_max >= 1 && (uint64_t)qi.du + qi.dv < 2ull * qi.nwalks) qi.depth = 1;
             }
         }
         if (status_bits) atomicOr(status, status_bits);
         info[q] = qi;
-        tasks[q] = qi.valid ? 2u * ((qi.nwalks + bouquet - 1) / bouquet) : 0u;
+        if (depth_out) depth_out[q] = qi.depth;
+        tasks[q] = qi.valid && qi.tau > qi.depth ? 2u * ((qi.nwalks + bouquet - 1) / bouquet) : 0u;
         if (!qi.valid) sc[q] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
     }
 }
@@ -104,7 +110,7 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
 // j of lane l is walk chunk*32W + j*32 + l, so a coupling group of 32 fills
 // one lockstep slot.
 //
-// HUB: the graph's hub table (the highest-degree vertex of each of 2^hub_bits
+// HUB: the graph's hub table (the highest-degree vertex of each of hub_slots
 // hash slots) is copied into shared memory with the hubs' vertex records, and
 // a step that lands on a hub reads the record there instead of from L2/HBM.
 // The grid is then 2 blocks of kHubAescThreads per SM (40 warps, the same as
@@ -129,12 +135,11 @@ __global__ void __launch_bounds__(count_threads<HUB>(), count_min_blocks<W, COUP
 aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *__restrict__ info,
                   const uint64_t *__restrict__ begin, const uint32_t *__restrict__ bucket, uint64_t k,
                   uint64_t seed, Sampler smp, unsigned long long *__restrict__ next_task,
-                  uint32_t *__restrict__ counts, const uint32_t *__restrict__ hub_tag, uint32_t hub_bits) {
+                  uint32_t *__restrict__ counts, const uint32_t *__restrict__ hub_tag, uint32_t hub_slots) {
     extern __shared__ __align__(16) unsigned char hub_smem[];
     uint2 *s_rec = reinterpret_cast<uint2 *>(hub_smem);
-    const uint32_t slots = HUB ? (1u << hub_bits) : 0u;
+    const uint32_t slots = HUB ? hub_slots : 0u;
     uint32_t *s_tag = reinterpret_cast<uint32_t *>(s_rec + slots);
-    const uint32_t hub_shift = 32 - hub_bits;
     if constexpr (HUB) {
         for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
             const uint32_t t = hub_tag[i];
@@ -219,7 +224,7 @@ aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *_
                 }
 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    slot[j] = (cur[j] * kHubHash) >> hub_shift;
+                    slot[j] = hub_slot(cur[j], slots);
                     hub[j] = mv[j] && s_tag[slot[j]] == cur[j];
                 }
 #pragma unroll
@@ -282,6 +287,120 @@ __global__ void finalize_kernel(const QueryInfo *__restrict__ info, uint64_t k, 
     }
 }
 
+// ------------------------------------------------------ AESC with a push phase
+
+constexpr uint32_t kPushQ = 1u << 30;  // fixed-point scale of the pushed values
+
+// Pushed value r_x(y) at depth 0 (Q [y == x]) or 1 (floor(Q / d_y) when y is
+// a neighbour of x: a walk from y stands on x one step later with
+// probability 1/d_y exactly then).  The row of x is searched in the plain
+// CSR ids; every walk of a task searches the same two rows, which stay in L1.
+__device__ __forceinline__ uint64_t pushed_value(const uint32_t *__restrict__ nbrs, int64_t lo, int64_t hi,
+                                                 uint32_t x, uint32_t y, uint32_t dy, uint32_t depth) {
+    if (depth == 0) return y == x ? (uint64_t)kPushQ : 0ull;
+    const int64_t p = lower_bound_row(nbrs, lo, hi, y);
+    return (p < hi && __ldg(nbrs + p) == y) ? (uint64_t)(kPushQ / dy) : 0ull;
+}
+
+// Persistent counting kernel of the push estimator: the tasks, streams and
+// walk indices of aesc_count_kernel (independent sampler), walks of tau -
+// depth steps; at step l a walk adds w r_u(cur) and w r_v(cur), w = 2 if
+// l + depth < tau else 1, to 64-bit fixed-point accumulators
+// acc[4q + 2 side + {0, 1}] (A_uu, A_uv from u; A_vu, A_vv from v).
+template <typename EL, int W>
+__global__ void __launch_bounds__(kThreads, (W <= 4) ? 4 : 1)
+aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
+                 const QueryInfo *__restrict__ info, const uint64_t *__restrict__ begin,
+                 const uint32_t *__restrict__ bucket, uint64_t k, uint64_t seed,
+                 unsigned long long *__restrict__ next_task, unsigned long long *__restrict__ acc) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t total = begin[k];
+    const uint32_t shift = bucket_shift(total, k);
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(next_task, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        const uint64_t q = task_edge(begin, bucket, k, total, shift, t);
+        const QueryInfo qi = info[q];
+        const uint64_t local = t - begin[q];
+        const uint32_t side = (uint32_t)(local & 1);
+        const uint64_t stream = 2 * qi.edge + side;
+        const uint32_t start = side ? qi.v : qi.u;
+        const uint64_t k0 = (local >> 1) * 32ull * W;
+        const int64_t lo_u = __ldg(offsets + qi.u), hi_u = lo_u + qi.du;
+        const int64_t lo_v = __ldg(offsets + qi.v), hi_v = lo_v + qi.dv;
+
+        uint64_t st[W];
+        uint32_t cur[W], deg[W];
+        uint64_t off[W];
+        bool act[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint64_t kk = k0 + (uint64_t)lane * W + j;
+            st[j] = walk_key(seed, stream, kk);
+            act[j] = kk < qi.nwalks;
+        }
+        uint64_t off0;
+        uint32_t deg0;
+        start_record(offsets, start, off0, deg0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            cur[j] = start;
+            off[j] = off0;
+            deg[j] = act[j] ? deg0 : 0u;
+        }
+        uint64_t a_u = 0, a_v = 0;
+        const uint32_t steps = qi.tau - qi.depth;
+        for (uint32_t l = 1; l <= steps; ++l) {
+            const uint64_t weight = l + qi.depth < qi.tau ? 2ull : 1ull;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                st[j] += kGolden;
+                if (deg[j]) {
+                    const uint32_t kk = choose(sample_word<false>(st[j], 0ull, cur[j], 0u), deg[j]);
+                    el.next(off[j] + kk, cur[j], off[j], deg[j]);
+                    a_u += weight * pushed_value(nbrs, lo_u, hi_u, qi.u, cur[j], deg[j], qi.depth);
+                    a_v += weight * pushed_value(nbrs, lo_v, hi_v, qi.v, cur[j], deg[j], qi.depth);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            a_u += __shfl_down_sync(0xffffffffu, a_u, d);
+            a_v += __shfl_down_sync(0xffffffffu, a_v, d);
+        }
+        if (lane == 0) {
+            if (a_u) atomicAdd(acc + 4 * q + 2 * side + 0, (unsigned long long)a_u);
+            if (a_v) atomicAdd(acc + 4 * q + 2 * side + 1, (unsigned long long)a_v);
+        }
+    }
+}
+
+// g(u, v) = (X_u + (A_uu - A_vu) / N) / (2 Q d_u) with X_u = 2Q, less
+// w_1 floor(Q / d_v) at depth 1 (w_1 = 2 if tau > 1 else 1); SC = g(u, v) +
+// g(v, u); every operation rounded to nearest on its own, in this order.
+__global__ void finalize_push_kernel(const QueryInfo *__restrict__ info, uint64_t k,
+                                     const unsigned long long *__restrict__ acc, double *__restrict__ sc) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const QueryInfo qi = info[q];
+        if (!qi.valid) continue;
+        int64_t xu = 2 * (int64_t)kPushQ, xv = 2 * (int64_t)kPushQ;
+        if (qi.depth == 1) {
+            const int64_t w1 = qi.tau > 1 ? 2 : 1;
+            xu -= w1 * (int64_t)(kPushQ / qi.dv);
+            xv -= w1 * (int64_t)(kPushQ / qi.du);
+        }
+        const double du = (double)qi.du, dv = (double)qi.dv, nw = (double)qi.nwalks;
+        const double yu = (double)(int64_t)(acc[4 * q + 0] - acc[4 * q + 2]);
+        const double yv = (double)(int64_t)(acc[4 * q + 3] - acc[4 * q + 1]);
+        const double gu = __ddiv_rn(__dadd_rn((double)xu, __ddiv_rn(yu, nw)), __dmul_rn(2.0 * (double)kPushQ, du));
+        const double gv = __ddiv_rn(__dadd_rn((double)xv, __ddiv_rn(yv, nw)), __dmul_rn(2.0 * (double)kPushQ, dv));
+        sc[q] = __dadd_rn(gu, gv);
+    }
+}
+
 unsigned blocks_for(uint64_t items, uint64_t per_block) {
     uint64_t b = (items + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -303,13 +422,13 @@ int launch_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint6
     const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
     if constexpr (EL::kSplit) {
         if (g.hub_tag && g.rec8 && tuning_aesc_hub()) {
-            const size_t smem = (size_t)12 << g.hub_bits;
+            const size_t smem = (size_t)12 * g.hub_slots;
             auto kernel = aesc_count_kernel<EL, W, COUPLED, true>;
             if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kHubAescThreads, smem) == cudaSuccess &&
                 per_sm >= 1) {
                 kernel<<<sms * per_sm, kHubAescThreads, smem, s>>>(el, g.offsets, info, begin, bucket, k, seed, smp,
-                                                                  next_task, counts, g.hub_tag, g.hub_bits);
+                                                                  next_task, counts, g.hub_tag, g.hub_slots);
                 BQ_CUDA(cudaGetLastError());
                 return BQ_OK;
             }
@@ -383,8 +502,8 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
             uv = all_uv;
         }
         count_launches(1);
-        prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, info, tasks,
-                                                                    sc, status);
+        prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, 0u, info, tasks,
+                                                                    nullptr, sc, status);
         rc = scan_u32_to_u64(tasks, begin, k, s);
         if (rc == BQ_OK) {
             count_launches(1);
@@ -405,6 +524,97 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
         finalize_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, counts, sc);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "finalize_kernel");
+    }
+    scratch_free(buf, s);
+    return rc;
+}
+
+}  // namespace bq
+
+namespace bq {
+namespace {
+
+template <typename EL, int W>
+int launch_push_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+                      uint64_t seed, unsigned long long *next_task, unsigned long long *acc, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto kernel = aesc_push_kernel<EL, W>;
+    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
+    kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, g.nbrs, info, begin, bucket, k, seed, next_task, acc);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+}  // namespace
+
+int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k, const uint32_t *tau,
+                     const uint32_t *nwalks, uint32_t push_max, uint32_t *depth_out, uint64_t *acc, double *sc,
+                     uint32_t *status, cudaStream_t s) {
+    if (k == 0) return BQ_OK;
+    int w = tuning_aesc_walks_per_lane();
+    if (w != 2 && w != 4 && w != 8) w = 4;
+    const uint32_t bouquet = 32u * (uint32_t)w;
+    if (k >= kMaxBucketEdges) return fail(BQ_EINVAL, "k = %llu edges in one estimate", (unsigned long long)k);
+    // scratch: info[k] | begin[k + 1] bucket[k + 1] | tasks[k] | next_task |
+    // (edges[2k] if all-edges)
+    const size_t info_bytes = sizeof(QueryInfo) * k;
+    const size_t begin_bytes = sizeof(uint64_t) * (k + 1) + ((sizeof(uint32_t) * bucket_count(k) + 7) & ~(size_t)7);
+    const size_t task_bytes = sizeof(uint32_t) * ((k + 1) & ~1ull);
+    const size_t edge_bytes = edges_uv ? 0 : sizeof(uint32_t) * 2 * k;
+    const size_t bytes = info_bytes + begin_bytes + task_bytes + 16 + edge_bytes;
+    char *buf = nullptr;
+    int rc = scratch_alloc((void **)&buf, bytes, s);
+    if (rc) return rc;
+    QueryInfo *info = (QueryInfo *)buf;
+    uint64_t *begin = (uint64_t *)(buf + info_bytes);
+    uint32_t *tasks = (uint32_t *)(buf + info_bytes + begin_bytes);
+    unsigned long long *next_task = (unsigned long long *)(buf + info_bytes + begin_bytes + task_bytes);
+    uint32_t *all_uv = (uint32_t *)(buf + info_bytes + begin_bytes + task_bytes + 16);
+    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(uint64_t) * 4 * k, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next_task, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        scratch_free(buf, s);
+        return cuda_fail(e, "aesc push setup");
+    }
+    const uint32_t *uv = edges_uv;
+    {
+        ProfScope prof(kProfAescAux, s);
+        if (!uv) {
+            count_launches(1);
+            canonical_edges_kernel<<<blocks_for((uint64_t)g.n * 32, kThreads), kThreads, 0, s>>>(g, all_uv);
+            uv = all_uv;
+        }
+        count_launches(1);
+        prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, push_max, info,
+                                                                    tasks, depth_out, sc, status);
+        rc = scan_u32_to_u64(tasks, begin, k, s);
+        if (rc == BQ_OK) {
+            count_launches(1);
+            build_bucket_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(
+                begin, k, reinterpret_cast<uint32_t *>(begin + k + 1));
+        }
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAesc, s);
+        count_launches(1);
+        rc = with_edges(g, [&](auto el) {
+            using EL = decltype(el);
+            if (w == 2) return launch_push_count<EL, 2>(el, g, info, begin, k, seed, next_task, acc64, s);
+            if (w == 8) return launch_push_count<EL, 8>(el, g, info, begin, k, seed, next_task, acc64, s);
+            return launch_push_count<EL, 4>(el, g, info, begin, k, seed, next_task, acc64, s);
+        });
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAescAux, s);
+        count_launches(1);
+        finalize_push_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, acc64, sc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "finalize_push_kernel");
     }
     scratch_free(buf, s);
     return rc;

@@ -25,7 +25,7 @@ std::atomic<int> g_walks_per_lane{4};
 std::atomic<int> g_aggregate{0};
 std::atomic<int> g_aesc_walks_per_lane{4};
 std::atomic<int> g_edge_records{1};
-std::atomic<int> g_hub_bits{13};
+std::atomic<int> g_hub_slots{8192};
 std::atomic<int> g_l2_hints{0};
 std::atomic<int> g_aesc_hub{0};
 }  // namespace
@@ -144,7 +144,7 @@ int tuning_walks_per_lane() { return g_walks_per_lane.load(); }
 bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
 int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
 int tuning_layout() { return g_edge_records.load(); }
-int tuning_hub_bits() { return g_hub_bits.load(); }
+int tuning_hub_slots() { return g_hub_slots.load(); }
 bool tuning_l2_hints() { return g_l2_hints.load() != 0; }
 bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
 
@@ -583,6 +583,57 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
     return rc;
 }
 
+int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
+                          const uint32_t *tau_dev, const uint32_t *nwalks_dev, uint32_t push_max, uint32_t flags,
+                          uint32_t *depth_dev, uint64_t *acc_dev, double *sc_dev, void *stream) {
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
+    if (push_max > 1) return fail(BQ_EINVAL, "push_max = %u (0 or 1)", push_max);
+    if (k && (!tau_dev || !nwalks_dev || !acc_dev || !sc_dev))
+        return fail(BQ_EINVAL, "tau, nwalks, acc or sc is NULL");
+    if (!edges_uv_dev && (k != g->nnz / 2 || k != g->m_upper))
+        return fail(BQ_EINVAL, "all-edges estimate needs k = m = %llu (got %llu; %llu edges above the diagonal)",
+                    (unsigned long long)(g->nnz / 2), (unsigned long long)k, (unsigned long long)g->m_upper);
+    if (k == 0) return BQ_OK;
+    DeviceGuard guard(g->device);
+    uint32_t *status = nullptr;
+    int rc = status_word(g->device, &status);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(flags & BQ_HOST_IO))
+        return launch_aesc_push(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, push_max, depth_dev, acc_dev,
+                                sc_dev, status, s);
+
+    const size_t eb = edges_uv_dev ? sizeof(uint32_t) * 2 * k : 0;
+    const size_t tb = sizeof(uint32_t) * k, ab = sizeof(uint64_t) * 4 * k, scb = sizeof(double) * k;
+    char *buf = nullptr;
+    rc = scratch_alloc((void **)&buf, scb + ab + 3 * tb + eb, s);
+    if (rc) return rc;
+    double *d_sc = (double *)buf;
+    uint64_t *d_acc = (uint64_t *)(buf + scb);
+    uint32_t *d_tau = (uint32_t *)(buf + scb + ab);
+    uint32_t *d_nw = (uint32_t *)(buf + scb + ab + tb);
+    uint32_t *d_depth = (uint32_t *)(buf + scb + ab + 2 * tb);
+    uint32_t *d_uv = edges_uv_dev ? (uint32_t *)(buf + scb + ab + 3 * tb) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_tau, tau_dev, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_nw, nwalks_dev, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && d_uv) e = cudaMemcpyAsync(d_uv, edges_uv_dev, eb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "host-io upload");
+    if (rc == BQ_OK)
+        rc = launch_aesc_push(g->view(), seed, d_uv, k, d_tau, d_nw, push_max, d_depth, d_acc, d_sc, status, s);
+    if (rc == BQ_OK) {
+        e = cudaMemcpyAsync(acc_dev, d_acc, ab, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc_dev, d_sc, scb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && depth_dev) e = cudaMemcpyAsync(depth_dev, d_depth, tb, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "host-io download");
+    }
+    scratch_free(buf, s);
+    if (rc == BQ_OK) rc = bq_sync(stream);
+    else cudaStreamSynchronize(s);
+    return rc;
+}
+
 int bq_sync(void *stream) {
     g_last_error[0] = 0;
     cudaStream_t s = (cudaStream_t)stream;
@@ -653,7 +704,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->aggregate_visits = (uint32_t)g_aggregate.load();
     out->aesc_lanes = (uint32_t)g_aesc_walks_per_lane.load();
     out->layout = (uint32_t)g_edge_records.load();
-    out->hub_bits = (uint32_t)g_hub_bits.load();
+    out->hub_slots = (uint32_t)g_hub_slots.load();
     out->l2_hints = (uint32_t)g_l2_hints.load();
     out->aesc_hub = (uint32_t)g_aesc_hub.load();
     return BQ_OK;
@@ -667,15 +718,15 @@ int bq_set_tuning(const bq_tuning *in) {
     if (a != 2 && a != 4 && a != 8) return fail(BQ_EINVAL, "aesc_lanes must be 2, 4 or 8");
     if (in->aggregate_visits > 1) return fail(BQ_EINVAL, "aggregate_visits must be 0 or 1");
     if (in->layout > 5) return fail(BQ_EINVAL, "layout must be 0 to 5");
-    if (in->hub_bits != 0 && (in->hub_bits < 10 || in->hub_bits > 13))
-        return fail(BQ_EINVAL, "hub_bits must be 0 or 10..13");
+    if (in->hub_slots != 0 && (in->hub_slots < 1024 || in->hub_slots > kHubSlotsMax))
+        return fail(BQ_EINVAL, "hub_slots must be 0 or 1024..%u", kHubSlotsMax);
     if (in->l2_hints > 1) return fail(BQ_EINVAL, "l2_hints must be 0 or 1");
     if (in->aesc_hub > 1) return fail(BQ_EINVAL, "aesc_hub must be 0 or 1");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
     g_edge_records.store((int)in->layout);
-    g_hub_bits.store((int)in->hub_bits);
+    g_hub_slots.store((int)in->hub_slots);
     g_l2_hints.store((int)in->l2_hints);
     g_aesc_hub.store((int)in->aesc_hub);
     return BQ_OK;

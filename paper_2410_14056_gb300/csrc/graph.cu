@@ -303,13 +303,13 @@ __global__ void build_packed_ids_kernel(const uint32_t *__restrict__ nbrs, uint6
 
 // Hub table: every vertex with a neighbour bids for slot hash(v); the highest
 // degree wins (ties: the smaller id).  key = degree << 32 | (2^32 - 1 - v).
-__global__ void hub_select_kernel(const int64_t *__restrict__ off, uint32_t n, uint32_t hub_bits,
+__global__ void hub_select_kernel(const int64_t *__restrict__ off, uint32_t n, uint32_t slots,
                                   unsigned long long *__restrict__ best) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t deg = (uint64_t)(off[v + 1] - off[v]);
         if (deg == 0) continue;
-        const uint32_t slot = ((uint32_t)v * kHubHash) >> (32 - hub_bits);
+        const uint32_t slot = hub_slot((uint32_t)v, slots);
         atomicMax(best + slot, (unsigned long long)((deg << 32) | (0xffffffffull - v)));
     }
 }
@@ -542,15 +542,14 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
             }
         }
         g->layout = g->d_pk ? 5 : (g->d_edge8 ? 2 : (g->d_edge16 ? 3 : (compact ? 0 : 4)));
-        const int hub_bits = tuning_hub_bits();
-        if (hub_bits > 0 && compact && n > 0) {
-            const uint32_t slots = 1u << hub_bits;
+        const uint32_t slots = (uint32_t)tuning_hub_slots();
+        if (slots > 0 && compact && n > 0) {
             unsigned long long *best = nullptr;
             e = cudaMalloc(&best, sizeof(unsigned long long) * slots);
             if (e == cudaSuccess) e = cudaMalloc(&g->d_hub_tag, sizeof(uint32_t) * slots);
             if (e == cudaSuccess) e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * slots, s);
             if (e == cudaSuccess) {
-                hub_select_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, n, (uint32_t)hub_bits, best);
+                hub_select_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, n, slots, best);
                 hub_finish_kernel<<<grid_for(slots, 256), 256, 0, s>>>(best, slots, g->d_hub_tag);
                 e = cudaStreamSynchronize(s);
             }
@@ -559,7 +558,7 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
                 rc = cuda_fail(e, "hub table");
                 goto done;
             }
-            g->hub_bits = (uint32_t)hub_bits;
+            g->hub_slots = slots;
             g->device_bytes += sizeof(uint32_t) * slots;
         }
     }

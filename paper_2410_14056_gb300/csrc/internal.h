@@ -23,6 +23,12 @@ enum StatusBits : uint32_t {
 
 constexpr uint32_t kNoHub = 0xffffffffu;
 constexpr uint32_t kHubHash = 0x9E3779B1u;
+constexpr uint32_t kHubSlotsMax = 13312;  // 16 B per slot: 208 KiB of shared memory
+
+// Hub-table slot of vertex v: the high half of (v * kHubHash mod 2^32) * slots.
+__host__ __device__ __forceinline__ uint32_t hub_slot(uint32_t v, uint32_t slots) {
+    return (uint32_t)(((uint64_t)(v * kHubHash) * slots) >> 32);
+}
 
 // Stream reserved for walk-batch walks; AESC walks use stream 2 * edge + side.
 constexpr uint64_t kBatchStream = 0x4000000000000000ull;
@@ -60,10 +66,10 @@ struct DeviceGraph {
     // never straddles a chunk and one aligned vector load reads it.
     const uint4 *pk;
     uint32_t pk_bits, pk_q, pk_mask;
-    // Hub table: slot (v * 0x9E3779B1) >> (32 - hub_bits) holds the
-    // highest-degree vertex hashing there (kNoHub when empty); null if none.
+    // Hub table: slot hub_slot(v, hub_slots) holds the highest-degree
+    // vertex hashing there (kNoHub when empty); null if none.
     const uint32_t *hub_tag;
-    uint32_t hub_bits;
+    uint32_t hub_slots;
     bool compact() const { return rec8 != nullptr; }
 };
 
@@ -130,7 +136,7 @@ struct bq_graph {
     uint32_t pk_bits = 0, pk_q = 0, pk_mask = 0;
     int layout = 0;  // layout chosen at creation (bq_tuning.layout values)
     uint32_t *d_hub_tag = nullptr;
-    uint32_t hub_bits = 0;
+    uint32_t hub_slots = 0;
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
     uint64_t device_bytes = 0;
@@ -162,7 +168,7 @@ struct bq_graph {
         v.pk_q = pk_q;
         v.pk_mask = pk_mask;
         v.hub_tag = d_hub_tag;
-        v.hub_bits = hub_bits;
+        v.hub_slots = hub_slots;
         return v;
     }
 };
@@ -195,7 +201,7 @@ int tuning_walks_per_lane();
 bool tuning_aggregate_visits();
 int tuning_aesc_walks_per_lane();
 int tuning_layout();    // graph layout built at creation (bq_tuning.layout)
-int tuning_hub_bits();  // hub table size built at creation (bq_tuning.hub_bits)
+int tuning_hub_slots();  // hub table size built at creation (bq_tuning.hub_slots)
 bool tuning_l2_hints(); // L2 eviction policies on the walk kernel's loads
 bool tuning_aesc_hub();  // AESC counting reads hub records from shared memory
 
@@ -257,5 +263,8 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,
                 uint64_t k, const uint32_t *tau, const uint32_t *nwalks,
                 const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
                 cudaStream_t s);
+int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
+                     const uint32_t *tau, const uint32_t *nwalks, uint32_t push_max, uint32_t *depth_out,
+                     uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s);
 
 }  // namespace bq

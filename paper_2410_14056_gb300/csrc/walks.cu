@@ -202,7 +202,7 @@ constexpr int kHubThreads = 1024;
 
 template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kHubThreads, 1)
-walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ hub_tag, uint32_t hub_bits,
+walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ hub_tag, uint32_t hub_slots,
                 const uint32_t *__restrict__ sorted_id, const uint32_t *__restrict__ sorted_start,
                 const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps, uint64_t seed, Sampler smp,
                 bool visit_start, uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
@@ -210,8 +210,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
     extern __shared__ __align__(16) unsigned char hub_smem[];
     const uint64_t pol_keep = l2_hints ? l2_policy_keep() : 0ull;
     const uint64_t pol_stream = l2_hints ? l2_policy_stream() : 0ull;
-    const uint32_t slots = 1u << hub_bits;
-    const uint32_t shift = 32 - hub_bits;
+    const uint32_t slots = hub_slots;
     uint2 *s_rec = reinterpret_cast<uint2 *>(hub_smem);
     uint32_t *s_tag = reinterpret_cast<uint32_t *>(s_rec + slots);
     uint32_t *s_cnt = s_tag + slots;
@@ -262,7 +261,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
             if (act[j]) {
                 if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1)] = cur[j];
                 if (visit_start) {
-                    const uint32_t slot = (cur[j] * kHubHash) >> shift;
+                    const uint32_t slot = hub_slot(cur[j], slots);
                     if (s_tag[slot] == cur[j]) atomicAdd(s_cnt + slot, 1u);
                     else atomicAdd(visits + cur[j], 1u);
                 }
@@ -283,7 +282,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 if (!act[j]) continue;
-                const uint32_t slot = (cur[j] * kHubHash) >> shift;
+                const uint32_t slot = hub_slot(cur[j], slots);
                 if (s_tag[slot] == cur[j]) {
                     atomicAdd(s_cnt + slot, 1u);
                     if constexpr (EL::kSplit) {
@@ -377,7 +376,7 @@ template <typename EL, int W, bool COUPLED>
 bool launch_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
                   uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                   uint32_t *paths, unsigned long long *next_chunk, cudaStream_t s) {
-    const size_t smem = (size_t)16 << g.hub_bits;
+    const size_t smem = (size_t)16 * g.hub_slots;
     auto kernel = walk_hub_kernel<EL, W, COUPLED>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -393,7 +392,7 @@ bool launch_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32
     }
     ProfScope prof(kProfWalk, s);
     count_launches(1);
-    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.offsets, g.hub_tag, g.hub_bits, sid, sst, n_valid, n_steps,
+    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.offsets, g.hub_tag, g.hub_slots, sid, sst, n_valid, n_steps,
                                                    seed, smp, visit_start, visits, paths, next_chunk,
                                                    tuning_l2_hints());
     return true;

@@ -147,15 +147,15 @@ def test_hub_table_never_changes_results(env, layout):
     nw = rng.integers(1, 900, uv.shape[0]).astype(np.uint32)
     old = bq.get_tuning()
     try:
-        for hub_bits in (0, 10, 13):
-            bq.set_tuning(layout=layout, hub_bits=hub_bits)
+        for hub_slots in (0, 1024, 5000, 13312):
+            bq.set_tuning(layout=layout, hub_slots=hub_slots)
             graph = bq.Graph.from_csr(g)
             for sampler in (None, (1, 4, 32)):
                 want = oracle.aesc_estimate(g, 21, uv, tau, nw, sampler=sampler)
                 for hub in (1, 0):
                     bq.set_tuning(aesc_hub=hub)
                     counts, sc = bq.aesc_estimate_host(graph, 21, uv, tau, nw, sampler=sampler)
-                    assert np.array_equal(counts, want[0]) and same_bits(sc, want[1]), (hub_bits, sampler, hub)
+                    assert np.array_equal(counts, want[0]) and same_bits(sc, want[1]), (hub_slots, sampler, hub)
             graph.close()
     finally:
         bq.set_tuning(**old)

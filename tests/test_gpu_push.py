@@ -1,0 +1,130 @@
+"""AESC with a push phase (depth 0 or 1) on the GPU: depths, fixed-point
+accumulators and FP64 estimates bit-identical to the oracle's, for every
+graph layout and lane count, through device tensors and host buffers."""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import all_edges, chung_lu, er_with_path, gnp_connected, rmat
+
+pytestmark = pytest.mark.gpu
+
+SCHED = (2.0, 2, 64, 9.0, 32)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_14056_gb300 as bq
+    assert torch.cuda.is_available()
+    return bq, torch
+
+
+def same_bits(a, b):
+    return np.array_equal(np.asarray(a, np.float64).view(np.uint64), np.asarray(b, np.float64).view(np.uint64))
+
+
+def check(bq, graph, g, seed, uv, tau, nw, push_max):
+    depth, acc, sc = bq.aesc_estimate_push_host(graph, seed, uv, tau, nw, push_max)
+    od, oa, osc = oracle.aesc_push_estimate(g, seed, uv if uv is not None else all_edges(g), tau, nw, push_max)
+    assert np.array_equal(depth, od)
+    assert np.array_equal(acc, oa)
+    assert same_bits(sc, osc)
+    return depth
+
+
+@pytest.mark.parametrize("push_max", [0, 1])
+def test_subset_bit_exact_both_depths(env, push_max):
+    bq, torch = env
+    g = er_with_path(1000, 5000, 1)
+    graph = bq.Graph.from_csr(g)
+    rng = np.random.default_rng(4)
+    uv_all = all_edges(g)
+    uv = uv_all[rng.choice(uv_all.shape[0], 300, replace=False)]
+    uv[::2] = uv[::2, ::-1]
+    eps = np.where(np.arange(300) % 3 == 0, 0.05, 0.2)
+    tau = np.zeros(300, np.uint32)
+    nw = np.zeros(300, np.uint32)
+    for e in (0.05, 0.2):
+        sel = eps == e
+        t, n = oracle.plan_scheduled(g, uv[sel], e, *SCHED)
+        tau[sel], nw[sel] = t, n
+    nw[::3] = 4  # 2N below d(u) + d(v): these edges stay at depth 0
+    depth = check(bq, graph, g, 9, uv, tau, nw, push_max)
+    if push_max:
+        assert depth.any() and not depth.all()  # both depths in one launch
+    else:
+        assert not depth.any()
+
+
+def test_all_edges_and_tau_one(env):
+    bq, torch = env
+    g = gnp_connected(40, 0.15, 6)
+    graph = bq.Graph.from_csr(g)
+    k = all_edges(g).shape[0]
+    tau = (np.arange(k, dtype=np.uint32) % 5) + 1  # includes tau = 1: depth-1 edges without walks
+    nw = ((np.arange(k, dtype=np.uint32) * 53) % 700 + 1).astype(np.uint32)
+    depth = check(bq, graph, g, 13, None, tau, nw, 1)
+    assert np.any((depth == 1) & (tau == 1))
+
+
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
+def test_layouts_and_lanes_never_change_results(env, layout):
+    bq, torch = env
+    g = rmat(12, 8, seed=5)
+    rng = np.random.default_rng(2)
+    uv_all = all_edges(g)
+    uv = uv_all[rng.choice(uv_all.shape[0], 400, replace=False)]
+    tau, nw = oracle.plan_scheduled(g, uv, 0.1, *SCHED)
+    want = oracle.aesc_push_estimate(g, 5, uv, tau, nw, 1)
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(layout=layout)
+        graph = bq.Graph.from_csr(g)
+        for lanes in (2, 4, 8):
+            bq.set_tuning(aesc_lanes=lanes)
+            depth, acc, sc = bq.aesc_estimate_push_host(graph, 5, uv, tau, nw, 1)
+            assert np.array_equal(depth, want[0]) and np.array_equal(acc, want[1]) and same_bits(sc, want[2]), lanes
+        graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
+def test_device_tensors_match_host_buffers(env):
+    bq, torch = env
+    g = chung_lu(20000, 8.0, 2.2, 3)
+    graph = bq.Graph.from_csr(g)
+    rng = np.random.default_rng(6)
+    uv_all = all_edges(g)
+    uv = uv_all[rng.choice(uv_all.shape[0], 500, replace=False)]
+    tau, nw = oracle.plan_scheduled(g, uv, 0.05, *SCHED)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+    depth, acc, sc = bq.aesc_estimate_push(graph, 77, dev(uv), dev(tau), dev(nw), 1)
+    bq.sync()
+    check(bq, graph, g, 77, uv, tau, nw, 1)
+    d2, a2, s2 = bq.aesc_estimate_push_host(graph, 77, uv, tau, nw, 1)
+    assert np.array_equal(depth.cpu().numpy().view(np.uint32), d2)
+    assert np.array_equal(acc.cpu().numpy().view(np.uint64), a2)
+    assert same_bits(sc.cpu().numpy(), s2)
+
+
+def test_errors(env):
+    bq, torch = env
+    g = gnp_connected(30, 0.2, 2)
+    graph = bq.Graph.from_csr(g)
+    uv = all_edges(g)[:3]
+    tau = np.full(3, 3, np.uint32)
+    nw = np.full(3, 10, np.uint32)
+    with pytest.raises(bq.BouquetError) as ei:
+        bq.aesc_estimate_push_host(graph, 1, uv, tau, nw, push_max=2)
+    assert ei.value.code == bq.EINVAL
+    row0 = set(g.row(0).tolist())
+    non = next(x for x in range(1, g.n) if x not in row0)
+    bad = np.array([[0, non]], np.uint32)
+    with pytest.raises(bq.BouquetError) as ei:
+        bq.aesc_estimate_push_host(graph, 1, bad, tau[:1], nw[:1])
+    assert ei.value.code == bq.ENOEDGE

@@ -111,16 +111,16 @@ def test_tuning_never_changes_results(env):
         bq.set_tuning(**old)
 
 
-@pytest.mark.parametrize("hub_bits", [0, 10, 13])
+@pytest.mark.parametrize("hub_slots", [0, 1024, 5000, 8192, 13312])
 @pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
-def test_every_graph_layout_bit_exact(env, layout, hub_bits):
+def test_every_graph_layout_bit_exact(env, layout, hub_slots):
     """Plain or bit-packed neighbour ids with 8- or 16-byte vertex records,
     8- or 16-byte edge records, with or without the shared-memory hub table:
     many ways to read a step, one result."""
     bq, torch = env
     old = bq.get_tuning()
     try:
-        bq.set_tuning(layout=layout, hub_bits=hub_bits)
+        bq.set_tuning(layout=layout, hub_slots=hub_slots)
         for name in ("rmat12", "isolated", "cycle10"):
             g = GRAPHS[name]
             graph = bq.Graph.from_csr(g)

@@ -54,6 +54,7 @@ def test_argument_errors_without_device(lib):
     assert lib.bq_graph_create(3, None, None, 0, None, None) == bq.EINVAL
     assert lib.bq_walk_batch(None, 0, None, 0, 1, 0, None, 0, None, None, None) == bq.EINVAL
     assert lib.bq_aesc_plan(None, None, 0, 0.1, 0.01, 0, None, None, None) == bq.EINVAL
+    assert lib.bq_aesc_estimate_push(None, 0, None, 0, None, None, 1, 0, None, None, None, None) == bq.EINVAL
     assert lib.bq_graph_destroy(None) == bq.OK
 
 
@@ -74,7 +75,7 @@ def test_tuning_roundtrip_and_validation(lib):
     try:
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
-                                   "layout": old["layout"], "hub_bits": old["hub_bits"],
+                                   "layout": old["layout"], "hub_slots": old["hub_slots"],
                                    "l2_hints": old["l2_hints"], "aesc_hub": old["aesc_hub"]}
         assert old["aesc_hub"] == 0  # off by default
         bq.set_tuning(aesc_hub=1)
@@ -83,11 +84,13 @@ def test_tuning_roundtrip_and_validation(lib):
             bq.set_tuning(aesc_hub=2)
         with pytest.raises(bq.BouquetError):
             bq.set_tuning(layout=6)
-        for bad in (1, 9, 14):
+        assert old["hub_slots"] == 8192
+        for bad in (1, 1023, 13313, 1 << 14):
             with pytest.raises(bq.BouquetError):
-                bq.set_tuning(hub_bits=bad)
-        bq.set_tuning(hub_bits=0)
-        assert bq.get_tuning()["hub_bits"] == 0
+                bq.set_tuning(hub_slots=bad)
+        for ok in (0, 1024, 5000, 13312):
+            bq.set_tuning(hub_slots=ok)
+            assert bq.get_tuning()["hub_slots"] == ok
         with pytest.raises(bq.BouquetError) as ei:
             bq.set_tuning(walk_lanes=3)
         assert ei.value.code == bq.EINVAL

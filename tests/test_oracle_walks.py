@@ -148,3 +148,37 @@ def test_paths_by_id_replays_batch_walks():
     _, cp = oracle.walk_batch(g, 55, starts, 12, sampler=(1, 4, 8), want_paths=True)
     sub = oracle.walk_paths_by_id(g, 55, ids, starts[ids.astype(np.int64)], 12, sampler=(1, 4, 8))
     assert np.array_equal(sub, cp[ids.astype(np.int64)])
+
+
+def test_literal_saba_word_collapses_walks():
+    """The paper's SABA word taken literally (Eq. select-proposed, one seed
+    X_W per walk xor a shared hash of (vertex, length)) decides a walk's
+    choices by the top bits of X_W alone on a low-degree graph: on C10
+    thousands of walks follow a handful of paths, and the l-step law is far
+    from P^l, where independent keys give every one of the 2^8 paths."""
+    g = cycle(10)
+    starts = np.zeros(4096, np.uint32)
+    _, lit = oracle.walk_batch(g, 5, starts, 8, sampler=(2, 0, 1), want_paths=True)
+    _, ind = oracle.walk_batch(g, 5, starts, 8, want_paths=True)
+    assert len({tuple(r) for r in lit.tolist()}) <= 8
+    assert len({tuple(r) for r in ind.tolist()}) == 256
+    for row in lit:  # still walks on the graph
+        for a, b in zip(row[:-1], row[1:]):
+            assert b in g.row(int(a))
+    law = exact.walk_distribution(g, 0, 8)
+    emp = np.bincount(lit[:, 8], minlength=g.n) / lit.shape[0]
+    assert np.abs(emp - law).max() > 0.2
+
+
+def test_literal_saba_word_is_per_walk_and_not_for_aesc():
+    g = rmat(8, 8, seed=1)
+    starts = np.arange(200, dtype=np.uint32) % g.n
+    starts = starts[np.diff(g.offsets)[starts] > 0]
+    _, p1 = oracle.walk_batch(g, 9, starts, 6, sampler=(2, 0, 1), want_paths=True)
+    ids = np.arange(starts.size, dtype=np.uint64)[::-1].copy()
+    p2 = oracle.walk_paths_by_id(g, 9, ids, starts[::-1].copy(), 6, sampler=(2, 0, 1))
+    assert np.array_equal(p2[::-1], p1)
+    uv = np.array([[int(g.nbrs[0]), 0]], np.uint32) if g.offsets[1] > 0 else None
+    if uv is not None:
+        with pytest.raises(oracle.OracleError):
+            oracle.aesc_counts(g, 1, uv, np.array([3], np.uint32), np.array([4], np.uint32), sampler=(2, 0, 1))
