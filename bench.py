@@ -412,6 +412,45 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     }
 
 
+def sampler_rows(bq, torch, graph, g, seed, st, args):
+    """The bouquet walk batch with each sampler (independent, coupled with 8
+    shared bits in groups of 32, the paper's SABA word taken literally), and
+    how far walks from one start spread: 64 starts x 4096 walks x 16 steps,
+    distinct vertices per start at steps 1, 4, 16 and distinct whole paths."""
+    import numpy as np
+    rows = {}
+    rng = np.random.default_rng(5)
+    live = np.flatnonzero(np.diff(g.offsets) > 0)
+    picks = rng.choice(live, 64, replace=False).astype(np.uint32)
+    dstarts = torch.from_numpy(np.repeat(picks, 4096).view(np.int32)).cuda()
+    visits = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+    for name, smp in (("independent", None), ("coupled_t8_w32", (1, 8, 32)), ("saba_literal", (2, 0, 1))):
+        for _ in range(3):
+            visits.zero_()
+            bq.walk_batch(graph, seed, st, N_STEPS, sampler=smp, visits=visits)
+        bq.sync()
+        evs = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            visits.zero_()
+            bq.walk_batch(graph, seed, st, N_STEPS, sampler=smp, visits=visits)
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        bq.sync()
+        ms = min(a.elapsed_time(b) for a, b in evs)
+        paths = torch.zeros((dstarts.numel(), 17), dtype=torch.int32, device="cuda")
+        bq.walk_batch(graph, seed + 1, dstarts, 16, sampler=smp, paths=paths)
+        bq.sync()
+        p = paths.cpu().numpy().reshape(64, 4096, 17)
+        spread = {f"step{l}": float(np.mean([np.unique(p[i, :, l]).size for i in range(64)])) for l in (1, 4, 16)}
+        whole = float(np.mean([np.unique(p[i], axis=0).shape[0] for i in range(64)]))
+        rows[name] = {"ms_per_step": ms, "walk_steps_per_s": N_WALKS * N_STEPS / (ms / 1e3),
+                      "distinct_vertices_per_start": spread, "distinct_paths_per_4096": whole}
+    return rows
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -519,6 +558,8 @@ def run_ours(args):
                "d2h_bytes_per_step": int(4 * g.n), "ms_per_step": e2e_s * 1e3,
                "api": "bq_walk_batch with BQ_HOST_IO (pinned host buffers)"}
 
+    samplers = sampler_rows(bq, torch, graph, g, seed, st, args) if rank == 0 and not args.no_aesc else None
+
     aesc = aesc_pl = None
     if not args.no_aesc and rank == 0:
         aesc = aesc_measure(bq, torch, max(5, args.steps), args.warmup)
@@ -551,6 +592,7 @@ def run_ours(args):
             "naive": {"value": whole_job_rate(world, steps_per_batch, naive_ms / 1e3), "unit": "walk-steps/s",
                       "ms_per_step": naive_ms,
                       "bouquet_speedup": naive_ms / ms_per_step},
+            "samplers": samplers,
             "aesc": aesc,
             "aesc_powerlaw": aesc_pl,
         }

@@ -127,9 +127,19 @@ int bq_graph_set_spectrum(bq_graph *g, double lambda2, double lambda_neg);
                                  (step, vertex): similar walks stay together
                                  (the aim of SABA, Sec. 3.3), each walk still
                                  an exact random walk */
+#define BQ_SAMPLER_SABA 2u    /* walk batches only, for comparison: Eq.
+                                 select-proposed taken literally, r = X_W xor
+                                 h(cur, l) with X_W the walk's fixed 32-bit
+                                 seed (low half of its key) and h one hash of
+                                 (vertex, step) for the whole batch; in
+                                 bouquet mode the walks of each start are
+                                 ordered by X_W (SABA's arrangement).  Its
+                                 walks are NOT exact random walks (later
+                                 choices follow from X_W's top bits), so
+                                 AESC calls refuse it; t and width unused */
 
 typedef struct bq_sampler {
-    uint32_t kind;  /* BQ_SAMPLER_IND or BQ_SAMPLER_COUPLED */
+    uint32_t kind;  /* BQ_SAMPLER_IND, BQ_SAMPLER_COUPLED or BQ_SAMPLER_SABA */
     uint32_t t;     /* COUPLED: shared bits, 0..32 (32 = move together) */
     uint32_t width; /* COUPLED: group size, >= 1 */
 } bq_sampler;

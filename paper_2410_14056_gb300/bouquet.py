@@ -41,6 +41,7 @@ HOST_IO = 0x2
 
 SAMPLER_IND = 0
 SAMPLER_COUPLED = 1
+SAMPLER_SABA = 2  # the literal SABA word: walk batches only, for comparison
 
 PLAN_CERTIFIED = 0
 PLAN_SCHEDULED = 1

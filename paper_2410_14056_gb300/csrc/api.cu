@@ -162,12 +162,21 @@ struct DeviceGuard {
     }
 };
 
-int check_sampler(const bq_sampler *in, Sampler &out) {
+// The literal SABA word (walk batches only) runs on the coupled path with
+// t = kSabaT and one group for the whole batch.
+int check_sampler(const bq_sampler *in, Sampler &out, bool allow_saba = false) {
     out.kind = 0;
     out.t = 0;
     out.width = 1;
     if (!in) return BQ_OK;
     if (in->kind == BQ_SAMPLER_IND) return BQ_OK;
+    if (in->kind == BQ_SAMPLER_SABA) {
+        if (!allow_saba) return fail(BQ_EINVAL, "the literal SABA sampler is for walk batches only");
+        out.kind = 1;
+        out.t = kSabaT;
+        out.width = 1;
+        return BQ_OK;
+    }
     if (in->kind != BQ_SAMPLER_COUPLED) return fail(BQ_EINVAL, "unknown sampler kind %u", in->kind);
     if (in->width < 1) return fail(BQ_EINVAL, "coupled sampler needs width >= 1");
     if (in->t > 32) return fail(BQ_EINVAL, "coupled sampler needs 0 <= t <= 32 (got %u)", in->t);
@@ -211,7 +220,9 @@ void host_structure(bq_graph *g) {
 
 }  // namespace
 
-int validate_sampler(const bq_sampler *in, Sampler &out) { return check_sampler(in, out); }
+int validate_sampler(const bq_sampler *in, Sampler &out, bool allow_saba) {
+    return check_sampler(in, out, allow_saba);
+}
 
 }  // namespace bq
 
@@ -377,7 +388,7 @@ int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, 
     if (paths_dev && n_walks > UINT64_MAX / ((uint64_t)n_steps + 1) / sizeof(uint32_t))
         return fail(BQ_EINVAL, "paths array size overflows");
     Sampler smp;
-    int rc = check_sampler(sampler, smp);
+    int rc = check_sampler(sampler, smp, true);
     if (rc) return rc;
     if (n_walks == 0) return BQ_OK;
     DeviceGuard guard(g->device);

@@ -17,6 +17,8 @@
 
 #include <stdint.h>
 
+#include "internal.h"
+
 namespace bq {
 
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
@@ -75,14 +77,16 @@ __device__ __forceinline__ uint32_t step_word(uint64_t state, uint32_t cur) {
 
 __device__ __forceinline__ uint32_t choose(uint32_t r, uint32_t d) { return __umulhi(r, d); }
 
-// Random word of the sampler: independent, or shared-top-bits coupling.
+// Random word of the sampler: independent, or shared-top-bits coupling; or,
+// with t == kSabaT, Eq. select-proposed literally: the walk's fixed seed xw
+// xor the shared hash of (cur, l) (group_state is then one key for the batch).
 template <bool COUPLED>
 __device__ __forceinline__ uint32_t sample_word(uint64_t own_state, uint64_t group_state,
-                                                uint32_t cur, uint32_t t) {
-    const uint32_t own = step_word(own_state, cur);
-    if (!COUPLED) return own;
+                                                uint32_t cur, uint32_t t, uint32_t xw = 0u) {
+    if (!COUPLED) return step_word(own_state, cur);
     const uint32_t shared = step_word(group_state, cur);
-    return shared ^ (t >= 32 ? 0u : (own >> t));
+    if (t == kSabaT) return shared ^ xw;
+    return shared ^ (t >= 32 ? 0u : (step_word(own_state, cur) >> t));
 }
 
 }  // namespace bq

@@ -36,10 +36,13 @@ constexpr uint64_t kBatchStream = 0x4000000000000000ull;
 constexpr uint64_t kGroupBit = 0x8000000000000000ull;
 
 struct Sampler {
-    uint32_t kind;   // 0 independent, 1 coupled
-    uint32_t t;      // coupled: shared top bits
+    uint32_t kind;   // 0 independent, 1 coupled (also the literal SABA word)
+    uint32_t t;      // coupled: shared top bits; kSabaT: the literal SABA word
     uint32_t width;  // coupled: group width
 };
+
+// Sampler::t of the paper's SABA word taken literally (BQ_SAMPLER_SABA).
+constexpr uint32_t kSabaT = 0xffffffffu;
 
 // Device view of a graph.  Vertex records are 8 bytes {row offset, degree}
 // when nnz < 2^32 (compact), else 16 bytes {offset lo, offset hi, degree, 0}.
@@ -246,7 +249,7 @@ size_t scan_u32_to_u64_ws_bytes(uint64_t n);
 int scan_u32_to_u64_ws(const uint32_t *in, uint64_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s);
 // api.cu: the device's status word if it was already allocated (never allocates).
 int existing_status_word(int device, uint32_t **out);
-int validate_sampler(const bq_sampler *in, Sampler &out);
+int validate_sampler(const bq_sampler *in, Sampler &out, bool allow_saba = false);
 
 // ---- batch.cu, used by the server: one query's edges (prepare + task scan),
 // an iteration over windows of several queries' tasks, and the finalize.

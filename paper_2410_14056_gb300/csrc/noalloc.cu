@@ -62,7 +62,7 @@ extern "C" int bq_walk_batch_noalloc(const bq_graph *g, uint64_t seed, const uin
     if (paths_dev && n_walks > UINT64_MAX / ((uint64_t)n_steps + 1) / sizeof(uint32_t))
         return fail(BQ_EINVAL, "paths array size overflows");
     Sampler smp;
-    int rc = validate_sampler(sampler, smp);
+    int rc = validate_sampler(sampler, smp, true);
     if (rc) return rc;
     const size_t need = walk_batch_scratch_bytes(g->n, n_walks);
     if (need > kStaticScratchBytes)

@@ -68,7 +68,9 @@ walk_naive_kernel(RL rl, const uint32_t *__restrict__ nbrs, uint32_t n, const ui
             continue;
         }
         uint64_t st = walk_key(seed, kBatchStream, i);
-        uint64_t gs = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, i / smp.width) : 0;
+        const bool saba = COUPLED && smp.t == kSabaT;
+        uint64_t gs = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, saba ? 0 : i / smp.width) : 0;
+        const uint32_t xw = (uint32_t)st;
         uint32_t *row = paths ? paths + i * ((uint64_t)n_steps + 1) : nullptr;
         if (row) row[0] = cur;
         if (visit_start) add_visits(visits, cur, 1, checked, status);
@@ -78,7 +80,7 @@ walk_naive_kernel(RL rl, const uint32_t *__restrict__ nbrs, uint32_t n, const ui
             uint64_t off;
             uint32_t d;
             rl.load(cur, off, d);
-            if (d) cur = nbrs[off + choose(sample_word<COUPLED>(st, gs, cur, smp.t), d)];
+            if (d) cur = nbrs[off + choose(sample_word<COUPLED>(st, gs, cur, smp.t, xw), d)];
             add_visits(visits, cur, 1, checked, status);
             if (row) row[l] = cur;
         }
@@ -113,6 +115,63 @@ __global__ void scatter_starts_kernel(const uint32_t *__restrict__ starts, uint6
     }
 }
 
+// The paper's SABA arrangement for the literal SABA word: inside each start
+// vertex's bucket, walks ordered by their seed X_W (the low 32 bits of the
+// walk key; ties by id), so that a bouquet holds walks whose seeds, and so
+// whose first choices, are close.  One block per bucket, a bitonic sort in
+// shared memory of runs of up to kSabaRun walks (longer buckets are ordered
+// run by run).  The order changes which walks share a warp, not any result.
+constexpr uint32_t kSabaRun = 1024;
+
+__global__ void __launch_bounds__(256)
+saba_order_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ cursor, uint32_t n,
+                  uint64_t seed, uint32_t *__restrict__ sorted_id) {
+    __shared__ uint32_t s_key[kSabaRun];
+    __shared__ uint32_t s_id[kSabaRun];
+    for (uint32_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const uint32_t c = counts[v];
+        if (c < 2) continue;
+        const uint32_t end = cursor[v];  // after the scatter: one past v's bucket
+        for (uint32_t lo = end - c; lo < end; lo += kSabaRun) {
+            const uint32_t len = end - lo < kSabaRun ? end - lo : kSabaRun;
+            uint32_t m = 2;
+            while (m < len) m <<= 1;
+            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+                if (i < len) {
+                    const uint32_t id = sorted_id[lo + i];
+                    s_id[i] = id;
+                    s_key[i] = (uint32_t)walk_key(seed, kBatchStream, id);
+                } else {
+                    s_id[i] = 0xffffffffu;
+                    s_key[i] = 0xffffffffu;
+                }
+            }
+            __syncthreads();
+            for (uint32_t k = 2; k <= m; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+                        const uint32_t p = i ^ j;
+                        if (p > i) {
+                            const bool up = (i & k) == 0;
+                            const uint64_t a = ((uint64_t)s_key[i] << 32) | s_id[i];
+                            const uint64_t b = ((uint64_t)s_key[p] << 32) | s_id[p];
+                            if ((a > b) == up) {
+                                s_key[i] = (uint32_t)(b >> 32);
+                                s_id[i] = (uint32_t)b;
+                                s_key[p] = (uint32_t)(a >> 32);
+                                s_id[p] = (uint32_t)a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sorted_id[lo + i] = s_id[i];
+            __syncthreads();
+        }
+    }
+}
+
 // -------------------------------------------------------------- bouquet
 
 // Warp w owns grouped slots [w * 32 * W, (w + 1) * 32 * W); slot j of lane l
@@ -137,6 +196,7 @@ walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *
 
     uint32_t cur[W], id[W], deg[W], amask[W];
     uint64_t off[W], st[W], gs[W];
+    uint32_t xw[W];  // the walk's fixed seed (literal SABA word only)
     bool act[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
@@ -149,7 +209,9 @@ walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *
         deg[j] = 0;
         if (act[j]) start_record(offsets, cur[j], off[j], deg[j]);
         st[j] = walk_key(seed, kBatchStream, id[j]);
-        gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, id[j] / smp.width) : 0ull;
+        gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, smp.t == kSabaT ? 0 : id[j] / smp.width)
+                        : 0ull;
+        xw[j] = (uint32_t)st[j];
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
@@ -170,7 +232,7 @@ walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *
             st[j] += kGolden;
             if (COUPLED) gs[j] += kGolden;
             if (deg[j]) {
-                const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t, xw[j]), deg[j]);
                 el.next(off[j] + k, cur[j], off[j], deg[j]);
             }
         }
@@ -242,6 +304,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
 
         uint32_t cur[W], id[W], deg[W];
         uint64_t off[W], st[W], gs[W];
+        uint32_t xw[W];  // the walk's fixed seed (literal SABA word only)
         bool act[W], moved[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
@@ -257,7 +320,9 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
             deg[j] = 0;
             if (act[j]) start_record(offsets, cur[j], off[j], deg[j]);
             st[j] = walk_key(seed, kBatchStream, id[j]);
-            gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, id[j] / smp.width) : 0ull;
+            gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, smp.t == kSabaT ? 0 : id[j] / smp.width)
+                            : 0ull;
+            xw[j] = (uint32_t)st[j];
             if (act[j]) {
                 if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1)] = cur[j];
                 if (visit_start) {
@@ -274,7 +339,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
                 if (COUPLED) gs[j] += kGolden;
                 moved[j] = deg[j] != 0;
                 if (moved[j]) {
-                    const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                    const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t, xw[j]), deg[j]);
                     if constexpr (EL::kSplit) cur[j] = l2_hints ? el.id(off[j] + k, pol_keep) : el.id(off[j] + k);
                     else el.next(off[j] + k, cur[j], off[j], deg[j]);
                 }
@@ -454,6 +519,15 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
     uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n, *sid = cursor + n + 1, *sst = sid + n_walks;
     int rc = group_by_start(g, starts, n_walks, counts, cursor, sid, sst, status, scan_ws, scan_ws_bytes, s);
     if (rc) return rc;
+    if (smp.kind == 1 && smp.t == kSabaT) {
+        ProfScope prof(kProfGroup, s);
+        count_launches(1);
+        int dev = 0, sms = 0;
+        BQ_CUDA(cudaGetDevice(&dev));
+        BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        saba_order_kernel<<<sms * 8, 256, 0, s>>>(counts, cursor, g.n, seed, sid);
+        BQ_CUDA(cudaGetLastError());
+    }
     if (g.hub_tag && !checked) {
         auto *next_chunk = reinterpret_cast<unsigned long long *>(scratch + bouquet_counter_offset(g.n, n_walks));
         BQ_CUDA(cudaMemsetAsync(next_chunk, 0, sizeof(unsigned long long), s));

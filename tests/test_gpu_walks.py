@@ -58,7 +58,7 @@ def test_visits_bit_exact(env, name, n_walks, n_steps):
         assert np.array_equal(host_u32(vis), want), (name, mode)
 
 
-@pytest.mark.parametrize("sampler", [None, (1, 3, 8), (1, 32, 32), (1, 0, 5)])
+@pytest.mark.parametrize("sampler", [None, (1, 3, 8), (1, 32, 32), (1, 0, 5), (2, 0, 1)])
 def test_paths_and_start_visits_bit_exact(env, sampler):
     bq, torch = env
     g = GRAPHS["rmat12"]
@@ -127,7 +127,7 @@ def test_every_graph_layout_bit_exact(env, layout, hub_slots):
             rng = np.random.default_rng(layout)
             starts = rng.integers(0, g.n, 20011).astype(np.uint32)
             st = dev_u32(torch, starts)
-            for sampler in (None, (1, 5, 32)):
+            for sampler in (None, (1, 5, 32), (2, 0, 1)):
                 want_v, want_p = oracle.walk_batch(g, 41, starts, 17, sampler=sampler,
                                                    include_start=True, want_paths=True)
                 for mode in (bq.MODE_BOUQUET, bq.MODE_NAIVE):
@@ -211,3 +211,29 @@ def test_full_size_rmat_batch(env):
     # the host-buffer path used for the end-to-end number
     vh = bq.walk_batch_host(graph, 2024, starts, n_steps)
     assert np.array_equal(vh, host_u32(vb))
+
+
+def test_literal_saba_word_orders_buckets_and_is_refused_by_aesc(env):
+    """The literal SABA sampler: the same paths as the oracle in both modes
+    (the bucket ordering by seed changes no result), and AESC calls refuse
+    it."""
+    bq, torch = env
+    from workloads import all_edges
+    g = GRAPHS["rmat12"]
+    graph = bq.Graph.from_csr(g)
+    rng = np.random.default_rng(3)
+    live = np.flatnonzero(np.diff(g.offsets) > 0)
+    starts = live[rng.integers(0, 40, 30011)].astype(np.uint32)  # big buckets: runs of 1024
+    starts[:3000] = live[0]
+    want_v, want_p = oracle.walk_batch(g, 12, starts, 9, sampler=(2, 0, 1), want_paths=True)
+    st = dev_u32(torch, starts)
+    for mode in (bq.MODE_NAIVE, bq.MODE_BOUQUET):
+        paths = torch.zeros((starts.size, 10), dtype=torch.int32, device="cuda")
+        vis = bq.walk_batch(graph, 12, st, 9, mode=mode, sampler=(2, 0, 1), paths=paths)
+        bq.sync()
+        assert np.array_equal(host_u32(vis), want_v), mode
+        assert np.array_equal(host_u32(paths), want_p), mode
+    uv = all_edges(g)[:4]
+    with pytest.raises(bq.BouquetError) as ei:
+        bq.aesc_estimate_host(graph, 1, uv, np.full(4, 3, np.uint32), np.full(4, 5, np.uint32), sampler=(2, 0, 1))
+    assert ei.value.code == bq.EINVAL
