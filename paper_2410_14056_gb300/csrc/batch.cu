@@ -25,7 +25,7 @@ constexpr int kThreads = 256;
 // bound, so the common shapes keep 40 warps per SM (<= 48 registers).
 template <int W, bool COUPLED>
 constexpr int count_min_blocks() {
-    return (!COUPLED && W <= 4) ? 5 : 1;
+    return (!COUPLED && W <= 2) ? 6 : ((!COUPLED && W <= 4) ? 5 : 1);
 }
 
 __device__ __forceinline__ int64_t lower_bound_row(const uint32_t *__restrict__ nbrs, int64_t lo, int64_t hi,
@@ -529,37 +529,47 @@ int serve_prepare(const QueryDesc *d_qd, uint64_t k, uint32_t bouquet, BInfo *in
     return scan_u32_to_u64_ws(tasks, begin, k, ws, ws_bytes, s);
 }
 
+// Persistent grid of a serve_count_kernel shape (SMs x resident blocks),
+// taken once per process: every iteration of a server launches it.
+template <int W, bool COUPLED>
+int serve_grid() {
+    static const int grid = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_count_kernel<W, COUPLED>, kThreads, 0) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return sms * (per_sm < 1 ? 1 : per_sm);
+    }();
+    return grid;
+}
+
+template <int W, bool COUPLED>
+int launch_serve(const ServeItem *d_items, uint32_t n_items, uint64_t total_items, const Sampler &smp,
+                 unsigned long long *counter, cudaStream_t s) {
+    const int grid = serve_grid<W, COUPLED>();
+    if (grid <= 0) return fail(BQ_ECUDA, "serve_count_kernel: no launch configuration");
+    serve_count_kernel<W, COUPLED><<<grid, kThreads, 0, s>>>(d_items, n_items, total_items, smp, counter);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
 int serve_iterate(const ServeItem *d_items, uint32_t n_items, uint64_t total_items, int lanes, const Sampler &smp,
                   unsigned long long *counter, cudaStream_t s) {
     if (total_items == 0) return BQ_OK;
     BQ_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
-    int dev = 0, sms = 0;
-    BQ_CUDA(cudaGetDevice(&dev));
-    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const bool c = smp.kind == 1;
-    int per_sm = 0;
-#define BQ_SERVE(WW)                                                                                             \
-    do {                                                                                                         \
-        if (c) {                                                                                                 \
-            BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_count_kernel<WW, true>, kThreads, \
-                                                                  0));                                           \
-            serve_count_kernel<WW, true><<<sms * (per_sm < 1 ? 1 : per_sm), kThreads, 0, s>>>(                    \
-                d_items, n_items, total_items, smp, counter);                                                    \
-        } else {                                                                                                 \
-            BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_count_kernel<WW, false>,         \
-                                                                  kThreads, 0));                                 \
-            serve_count_kernel<WW, false><<<sms * (per_sm < 1 ? 1 : per_sm), kThreads, 0, s>>>(                   \
-                d_items, n_items, total_items, smp, counter);                                                    \
-        }                                                                                                        \
-    } while (0)
     ProfScope prof(kProfAesc, s);
     count_launches(1);
-    if (lanes == 2) BQ_SERVE(2);
-    else if (lanes == 8) BQ_SERVE(8);
-    else BQ_SERVE(4);
-#undef BQ_SERVE
-    BQ_CUDA(cudaGetLastError());
-    return BQ_OK;
+    if (lanes == 2) return c ? launch_serve<2, true>(d_items, n_items, total_items, smp, counter, s)
+                             : launch_serve<2, false>(d_items, n_items, total_items, smp, counter, s);
+    if (lanes == 8) return c ? launch_serve<8, true>(d_items, n_items, total_items, smp, counter, s)
+                             : launch_serve<8, false>(d_items, n_items, total_items, smp, counter, s);
+    return c ? launch_serve<4, true>(d_items, n_items, total_items, smp, counter, s)
+             : launch_serve<4, false>(d_items, n_items, total_items, smp, counter, s);
 }
 
 int serve_finalize(const QueryDesc *d_qd, const BInfo *info, uint64_t k, cudaStream_t s) {
