@@ -833,7 +833,9 @@ def run_serving(args):
         saturation = {"requests": len(sat_reqs), "edges": sat_edges, "wall_s": wall,
                       "requests_per_s": sat_rps, "edges_per_s": sat_edges / wall,
                       "walk_steps_per_s": steps / wall, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
-                      "iterations": st1["iterations"] - st0["iterations"]}
+                      "iterations": st1["iterations"] - st0["iterations"],
+                      "worker_s": {k: st1[f"worker_{k}_s"] - st0[f"worker_{k}_s"]
+                                   for k in ("admit", "launch", "complete", "idle")}}
         loads = []
         for f in SERVE_LOADS:
             rate = f * sat_rps

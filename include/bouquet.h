@@ -364,6 +364,10 @@ typedef struct bq_server_stats {
     double p50_ms, p99_ms; /* latency submit -> result ready, completed requests */
     double uptime_s;
     uint32_t inflight, pending;
+    /* the worker thread's time: admitting requests (upload, prepare),
+     * launching iterations (including waits for a free descriptor slot),
+     * completing requests (waits for results, copies, frees), and idle */
+    double worker_admit_s, worker_launch_s, worker_complete_s, worker_idle_s;
 } bq_server_stats;
 
 /* Start a server over graphs (all on the current device, nnz < 2^32; they
@@ -417,7 +421,7 @@ typedef struct bq_tuning {
                                   0: plain uint32 CSR + 8-byte vertex records
                                      {row offset, degree};
                                   1 (default): automatic: 2 when the 8-byte
-                                     edge records fit in half of L2, else 5;
+                                     edge records fit in L2, else 5;
                                   2: per CSR entry an edge record {id, row
                                      offset, degree}, 8 packed bytes when the
                                      fields fit, else 16 (one load per step,

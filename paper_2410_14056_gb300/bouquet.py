@@ -103,7 +103,9 @@ class ServerStats(ctypes.Structure):
                 ("iterations", ctypes.c_uint64), ("walk_steps", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("uptime_s", ctypes.c_double), ("inflight", ctypes.c_uint32),
-                ("pending", ctypes.c_uint32)]
+                ("pending", ctypes.c_uint32), ("worker_admit_s", ctypes.c_double),
+                ("worker_launch_s", ctypes.c_double), ("worker_complete_s", ctypes.c_double),
+                ("worker_idle_s", ctypes.c_double)]
 
 
 # every symbol include/bouquet.h declares

@@ -143,6 +143,7 @@ struct bq_server {
     bq::Clock::time_point t_start;
     uint64_t submitted = 0, completed = 0, failed = 0, edges_completed = 0, iterations = 0;
     double walk_steps = 0;
+    double t_admit = 0, t_launch = 0, t_complete = 0, t_idle = 0;  // worker seconds per phase
     std::vector<double> latencies_ms;
 };
 
@@ -365,17 +366,29 @@ void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
     srv->cv_done.notify_all();
 }
 
+// Requests admitted per pass while others are on the GPU, so that a burst
+// of arrivals does not hold back the next iteration's launch.
+constexpr size_t kAdmitPerPass = 32;
+
 void worker_main(bq_server *srv) {
     cudaSetDevice(srv->device);
     const uint64_t budget = srv->cfg.device_budget_bytes;
+    auto lap = [](Clock::time_point &t0) {
+        const auto t1 = Clock::now();
+        const double s = std::chrono::duration<double>(t1 - t0).count();
+        t0 = t1;
+        return s;
+    };
     for (;;) {
         // admission: FIFO, while slots and device memory allow
         std::vector<RequestPtr> admitted;
         bool idle = false;
+        auto t0 = Clock::now();
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             for (;;) {
                 if (srv->pending.empty()) break;
+                if (!srv->inflight.empty() && admitted.size() >= kAdmitPerPass) break;
                 RequestPtr r = srv->pending.front();
                 const size_t bytes = request_bytes(r->k);
                 if (bytes > budget) {
@@ -399,6 +412,7 @@ void worker_main(bq_server *srv) {
             if (idle) {
                 if (srv->stop && srv->pending.empty()) return;
                 srv->cv_work.wait(lk, [srv] { return srv->stop || !srv->pending.empty(); });
+                srv->t_idle += lap(t0);
                 continue;
             }
         }
@@ -414,8 +428,15 @@ void worker_main(bq_server *srv) {
         // requests with nothing to count go straight to finalization
         for (auto &r : srv->inflight)
             if (!r->finalizing && r->tasks_total == 0) start_finalize(srv, *r);
+        const double ta = lap(t0);
         const bool launched = iterate(srv);
+        const double tl = lap(t0);
         poll_completions(srv, !launched);
+        const double tc = lap(t0);
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->t_admit += ta;
+        srv->t_launch += tl;
+        srv->t_complete += tc;
     }
 }
 
@@ -586,6 +607,10 @@ int bq_server_stats_get(bq_server *srv, bq_server_stats *out) {
         out->walk_steps = srv->walk_steps;
         out->inflight = (uint32_t)srv->inflight.size();
         out->pending = (uint32_t)srv->pending.size();
+        out->worker_admit_s = srv->t_admit;
+        out->worker_launch_s = srv->t_launch;
+        out->worker_complete_s = srv->t_complete;
+        out->worker_idle_s = srv->t_idle;
         lat = srv->latencies_ms;
     }
     out->p50_ms = percentile(lat, 0.50);
