@@ -733,7 +733,7 @@ def run_batched(args):
 SERVE_LOADS = (0.5, 0.8, 1.0)
 SERVE_SATURATION_REQUESTS = 2000
 SERVE_LOAD_SECONDS = 3.0
-SERVE_SUBMITTERS = 8
+SERVE_SUBMITTERS = 12
 
 
 def serving_graphs(bq, torch):

@@ -91,10 +91,13 @@ struct Request {
     // device
     char *dbuf = nullptr;
     size_t dbytes = 0;
-    cudaEvent_t done_ev = nullptr;
+    cudaEvent_t fin_ev = nullptr;   // finalize done on the compute stream
+    cudaEvent_t done_ev = nullptr;  // results in h_out (copy stream)
     bool finalizing = false;
-    // host image of the output sections
-    std::vector<char> out;
+    // pinned host image of the output sections (from the server's pool;
+    // returned when the waiter has copied it out)
+    char *h_out = nullptr;
+    size_t h_out_cap = 0;
 
     QueryDesc *d_qd() const { return reinterpret_cast<QueryDesc *>(dbuf + L.qd); }
     BInfo *d_info() const { return reinterpret_cast<BInfo *>(dbuf + L.info); }
@@ -108,6 +111,50 @@ using RequestPtr = std::shared_ptr<Request>;
 
 size_t request_bytes(uint64_t k) { return layout_of(k).total; }
 
+// Pinned host blocks for result images, reused by size class (powers of two
+// from 4 KiB), so that results come back by asynchronous DMA.  Blocks are
+// allocated on the worker thread and returned by waiters.
+struct PinnedPool {
+    std::mutex mu;
+    std::unordered_map<size_t, std::vector<char *>> free;
+    std::vector<char *> all;
+    static size_t size_class(size_t bytes) {
+        size_t c = 4096;
+        while (c < bytes) c <<= 1;
+        return c;
+    }
+    char *get(size_t bytes, size_t &cap) {
+        cap = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto &v = free[cap];
+            if (!v.empty()) {
+                char *p = v.back();
+                v.pop_back();
+                return p;
+            }
+        }
+        char *p = nullptr;
+        if (cudaMallocHost((void **)&p, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        all.push_back(p);
+        return p;
+    }
+    void put(char *p, size_t cap) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        free[cap].push_back(p);
+    }
+    void release() {
+        for (char *p : all) cudaFreeHost(p);
+        all.clear();
+        free.clear();
+    }
+};
+
 }  // namespace
 }  // namespace bq
 
@@ -119,14 +166,16 @@ struct bq_server {
     int lanes = 4;
     cudaStream_t stream = nullptr, copy_stream = nullptr;
     // iteration descriptors: pinned host ring and device ring
-    static constexpr int kRing = 2;
-    bq::ServeItem *h_items[kRing] = {nullptr, nullptr};
-    bq::ServeItem *d_items[kRing] = {nullptr, nullptr};
+    static constexpr int kRing = 4;  // iterations the worker may run ahead of the GPU
+    bq::ServeItem *h_items[kRing] = {};
+    bq::ServeItem *d_items[kRing] = {};
     unsigned long long *d_counter = nullptr;
-    cudaEvent_t ring_ev[kRing] = {nullptr, nullptr};
-    bool ring_used[kRing] = {false, false};
+    cudaEvent_t ring_ev[kRing] = {};
+    bool ring_used[kRing] = {};
     int ring_next = 0;
     uint32_t *status = nullptr;
+    bq::PinnedPool pinned;
+    std::vector<cudaEvent_t> events;  // free events (worker thread only)
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -151,6 +200,26 @@ namespace bq {
 namespace {
 
 uint32_t bouquet_of(const bq_server *srv) { return 32u * (uint32_t)srv->lanes; }
+
+// Events are reused (worker thread only).
+cudaEvent_t take_event(bq_server *srv) {
+    if (!srv->events.empty()) {
+        cudaEvent_t e = srv->events.back();
+        srv->events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void give_event(bq_server *srv, cudaEvent_t &e) {
+    if (e) srv->events.push_back(e);
+    e = nullptr;
+}
 
 // Plan one request on the host (the submitting thread, no lock): copy the
 // pairs into the request's input image and fill tau and N per edge from the
@@ -218,17 +287,29 @@ int admit(bq_server *srv, Request &r) {
     // pageable source: the call returns once the image is staged
     e = cudaMemcpyAsync(r.dbuf, r.in.data(), r.L.in_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.dbuf + r.L.out, 0, 16, s);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "server: request upload");
+    r.fin_ev = take_event(srv);
+    r.done_ev = take_event(srv);
+    if (!r.fin_ev || !r.done_ev) return fail(BQ_ECUDA, "server: cannot create events");
     std::vector<char>().swap(r.in);
     return serve_prepare(r.d_qd(), r.k, bouquet_of(srv), r.d_info(), reinterpret_cast<uint32_t *>(r.dbuf + r.L.tasks),
                          r.d_begin(), r.dbuf + r.L.ws, r.L.ws_bytes, reinterpret_cast<uint32_t *>(r.dbuf + r.L.out),
                          s);
 }
 
+// Finalize on the compute stream; the copy stream then brings the output
+// section back into a pinned block and frees the request's device memory,
+// so the compute stream goes on with other requests meanwhile.
 void start_finalize(bq_server *srv, Request &r) {
     serve_finalize(r.d_qd(), r.d_info(), r.k, srv->stream);
-    cudaEventRecord(r.done_ev, srv->stream);
+    cudaEventRecord(r.fin_ev, srv->stream);
+    r.h_out = srv->pinned.get(r.L.out_bytes, r.h_out_cap);
+    cudaStreamWaitEvent(srv->copy_stream, r.fin_ev, 0);
+    if (r.h_out)
+        cudaMemcpyAsync(r.h_out, r.dbuf + r.L.out, r.L.out_bytes, cudaMemcpyDeviceToHost, srv->copy_stream);
+    cudaFreeAsync(r.dbuf, srv->copy_stream);
+    r.dbuf = nullptr;
+    cudaEventRecord(r.done_ev, srv->copy_stream);
     r.finalizing = true;
 }
 
@@ -291,19 +372,17 @@ void poll_completions(bq_server *srv, bool block) {
     std::vector<RequestPtr> finished;
     for (auto &r : srv->inflight) {
         if (!r->finalizing) continue;
-        cudaError_t q = block && finished.empty() ? cudaEventSynchronize(r->done_ev) : cudaEventQuery(r->done_ev);
-        if (q == cudaErrorNotReady) continue;
-        r->out.resize(r->L.out_bytes);
-        cudaError_t e = q;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(r->out.data(), r->dbuf + r->L.out, r->L.out_bytes, cudaMemcpyDeviceToHost,
-                                srv->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(srv->copy_stream);
+        const cudaError_t e =
+            block && finished.empty() ? cudaEventSynchronize(r->done_ev) : cudaEventQuery(r->done_ev);
+        if (e == cudaErrorNotReady) continue;
         uint32_t bits = 0;
-        if (e == cudaSuccess) memcpy(&bits, r->out.data(), sizeof(bits));
+        if (e == cudaSuccess && r->h_out) memcpy(&bits, r->h_out, sizeof(bits));
         if (e != cudaSuccess) {
             r->status = BQ_ECUDA;
             r->error = cudaGetErrorString(e);
+        } else if (!r->h_out) {
+            r->status = BQ_ENOMEM;
+            r->error = "no pinned host memory for the results";
         } else if (bits & kStatusNoEdge) {
             r->status = BQ_ENOEDGE;
             r->error = "a queried pair is not an edge";
@@ -317,10 +396,12 @@ void poll_completions(bq_server *srv, bool block) {
     std::lock_guard<std::mutex> lk(srv->mu);
     const auto now = Clock::now();
     for (auto &r : finished) {
-        cudaFreeAsync(r->dbuf, srv->copy_stream);
-        r->dbuf = nullptr;
-        cudaEventDestroy(r->done_ev);
-        r->done_ev = nullptr;
+        give_event(srv, r->fin_ev);
+        give_event(srv, r->done_ev);
+        if (r->status != BQ_OK) {  // nothing to read: the block goes back now
+            srv->pinned.put(r->h_out, r->h_out_cap);
+            r->h_out = nullptr;
+        }
         srv->held_bytes -= r->dbytes;
         r->t_done = now;
         if (r->status != BQ_OK) {
@@ -350,10 +431,8 @@ void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
         cudaFreeAsync(r->dbuf, srv->stream);
         r->dbuf = nullptr;
     }
-    if (r->done_ev) {
-        cudaEventDestroy(r->done_ev);
-        r->done_ev = nullptr;
-    }
+    give_event(srv, r->fin_ev);
+    give_event(srv, r->done_ev);
     const char *msg = bq_last_error();
     std::lock_guard<std::mutex> lk(srv->mu);
     r->status = status;
@@ -368,7 +447,7 @@ void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
 
 // Requests admitted per pass while others are on the GPU, so that a burst
 // of arrivals does not hold back the next iteration's launch.
-constexpr size_t kAdmitPerPass = 32;
+constexpr size_t kAdmitPerPass = 8;
 
 void worker_main(bq_server *srv) {
     cudaSetDevice(srv->device);
@@ -462,6 +541,9 @@ void server_free(bq_server *srv) {
         if (srv->h_items[i]) cudaFreeHost(srv->h_items[i]);
         if (srv->d_items[i]) cudaFree(srv->d_items[i]);
     }
+    for (cudaEvent_t e : srv->events) cudaEventDestroy(e);
+    srv->events.clear();
+    srv->pinned.release();
     if (srv->d_counter) cudaFree(srv->d_counter);
     if (srv->status) cudaFree(srv->status);
     if (srv->stream) cudaStreamDestroy(srv->stream);
@@ -588,8 +670,10 @@ int bq_server_wait(bq_server *srv, uint64_t request_id, double timeout_s, double
     if (r->status != BQ_OK)
         return fail(r->status, "request %llu: %s", (unsigned long long)request_id,
                     r->error.empty() ? bq_strerror(r->status) : r->error.c_str());
-    if (sc && r->k) memcpy(sc, r->out.data() + (r->L.sc - r->L.out), 8 * r->k);
-    if (counts && r->k) memcpy(counts, r->out.data() + (r->L.counts - r->L.out), 16 * r->k);
+    if (sc && r->k) memcpy(sc, r->h_out + (r->L.sc - r->L.out), 8 * r->k);
+    if (counts && r->k) memcpy(counts, r->h_out + (r->L.counts - r->L.out), 16 * r->k);
+    srv->pinned.put(r->h_out, r->h_out_cap);
+    r->h_out = nullptr;
     return BQ_OK;
 }
 
