@@ -353,7 +353,8 @@ typedef struct bq_server_config {
     uint32_t tau_max;
     double n_scale;
     uint32_t n_min;
-    uint32_t reserved;
+    uint32_t planner_threads;     /* threads planning submitted requests (0: half the
+                                     host cores, at most 8) */
 } bq_server_config;
 
 typedef struct bq_server_stats {
@@ -375,15 +376,15 @@ typedef struct bq_server_stats {
  * tau_scale 2, tau_add 2, tau_max 64, n_scale 9, n_min 32. */
 int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server_config *cfg, bq_server **out);
 
-/* Plan and queue a request: k vertex pairs (host, copied) of graph `graph`,
- * absolute error eps, walks keyed by seed.  The scheduled plan (from the
- * endpoint degrees) is computed on the calling thread, so several threads
- * may submit at once; the call then returns with *request_id without waiting
- * for the GPU.  Errors, with no request created: BQ_ENOEDGE (an id >= n,
- * equal endpoints, or an endpoint without neighbours), BQ_EOVERFLOW (2 N tau
- * >= 2^32 for an edge), BQ_EBUSY (max_pending requests already queued),
- * BQ_EINVAL (bad arguments, server stopping).  Whether each pair is an edge
- * is checked on the GPU; bq_server_wait reports a pair that is not. */
+/* Queue a request: k vertex pairs (host, copied) of graph `graph`, absolute
+ * error eps, walks keyed by seed.  Returns with *request_id after copying
+ * the pairs; the server's planner threads compute the scheduled plan (from
+ * the endpoint degrees) and its worker runs it.  Errors, with no request
+ * created: BQ_ENOEDGE (an id >= n or equal endpoints), BQ_EBUSY
+ * (max_pending requests queued), BQ_EINVAL (bad arguments, server
+ * stopping).  An endpoint without neighbours, 2 N tau >= 2^32 for an edge,
+ * and a pair that is not an edge (checked on the GPU) are reported by
+ * bq_server_wait (BQ_ENOEDGE, BQ_EOVERFLOW). */
 int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, uint64_t k, double eps,
                      uint64_t seed, uint64_t *request_id);
 
@@ -391,6 +392,7 @@ int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, u
  * doubles) and, if not NULL, counters (4k, layout of bq_aesc_estimate) and
  * latency (submit call -> results on the host, ms).  Returns the request's
  * status: BQ_OK, BQ_ENOEDGE (a pair is not an edge; nothing is copied),
+ * BQ_EOVERFLOW (2 N tau >= 2^32 for an edge),
  * BQ_ENOMEM (it alone needs more than the device budget, or the allocation
  * failed), BQ_ECUDA; or BQ_ETIMEOUT (the request is still
  * running or queued: wait again).  Each request is returned once; waiting

@@ -94,7 +94,7 @@ class ServerConfig(ctypes.Structure):
                 ("max_pending", ctypes.c_uint32), ("tasks_per_iteration", ctypes.c_uint64),
                 ("tau_scale", ctypes.c_double), ("tau_add", ctypes.c_uint32),
                 ("tau_max", ctypes.c_uint32), ("n_scale", ctypes.c_double),
-                ("n_min", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("n_min", ctypes.c_uint32), ("planner_threads", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):

@@ -1,9 +1,10 @@
 // Serving loop: SC queries on resident graphs with continuous batching.
 //
-// A request is planned on the submitting thread (scheduled plan, host) and
-// queued.  A worker thread owns a non-blocking stream; it admits queued
-// requests while the device memory they need and the number of requests on
-// the GPU fit the configured limits (uploading each and preparing its edges),
+// A submitted request is queued for a pool of planner threads, which compute
+// its scheduled plan on the host.  A worker thread owns a non-blocking
+// stream; it admits planned requests while the device memory they need and
+// the number of requests on the GPU fit the configured limits (uploading
+// each and preparing its edges),
 // then runs iterations: each iteration is one persistent counting launch over
 // a window of tasks of every admitted request.  A request whose last tasks
 // were launched is finalized and its results copied back on a second stream;
@@ -179,7 +180,11 @@ struct bq_server {
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<bq::RequestPtr> pending;
+    std::deque<bq::RequestPtr> to_plan;  // submitted, waiting for a planner thread
+    uint32_t planning = 0;                // requests being planned now
+    std::condition_variable cv_plan;
+    std::vector<std::thread> planners;
+    std::deque<bq::RequestPtr> pending;   // planned, waiting for admission
     std::vector<bq::RequestPtr> inflight;
     std::unordered_map<uint64_t, bq::RequestPtr> done;
     std::unordered_set<uint64_t> live;  // submitted and not yet returned by bq_server_wait
@@ -221,18 +226,15 @@ void give_event(bq_server *srv, cudaEvent_t &e) {
     e = nullptr;
 }
 
-// Plan one request on the host (the submitting thread, no lock): copy the
-// pairs into the request's input image and fill tau and N per edge from the
-// endpoint degrees (the scheduled plan), count its bouquet tasks and walk
-// steps.  Pairs with an id out of range, equal endpoints or an endpoint of
-// degree 0 are rejected here; whether a pair is an edge is checked on the
-// GPU (the prepare kernel's row search), whose status comes back with the
-// results.
-int plan_request(bq_server *srv, Request &r, const uint32_t *edges_uv) {
+// Plan one request on the host (a planner thread, no lock): fill tau and N
+// per edge of its input image from the endpoint degrees (the scheduled
+// plan), count its bouquet tasks and walk steps.  A pair with an endpoint of
+// degree 0 fails here (BQ_ENOEDGE), as does 2 N tau >= 2^32 (BQ_EOVERFLOW);
+// whether a pair is an edge is checked on the GPU (the prepare kernel's row
+// search), whose status comes back with the results.
+int plan_request(bq_server *srv, Request &r) {
     const bq_graph *g = srv->graphs[r.graph];
-    r.L = layout_of(r.k);
-    r.in.assign(r.L.in_bytes, 0);
-    if (r.k) memcpy(r.h_uv(), edges_uv, 8 * r.k);
+    const uint32_t *edges_uv = r.h_uv();
     const bq_schedule sched{srv->cfg.tau_scale, srv->cfg.tau_add, srv->cfg.tau_max,
                             srv->cfg.n_scale,   srv->cfg.n_min,   0};
     const int64_t *off = g->h_offsets.data();
@@ -445,6 +447,41 @@ void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
     srv->cv_done.notify_all();
 }
 
+// Planner thread: plans submitted requests (host work proportional to their
+// edges) and hands them to the worker; a request that cannot be planned is
+// completed at once with its error.
+void planner_main(bq_server *srv) {
+    for (;;) {
+        RequestPtr r;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv_plan.wait(lk, [srv] { return srv->stop || !srv->to_plan.empty(); });
+            if (srv->to_plan.empty()) return;  // stopping, and nothing left to plan
+            r = srv->to_plan.front();
+            srv->to_plan.pop_front();
+            ++srv->planning;
+        }
+        clear_error();
+        const int rc = plan_request(srv, *r);
+        const std::string msg = rc != BQ_OK ? std::string(bq_last_error()) : std::string();
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            --srv->planning;
+            if (rc == BQ_OK) {
+                srv->pending.push_back(r);
+            } else {
+                r->status = rc;
+                r->error = msg;
+                r->t_done = Clock::now();
+                ++srv->failed;
+                srv->done[r->id] = r;
+                srv->cv_done.notify_all();
+            }
+        }
+        srv->cv_work.notify_one();
+    }
+}
+
 // Requests admitted per pass while others are on the GPU, so that a burst
 // of arrivals does not hold back the next iteration's launch.
 constexpr size_t kAdmitPerPass = 8;
@@ -489,8 +526,9 @@ void worker_main(bq_server *srv) {
             }
             idle = admitted.empty() && srv->inflight.empty();
             if (idle) {
-                if (srv->stop && srv->pending.empty()) return;
-                srv->cv_work.wait(lk, [srv] { return srv->stop || !srv->pending.empty(); });
+                auto drained = [srv] { return srv->to_plan.empty() && srv->planning == 0; };
+                if (srv->stop && srv->pending.empty() && drained()) return;
+                srv->cv_work.wait(lk, [&] { return !srv->pending.empty() || (srv->stop && drained()); });
                 srv->t_idle += lap(t0);
                 continue;
             }
@@ -610,7 +648,13 @@ int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server
         return rc;
     }
     srv->t_start = Clock::now();
+    uint32_t planners = c.planner_threads;
+    if (!planners) {
+        const unsigned hw = std::thread::hardware_concurrency();
+        planners = std::max(1u, std::min(8u, hw / 2));
+    }
     srv->worker = std::thread(worker_main, srv);
+    for (uint32_t i = 0; i < planners; ++i) srv->planners.emplace_back(planner_main, srv);
     *out = srv;
     return BQ_OK;
 }
@@ -623,26 +667,33 @@ int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, u
     if (k && !edges_uv) return fail(BQ_EINVAL, "edges_uv is NULL");
     if (!(eps > 0.0) || !(eps < 1e6)) return fail(BQ_EINVAL, "eps = %g must be positive", eps);
     if (k >= (1ull << 32)) return fail(BQ_EINVAL, "k = %llu edges in one request", (unsigned long long)k);
+    const uint32_t n = srv->graphs[graph]->n;
+    for (uint64_t i = 0; i < k; ++i) {
+        const uint32_t a = edges_uv[2 * i], b = edges_uv[2 * i + 1];
+        if (a >= n || b >= n || a == b)
+            return fail(BQ_ENOEDGE, "pair %llu: (%u, %u) is not an edge", (unsigned long long)i, a, b);
+    }
     auto r = std::make_shared<Request>();
     r->t_submit = Clock::now();
     r->graph = graph;
     r->k = k;
     r->eps = eps;
     r->seed = seed;
-    const int rc = plan_request(srv, *r, edges_uv);
-    if (rc != BQ_OK) return rc;
+    r->L = layout_of(k);
+    r->in.assign(r->L.in_bytes, 0);
+    if (k) memcpy(r->h_uv(), edges_uv, 8 * k);
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if (srv->stop) return fail(BQ_EINVAL, "server is stopping");
-        if (srv->pending.size() >= srv->cfg.max_pending)
+        if (srv->to_plan.size() + srv->planning + srv->pending.size() >= srv->cfg.max_pending)
             return fail(BQ_EBUSY, "server queue is full (%u requests)", srv->cfg.max_pending);
         r->id = srv->next_id++;
-        srv->pending.push_back(r);
+        srv->to_plan.push_back(r);
         srv->live.insert(r->id);
         ++srv->submitted;
         *request_id = r->id;
     }
-    srv->cv_work.notify_one();
+    srv->cv_plan.notify_one();
     return BQ_OK;
 }
 
@@ -690,7 +741,7 @@ int bq_server_stats_get(bq_server *srv, bq_server_stats *out) {
         out->iterations = srv->iterations;
         out->walk_steps = srv->walk_steps;
         out->inflight = (uint32_t)srv->inflight.size();
-        out->pending = (uint32_t)srv->pending.size();
+        out->pending = (uint32_t)(srv->to_plan.size() + srv->planning + srv->pending.size());
         out->worker_admit_s = srv->t_admit;
         out->worker_launch_s = srv->t_launch;
         out->worker_complete_s = srv->t_complete;
@@ -710,6 +761,10 @@ int bq_server_destroy(bq_server *srv) {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->stop = true;
     }
+    srv->cv_plan.notify_all();
+    srv->cv_work.notify_all();
+    for (auto &t : srv->planners)
+        if (t.joinable()) t.join();
     srv->cv_work.notify_all();
     if (srv->worker.joinable()) srv->worker.join();
     int prev = 0;
