@@ -102,6 +102,13 @@ def lib():
                 c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double,
                 c.c_double, c.c_double, c.c_uint32, u32p, u32p]
             L.orc_plan_certified.restype = c.c_int
+            L.orc_trunc_bound_omega.argtypes = [c.c_double, c.c_uint32, f64p, f64p, f64p, c.c_double,
+                                                c.c_double, c.c_uint32]
+            L.orc_trunc_bound_omega.restype = c.c_double
+            L.orc_plan_certified_omega.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double, c.c_uint32, f64p, f64p,
+                c.c_double, c.c_double, c.c_uint32, u32p, u32p]
+            L.orc_plan_certified_omega.restype = c.c_int
             L.orc_plan_scheduled.argtypes = [
                 c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double, c.c_uint32,
                 c.c_uint32, c.c_double, c.c_uint32, u32p, u32p]
@@ -243,6 +250,32 @@ def plan_scheduled(g, uv: np.ndarray, eps: float, tau_scale: float, tau_add: int
         _p(tau, ctypes.c_uint32), _p(nw, ctypes.c_uint32))
     _check(rc, "plan_scheduled")
     return tau, nw
+
+
+def plan_certified_omega(g, uv: np.ndarray, eps: float, delta: float, lambdas: np.ndarray,
+                         vecs: np.ndarray, lambda_rest: float, lambda_neg: float, tau_max: int = 1 << 20):
+    """Certified plan with omega = len(lambdas) known eigenpairs; vecs is
+    (n, omega) with vecs[v, k] = psi_k(v) / sqrt(d(v))."""
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    vv = np.ascontiguousarray(vecs, dtype=np.float64).reshape(g.n, lam.size) if lam.size else np.zeros(1)
+    tau = np.zeros(q.shape[0], np.uint32)
+    nw = np.zeros(q.shape[0], np.uint32)
+    rc = lib().orc_plan_certified_omega(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), q.shape[0], _p(q, ctypes.c_uint32),
+        eps, delta, lam.size, _p(lam, ctypes.c_double), _p(vv, ctypes.c_double), lambda_rest, lambda_neg,
+        tau_max, _p(tau, ctypes.c_uint32), _p(nw, ctypes.c_uint32))
+    _check(rc, "plan_certified_omega")
+    return tau, nw
+
+
+def trunc_bound_omega(s_e: float, lambdas, cu, cv, lambda_rest: float, lambda_neg: float, tau: int) -> float:
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    a = np.ascontiguousarray(cu, dtype=np.float64)
+    b = np.ascontiguousarray(cv, dtype=np.float64)
+    return float(lib().orc_trunc_bound_omega(s_e, lam.size, _p(lam, ctypes.c_double), _p(a, ctypes.c_double),
+                                             _p(b, ctypes.c_double), lambda_rest, lambda_neg, tau))
 
 
 def trunc_bound(s_e: float, lambda2: float, lambda_neg: float, tau: int) -> float:

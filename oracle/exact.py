@@ -139,6 +139,22 @@ def spectrum(g):
     return lam, lambda2, lambda_neg
 
 
+def eigen_embedding(g, omega: int):
+    """The omega largest eigenvalues of N = D^-1/2 A D^-1/2 after the
+    eigenvalue 1 (connected graph), their unit eigenvectors scaled by
+    1/sqrt(d) as an (n, omega) array, the next eigenvalue (0.0 if none) and
+    the most negative eigenvalue other than an exact -1 (as spectrum())."""
+    d = g.degrees.astype(np.float64)
+    A = adjacency(g)
+    s = 1.0 / np.sqrt(d)
+    lam, vec = np.linalg.eigh(A * s[:, None] * s[None, :])
+    order = np.argsort(lam)[::-1][1:]  # drop the eigenvalue 1
+    top = order[:omega]
+    rest = float(lam[order[omega]]) if order.size > omega else 0.0
+    _, _, lambda_neg = spectrum(g)
+    return lam[top].copy(), vec[:, top] * s[:, None], rest, lambda_neg
+
+
 def transition(g) -> np.ndarray:
     A = adjacency(g)
     return A / A.sum(axis=1, keepdims=True)

@@ -590,6 +590,85 @@ double orc_trunc_bound(double s_e, double lambda2, double lambda_neg, uint32_t t
     return s_e * (p > q ? p : q);
 }
 
+/* Truncation bound with omega known eigenpairs (the eigenvector refinement
+ * of CalculateTau in Alg. 1).  lambdas[0..omega) are the largest eigenvalues
+ * of D^-1/2 A D^-1/2 after the eigenvalue 1, with unit eigenvectors psi_k;
+ * vecs[v * omega + k] = psi_k(v) / sqrt(d(v)).  For the edge {u, v},
+ * c_k = vecs[u, k] - vecs[v, k] and the known modes' error is exact:
+ *   E(tau) = sum_k c_k^2 lambda_k^tau (1 + lambda_k) / (2 (1 - lambda_k));
+ * the modes not given carry the rest of s_e = sum of all c_k^2, and each has
+ * an eigenvalue in [lambda_neg, lambda_rest] (or exactly -1, whose term is
+ * zero), so
+ *   |R - S_tau| <= |E(tau)| + max(0, s_e - sum_k c_k^2) max(P(tau), Q(tau))
+ * with P taken at lambda_rest and Q at lambda_neg. */
+double orc_trunc_bound_omega(double s_e, uint32_t omega, const double *lambdas, const double *cu,
+                             const double *cv, double lambda_rest, double lambda_neg, uint32_t tau)
+{
+    double known = 0.0, mass = 0.0, rest, p, q;
+    uint32_t j;
+    for (j = 0; j < omega; j++) {
+        double c = cu[j] - cv[j], l = lambdas[j];
+        known += c * c * pow(l, (double)tau) * (1.0 + l) / (2.0 * (1.0 - l));
+        mass += c * c;
+    }
+    rest = s_e - mass;
+    if (rest < 0.0)
+        rest = 0.0;
+    p = trunc_p(lambda_rest, tau);
+    q = trunc_q(lambda_neg, tau);
+    return fabs(known) + rest * (p > q ? p : q);
+}
+
+/* The certified plan with that bound for tau (N as orc_plan_certified). */
+int orc_plan_certified_omega(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                             uint64_t k, const uint32_t *uv, double eps, double delta,
+                             uint32_t omega, const double *lambdas, const double *vecs,
+                             double lambda_rest, double lambda_neg, uint32_t tau_max,
+                             uint32_t *tau, uint32_t *nwalks)
+{
+    uint64_t m = (uint64_t)(offsets[n] / 2);
+    uint64_t *ub, q, id;
+    double logterm;
+    if (!(eps > 0.0) || !(delta > 0.0) || !(delta < 1.0) || m == 0 || (omega && (!lambdas || !vecs)))
+        return ORC_EINVAL;
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub)
+        return ORC_EINVAL;
+    logterm = log(2.0 * (double)m / delta);
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        double du, dv, s, nw, h;
+        uint32_t tq = 1;
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &id) != ORC_OK) {
+            free(ub);
+            return ORC_ENOEDGE;
+        }
+        du = (double)(offsets[a + 1] - offsets[a]);
+        dv = (double)(offsets[b + 1] - offsets[b]);
+        s = 1.0 / du + 1.0 / dv;
+        while (orc_trunc_bound_omega(s, omega, lambdas, vecs + (uint64_t)a * omega, vecs + (uint64_t)b * omega,
+                                     lambda_rest, lambda_neg, tq) > eps / 2.0) {
+            if (tq >= tau_max) {
+                free(ub);
+                return ORC_EOVERFLOW;
+            }
+            tq++;
+        }
+        h = (double)tq - 0.5;
+        nw = ceil(8.0 * h * h * s * s * logterm / (eps * eps));
+        if (nw < 1.0)
+            nw = 1.0;
+        if (nw * 2.0 * (double)tq >= 4294967296.0) {
+            free(ub);
+            return ORC_EOVERFLOW;
+        }
+        tau[q] = tq;
+        nwalks[q] = (uint32_t)nw;
+    }
+    free(ub);
+    return ORC_OK;
+}
+
 /* Scheduled (uncertified) plan, for graphs on which the certified bounds
  * explode (slow mixing):
  *   tau = clamp(ceil(tau_scale * ln(s_e / eps)) + tau_add, 1, tau_max)
