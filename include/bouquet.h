@@ -110,6 +110,24 @@ int bq_graph_info(bq_graph *g, bq_graph_info_t *info);
  */
 int bq_graph_set_spectrum(bq_graph *g, double lambda2, double lambda_neg);
 
+/*
+ * Eigenvector refinement of the certified plan (CalculateTau's use of the
+ * top eigenvectors, Alg. 1 and Sec. 2.3): the omega largest eigenvalues of
+ * D^-1/2 A D^-1/2 after the eigenvalue 1 (lambdas, host, omega doubles), their
+ * unit eigenvectors divided by sqrt(d(v)) (vecs, host, n * omega doubles,
+ * vecs[v * omega + k]), and lambda_rest, the largest eigenvalue not given.
+ * The certified plan then takes, per edge {u, v}, the exact error of the
+ * known modes, sum_k c_k^2 lambda_k^tau (1 + lambda_k) / (2 (1 - lambda_k))
+ * with c_k = vecs[u, k] - vecs[v, k], plus the remaining mass s_e - sum_k
+ * c_k^2 times the worst factor over [lambda_neg, lambda_rest] (lambda_neg
+ * from bq_graph_set_spectrum, still required), and keeps N's formula: tau and
+ * N are never larger than without them.  The arrays are copied; omega = 0
+ * clears them.  Errors: BQ_EINVAL (omega >= n, eigenvalues outside [-1, 1),
+ * non-finite vectors, NULL arrays).
+ */
+int bq_graph_set_eigvecs(bq_graph *g, uint32_t omega, const double *lambdas, const double *vecs,
+                         double lambda_rest);
+
 /* ---------------------------------------------------------- bq_walk_batch */
 #define BQ_MODE_NAIVE 0u   /* one walk per thread, walks in input order */
 #define BQ_MODE_BOUQUET 1u /* walks grouped by start vertex, one bouquet of

@@ -116,7 +116,7 @@ EXPORTS = (
     "bq_profile_read", "bq_walk_batch_noalloc", "bq_batch_create", "bq_batch_run",
     "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
     "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
-    "bq_server_destroy", "bq_aesc_estimate_push",
+    "bq_server_destroy", "bq_aesc_estimate_push", "bq_graph_set_eigvecs",
 )
 
 _lock = threading.Lock()
@@ -142,6 +142,7 @@ def load_library(path: str | None = None):
         L.bq_graph_destroy.argtypes = [vp]
         L.bq_graph_info.argtypes = [vp, c.POINTER(GraphInfo)]
         L.bq_graph_set_spectrum.argtypes = [vp, f64, f64]
+        L.bq_graph_set_eigvecs.argtypes = [vp, u32, vp, vp, f64]
         L.bq_walk_batch.argtypes = [vp, u64, vp, u64, u32, u32, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_aesc_plan.argtypes = [vp, vp, u64, f64, f64, u32, c.POINTER(Schedule), vp, vp]
         L.bq_aesc_estimate.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp, vp]
@@ -265,6 +266,17 @@ class Graph:
 
     def set_spectrum(self, lambda2: float, lambda_neg: float):
         _check(load_library().bq_graph_set_spectrum(self.handle, float(lambda2), float(lambda_neg)))
+
+    def set_eigvecs(self, lambdas, vecs, lambda_rest: float):
+        """Top eigenpairs for the certified plan: lambdas (omega,), vecs
+        (n, omega) eigenvectors divided by sqrt(degree); omega = 0 clears."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64).reshape(-1)
+        vv = np.ascontiguousarray(vecs, dtype=np.float64).reshape(-1)
+        if lam.size and vv.size != self.n * lam.size:
+            raise ValueError("vecs must have n * omega entries")
+        _check(load_library().bq_graph_set_eigvecs(self.handle, lam.size, _hptr(lam, "lambdas", np.float64) if lam.size else None,
+                                                   _hptr(vv, "vecs", np.float64) if lam.size else None,
+                                                   float(lambda_rest)))
 
     def close(self):
         if getattr(self, "_h", None):

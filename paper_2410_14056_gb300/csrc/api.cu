@@ -374,6 +374,34 @@ int bq_graph_set_spectrum(bq_graph *g, double lambda2, double lambda_neg) {
     return BQ_OK;
 }
 
+int bq_graph_set_eigvecs(bq_graph *g, uint32_t omega, const double *lambdas, const double *vecs,
+                         double lambda_rest) {
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (omega == 0) {
+        g->omega = 0;
+        g->eig_lambdas.clear();
+        g->eig_vecs.clear();
+        g->eig_rest = 0.0;
+        return BQ_OK;
+    }
+    if (!lambdas || !vecs) return fail(BQ_EINVAL, "lambdas or vecs is NULL");
+    if (omega >= g->n) return fail(BQ_EINVAL, "omega = %u must be below n = %u", omega, g->n);
+    for (uint32_t j = 0; j < omega; ++j)
+        if (!(lambdas[j] < 1.0) || !(lambdas[j] >= -1.0))
+            return fail(BQ_EINVAL, "eigenvalue %u = %g must lie in [-1, 1)", j, lambdas[j]);
+    if (!(lambda_rest < 1.0) || !(lambda_rest >= -1.0))
+        return fail(BQ_EINVAL, "lambda_rest = %g must lie in [-1, 1)", lambda_rest);
+    const size_t count = (size_t)g->n * omega;
+    for (size_t i = 0; i < count; ++i)
+        if (!std::isfinite(vecs[i])) return fail(BQ_EINVAL, "vecs[%zu] is not finite", i);
+    g->eig_lambdas.assign(lambdas, lambdas + omega);
+    g->eig_vecs.assign(vecs, vecs + count);
+    g->eig_rest = lambda_rest;
+    g->omega = omega;
+    return BQ_OK;
+}
+
 int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, uint64_t n_walks, uint32_t n_steps,
                   uint32_t mode, const bq_sampler *sampler, uint32_t flags, uint32_t *visits_dev, uint32_t *paths_dev,
                   void *stream) {
@@ -442,6 +470,25 @@ double trunc_factor(double lambda2, double lambda_neg, uint32_t tau) {
         neg = pow(x, (double)tau) * (1.0 - x) / (2.0 * (1.0 + x));
     }
     return std::max(pos, neg);
+}
+
+// Truncation bound with the graph's omega known eigenpairs: the known modes'
+// error sum_k c_k^2 lambda_k^tau (1 + lambda_k) / (2 (1 - lambda_k)) exactly
+// (c_k = psi_k(u)/sqrt(d_u) - psi_k(v)/sqrt(d_v)), the remaining mass
+// s_e - sum_k c_k^2 times the worst factor of the eigenvalues not given.
+double trunc_bound_omega(const bq_graph *g, uint32_t u, uint32_t v, double s_e, uint32_t tau) {
+    const uint32_t w = g->omega;
+    const double *cu = g->eig_vecs.data() + (size_t)u * w;
+    const double *cv = g->eig_vecs.data() + (size_t)v * w;
+    double known = 0.0, mass = 0.0;
+    for (uint32_t j = 0; j < w; ++j) {
+        const double c = cu[j] - cv[j], l = g->eig_lambdas[j];
+        known += c * c * pow(l, (double)tau) * (1.0 + l) / (2.0 * (1.0 - l));
+        mass += c * c;
+    }
+    double rest = s_e - mass;
+    if (rest < 0.0) rest = 0.0;
+    return fabs(known) + rest * trunc_factor(g->eig_rest, g->lambda_neg, tau);
 }
 
 // Position of v in the sorted row of u, or -1.
@@ -524,7 +571,8 @@ int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, 
         double nw = 0.0;
         if (plan_mode == BQ_PLAN_CERTIFIED) {
             const uint32_t tau_cap = 1u << 20;
-            while (s_e * trunc_factor(g->lambda2, g->lambda_neg, t) > eps / 2.0) {
+            while ((g->omega ? trunc_bound_omega(g, a, b, s_e, t) : s_e * trunc_factor(g->lambda2, g->lambda_neg, t)) >
+                   eps / 2.0) {
                 if (t >= tau_cap)
                     return fail(BQ_EOVERFLOW, "query %llu: truncation length exceeds %u", (unsigned long long)q,
                                 tau_cap);

@@ -150,6 +150,12 @@ struct bq_graph {
     int n_components = -1;
     bool has_spectrum = false;
     double lambda2 = 0.0, lambda_neg = 0.0;
+    // omega known eigenpairs for the certified plan (bq_graph_set_eigvecs):
+    // eigenvalues, eigenvectors scaled by 1/sqrt(d) (n x omega, row per
+    // vertex), and the largest eigenvalue not given
+    uint32_t omega = 0;
+    std::vector<double> eig_lambdas, eig_vecs;
+    double eig_rest = 0.0;
 
     bq::DeviceGraph view() const {
         bq::DeviceGraph v;

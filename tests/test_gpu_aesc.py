@@ -247,3 +247,32 @@ def test_planner_errors(env):
     with pytest.raises(bq.BouquetError) as ei:
         bq.aesc_plan(graph, np.array([[0, 1]], np.uint32), 1e-3)
     assert ei.value.code == bq.EOVERFLOW
+
+
+@pytest.mark.parametrize("omega", [1, 3, 8])
+def test_certified_plan_with_eigenvectors(env, omega):
+    """bq_graph_set_eigvecs: the library's certified plan equals the oracle's
+    omega plan (never longer than the plain plan), and the estimate with it
+    meets eps against the exact SC."""
+    bq, torch = env
+    from oracle import exact
+    from workloads import cycle, grid_deleted
+    for g in (gnp_connected(14, 0.3, 4), cycle(10), grid_deleted(5, 6, 0.0, 1)):
+        graph = bq.Graph.from_csr(g)
+        uv = all_edges(g)
+        _, l2, lneg = exact.spectrum(g)
+        graph.set_spectrum(l2, lneg)
+        w = min(omega, g.n - 2)
+        lam, vecs, rest, _ = exact.eigen_embedding(g, w)
+        graph.set_eigvecs(lam, vecs, rest)
+        tau, nw = bq.aesc_plan(graph, uv, 0.1, 0.01)
+        otau, onw = oracle.plan_certified_omega(g, uv, 0.1, 0.01, lam, vecs, rest, lneg)
+        assert np.array_equal(tau, otau) and np.array_equal(nw, onw)
+        graph.set_eigvecs(np.zeros(0), np.zeros(0), 0.0)  # cleared: the plain plan
+        ptau, pnw = bq.aesc_plan(graph, uv, 0.1, 0.01)
+        assert np.all(tau <= ptau) and np.all(nw <= pnw)
+        counts, sc = bq.aesc_estimate_host(graph, 31, uv, tau, nw)
+        assert np.max(np.abs(sc - exact.sc_pinv(g, uv))) <= 0.1
+        with pytest.raises(bq.BouquetError):
+            graph.set_eigvecs(np.array([1.0]), np.zeros(g.n), 0.0)  # eigenvalue 1 is excluded
+        graph.close()
