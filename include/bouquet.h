@@ -365,7 +365,8 @@ typedef struct bq_server_config {
     uint32_t max_inflight;        /* requests on the GPU at once (0: 256) */
     uint32_t max_pending;         /* queued requests before submit says BQ_EBUSY (0: 65536) */
     uint64_t tasks_per_iteration; /* bouquet tasks per iteration launch, shared by the
-                                     admitted requests (0: 2^16) */
+                                     admitted requests (0: 2^16); a backlog grows it up
+                                     to 8x (half of the tasks left) */
     double tau_scale;             /* scheduled plan of every request (bq_schedule) */
     uint32_t tau_add;
     uint32_t tau_max;

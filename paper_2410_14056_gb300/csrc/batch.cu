@@ -49,60 +49,66 @@ __device__ __forceinline__ uint64_t last_le(const uint64_t *__restrict__ a, uint
     return lo;
 }
 
+// Prepare edge i of query d (query index q): normalised endpoints, canonical
+// id, degrees and plan into *bi, its task count into *tasks; counters zeroed,
+// NaN estimate when the edge is not valid (status bits set).
+__device__ __forceinline__ void prepare_edge(const QueryDesc &d, uint64_t i, uint32_t q, uint32_t bouquet,
+                                             BInfo *bi_out, uint32_t *tasks_out, uint32_t *status) {
+    const GraphDesc &g = d.g;
+    uint32_t a, b;
+    if (d.uv) {
+        a = d.uv[2 * i];
+        b = d.uv[2 * i + 1];
+    } else {  // canonical edge i: u = last vertex with upper_before[u] <= i
+        const uint32_t u = (uint32_t)last_le(g.upper_before, g.n, i);
+        const int64_t first = lower_bound_row(g.nbrs, g.offsets[u], g.offsets[u + 1], u + 1);
+        a = u;
+        b = g.nbrs[first + (int64_t)(i - g.upper_before[u])];
+    }
+    BInfo bi;
+    bi.u = a < b ? a : b;
+    bi.v = a < b ? b : a;
+    bi.tau = d.tau[i];
+    bi.nwalks = d.nwalks[i];
+    bi.valid = 0;
+    bi.edge = 0;
+    bi.du = bi.dv = 0;
+    bi.query = q;
+    uint32_t bits = 0;
+    if (a >= g.n || b >= g.n || a == b) {
+        bits = kStatusNoEdge;
+    } else {
+        const int64_t lo = g.offsets[bi.u], hi = g.offsets[bi.u + 1];
+        const int64_t pos = lower_bound_row(g.nbrs, lo, hi, bi.v);
+        if (pos >= hi || g.nbrs[pos] != bi.v) {
+            bits = kStatusNoEdge;
+        } else {
+            const int64_t first = lower_bound_row(g.nbrs, lo, hi, bi.u + 1);
+            bi.edge = g.upper_before[bi.u] + (uint64_t)(pos - first);
+            bi.du = (uint32_t)(hi - lo);
+            bi.dv = (uint32_t)(g.offsets[bi.v + 1] - g.offsets[bi.v]);
+            if (bi.tau == 0 || bi.nwalks == 0) bits = kStatusBadIndex;
+            else if (2ull * bi.nwalks * bi.tau >= (1ull << 32)) bits = kStatusOverflow;
+            else bi.valid = 1;
+        }
+    }
+    if (bits) atomicOr(status, bits);
+    *bi_out = bi;
+    *tasks_out = bi.valid ? 2u * ((bi.nwalks + bouquet - 1) / bouquet) : 0u;
+    d.counts[4 * i + 0] = 0u;
+    d.counts[4 * i + 1] = 0u;
+    d.counts[4 * i + 2] = 0u;
+    d.counts[4 * i + 3] = 0u;
+    if (!bi.valid) d.sc[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 __global__ void batch_prepare_kernel(const QueryDesc *__restrict__ qd, const uint64_t *__restrict__ ebase,
                                      uint32_t nq, uint64_t total, uint32_t bouquet, BInfo *__restrict__ info,
                                      uint32_t *__restrict__ tasks, uint32_t *status) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
          e += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t q = (uint32_t)last_le(ebase, nq, e);
-        const QueryDesc &d = qd[q];
-        const GraphDesc &g = d.g;
-        const uint64_t i = e - d.ebase;
-        uint32_t a, b;
-        if (d.uv) {
-            a = d.uv[2 * i];
-            b = d.uv[2 * i + 1];
-        } else {  // canonical edge i: u = last vertex with upper_before[u] <= i
-            const uint32_t u = (uint32_t)last_le(g.upper_before, g.n, i);
-            const int64_t first = lower_bound_row(g.nbrs, g.offsets[u], g.offsets[u + 1], u + 1);
-            a = u;
-            b = g.nbrs[first + (int64_t)(i - g.upper_before[u])];
-        }
-        BInfo bi;
-        bi.u = a < b ? a : b;
-        bi.v = a < b ? b : a;
-        bi.tau = d.tau[i];
-        bi.nwalks = d.nwalks[i];
-        bi.valid = 0;
-        bi.edge = 0;
-        bi.du = bi.dv = 0;
-        bi.query = q;
-        uint32_t bits = 0;
-        if (a >= g.n || b >= g.n || a == b) {
-            bits = kStatusNoEdge;
-        } else {
-            const int64_t lo = g.offsets[bi.u], hi = g.offsets[bi.u + 1];
-            const int64_t pos = lower_bound_row(g.nbrs, lo, hi, bi.v);
-            if (pos >= hi || g.nbrs[pos] != bi.v) {
-                bits = kStatusNoEdge;
-            } else {
-                const int64_t first = lower_bound_row(g.nbrs, lo, hi, bi.u + 1);
-                bi.edge = g.upper_before[bi.u] + (uint64_t)(pos - first);
-                bi.du = (uint32_t)(hi - lo);
-                bi.dv = (uint32_t)(g.offsets[bi.v + 1] - g.offsets[bi.v]);
-                if (bi.tau == 0 || bi.nwalks == 0) bits = kStatusBadIndex;
-                else if (2ull * bi.nwalks * bi.tau >= (1ull << 32)) bits = kStatusOverflow;
-                else bi.valid = 1;
-            }
-        }
-        if (bits) atomicOr(status, bits);
-        info[e] = bi;
-        tasks[e] = bi.valid ? 2u * ((bi.nwalks + bouquet - 1) / bouquet) : 0u;
-        d.counts[4 * i + 0] = 0u;
-        d.counts[4 * i + 1] = 0u;
-        d.counts[4 * i + 2] = 0u;
-        d.counts[4 * i + 3] = 0u;
-        if (!bi.valid) d.sc[i] = __longlong_as_double(0x7ff8000000000000ll);
+        prepare_edge(qd[q], e - qd[q].ebase, q, bouquet, info + e, tasks + e, status);
     }
 }
 
@@ -242,6 +248,18 @@ serve_count_kernel(const ServeItem *__restrict__ items, uint32_t n_items, uint64
     }
 }
 
+// Estimate of edge i of query d from its counters (every operation rounded
+// to nearest on its own, as the single-query finalize).
+__device__ __forceinline__ void finalize_edge(const QueryDesc &d, const BInfo &bi, uint64_t i) {
+    const double du = (double)bi.du, dv = (double)bi.dv;
+    const double s = __dadd_rn(__ddiv_rn(1.0, du), __ddiv_rn(1.0, dv));
+    const uint32_t *c = d.counts + 4 * i;
+    const double x = (double)((int64_t)c[0] - (int64_t)c[2]);
+    const double y = (double)((int64_t)c[3] - (int64_t)c[1]);
+    const double mean = __ddiv_rn(__dadd_rn(__ddiv_rn(x, du), __ddiv_rn(y, dv)), __dmul_rn(2.0, (double)bi.nwalks));
+    d.sc[i] = __dadd_rn(s, mean);
+}
+
 __global__ void batch_finalize_kernel(const QueryDesc *__restrict__ qd, const BInfo *__restrict__ info,
                                       uint64_t total) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
@@ -249,14 +267,77 @@ __global__ void batch_finalize_kernel(const QueryDesc *__restrict__ qd, const BI
         const BInfo bi = info[e];
         if (!bi.valid) continue;
         const QueryDesc &d = qd[bi.query];
-        const uint64_t i = e - d.ebase;
-        const double du = (double)bi.du, dv = (double)bi.dv;
-        const double s = __dadd_rn(__ddiv_rn(1.0, du), __ddiv_rn(1.0, dv));
-        const uint32_t *c = d.counts + 4 * i;
-        const double x = (double)((int64_t)c[0] - (int64_t)c[2]);
-        const double y = (double)((int64_t)c[3] - (int64_t)c[1]);
-        const double mean = __ddiv_rn(__dadd_rn(__ddiv_rn(x, du), __ddiv_rn(y, dv)), __dmul_rn(2.0, (double)bi.nwalks));
-        d.sc[i] = __dadd_rn(s, mean);
+        finalize_edge(d, bi, e - d.ebase);
+    }
+}
+
+// ------------------------------------------------- server: per-pass launches
+
+// Several requests' prepare, task scan or finalize in one launch; the list
+// travels as a kernel parameter.  Request r owns edges [edge_base[r],
+// edge_base[r + 1]) of the launch.
+__global__ void serve_prepare_many_kernel(ServeMany L, uint32_t bouquet) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < L.edge_base[L.m];
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t r = 0;
+        while (L.edge_base[r + 1] <= e) ++r;
+        const uint64_t i = e - L.edge_base[r];
+        prepare_edge(*L.qd[r], i, 0, bouquet, L.info[r] + i, L.tasks[r] + i, L.status[r]);
+    }
+}
+
+// Exclusive scan of request blockIdx.x's task counts into begin[0..k]: one
+// block per request, a running carry over tiles of the block's width.
+__global__ void __launch_bounds__(1024) serve_scan_many_kernel(ServeMany L) {
+    __shared__ uint64_t s_warp[32];
+    __shared__ uint64_t s_carry;
+    const uint32_t r = blockIdx.x;
+    const uint64_t k = L.edge_base[r + 1] - L.edge_base[r];
+    const uint32_t *tasks = L.tasks[r];
+    uint64_t *begin = L.begin[r];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < k; base += blockDim.x) {
+        const uint64_t idx = base + threadIdx.x;
+        const uint64_t x = idx < k ? tasks[idx] : 0ull;
+        uint64_t incl = x;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t nw = blockDim.x >> 5;
+            uint64_t w = lane < nw ? s_warp[lane] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) s_warp[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const uint64_t warp_before = warp ? s_warp[warp - 1] : 0ull;
+        const uint64_t carry = s_carry;
+        if (idx < k) begin[idx] = carry + warp_before + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + s_warp[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) begin[k] = s_carry;
+}
+
+__global__ void serve_finalize_many_kernel(ServeMany L) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < L.edge_base[L.m];
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t r = 0;
+        while (L.edge_base[r + 1] <= e) ++r;
+        const uint64_t i = e - L.edge_base[r];
+        const BInfo bi = L.info[r][i];
+        if (bi.valid) finalize_edge(*L.qd[r], bi, i);
     }
 }
 
@@ -514,20 +595,6 @@ GraphDesc graph_desc(const bq_graph *g) {
     return d;
 }
 
-size_t serve_scan_ws_bytes(uint64_t k) { return scan_u32_to_u64_ws_bytes(k); }
-
-// One request (a single-query descriptor with ebase 0): edge info, task counts
-// and their prefix.
-int serve_prepare(const QueryDesc *d_qd, uint64_t k, uint32_t bouquet, BInfo *info, uint32_t *tasks,
-                  uint64_t *begin, void *ws, size_t ws_bytes, uint32_t *status, cudaStream_t s) {
-    if (k == 0) return BQ_OK;
-    count_launches(1);
-    // with one query the query index is 0 and the ebase array is not read
-    batch_prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(d_qd, begin, 1, k, bouquet, info, tasks,
-                                                                      status);
-    BQ_CUDA(cudaGetLastError());
-    return scan_u32_to_u64_ws(tasks, begin, k, ws, ws_bytes, s);
-}
 
 // Persistent grid of a serve_count_kernel shape (SMs x resident blocks),
 // taken once per process: every iteration of a server launches it.
@@ -572,12 +639,28 @@ int serve_iterate(const ServeItem *d_items, uint32_t n_items, uint64_t total_ite
              : launch_serve<4, false>(d_items, n_items, total_items, smp, counter, s);
 }
 
-int serve_finalize(const QueryDesc *d_qd, const BInfo *info, uint64_t k, cudaStream_t s) {
-    if (k == 0) return BQ_OK;
+int serve_prepare_many(const ServeMany &L, uint32_t bouquet, cudaStream_t s) {
+    if (L.m == 0) return BQ_OK;
+    const uint64_t edges = L.edge_base[L.m];
+    if (edges) {
+        count_launches(1);
+        serve_prepare_many_kernel<<<blocks_for(edges, kThreads), kThreads, 0, s>>>(L, bouquet);
+        BQ_CUDA(cudaGetLastError());
+    }
     count_launches(1);
-    batch_finalize_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(d_qd, info, k);
+    serve_scan_many_kernel<<<L.m, 1024, 0, s>>>(L);
     BQ_CUDA(cudaGetLastError());
     return BQ_OK;
 }
+
+int serve_finalize_many(const ServeMany &L, cudaStream_t s) {
+    const uint64_t edges = L.m ? L.edge_base[L.m] : 0;
+    if (edges == 0) return BQ_OK;
+    count_launches(1);
+    serve_finalize_many_kernel<<<blocks_for(edges, kThreads), kThreads, 0, s>>>(L);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
 
 }  // namespace bq

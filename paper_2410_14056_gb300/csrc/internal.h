@@ -108,6 +108,19 @@ struct BInfo {
     uint32_t du, dv, tau, nwalks, valid, query;
 };
 
+// Up to kServeMany server requests in one prepare / scan / finalize launch
+// (passed by value as the kernel parameter).
+constexpr uint32_t kServeMany = 32;
+struct ServeMany {
+    const QueryDesc *qd[kServeMany];
+    BInfo *info[kServeMany];
+    uint32_t *tasks[kServeMany];
+    uint64_t *begin[kServeMany];
+    uint32_t *status[kServeMany];
+    uint64_t edge_base[kServeMany + 1];
+    uint32_t m;
+};
+
 // One in-flight request in a server iteration: its tasks [task_lo, task_lo +
 // count) are work items [item_base, item_base + count) of the launch.
 struct ServeItem {
@@ -260,12 +273,11 @@ int validate_sampler(const bq_sampler *in, Sampler &out, bool allow_saba = false
 // ---- batch.cu, used by the server: one query's edges (prepare + task scan),
 // an iteration over windows of several queries' tasks, and the finalize.
 GraphDesc graph_desc(const bq_graph *g);
-size_t serve_scan_ws_bytes(uint64_t k);
-int serve_prepare(const QueryDesc *d_qd, uint64_t k, uint32_t bouquet, BInfo *info, uint32_t *tasks,
-                  uint64_t *begin, void *ws, size_t ws_bytes, uint32_t *status, cudaStream_t s);
 int serve_iterate(const ServeItem *d_items, uint32_t n_items, uint64_t total_items, int lanes, const Sampler &smp,
                   unsigned long long *counter, cudaStream_t s);
-int serve_finalize(const QueryDesc *d_qd, const BInfo *info, uint64_t k, cudaStream_t s);
+// prepare + task scan, or finalize, of up to kServeMany requests in one launch each
+int serve_prepare_many(const ServeMany &L, uint32_t bouquet, cudaStream_t s);
+int serve_finalize_many(const ServeMany &L, cudaStream_t s);
 
 // ---- aesc.cu
 int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,

@@ -34,11 +34,11 @@ using Clock = std::chrono::steady_clock;
 
 // Device layout of a request with k edges (byte offsets; 256-aligned
 // sections).  Inputs, uploaded by one copy: descriptor | uv[2k] | tau[k] |
-// nwalks[k].  Work: info[k] | tasks[k] | begin[k + 1] | scan workspace.
+// nwalks[k].  Work: info[k] | tasks[k] | begin[k + 1].
 // Outputs, read back by one copy: status word (16 B) | counts[4k] | sc[k].
 struct Layout {
     size_t qd, uv, tau, nw, in_bytes;
-    size_t info, tasks, begin, ws, ws_bytes;
+    size_t info, tasks, begin;
     size_t out, counts, sc, out_bytes;
     size_t total;
 };
@@ -62,9 +62,6 @@ Layout layout_of(uint64_t k) {
     p += up(4 * k);
     L.begin = p;
     p += up(8 * (k + 1));
-    L.ws = p;
-    L.ws_bytes = serve_scan_ws_bytes(k);
-    p += up(L.ws_bytes);
     L.out = p;
     L.counts = p + 16;
     L.sc = L.counts + 16 * k;
@@ -84,9 +81,13 @@ struct Request {
     Clock::time_point t_submit, t_done;
     int status = BQ_OK;
     std::string error;  // message of a failed request
-    // host image of the input sections (pairs and plan, filled on the
-    // submitting thread; the descriptor is written at admission)
-    std::vector<char> in;
+    // the pairs as submitted, until a planner moves them into h_in
+    std::vector<uint32_t> uv_in;
+    // pinned host image of the input sections (pairs and plan, written by a
+    // planner thread; the descriptor is written at admission), uploaded by
+    // one asynchronous copy and returned to the pool when the request ends
+    char *h_in = nullptr;
+    size_t h_in_cap = 0;
     double walk_steps = 0;
     uint64_t tasks_total = 0, tasks_launched = 0;
     // device
@@ -103,9 +104,9 @@ struct Request {
     QueryDesc *d_qd() const { return reinterpret_cast<QueryDesc *>(dbuf + L.qd); }
     BInfo *d_info() const { return reinterpret_cast<BInfo *>(dbuf + L.info); }
     uint64_t *d_begin() const { return reinterpret_cast<uint64_t *>(dbuf + L.begin); }
-    uint32_t *h_uv() { return reinterpret_cast<uint32_t *>(in.data() + L.uv); }
-    uint32_t *h_tau() { return reinterpret_cast<uint32_t *>(in.data() + L.tau); }
-    uint32_t *h_nw() { return reinterpret_cast<uint32_t *>(in.data() + L.nw); }
+    uint32_t *h_uv() { return reinterpret_cast<uint32_t *>(h_in + L.uv); }
+    uint32_t *h_tau() { return reinterpret_cast<uint32_t *>(h_in + L.tau); }
+    uint32_t *h_nw() { return reinterpret_cast<uint32_t *>(h_in + L.nw); }
 };
 
 using RequestPtr = std::shared_ptr<Request>;
@@ -234,6 +235,10 @@ void give_event(bq_server *srv, cudaEvent_t &e) {
 // search), whose status comes back with the results.
 int plan_request(bq_server *srv, Request &r) {
     const bq_graph *g = srv->graphs[r.graph];
+    r.h_in = srv->pinned.get(r.L.in_bytes, r.h_in_cap);
+    if (!r.h_in) return fail(BQ_ENOMEM, "server: no pinned host memory for a request");
+    if (r.k) memcpy(r.h_uv(), r.uv_in.data(), 8 * r.k);
+    std::vector<uint32_t>().swap(r.uv_in);
     const uint32_t *edges_uv = r.h_uv();
     const bq_schedule sched{srv->cfg.tau_scale, srv->cfg.tau_add, srv->cfg.tau_max,
                             srv->cfg.n_scale,   srv->cfg.n_min,   0};
@@ -285,25 +290,46 @@ int admit(bq_server *srv, Request &r) {
     qd.sc = reinterpret_cast<double *>(r.dbuf + r.L.sc);
     qd.k = r.k;
     qd.ebase = 0;
-    memcpy(r.in.data() + r.L.qd, &qd, sizeof(qd));
-    // pageable source: the call returns once the image is staged
-    e = cudaMemcpyAsync(r.dbuf, r.in.data(), r.L.in_bytes, cudaMemcpyHostToDevice, s);
+    memcpy(r.h_in + r.L.qd, &qd, sizeof(qd));
+    e = cudaMemcpyAsync(r.dbuf, r.h_in, r.L.in_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.dbuf + r.L.out, 0, 16, s);
     if (e != cudaSuccess) return cuda_fail(e, "server: request upload");
     r.fin_ev = take_event(srv);
     r.done_ev = take_event(srv);
     if (!r.fin_ev || !r.done_ev) return fail(BQ_ECUDA, "server: cannot create events");
-    std::vector<char>().swap(r.in);
-    return serve_prepare(r.d_qd(), r.k, bouquet_of(srv), r.d_info(), reinterpret_cast<uint32_t *>(r.dbuf + r.L.tasks),
-                         r.d_begin(), r.dbuf + r.L.ws, r.L.ws_bytes, reinterpret_cast<uint32_t *>(r.dbuf + r.L.out),
-                         s);
+    return BQ_OK;  // prepared with the rest of its admission pass (prepare_pass)
+}
+
+// The requests' slots in a multi-request launch list.
+void add_to_list(ServeMany &L, Request &r) {
+    const uint32_t j = L.m++;
+    L.qd[j] = r.d_qd();
+    L.info[j] = r.d_info();
+    L.tasks[j] = reinterpret_cast<uint32_t *>(r.dbuf + r.L.tasks);
+    L.begin[j] = r.d_begin();
+    L.status[j] = reinterpret_cast<uint32_t *>(r.dbuf + r.L.out);
+    L.edge_base[j + 1] = L.edge_base[j] + r.k;
+}
+
+// Edge info, task counts and task prefix of a pass's admitted requests: two
+// launches per kServeMany requests instead of several per request.
+int prepare_pass(bq_server *srv, const std::vector<Request *> &reqs) {
+    ServeMany L{};
+    for (size_t i = 0; i < reqs.size(); ++i) {
+        add_to_list(L, *reqs[i]);
+        if (L.m == kServeMany || i + 1 == reqs.size()) {
+            const int rc = serve_prepare_many(L, bouquet_of(srv), srv->stream);
+            if (rc) return rc;
+            L = ServeMany{};
+        }
+    }
+    return BQ_OK;
 }
 
 // Finalize on the compute stream; the copy stream then brings the output
 // section back into a pinned block and frees the request's device memory,
 // so the compute stream goes on with other requests meanwhile.
-void start_finalize(bq_server *srv, Request &r) {
-    serve_finalize(r.d_qd(), r.d_info(), r.k, srv->stream);
+void finish_copy(bq_server *srv, Request &r) {
     cudaEventRecord(r.fin_ev, srv->stream);
     r.h_out = srv->pinned.get(r.L.out_bytes, r.h_out_cap);
     cudaStreamWaitEvent(srv->copy_stream, r.fin_ev, 0);
@@ -315,6 +341,22 @@ void start_finalize(bq_server *srv, Request &r) {
     r.finalizing = true;
 }
 
+// Finalize a set of requests (one launch per kServeMany), then start each
+// one's result copy.
+void finalize_many(bq_server *srv, const std::vector<Request *> &reqs) {
+    ServeMany L{};
+    size_t first = 0;
+    for (size_t i = 0; i < reqs.size(); ++i) {
+        add_to_list(L, *reqs[i]);
+        if (L.m == kServeMany || i + 1 == reqs.size()) {
+            serve_finalize_many(L, srv->stream);
+            for (size_t j = first; j <= i; ++j) finish_copy(srv, *reqs[j]);
+            first = i + 1;
+            L = ServeMany{};
+        }
+    }
+}
+
 // One iteration: a window of tasks of every admitted request, one launch.
 // Returns false when no request has tasks left to launch.
 bool iterate(bq_server *srv) {
@@ -322,7 +364,13 @@ bool iterate(bq_server *srv) {
     for (auto &r : srv->inflight)
         if (!r->finalizing && r->tasks_launched < r->tasks_total) active.push_back(r.get());
     if (active.empty()) return false;
-    const uint64_t budget = srv->cfg.tasks_per_iteration;
+    // The window grows with the backlog (half of the tasks left, at most 8
+    // configured windows): a busy server amortises each launch over more work,
+    // a lightly loaded one keeps iterations short for latency.
+    uint64_t remaining = 0;
+    for (Request *r : active) remaining += r->tasks_total - r->tasks_launched;
+    const uint64_t window = srv->cfg.tasks_per_iteration;
+    const uint64_t budget = std::min(std::max(window, remaining / 2), 8 * window);
     std::vector<uint64_t> take(active.size(), 0);
     uint64_t used = 0;
     // fair share, then hand what is left to requests that still have tasks
@@ -362,8 +410,10 @@ bool iterate(bq_server *srv) {
     cudaEventRecord(srv->ring_ev[slot], srv->stream);
     srv->ring_used[slot] = true;
     srv->ring_next = (slot + 1) % bq_server::kRing;
+    std::vector<Request *> finished;
     for (Request *r : active)
-        if (r->tasks_launched == r->tasks_total) start_finalize(srv, *r);
+        if (r->tasks_launched == r->tasks_total) finished.push_back(r);
+    finalize_many(srv, finished);
     ++srv->iterations;
     return true;
 }
@@ -400,6 +450,8 @@ void poll_completions(bq_server *srv, bool block) {
     for (auto &r : finished) {
         give_event(srv, r->fin_ev);
         give_event(srv, r->done_ev);
+        srv->pinned.put(r->h_in, r->h_in_cap);  // its upload finished long before
+        r->h_in = nullptr;
         if (r->status != BQ_OK) {  // nothing to read: the block goes back now
             srv->pinned.put(r->h_out, r->h_out_cap);
             r->h_out = nullptr;
@@ -430,11 +482,16 @@ namespace {
 // error status (its memory, if any, is released).
 void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
     if (r->dbuf) {
+        // a failed admission may have its upload in flight: let it finish
+        // before the pinned image goes back to the pool (a rare path)
+        cudaStreamSynchronize(srv->stream);
         cudaFreeAsync(r->dbuf, srv->stream);
         r->dbuf = nullptr;
     }
     give_event(srv, r->fin_ev);
     give_event(srv, r->done_ev);
+    srv->pinned.put(r->h_in, r->h_in_cap);
+    r->h_in = nullptr;
     const char *msg = bq_last_error();
     std::lock_guard<std::mutex> lk(srv->mu);
     r->status = status;
@@ -451,6 +508,7 @@ void complete_failed(bq_server *srv, const RequestPtr &r, int status) {
 // edges) and hands them to the worker; a request that cannot be planned is
 // completed at once with its error.
 void planner_main(bq_server *srv) {
+    cudaSetDevice(srv->device);
     for (;;) {
         RequestPtr r;
         {
@@ -470,6 +528,8 @@ void planner_main(bq_server *srv) {
             if (rc == BQ_OK) {
                 srv->pending.push_back(r);
             } else {
+                srv->pinned.put(r->h_in, r->h_in_cap);
+                r->h_in = nullptr;
                 r->status = rc;
                 r->error = msg;
                 r->t_done = Clock::now();
@@ -533,18 +593,26 @@ void worker_main(bq_server *srv) {
                 continue;
             }
         }
+        std::vector<Request *> pass, empty;
         for (auto &r : admitted) {
             const int rc = admit(srv, *r);
             if (rc != BQ_OK) {
                 complete_failed(srv, r, rc);
                 continue;
             }
+            pass.push_back(r.get());
+            if (r->tasks_total == 0) empty.push_back(r.get());
             std::lock_guard<std::mutex> lk(srv->mu);
             srv->inflight.push_back(r);
         }
+        if (!pass.empty()) {
+            const int rc = prepare_pass(srv, pass);
+            if (rc != BQ_OK) {  // a launch failed: the context is unusable; fail the pass
+                for (Request *p : pass) p->status = rc;
+            }
+        }
         // requests with nothing to count go straight to finalization
-        for (auto &r : srv->inflight)
-            if (!r->finalizing && r->tasks_total == 0) start_finalize(srv, *r);
+        finalize_many(srv, empty);
         const double ta = lap(t0);
         const bool launched = iterate(srv);
         const double tl = lap(t0);
@@ -647,6 +715,15 @@ int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server
         server_free(srv);
         return rc;
     }
+    {
+        // the stream-ordered pool keeps freed request memory (set once per device)
+        uint32_t *unused = nullptr;
+        const int rc = status_word(dev, &unused);
+        if (rc) {
+            server_free(srv);
+            return rc;
+        }
+    }
     srv->t_start = Clock::now();
     uint32_t planners = c.planner_threads;
     if (!planners) {
@@ -680,8 +757,7 @@ int bq_server_submit(bq_server *srv, uint32_t graph, const uint32_t *edges_uv, u
     r->eps = eps;
     r->seed = seed;
     r->L = layout_of(k);
-    r->in.assign(r->L.in_bytes, 0);
-    if (k) memcpy(r->h_uv(), edges_uv, 8 * k);
+    r->uv_in.assign(edges_uv, edges_uv + 2 * k);
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if (srv->stop) return fail(BQ_EINVAL, "server is stopping");
