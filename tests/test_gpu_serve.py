@@ -172,3 +172,23 @@ def test_destroy_finishes_queued_requests(env):
     t0 = time.time()
     srv.close()  # joins the worker after the queue drains
     assert time.time() - t0 < 120
+
+
+def test_concurrent_clients(env):
+    """Four client threads submit and wait at once (the binding releases the
+    GIL in the library calls); every result equals the oracle's."""
+    import concurrent.futures as cf
+    bq, hosts, graphs = env
+    rng = np.random.default_rng(21)
+    reqs = requests(hosts, rng, 24)
+    with bq.Server(graphs, tasks_per_iteration=128, planner_threads=3, **SCHED) as srv:
+        def client(chunk):
+            ids = [srv.submit(*r) for r in chunk]
+            return [srv.wait(rid, timeout=120, counts=True) for rid in ids]
+        with cf.ThreadPoolExecutor(4) as pool:
+            outs = list(pool.map(client, [reqs[i::4] for i in range(4)]))
+        st = srv.stats()
+    for i in range(4):
+        for req, (sc, counts, _) in zip(reqs[i::4], outs[i]):
+            check_against_oracle(hosts, req, sc, counts)
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["pending"] == 0
