@@ -302,6 +302,40 @@ __device__ __forceinline__ uint64_t pushed_value(const uint32_t *__restrict__ nb
     return (p < hi && __ldg(nbrs + p) == y) ? (uint64_t)(kPushQ / dy) : 0ull;
 }
 
+// Per-warp shared-memory set of N(u) and N(v) for a depth-1 task with small
+// rows: open addressing over kPushSetSlots slots (load <= 1/2), key = vertex
+// id (kPushEmpty when free), flags bit 0 = neighbour of u, bit 1 = of v.
+constexpr uint32_t kPushSetSlots = 128;
+constexpr uint32_t kPushSetMaxRows = kPushSetSlots / 2;  // d(u) + d(v) admitted
+constexpr uint32_t kPushEmpty = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t push_set_slot(uint32_t y) {
+    return (y * 0x9E3779B1u) >> (32 - 7);  // 7 = log2(kPushSetSlots)
+}
+
+__device__ __forceinline__ void push_set_insert(uint32_t *keys, uint32_t *flags, uint32_t y, uint32_t bit) {
+    uint32_t h = push_set_slot(y);
+    for (uint32_t probe = 0; probe < kPushSetSlots; ++probe) {  // bounded: the set is at most half full
+        const uint32_t prev = atomicCAS(keys + h, kPushEmpty, y);
+        if (prev == kPushEmpty || prev == y) {
+            atomicOr(flags + h, bit);
+            return;
+        }
+        h = (h + 1) & (kPushSetSlots - 1);
+    }
+}
+
+__device__ __forceinline__ uint32_t push_set_flags(const uint32_t *keys, const uint32_t *flags, uint32_t y) {
+    uint32_t h = push_set_slot(y);
+    for (uint32_t probe = 0; probe < kPushSetSlots; ++probe) {
+        const uint32_t key = keys[h];
+        if (key == y) return flags[h];
+        if (key == kPushEmpty) return 0u;
+        h = (h + 1) & (kPushSetSlots - 1);
+    }
+    return 0u;
+}
+
 // Persistent counting kernel of the push estimator: the tasks, streams and
 // walk indices of aesc_count_kernel (independent sampler), walks of tau -
 // depth steps; at step l a walk adds w r_u(cur) and w r_v(cur), w = 2 if
@@ -313,7 +347,11 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
                  const QueryInfo *__restrict__ info, const uint64_t *__restrict__ begin,
                  const uint32_t *__restrict__ bucket, uint64_t k, uint64_t seed,
                  unsigned long long *__restrict__ next_task, unsigned long long *__restrict__ acc) {
+    __shared__ uint32_t s_keys[kThreads / 32][kPushSetSlots];
+    __shared__ uint32_t s_flags[kThreads / 32][kPushSetSlots];
     const uint32_t lane = threadIdx.x & 31;
+    uint32_t *keys = s_keys[threadIdx.x >> 5];
+    uint32_t *flags = s_flags[threadIdx.x >> 5];
     const uint64_t total = begin[k];
     const uint32_t shift = bucket_shift(total, k);
     while (true) {
@@ -330,6 +368,18 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
         const uint64_t k0 = (local >> 1) * 32ull * W;
         const int64_t lo_u = __ldg(offsets + qi.u), hi_u = lo_u + qi.du;
         const int64_t lo_v = __ldg(offsets + qi.v), hi_v = lo_v + qi.dv;
+        // small rows at depth 1: the warp hashes N(u) and N(v) into its set
+        const bool use_set = qi.depth == 1 && (uint64_t)qi.du + qi.dv <= kPushSetMaxRows;
+        if (use_set) {
+            for (uint32_t i = lane; i < kPushSetSlots; i += 32) {
+                keys[i] = kPushEmpty;
+                flags[i] = 0u;
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < qi.du; i += 32) push_set_insert(keys, flags, __ldg(nbrs + lo_u + i), 1u);
+            for (uint32_t i = lane; i < qi.dv; i += 32) push_set_insert(keys, flags, __ldg(nbrs + lo_v + i), 2u);
+            __syncwarp();
+        }
 
         uint64_t st[W];
         uint32_t cur[W], deg[W];
@@ -360,8 +410,17 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
                 if (deg[j]) {
                     const uint32_t kk = choose(sample_word<false>(st[j], 0ull, cur[j], 0u), deg[j]);
                     el.next(off[j] + kk, cur[j], off[j], deg[j]);
-                    a_u += weight * pushed_value(nbrs, lo_u, hi_u, qi.u, cur[j], deg[j], qi.depth);
-                    a_v += weight * pushed_value(nbrs, lo_v, hi_v, qi.v, cur[j], deg[j], qi.depth);
+                    if (use_set) {
+                        const uint32_t f = push_set_flags(keys, flags, cur[j]);
+                        if (f) {
+                            const uint64_t r = (uint64_t)(kPushQ / deg[j]);
+                            if (f & 1u) a_u += weight * r;
+                            if (f & 2u) a_v += weight * r;
+                        }
+                    } else {
+                        a_u += weight * pushed_value(nbrs, lo_u, hi_u, qi.u, cur[j], deg[j], qi.depth);
+                        a_v += weight * pushed_value(nbrs, lo_v, hi_v, qi.v, cur[j], deg[j], qi.depth);
+                    }
                 }
             }
         }
