@@ -64,7 +64,7 @@ def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
         cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
-            ["-Xlinker", "-rpath=" + cuda_lib, "-lpthread"]
+            ["-Xlinker", "-rpath=" + cuda_lib, "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

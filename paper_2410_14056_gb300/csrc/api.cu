@@ -251,6 +251,7 @@ const char *bq_strerror(int code) {
 
 int bq_graph_create(uint32_t n, const int64_t *offsets, const uint32_t *nbrs, uint32_t flags, void *cuda_stream,
                     bq_graph **out) {
+    bq::NvtxRange nvtx_range("bq_graph_create");
     g_last_error[0] = 0;
     if (!out) return fail(BQ_EINVAL, "out is NULL");
     *out = nullptr;
@@ -405,6 +406,7 @@ int bq_graph_set_eigvecs(bq_graph *g, uint32_t omega, const double *lambdas, con
 int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, uint64_t n_walks, uint32_t n_steps,
                   uint32_t mode, const bq_sampler *sampler, uint32_t flags, uint32_t *visits_dev, uint32_t *paths_dev,
                   void *stream) {
+    bq::NvtxRange nvtx_range("bq_walk_batch");
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (mode != BQ_MODE_NAIVE && mode != BQ_MODE_BOUQUET) return fail(BQ_EINVAL, "unknown mode %u", mode);
@@ -525,6 +527,7 @@ extern "C" {
 
 int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, double delta, uint32_t plan_mode,
                  const bq_schedule *sched, uint32_t *tau, uint32_t *nwalks) {
+    bq::NvtxRange nvtx_range("bq_aesc_plan");
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (!(eps > 0.0) || !(eps < 1e6)) return fail(BQ_EINVAL, "eps = %g must be positive", eps);
@@ -596,6 +599,7 @@ int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, 
 int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
                      const uint32_t *tau_dev, const uint32_t *nwalks_dev, const bq_sampler *sampler, uint32_t flags,
                      uint32_t *counts_dev, double *sc_dev, void *stream) {
+    bq::NvtxRange nvtx_range("bq_aesc_estimate");
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
@@ -645,6 +649,7 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
 int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
                           const uint32_t *tau_dev, const uint32_t *nwalks_dev, uint32_t push_max, uint32_t flags,
                           uint32_t *depth_dev, uint64_t *acc_dev, double *sc_dev, void *stream) {
+    bq::NvtxRange nvtx_range("bq_aesc_estimate_push");
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);

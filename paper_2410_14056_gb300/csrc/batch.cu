@@ -412,6 +412,7 @@ void free_batch(bq_batch *b) {
 extern "C" {
 
 int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_sampler *sampler, bq_batch **out) {
+    bq::NvtxRange nvtx_range("bq_batch_create");
     if (!out) return fail(BQ_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_queries == 0 || !queries) return fail(BQ_EINVAL, "a batch needs at least one query");
@@ -509,6 +510,7 @@ int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_s
 }
 
 int bq_batch_run(bq_batch *b, void *stream) {
+    bq::NvtxRange nvtx_range("bq_batch_run");
     if (!b) return fail(BQ_EINVAL, "batch is NULL");
     if (b->edges == 0) return BQ_OK;
     cudaStream_t s = (cudaStream_t)stream;

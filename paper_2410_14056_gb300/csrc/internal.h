@@ -7,6 +7,7 @@
 
 #include <string>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/bouquet.h"
 
@@ -196,6 +197,15 @@ struct bq_graph {
 };
 
 namespace bq {
+
+// ---- NVTX: a named range over each library call and server iteration
+// (shown by Nsight tools; a no-op when none is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---- error plumbing (api.cu)
 int fail(int code, const char *fmt, ...);

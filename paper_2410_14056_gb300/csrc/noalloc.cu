@@ -54,6 +54,7 @@ using namespace bq;
 extern "C" int bq_walk_batch_noalloc(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, uint64_t n_walks,
                                      uint32_t n_steps, const bq_sampler *sampler, uint32_t flags,
                                      uint32_t *visits_dev, uint32_t *paths_dev, void *stream) {
+    bq::NvtxRange nvtx_range("bq_walk_batch_noalloc");
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (flags & ~BQ_VISIT_START)
         return fail(BQ_EINVAL, "bq_walk_batch_noalloc takes device buffers only (flags 0x%x)", flags);

@@ -360,6 +360,7 @@ void finalize_many(bq_server *srv, const std::vector<Request *> &reqs) {
 // One iteration: a window of tasks of every admitted request, one launch.
 // Returns false when no request has tasks left to launch.
 bool iterate(bq_server *srv) {
+    NvtxRange nvtx_range("bq_server_iteration");
     std::vector<Request *> active;
     for (auto &r : srv->inflight)
         if (!r->finalizing && r->tasks_launched < r->tasks_total) active.push_back(r.get());

@@ -37,6 +37,7 @@ extern "C" {
 
 int bq_autotune_walks(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev, uint64_t n_walks,
                       uint32_t n_steps, uint32_t *visits_dev, void *stream, uint32_t *best, float *ms) {
+    bq::NvtxRange nvtx_range("bq_autotune_walks");
     if (!g || !best) return fail(BQ_EINVAL, "graph or best is NULL");
     bq_tuning saved;
     bq_get_tuning(&saved);
@@ -73,6 +74,7 @@ int bq_autotune_walks(const bq_graph *g, uint64_t seed, const uint32_t *starts_d
 
 int bq_autotune_aesc(const bq_aesc_query *queries, uint32_t n_queries, const bq_sampler *sampler, void *stream,
                      uint32_t *best, float *ms) {
+    bq::NvtxRange nvtx_range("bq_autotune_aesc");
     if (!best) return fail(BQ_EINVAL, "best is NULL");
     bq_tuning saved;
     bq_get_tuning(&saved);
