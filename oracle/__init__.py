@@ -5,8 +5,9 @@ package.  The product library never imports it and shares no code with it.
 
 Two parts:
   * ``walks.c`` (compiled here with gcc into ``_build/liboracle.so``): the
-    hash-keyed walks, walk-batch visit counts, AESC counters, the certified
-    planner and the FP64 finalize, as plain single-threaded loops.
+    hash-keyed walks, walk-batch visit counts, AESC counters, the planners
+    (certified, scheduled, and the pilot sample's moments and walk count)
+    and the FP64 finalize, as plain single-threaded loops.
   * ``exact.py`` (numpy, FP64): exact spanning centrality by the Laplacian
     pseudoinverse and by the matrix-tree theorem, the spectrum of
     D^-1/2 A D^-1/2, the truncated walk series, and E(eta) of Sec. 5.6.
@@ -113,6 +114,14 @@ def lib():
                 c.c_uint32, i64p, u32p, c.c_uint64, u32p, c.c_double, c.c_double, c.c_uint32,
                 c.c_uint32, c.c_double, c.c_uint32, u32p, u32p]
             L.orc_plan_scheduled.restype = c.c_int
+            L.orc_aesc_moments.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, c.c_uint64, u32p, u32p, u32p,
+                c.c_uint32, c.c_uint32, c.c_uint32, u64p]
+            L.orc_aesc_moments.restype = c.c_int
+            L.orc_plan_pilot_nwalks.argtypes = [
+                c.c_uint32, i64p, c.c_uint64, u32p, u32p, u64p, c.c_uint32, c.c_double,
+                c.c_double, c.c_uint32, u32p, f64p]
+            L.orc_plan_pilot_nwalks.restype = c.c_int
             _lib = L
     return _lib
 
@@ -360,3 +369,53 @@ def aesc_push_estimate(g, seed: int, uv, tau, nwalks, push_max: int = 1):
     """(depth, acc, sc) of the push-phase estimator."""
     depth, acc = aesc_push_counts(g, seed, uv, tau, nwalks, push_max)
     return depth, acc, aesc_push_finalize(g, uv, tau, nwalks, depth, acc)
+
+
+# ------------------------------------------- pilot sample of the scheduled plan
+
+def aesc_moments(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
+                 sampler=None) -> np.ndarray:
+    """uint64[k, 2, 5]: per query and side (0 from u, 1 from v) the sums of a,
+    b, a^2, b^2, a b over the side's first nwalks walks, a and b being one
+    walk's weighted hits of u and of v."""
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    mo = np.zeros(10 * q.shape[0], np.uint64)
+    kind, t, width = _sampler(sampler)
+    rc = lib().orc_aesc_moments(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed, q.shape[0],
+        _p(q, ctypes.c_uint32), _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
+        kind, t, width, _p(mo, ctypes.c_uint64))
+    _check(rc, "aesc_moments")
+    return mo.reshape(-1, 2, 5)
+
+
+def pilot_nwalks(g, uv: np.ndarray, tau: np.ndarray, moments: np.ndarray, n_pilot: int,
+                 eps: float, z: float, n_min: int):
+    """(nwalks uint32[k], var float64[k]): the pilot plan's walk count and
+    the per-sample variance it was computed from."""
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    mo = np.ascontiguousarray(moments, dtype=np.uint64).reshape(-1)
+    nw = np.zeros(q.shape[0], np.uint32)
+    var = np.zeros(q.shape[0], np.float64)
+    rc = lib().orc_plan_pilot_nwalks(
+        g.n, _p(off, ctypes.c_int64), q.shape[0], _p(q, ctypes.c_uint32), _p(ta, ctypes.c_uint32),
+        _p(mo, ctypes.c_uint64), int(n_pilot), float(eps), float(z), int(n_min),
+        _p(nw, ctypes.c_uint32), _p(var, ctypes.c_double))
+    _check(rc, "plan_pilot_nwalks")
+    return nw, var
+
+
+def plan_pilot(g, seed: int, uv: np.ndarray, eps: float, tau_scale: float, tau_add: int,
+               tau_max: int, n_min: int, n_pilot: int, z: float = 3.0, sampler=None):
+    """(tau, nwalks, moments, var): tau from the schedule, then n_pilot walks
+    per side (the estimate's first walks) give the sample variance and N."""
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    tau, _ = plan_scheduled(g, q, eps, tau_scale, tau_add, tau_max, 0.0, 1)
+    mo = aesc_moments(g, seed, q, tau, np.full(q.shape[0], n_pilot, np.uint32), sampler)
+    nw, var = pilot_nwalks(g, q, tau, mo, n_pilot, eps, z, n_min)
+    return tau, nw, mo, var

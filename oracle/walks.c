@@ -32,7 +32,8 @@
  *   plan            - CalculateTau / NWalks of Alg. 1, which the paper does
  *                     not define; here the spectral truncation bound and
  *                     Hoeffding's inequality (readings listed in the design
- *                     notes).
+ *                     notes), a schedule, or a schedule for tau and a pilot
+ *                     sample's variance for N.
  *   finalize        - the estimate s(e) = g(u,v) + g(v,u) of Alg. 1, with
  *                     g initialised to 1/d and incremented by the walk sums.
  */
@@ -391,6 +392,79 @@ int orc_aesc_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
     return ORC_OK;
 }
 
+/* ------------------------------------------- pilot sample (scheduled plan) */
+
+/* Moments of a pilot sample for query edge q = {u, v}, u < v: the first
+ * nwalks[q] walks of each side, i.e. the estimator's own walks (streams
+ * 2e + side, walk indices 0.., the same sampler), tau[q] steps each.  Walk w
+ * of a side scores a = its weighted hits of u and b = its weighted hits of v
+ * (weight 2 at steps l < tau, 1 at l = tau, as in the counters), and
+ *   moments[10q + 5 side + 0..4] = sum a, sum b, sum a^2, sum b^2, sum a b
+ * over that side's walks (side 0 from u, side 1 from v). */
+int orc_aesc_moments(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                     uint64_t seed, uint64_t k, const uint32_t *uv,
+                     const uint32_t *tau, const uint32_t *nwalks, uint32_t kind,
+                     uint32_t t, uint32_t width, uint64_t *moments)
+{
+    orc_sampler smp;
+    uint64_t *ub;
+    uint64_t q;
+    smp.kind = kind;
+    smp.t = t;
+    smp.width = width;
+    if (!sampler_ok(&smp) || kind == 2)
+        return ORC_EINVAL;
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub)
+        return ORC_EINVAL;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b;
+        uint32_t v = a < b ? b : a;
+        uint64_t e;
+        uint32_t side;
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &e) != ORC_OK) {
+            free(ub);
+            return ORC_ENOEDGE;
+        }
+        if (2ull * nwalks[q] * tau[q] >= 4294967296ull) {
+            free(ub);
+            return ORC_EOVERFLOW;
+        }
+        for (side = 0; side < 2; side++) {
+            uint64_t stream = 2 * e + side;
+            uint64_t w, *mo = moments + 10 * q + 5 * side;
+            mo[0] = mo[1] = mo[2] = mo[3] = mo[4] = 0;
+            for (w = 0; w < nwalks[q]; w++) {
+                uint64_t kw = orc_walk_key(seed, stream, w);
+                uint64_t kg = 0, hu = 0, hv = 0;
+                uint32_t cur = side == 0 ? u : v;
+                uint32_t l;
+                if (kind == 1)
+                    kg = orc_walk_key(seed, stream | ORC_GROUP_BIT, w / width);
+                for (l = 1; l <= tau[q]; l++) {
+                    int64_t lo = offsets[cur];
+                    uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
+                    uint32_t weight = l < tau[q] ? 2u : 1u;
+                    uint32_t r = sample_word(&smp, kw, kg, l, cur);
+                    cur = nbrs[lo + orc_choose(r, d)];
+                    if (cur == u)
+                        hu += weight;
+                    if (cur == v)
+                        hv += weight;
+                }
+                mo[0] += hu;
+                mo[1] += hv;
+                mo[2] += hu * hu;
+                mo[3] += hv * hv;
+                mo[4] += hu * hv;
+            }
+        }
+    }
+    free(ub);
+    return ORC_OK;
+}
+
 /* --------------------------------------------------------------- finalize */
 
 /* SC(e) estimate from the four counters:
@@ -719,6 +793,74 @@ int orc_plan_scheduled(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
         nwalks[q] = (uint32_t)nw;
     }
     free(ub);
+    return ORC_OK;
+}
+
+/* x - y of two unsigned integers as a double (the exact difference, rounded
+ * once). */
+static double signed_diff(uint64_t x, uint64_t y)
+{
+    return x >= y ? (double)(x - y) : -(double)(y - x);
+}
+
+/* Walk count of the pilot plan from the moments of orc_aesc_moments with
+ * n0 pilot walks per side.  One sample of the estimator is the pair of walk
+ * w from u (U) and walk w from v (V), and the estimate is s_e plus the mean
+ * over samples of
+ *   Y = ((a(U) - a(V)) / d_u + (b(V) - b(U)) / d_v) / 2
+ *     = ((a/d_u - b/d_v)(U) - (a/d_u - b/d_v)(V)) / 2.
+ * U and V are independent, so Var Y = (Var_0 + Var_1) / 4 with
+ * Var_s = Var(a)/d_u^2 + Var(b)/d_v^2 - 2 Cov(a, b)/(d_u d_v) on side s.
+ * The unbiased sample (co)variances are C / (n0 (n0 - 1)) with the integer
+ * centred sums C_aa = n0 S_aa - S_a^2, C_bb = n0 S_bb - S_b^2 and
+ * C_ab = n0 S_ab - S_a S_b, exact in 64 bits while 2 n0 tau < 2^32.  In FP64,
+ * one rounding per operation in this order:
+ *   caa = C_aa,0 + C_aa,1   cbb = C_bb,0 + C_bb,1   cab = C_ab,0 + C_ab,1
+ *   var = ((caa / (d_u d_u) + cbb / (d_v d_v)) - (2 cab) / (d_u d_v))
+ *         / ((4 n0) (n0 - 1)),   clamped at 0
+ *   N   = max(ceil((z z var) / ((eps/2) (eps/2))), n_min, 1)
+ * i.e. the normal-approximation half-width z sqrt(Var Y / N) is at most
+ * eps / 2.  var_out (may be NULL) receives var.  Returns ORC_EOVERFLOW when
+ * 2 N tau >= 2^32. */
+int orc_plan_pilot_nwalks(uint32_t n, const int64_t *offsets, uint64_t k,
+                          const uint32_t *uv, const uint32_t *tau,
+                          const uint64_t *moments, uint32_t n0, double eps,
+                          double z, uint32_t n_min, uint32_t *nwalks,
+                          double *var_out)
+{
+    uint64_t q;
+    if (n0 < 2 || !(eps > 0.0) || !(z > 0.0))
+        return ORC_EINVAL;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        double du, dv, caa = 0.0, cbb = 0.0, cab = 0.0, var, half, nw;
+        uint32_t side;
+        if (a >= n || b >= n)
+            return ORC_EINVAL;
+        du = (double)(offsets[(a < b ? a : b) + 1] - offsets[a < b ? a : b]);
+        dv = (double)(offsets[(a < b ? b : a) + 1] - offsets[a < b ? b : a]);
+        for (side = 0; side < 2; side++) {
+            const uint64_t *mo = moments + 10 * q + 5 * side;
+            caa = caa + signed_diff((uint64_t)n0 * mo[2], mo[0] * mo[0]);
+            cbb = cbb + signed_diff((uint64_t)n0 * mo[3], mo[1] * mo[1]);
+            cab = cab + signed_diff((uint64_t)n0 * mo[4], mo[0] * mo[1]);
+        }
+        var = ((caa / (du * du) + cbb / (dv * dv)) - (2.0 * cab) / (du * dv)) /
+              ((4.0 * (double)n0) * ((double)n0 - 1.0));
+        if (var < 0.0)
+            var = 0.0;
+        half = eps / 2.0;
+        nw = ceil((z * z * var) / (half * half));
+        if (nw < (double)n_min)
+            nw = (double)n_min;
+        if (nw < 1.0)
+            nw = 1.0;
+        if (var_out)
+            var_out[q] = var;
+        if (nw * 2.0 * (double)tau[q] >= 4294967296.0)
+            return ORC_EOVERFLOW;
+        nwalks[q] = (uint32_t)nw;
+    }
     return ORC_OK;
 }
 
