@@ -307,6 +307,8 @@ def aesc_measure(bq, torch, steps, warmup):
 
 
 POWERLAW_SCHEDULE = dict(tau_scale=2.0, tau_add=2, tau_max=64, n_scale=9.0, n_min=32)
+PILOT_WALKS = 64  # pilot walks per side of the pilot plan
+PILOT_Z = 3.0     # normal quantile of its half-width eps / 2
 
 
 def aesc_cpu_baseline(g, seed, uv, tau, nw, n_edges=100_000):
@@ -405,10 +407,41 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
             "subset_1000_max_abs_diff_vs_16N_2tau": float(pdiff.max()),
             "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(pdiff ** 2))),
             "plain_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(diff ** 2)))}
+    # the pilot plan: the same tau, N from PILOT_WALKS walks per side (z = PILOT_Z)
+    t0 = time.perf_counter()
+    ltau, lnw, _ = bq.aesc_plan_pilot(graph, 5, None, eps, sched, PILOT_WALKS, PILOT_Z, moments=False)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    ldtau = torch.from_numpy(ltau.view(np.int32)).cuda()
+    ldnw = torch.from_numpy(lnw.view(np.int32)).cuda()
+    bq.aesc_estimate(graph, 5, None, ldtau, ldnw, counts=counts, sc=sc)
+    bq.sync()
+    llat = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bq.aesc_estimate(graph, 5, None, ldtau, ldnw, counts=counts, sc=sc)
+        e1.record()
+        e1.synchronize()
+        llat.append(e0.elapsed_time(e1))
+    bq.sync()
+    lms = sum(llat) / len(llat)
+    lest = sc.cpu().numpy()
+    ldiff = np.abs(lest[pick] - ref)
+    pilot = {"n_pilot": PILOT_WALKS, "z": PILOT_Z, "plan_ms": plan_ms,
+             "pilot_walk_steps": float(np.sum(2.0 * PILOT_WALKS * ltau.astype(np.float64))),
+             "same_tau_as_schedule": bool(np.array_equal(ltau, tau)),
+             "walk_steps_per_call": float(np.sum(2.0 * ltau.astype(np.float64) * lnw)),
+             "nwalks_mean": float(lnw.mean()), "frac_edges_at_n_min": float(np.mean(lnw == sched.n_min)),
+             "edges_per_s": tau.size / (lms / 1e3), "ms_per_estimate": lms,
+             "foster_residual": abs(float(lest.sum()) - (g.n - 1)) / (g.n - 1),
+             "subset_1000_max_abs_diff_vs_16N_2tau": float(ldiff.max()),
+             "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(ldiff ** 2))),
+             "subset_1000_frac_within_half_eps": float(np.mean(ldiff <= eps / 2))}
     graph.close()
     cpu_line = aesc_cpu_baseline(g, 5, all_edges(g), tau, nw) if cpu else None
     return {
         "push_phase": push,
+        "pilot_plan": pilot,
         "cpu_baseline": cpu_line,
         "workload": f"chung-lu n=4M d=10 gamma=2.1 LCC (n={g.n}, m={g.m}), all edges, eps={eps}, "
                     "scheduled plan (uncertified)",

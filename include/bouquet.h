@@ -243,6 +243,39 @@ int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps,
                  double delta, uint32_t plan_mode, const bq_schedule *sched,
                  uint32_t *tau, uint32_t *nwalks);
 
+/*
+ * Pilot plan: tau from the schedule (as SCHEDULED), N from the sample
+ * variance of a pilot (NWalks of Alg. 1 left open by the paper; uncertified).
+ * The pilot runs on the GPU: the first n_pilot walks of each side of every
+ * query, i.e. the walks bq_aesc_estimate takes first for the same seed,
+ * sampler and tau, scored by a = weighted hits of u and b = weighted hits
+ * of v (weights 2 before tau, 1 at tau).  Per query q and side s (0 from u,
+ * 1 from v) moments[10q + 5s + 0..4] = sum a, sum b, sum a^2, sum b^2,
+ * sum a b.  One sample of the estimator has the value
+ *   Y = ((a(U) - a(V)) / d_u + (b(V) - b(U)) / d_v) / 2,
+ * and with the integer centred sums C_aa = n0 S_aa - S_a^2,
+ * C_bb = n0 S_bb - S_b^2, C_ab = n0 S_ab - S_a S_b (n0 = n_pilot) summed
+ * over both sides,
+ *   var = ((C_aa / d_u^2 + C_bb / d_v^2) - 2 C_ab / (d_u d_v))
+ *         / (4 n0 (n0 - 1))    (clamped at 0)
+ *   N   = max(ceil(z^2 var / (eps/2)^2), sched->n_min, 1),
+ * each FP64 operation rounded on its own in this order: the estimate's
+ * normal-approximation half-width z sqrt(var / N) is then at most eps / 2.
+ * sched->n_scale is not used.  tau is planned on the host; the pilot and N
+ * run on the GPU.
+ * edges_uv = k host pairs (NULL: all m edges in canonical order).  Outputs
+ * are host arrays: tau, nwalks uint32[k]; moments uint64[10k], or NULL to
+ * skip copying them back.  The call runs on `stream` and returns after
+ * synchronising it.
+ * Errors: BQ_EINVAL (n_pilot < 2, z or eps out of range, bad sampler or
+ * schedule), BQ_ENOEDGE, BQ_EOVERFLOW (2 n_pilot tau or 2 N tau >= 2^32),
+ * BQ_ENOMEM, BQ_ECUDA.
+ */
+int bq_aesc_plan_pilot(bq_graph *g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
+                       double eps, const bq_schedule *sched, uint32_t n_pilot, double z,
+                       const bq_sampler *sampler, uint32_t *tau, uint32_t *nwalks,
+                       uint64_t *moments, void *stream);
+
 /* ------------------------------------------------------ bq_aesc_estimate */
 /*
  * Estimate SC for k query edges (the walk loop and final sum of Alg. 1 at

@@ -116,7 +116,7 @@ EXPORTS = (
     "bq_profile_read", "bq_walk_batch_noalloc", "bq_batch_create", "bq_batch_run",
     "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
     "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
-    "bq_server_destroy", "bq_aesc_estimate_push", "bq_graph_set_eigvecs",
+    "bq_server_destroy", "bq_aesc_estimate_push", "bq_graph_set_eigvecs", "bq_aesc_plan_pilot",
 )
 
 _lock = threading.Lock()
@@ -145,6 +145,8 @@ def load_library(path: str | None = None):
         L.bq_graph_set_eigvecs.argtypes = [vp, u32, vp, vp, f64]
         L.bq_walk_batch.argtypes = [vp, u64, vp, u64, u32, u32, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_aesc_plan.argtypes = [vp, vp, u64, f64, f64, u32, c.POINTER(Schedule), vp, vp]
+        L.bq_aesc_plan_pilot.argtypes = [vp, u64, vp, u64, f64, c.POINTER(Schedule), u32, f64,
+                                         c.POINTER(Sampler), vp, vp, vp, vp]
         L.bq_aesc_estimate.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_aesc_estimate_push.argtypes = [vp, u64, vp, u64, vp, vp, u32, u32, vp, vp, vp, vp]
         L.bq_sync.argtypes = [vp]
@@ -355,6 +357,30 @@ def aesc_plan(graph: Graph, uv: np.ndarray | None, eps: float, delta: float = 0.
                           ctypes.byref(schedule) if schedule is not None else None,
                           _hptr(tau, "tau", np.uint32), _hptr(nw, "nwalks", np.uint32)))
     return tau, nw
+
+
+def aesc_plan_pilot(graph: Graph, seed: int, uv: np.ndarray | None, eps: float, schedule: Schedule,
+                    n_pilot: int, z: float = 3.0, sampler=None, stream=None, moments: bool = True):
+    """Pilot plan: tau from the schedule, N from the variance of n_pilot
+    walks per side run on the GPU.  Returns (tau, nwalks, moments) as numpy
+    arrays, moments uint64[k, 2, 5] (per side: sums of a, b, a^2, b^2, a b)
+    or None when not asked for."""
+    L = load_library()
+    if uv is None:
+        k = graph.info()["m"]
+        puv = None
+    else:
+        uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+        k = uv.shape[0]
+        puv = _hptr(uv, "edges", np.uint32)
+    tau = np.zeros(k, np.uint32)
+    nw = np.zeros(k, np.uint32)
+    mo = np.zeros(10 * k, np.uint64) if moments else None
+    _check(L.bq_aesc_plan_pilot(graph.handle, int(seed) & (2**64 - 1), puv, k, float(eps),
+                                ctypes.byref(schedule), int(n_pilot), float(z), _sampler(sampler),
+                                _hptr(tau, "tau", np.uint32), _hptr(nw, "nwalks", np.uint32),
+                                _hptr(mo, "moments", np.uint64), _stream_handle(stream)))
+    return tau, nw, (mo.reshape(-1, 2, 5) if moments else None)
 
 
 def aesc_estimate(graph: Graph, seed: int, uv, tau, nwalks, sampler=None, counts=None,

@@ -21,7 +21,10 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no FMA contraction (the planners round every FP64 operation on
+# its own, on x86 and on Arm alike)
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+              "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu", "batch.cu", "tune.cu", "serve.cu"]
 HEADERS = ["internal.h", "hash.cuh", "edges.cuh"]

@@ -99,7 +99,7 @@ __global__ void prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, u
         info[q] = qi;
         if (depth_out) depth_out[q] = qi.depth;
         tasks[q] = qi.valid && qi.tau > qi.depth ? 2u * ((qi.nwalks + bouquet - 1) / bouquet) : 0u;
-        if (!qi.valid) sc[q] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+        if (!qi.valid && sc) sc[q] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
     }
 }
 
@@ -264,6 +264,149 @@ aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *_
         if (lane == 0) {
             if (hit_u) atomicAdd(counts + 4 * q + 2 * side + 0, hit_u);
             if (hit_v) atomicAdd(counts + 4 * q + 2 * side + 1, hit_v);
+        }
+    }
+}
+
+// Pilot sample of the scheduled plan: the first nwalks walks of each side,
+// i.e. the estimator's own walks (same streams, walk indices and sampler),
+// each scored by a = its weighted hits of u and b = its weighted hits of v.
+// A lane keeps its two walks' scores apart; the warp adds the sums of a, b,
+// a^2, b^2 and a b over its 64 walks to the side's five 64-bit moments
+// moments[10q + 5 side + 0..4] with five atomics.
+constexpr int kMomentW = 2;
+
+template <typename EL, bool COUPLED>
+__global__ void __launch_bounds__(kThreads)
+aesc_moments_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *__restrict__ info,
+                    const uint64_t *__restrict__ begin, const uint32_t *__restrict__ bucket, uint64_t k,
+                    uint64_t seed, Sampler smp, unsigned long long *__restrict__ next_task,
+                    unsigned long long *__restrict__ moments) {
+    constexpr int W = kMomentW;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t total = begin[k];
+    const uint32_t shift = bucket_shift(total, k);
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(next_task, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        const uint64_t q = task_edge(begin, bucket, k, total, shift, t);
+        const QueryInfo qi = info[q];
+        const uint64_t local = t - begin[q];
+        const uint32_t side = (uint32_t)(local & 1);
+        const uint64_t k0 = (local >> 1) * 32ull * W;
+        const uint64_t stream = 2 * qi.edge + side;
+        const uint32_t start = side ? qi.v : qi.u;
+        uint64_t st[W], gs[W];
+        bool act[W];
+        if constexpr (COUPLED) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint64_t kk = k0 + (uint64_t)j * 32 + lane;
+                st[j] = walk_key(seed, stream, kk);
+                gs[j] = walk_key(seed, stream | kGroupBit, kk / smp.width);
+                act[j] = kk < qi.nwalks;
+            }
+        } else {
+            const uint64_t kk = k0 + (uint64_t)lane * W;
+            walk_key_pair(seed, stream, kk >> 1, st[0], st[1]);
+            gs[0] = gs[1] = 0;
+            act[0] = kk < qi.nwalks;
+            act[1] = kk + 1 < qi.nwalks;
+        }
+        uint64_t off0;
+        uint32_t deg0;
+        start_record(offsets, start, off0, deg0);
+        uint64_t off[W];
+        uint32_t cur[W], deg[W], ha[W], hb[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            cur[j] = start;
+            off[j] = off0;
+            deg[j] = act[j] ? deg0 : 0u;  // inactive walks never move or hit
+            ha[j] = hb[j] = 0;
+        }
+        for (uint32_t l = 1; l <= qi.tau; ++l) {
+            const uint32_t weight = l < qi.tau ? 2u : 1u;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                st[j] += kGolden;
+                if (COUPLED) gs[j] += kGolden;
+                if (deg[j]) {
+                    const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                    el.next(off[j] + kk, cur[j], off[j], deg[j]);
+                    ha[j] += cur[j] == qi.u ? weight : 0u;
+                    hb[j] += cur[j] == qi.v ? weight : 0u;
+                }
+            }
+        }
+        unsigned long long m[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            m[0] += ha[j];
+            m[1] += hb[j];
+            m[2] += (unsigned long long)ha[j] * ha[j];
+            m[3] += (unsigned long long)hb[j] * hb[j];
+            m[4] += (unsigned long long)ha[j] * hb[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) m[i] += __shfl_down_sync(0xffffffffu, m[i], d);
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (m[i]) atomicAdd(moments + 10 * q + 5 * side + i, m[i]);
+        }
+    }
+}
+
+// x - y of two unsigned integers as a double: the exact difference, rounded
+// once.
+__device__ __forceinline__ double signed_diff(uint64_t x, uint64_t y) {
+    return x >= y ? __ull2double_rn(x - y) : -__ull2double_rn(y - x);
+}
+
+// Walk count of the pilot plan.  One sample of the estimator has the value
+// Y = ((a(U) - a(V))/d_u + (b(V) - b(U))/d_v) / 2 with independent walks U
+// from u and V from v, so Var Y = (Var_0 + Var_1) / 4 with, on side s,
+// Var_s = Var a / d_u^2 + Var b / d_v^2 - 2 Cov(a, b) / (d_u d_v).  The
+// unbiased sample moments come from the exact integer centred sums
+// n0 S_aa - S_a^2, n0 S_bb - S_b^2, n0 S_ab - S_a S_b (exact in 64 bits while
+// 2 n0 tau < 2^32); N = max(ceil(z^2 var / (eps/2)^2), n_min, 1).  Every FP64
+// operation is rounded on its own (_rn intrinsics), in the documented order.
+__global__ void pilot_nwalks_kernel(const QueryInfo *__restrict__ info, uint64_t k,
+                                    const unsigned long long *__restrict__ moments, uint32_t n0, double eps,
+                                    double z, uint32_t n_min, uint32_t *__restrict__ nwalks, uint32_t *status) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const QueryInfo qi = info[q];
+        if (!qi.valid) {
+            nwalks[q] = 0;
+            continue;
+        }
+        const double du = (double)qi.du, dv = (double)qi.dv, n0d = (double)n0;
+        double caa = 0.0, cbb = 0.0, cab = 0.0;
+        for (int side = 0; side < 2; ++side) {
+            const unsigned long long *m = moments + 10 * q + 5 * side;
+            caa = __dadd_rn(caa, signed_diff((uint64_t)n0 * m[2], m[0] * m[0]));
+            cbb = __dadd_rn(cbb, signed_diff((uint64_t)n0 * m[3], m[1] * m[1]));
+            cab = __dadd_rn(cab, signed_diff((uint64_t)n0 * m[4], m[0] * m[1]));
+        }
+        const double num = __dsub_rn(__dadd_rn(__ddiv_rn(caa, __dmul_rn(du, du)), __ddiv_rn(cbb, __dmul_rn(dv, dv))),
+                                     __ddiv_rn(__dmul_rn(2.0, cab), __dmul_rn(du, dv)));
+        double var = __ddiv_rn(num, __dmul_rn(__dmul_rn(4.0, n0d), __dsub_rn(n0d, 1.0)));
+        if (var < 0.0) var = 0.0;
+        const double half = __dmul_rn(eps, 0.5);
+        double nw = ceil(__ddiv_rn(__dmul_rn(__dmul_rn(z, z), var), __dmul_rn(half, half)));
+        if (nw < (double)n_min) nw = (double)n_min;
+        if (nw < 1.0) nw = 1.0;
+        if (__dmul_rn(__dmul_rn(nw, 2.0), (double)qi.tau) >= 4294967296.0) {
+            atomicOr(status, kStatusOverflow);
+            nwalks[q] = 0;
+        } else {
+            nwalks[q] = (uint32_t)nw;
         }
     }
 }
@@ -674,6 +817,87 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
         finalize_push_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, acc64, sc);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "finalize_push_kernel");
+    }
+    scratch_free(buf, s);
+    return rc;
+}
+
+}  // namespace bq
+
+namespace bq {
+namespace {
+
+template <typename EL, bool COUPLED>
+int launch_moments(EL el, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+                   uint64_t seed, const Sampler &smp, unsigned long long *next_task, unsigned long long *moments,
+                   cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto kernel = aesc_moments_kernel<EL, COUPLED>;
+    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
+    kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, info, begin, bucket, k, seed, smp, next_task, moments);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+}  // namespace
+
+int launch_aesc_moments(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
+                        const uint32_t *tau, const uint32_t *nwalks, const Sampler &smp, uint64_t *moments,
+                        const PilotParams *pilot, uint32_t *nwalks_out, uint32_t *status, cudaStream_t s) {
+    if (k == 0) return BQ_OK;
+    if (!edges_uv) return fail(BQ_EINVAL, "pilot moments need explicit edges");
+    if (k >= kMaxBucketEdges) return fail(BQ_EINVAL, "k = %llu edges in one pilot", (unsigned long long)k);
+    const uint32_t bouquet = 32u * (uint32_t)kMomentW;
+    // scratch: info[k] | begin[k + 1] bucket[k + 1] | tasks[k] | next_task
+    const size_t info_bytes = sizeof(QueryInfo) * k;
+    const size_t begin_bytes = sizeof(uint64_t) * (k + 1) + ((sizeof(uint32_t) * bucket_count(k) + 7) & ~(size_t)7);
+    const size_t task_bytes = sizeof(uint32_t) * ((k + 1) & ~1ull);
+    char *buf = nullptr;
+    int rc = scratch_alloc((void **)&buf, info_bytes + begin_bytes + task_bytes + 16, s);
+    if (rc) return rc;
+    QueryInfo *info = (QueryInfo *)buf;
+    uint64_t *begin = (uint64_t *)(buf + info_bytes);
+    uint32_t *tasks = (uint32_t *)(buf + info_bytes + begin_bytes);
+    unsigned long long *next_task = (unsigned long long *)(buf + info_bytes + begin_bytes + task_bytes);
+    unsigned long long *mo = reinterpret_cast<unsigned long long *>(moments);
+    cudaError_t e = cudaMemsetAsync(moments, 0, sizeof(uint64_t) * 10 * k, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next_task, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        scratch_free(buf, s);
+        return cuda_fail(e, "pilot setup");
+    }
+    {
+        ProfScope prof(kProfAescAux, s);
+        count_launches(1);
+        prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, edges_uv, k, tau, nwalks, bouquet, 0u, info,
+                                                                    tasks, nullptr, nullptr, status);
+        rc = scan_u32_to_u64(tasks, begin, k, s);
+        if (rc == BQ_OK) {
+            count_launches(1);
+            build_bucket_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(
+                begin, k, reinterpret_cast<uint32_t *>(begin + k + 1));
+        }
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAesc, s);
+        count_launches(1);
+        rc = with_edges(g, [&](auto el) {
+            using EL = decltype(el);
+            return smp.kind == 1 ? launch_moments<EL, true>(el, g, info, begin, k, seed, smp, next_task, mo, s)
+                                 : launch_moments<EL, false>(el, g, info, begin, k, seed, smp, next_task, mo, s);
+        });
+    }
+    if (rc == BQ_OK && pilot) {
+        ProfScope prof(kProfAescAux, s);
+        count_launches(1);
+        pilot_nwalks_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, mo, pilot->n0, pilot->eps, pilot->z,
+                                                                         pilot->n_min, nwalks_out, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "pilot_nwalks_kernel");
     }
     scratch_free(buf, s);
     return rc;

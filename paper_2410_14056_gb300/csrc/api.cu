@@ -596,6 +596,72 @@ int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, 
     return BQ_OK;
 }
 
+int bq_aesc_plan_pilot(bq_graph *g, uint64_t seed, const uint32_t *edges_uv, uint64_t k, double eps,
+                       const bq_schedule *sched, uint32_t n_pilot, double z, const bq_sampler *sampler,
+                       uint32_t *tau, uint32_t *nwalks, uint64_t *moments, void *stream) {
+    bq::NvtxRange nvtx_range("bq_aesc_plan_pilot");
+    g_last_error[0] = 0;
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (!sched) return fail(BQ_EINVAL, "pilot plan needs a schedule");
+    if (n_pilot < 2) return fail(BQ_EINVAL, "n_pilot = %u (at least 2)", n_pilot);
+    if (!(z > 0.0) || !(z < 1e6)) return fail(BQ_EINVAL, "z = %g must be positive", z);
+    Sampler smp;
+    int rc = check_sampler(sampler, smp);
+    if (rc) return rc;
+    // tau from the schedule (its N part unused: n_scale 0, n_min 1)
+    bq_schedule tau_only = *sched;
+    tau_only.n_scale = 0.0;
+    tau_only.n_min = 1;
+    rc = bq_aesc_plan(g, edges_uv, k, eps, 0.0, BQ_PLAN_SCHEDULED, &tau_only, tau, nwalks);
+    if (rc || k == 0) return rc;
+    for (uint64_t q = 0; q < k; ++q)
+        if (2ull * n_pilot * tau[q] >= (1ull << 32))
+            return fail(BQ_EOVERFLOW, "query %llu: 2 * n_pilot * tau reaches 2^32", (unsigned long long)q);
+    // explicit pairs (canonical order when edges_uv is NULL)
+    std::vector<uint32_t> canon;
+    if (!edges_uv) {
+        canon.reserve(2 * k);
+        for (uint32_t u = 0; u < g->n; ++u)
+            for (int64_t j = g->h_offsets[u]; j < g->h_offsets[u + 1]; ++j)
+                if (g->h_nbrs[j] > u) {
+                    canon.push_back(u);
+                    canon.push_back(g->h_nbrs[j]);
+                }
+    }
+    const uint32_t *pairs = edges_uv ? edges_uv : canon.data();
+    std::vector<uint32_t> n0(k, n_pilot);
+    DeviceGuard guard(g->device);
+    uint32_t *status = nullptr;
+    rc = status_word(g->device, &status);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t eb = sizeof(uint32_t) * 2 * k, tb = sizeof(uint32_t) * k, mb = sizeof(uint64_t) * 10 * k;
+    char *buf = nullptr;
+    rc = scratch_alloc((void **)&buf, mb + eb + 3 * tb, s);
+    if (rc) return rc;
+    uint64_t *d_mo = (uint64_t *)buf;
+    uint32_t *d_uv = (uint32_t *)(buf + mb);
+    uint32_t *d_tau = (uint32_t *)(buf + mb + eb);
+    uint32_t *d_n0 = (uint32_t *)(buf + mb + eb + tb);
+    uint32_t *d_nw = (uint32_t *)(buf + mb + eb + 2 * tb);
+    cudaError_t e = cudaMemcpyAsync(d_uv, pairs, eb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tau, tau, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_n0, n0.data(), tb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "pilot upload");
+    const PilotParams pp{n_pilot, sched->n_min, eps, z};
+    if (rc == BQ_OK)
+        rc = launch_aesc_moments(g->view(), seed, d_uv, k, d_tau, d_n0, smp, d_mo, &pp, d_nw, status, s);
+    if (rc == BQ_OK) {
+        e = cudaMemcpyAsync(nwalks, d_nw, tb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && moments) e = cudaMemcpyAsync(moments, d_mo, mb, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "pilot download");
+    }
+    scratch_free(buf, s);
+    if (rc == BQ_OK) rc = bq_sync(stream);
+    else cudaStreamSynchronize(s);
+    return rc;
+}
+
 int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
                      const uint32_t *tau_dev, const uint32_t *nwalks_dev, const bq_sampler *sampler, uint32_t flags,
                      uint32_t *counts_dev, double *sc_dev, void *stream) {

@@ -294,6 +294,19 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,
                 uint64_t k, const uint32_t *tau, const uint32_t *nwalks,
                 const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
                 cudaStream_t s);
+// Pilot of the scheduled plan: per query and side the sums of a, b, a^2,
+// b^2, a b over the first nwalks[q] walks (a, b = one walk's weighted hits of
+// u and of v) into moments = device uint64[10k]; edges_uv explicit.  With
+// pilot != NULL (nwalks[q] = pilot->n0 for all q) the walk count of the pilot
+// plan is then written to nwalks_out (device uint32[k]).
+struct PilotParams {
+    uint32_t n0;
+    uint32_t n_min;
+    double eps, z;
+};
+int launch_aesc_moments(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
+                        const uint32_t *tau, const uint32_t *nwalks, const Sampler &smp, uint64_t *moments,
+                        const PilotParams *pilot, uint32_t *nwalks_out, uint32_t *status, cudaStream_t s);
 int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
                      const uint32_t *tau, const uint32_t *nwalks, uint32_t push_max, uint32_t *depth_out,
                      uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s);
