@@ -6,8 +6,9 @@ package.  The product library never imports it and shares no code with it.
 Two parts:
   * ``walks.c`` (compiled here with gcc into ``_build/liboracle.so``): the
     hash-keyed walks, walk-batch visit counts, AESC counters, the planners
-    (certified, scheduled, and the pilot sample's moments and walk count)
-    and the FP64 finalize, as plain single-threaded loops.
+    (certified, scheduled, and the pilot sample's moments and walk count),
+    the FP64 finalize, the push-phase and the vertex-centric (shared-walk)
+    estimators, as plain single-threaded loops.
   * ``exact.py`` (numpy, FP64): exact spanning centrality by the Laplacian
     pseudoinverse and by the matrix-tree theorem, the spectrum of
     D^-1/2 A D^-1/2, the truncated walk series, and E(eta) of Sec. 5.6.
@@ -122,6 +123,12 @@ def lib():
                 c.c_uint32, i64p, c.c_uint64, u32p, u32p, u64p, c.c_uint32, c.c_double,
                 c.c_double, c.c_uint32, u32p, f64p]
             L.orc_plan_pilot_nwalks.restype = c.c_int
+            L.orc_aesc_shared_counts.argtypes = [
+                c.c_uint32, i64p, u32p, c.c_uint64, c.c_uint64, u32p, u32p, u32p,
+                c.c_uint32, c.c_uint32, c.c_uint32, u32p, u32p]
+            L.orc_aesc_shared_counts.restype = c.c_int
+            L.orc_aesc_shared_finalize.argtypes = [c.c_uint32, i64p, c.c_uint64, u32p, u32p, u32p, f64p]
+            L.orc_aesc_shared_finalize.restype = c.c_int
             _lib = L
     return _lib
 
@@ -419,3 +426,46 @@ def plan_pilot(g, seed: int, uv: np.ndarray, eps: float, tau_scale: float, tau_a
     mo = aesc_moments(g, seed, q, tau, np.full(q.shape[0], n_pilot, np.uint32), sampler)
     nw, var = pilot_nwalks(g, q, tau, mo, n_pilot, eps, z, n_min)
     return tau, nw, mo, var
+
+
+# ------------------------------------------- AESC with walks shared per vertex
+
+VERTEX_STREAM = 1 << 61  # stream of vertex-centric walks: VERTEX_STREAM | x
+
+
+def aesc_shared_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
+                       sampler=None):
+    """(counts uint32[4k], nused uint32[2k]): C_uu, C_uv, C_vu, C_vv from the
+    walks shared per vertex, and the walk counts N_u, N_v they used."""
+    off, nb = _graph_arrays(g)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    counts = np.zeros(4 * q.shape[0], np.uint32)
+    nused = np.zeros(2 * q.shape[0], np.uint32)
+    kind, t, width = _sampler(sampler)
+    rc = lib().orc_aesc_shared_counts(
+        g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed, q.shape[0],
+        _p(q, ctypes.c_uint32), _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
+        kind, t, width, _p(counts, ctypes.c_uint32), _p(nused, ctypes.c_uint32))
+    _check(rc, "aesc_shared_counts")
+    return counts, nused
+
+
+def aesc_shared_finalize(g, uv: np.ndarray, counts: np.ndarray, nused: np.ndarray) -> np.ndarray:
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+    cn = np.ascontiguousarray(counts, dtype=np.uint32)
+    nu = np.ascontiguousarray(nused, dtype=np.uint32)
+    sc = np.zeros(q.shape[0], np.float64)
+    rc = lib().orc_aesc_shared_finalize(g.n, _p(off, ctypes.c_int64), q.shape[0], _p(q, ctypes.c_uint32),
+                                        _p(cn, ctypes.c_uint32), _p(nu, ctypes.c_uint32),
+                                        _p(sc, ctypes.c_double))
+    _check(rc, "aesc_shared_finalize")
+    return sc
+
+
+def aesc_shared_estimate(g, seed: int, uv, tau, nwalks, sampler=None):
+    """(counts, nused, sc) of the vertex-centric (shared-walk) estimator."""
+    counts, nused = aesc_shared_counts(g, seed, uv, tau, nwalks, sampler)
+    return counts, nused, aesc_shared_finalize(g, uv, counts, nused)

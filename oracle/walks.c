@@ -36,6 +36,10 @@
  *                     sample's variance for N.
  *   finalize        - the estimate s(e) = g(u,v) + g(v,u) of Alg. 1, with
  *                     g initialised to 1/d and incremented by the walk sums.
+ *   push phase      - Alg. 1's push step at depth 0 or 1, in fixed point.
+ *   shared walks    - the walk loop of Alg. 1 with the walks of a vertex
+ *                     serving every query edge at it (vertex-centric walk
+ *                     sharing, a neighbour test per step).
  */
 #include <math.h>
 #include <stdint.h>
@@ -462,6 +466,202 @@ int orc_aesc_moments(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
         }
     }
     free(ub);
+    return ORC_OK;
+}
+
+/* ------------------------------------- AESC with walks shared per vertex */
+
+/* Stream space of vertex-centric walks: walk w from vertex x has stream
+ * ORC_VERTEX_STREAM | x (edge streams 2 e + side stay below 2^61). */
+#define ORC_VERTEX_STREAM 0x2000000000000000ULL
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Vertex-centric counters: the walks from a vertex serve every query edge at
+ * that vertex (walks shared per vertex, with a neighbour-membership test per
+ * step).  Every endpoint x of a query edge runs N_x = max nwalks and
+ * tau_x = max tau over the query edges at x: walks w < N_x on stream
+ * ORC_VERTEX_STREAM | x, tau_x steps each.  For query q = {u, v}, u < v,
+ * with tau_q, each of the N_u walks from u adds weight w_l (2 for l < tau_q,
+ * 1 for l = tau_q, nothing beyond) at step l to C_uu when it stands on u and
+ * to C_uv when it stands on v; the N_v walks from v likewise to C_vu and C_vv.
+ *   counts[4q + 0..3] = C_uu, C_uv, C_vu, C_vv;  nused[2q + 0..1] = N_u, N_v.
+ * A repeated edge among the queries is rejected (ORC_EINVAL). */
+int orc_aesc_shared_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
+                           uint64_t seed, uint64_t k, const uint32_t *uv,
+                           const uint32_t *tau, const uint32_t *nwalks, uint32_t kind,
+                           uint32_t t, uint32_t width, uint32_t *counts, uint32_t *nused)
+{
+    orc_sampler smp;
+    uint64_t *ub = NULL, *ids = NULL, *cross = NULL, *qoff = NULL, *qlist = NULL;
+    uint32_t *vn = NULL, *vt = NULL;
+    uint64_t q, x;
+    int rc = ORC_OK;
+    smp.kind = kind;
+    smp.t = t;
+    smp.width = width;
+    if (!sampler_ok(&smp) || kind == 2)
+        return ORC_EINVAL;
+    ub = count_upper(n, offsets, nbrs);
+    ids = (uint64_t *)malloc((k + 1) * sizeof(uint64_t));
+    cross = (uint64_t *)calloc(2 * k + 1, sizeof(uint64_t));
+    qoff = (uint64_t *)calloc((size_t)n + 2, sizeof(uint64_t));
+    qlist = (uint64_t *)malloc((2 * k + 1) * sizeof(uint64_t));
+    vn = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
+    vt = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
+    if (!ub || !ids || !cross || !qoff || !qlist || !vn || !vt) {
+        rc = ORC_EINVAL;
+        goto done;
+    }
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        if (edge_id_of(n, offsets, nbrs, ub, a, b, &ids[q]) != ORC_OK) {
+            rc = ORC_ENOEDGE;
+            goto done;
+        }
+        if (tau[q] == 0 || nwalks[q] == 0) {
+            rc = ORC_EINVAL;
+            goto done;
+        }
+    }
+    qsort(ids, k, sizeof(uint64_t), cmp_u64);
+    for (q = 1; q < k; q++)
+        if (ids[q] == ids[q - 1]) {
+            rc = ORC_EINVAL;
+            goto done;
+        }
+    /* per-vertex plan and the list of query edges at each vertex */
+    for (q = 0; q < k; q++) {
+        uint32_t e[2];
+        int s2;
+        e[0] = uv[2 * q];
+        e[1] = uv[2 * q + 1];
+        for (s2 = 0; s2 < 2; s2++) {
+            if (nwalks[q] > vn[e[s2]])
+                vn[e[s2]] = nwalks[q];
+            if (tau[q] > vt[e[s2]])
+                vt[e[s2]] = tau[q];
+            qoff[e[s2] + 2]++;
+        }
+    }
+    for (x = 0; x < n; x++)
+        qoff[x + 2] += qoff[x + 1];
+    for (q = 0; q < k; q++) {
+        qlist[qoff[uv[2 * q] + 1]++] = q;
+        qlist[qoff[uv[2 * q + 1] + 1]++] = q;
+    }
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b, v = a < b ? b : a;
+        uint64_t big = vn[u] > vn[v] ? vn[u] : vn[v];
+        if (2ull * big * tau[q] >= 4294967296ull) {
+            rc = ORC_EOVERFLOW;
+            goto done;
+        }
+        nused[2 * q + 0] = vn[u];
+        nused[2 * q + 1] = vn[v];
+    }
+    for (x = 0; x < n; x++) {
+        uint64_t w, j, *ret;
+        uint64_t stream = ORC_VERTEX_STREAM | x;
+        uint32_t l;
+        if (vn[x] == 0)
+            continue;
+        ret = (uint64_t *)calloc((size_t)vt[x] + 1, sizeof(uint64_t));
+        if (!ret) {
+            rc = ORC_EINVAL;
+            goto done;
+        }
+        for (w = 0; w < vn[x]; w++) {
+            uint64_t kw = orc_walk_key(seed, stream, w);
+            uint64_t kg = 0;
+            uint32_t cur = (uint32_t)x;
+            if (kind == 1)
+                kg = orc_walk_key(seed, stream | ORC_GROUP_BIT, w / width);
+            for (l = 1; l <= vt[x]; l++) {
+                int64_t lo = offsets[cur];
+                uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
+                uint32_t r = sample_word(&smp, kw, kg, l, cur);
+                cur = nbrs[lo + orc_choose(r, d)];
+                if (cur == x)
+                    ret[l]++;
+                for (j = qoff[x]; j < qoff[x + 1]; j++) {
+                    uint64_t qq = qlist[j];
+                    uint32_t a = uv[2 * qq], b = uv[2 * qq + 1];
+                    uint32_t u = a < b ? a : b, v = a < b ? b : a;
+                    uint32_t other = x == u ? v : u;
+                    if (cur == other && l <= tau[qq])
+                        cross[2 * qq + (x == u ? 0 : 1)] += l < tau[qq] ? 2u : 1u;
+                }
+            }
+        }
+        /* return hits of x, weighted per query edge by its own tau */
+        for (j = qoff[x]; j < qoff[x + 1]; j++) {
+            uint64_t qq = qlist[j], c = 0;
+            uint32_t a = uv[2 * qq], b = uv[2 * qq + 1];
+            uint32_t u = a < b ? a : b;
+            for (l = 1; l <= tau[qq]; l++)
+                c += (l < tau[qq] ? 2u : 1u) * ret[l];
+            if (c > UINT32_MAX) {
+                free(ret);
+                rc = ORC_EOVERFLOW;
+                goto done;
+            }
+            counts[4 * qq + (x == u ? 0 : 3)] = (uint32_t)c;
+        }
+        free(ret);
+    }
+    for (q = 0; q < k; q++) {
+        if (cross[2 * q] > UINT32_MAX || cross[2 * q + 1] > UINT32_MAX) {
+            rc = ORC_EOVERFLOW;
+            goto done;
+        }
+        counts[4 * q + 1] = (uint32_t)cross[2 * q];
+        counts[4 * q + 2] = (uint32_t)cross[2 * q + 1];
+    }
+done:
+    free(ub);
+    free(ids);
+    free(cross);
+    free(qoff);
+    free(qlist);
+    free(vn);
+    free(vt);
+    return rc;
+}
+
+/* Estimate from the shared counters; the walks of u and of v may differ in
+ * number, so each hit count is divided by its own walk count:
+ *   est = s_e + ((C_uu/N_u - C_vu/N_v)/d_u + (C_vv/N_v - C_uv/N_u)/d_v) / 2,
+ * each operation rounded on its own, in this order. */
+int orc_aesc_shared_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
+                             const uint32_t *uv, const uint32_t *counts,
+                             const uint32_t *nused, double *sc)
+{
+    uint64_t q;
+    for (q = 0; q < k; q++) {
+        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        uint32_t u = a < b ? a : b;
+        uint32_t v = a < b ? b : a;
+        double du, dv, s, nu, nv, ruu, rvu, rvv, ruv, mean;
+        if (u >= n || v >= n || nused[2 * q] == 0 || nused[2 * q + 1] == 0)
+            return ORC_EINVAL;
+        du = (double)(offsets[u + 1] - offsets[u]);
+        dv = (double)(offsets[v + 1] - offsets[v]);
+        s = 1.0 / du + 1.0 / dv;
+        nu = (double)nused[2 * q];
+        nv = (double)nused[2 * q + 1];
+        ruu = (double)counts[4 * q + 0] / nu;
+        ruv = (double)counts[4 * q + 1] / nu;
+        rvu = (double)counts[4 * q + 2] / nv;
+        rvv = (double)counts[4 * q + 3] / nv;
+        mean = ((ruu - rvu) / du + (rvv - ruv) / dv) / 2.0;
+        sc[q] = s + mean;
+    }
     return ORC_OK;
 }
 
