@@ -331,6 +331,35 @@ int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edge
                           uint32_t push_max, uint32_t flags, uint32_t *depth_dev,
                           uint64_t *acc_dev, double *sc_dev, void *stream);
 
+/* ----------------------------------------------- bq_aesc_estimate_shared */
+/*
+ * Vertex-centric variant of bq_aesc_estimate: the walks of a vertex serve
+ * every query edge at that vertex (Alg. 1's walk loop with walks shared per
+ * vertex, a neighbour test per step).  Every endpoint x of a query edge runs
+ * N_x = max nwalks and tau_x = max tau over the query edges at x; walk
+ * w < N_x of x is keyed on stream 2^61 | x.  For query q = {u, v} (u < v)
+ * with tau_q, the N_u walks from u add, at each step l <= tau_q, weight 2
+ * (l < tau_q) or 1 (l = tau_q) to C_uu when on u and to C_uv when on v; the
+ * N_v walks from v likewise to C_vu and C_vv:
+ *   counts_dev[4q + 0..3] = C_uu, C_uv, C_vu, C_vv (uint32)
+ *   nused_dev[2q + 0..1]  = N_u, N_v (uint32; may be NULL)
+ *   sc_dev[q] = s_e + ((C_uu/N_u - C_vu/N_v)/d_u + (C_vv/N_v - C_uv/N_u)/d_v) / 2,
+ * each FP64 operation rounded on its own in that order.  Each edge keeps
+ * its own tau and at least its own N walks per side.  Queries must be
+ * distinct edges (a repeated edge, in either orientation, gives BQ_EINVAL at
+ * bq_sync).  The device path waits for `stream` once, after planning the
+ * vertices, to size the per-(vertex, step) return histograms; with
+ * BQ_HOST_IO every array is a host array and the call is synchronous.
+ * edges_uv_dev = NULL takes all m edges in canonical order (k = m).
+ * Device scratch: about 32 B per vertex, 4 B per CSR entry, 32 B per query.
+ * Errors: as bq_aesc_estimate; BQ_EOVERFLOW when 2 max(N_u, N_v) tau_q >=
+ * 2^32 (that estimate is NaN).
+ */
+int bq_aesc_estimate_shared(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev,
+                            uint64_t k, const uint32_t *tau_dev, const uint32_t *nwalks_dev,
+                            const bq_sampler *sampler, uint32_t flags, uint32_t *counts_dev,
+                            uint32_t *nused_dev, double *sc_dev, void *stream);
+
 /* ---------------------------------------------------------- AESC batches */
 /*
  * Many AESC estimates (on one or many graphs, of uneven sizes) run as one

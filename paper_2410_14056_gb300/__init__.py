@@ -9,6 +9,6 @@ from .bouquet import (  # noqa: F401
     BORROW, DEVICE_PTRS, EBUSY, EGRAPH, EINVAL, ENOEDGE, ENOMEM, EOVERFLOW, ETIMEOUT, HOST_IO, HOST_PTRS,
     MODE_BOUQUET, MODE_NAIVE, OK, PLAN_CERTIFIED, PLAN_SCHEDULED, REQUIRE_CONNECTED,
     SAMPLER_COUPLED, SAMPLER_IND, SAMPLER_SABA, SKIP_VALIDATE, VISIT_START, Batch, BouquetError, Graph, Sampler,
-    Schedule, Server, ServerConfig, aesc_estimate, aesc_estimate_push, aesc_estimate_push_host, autotune_aesc, autotune_walks, profile_enable, profile_read, aesc_estimate_host, aesc_plan, aesc_plan_pilot, get_tuning, load_library,
+    Schedule, Server, ServerConfig, aesc_estimate, aesc_estimate_push, aesc_estimate_push_host, aesc_estimate_shared, aesc_estimate_shared_host, autotune_aesc, autotune_walks, profile_enable, profile_read, aesc_estimate_host, aesc_plan, aesc_plan_pilot, get_tuning, load_library,
     set_tuning, sync, version, walk_batch, walk_batch_host,
 )

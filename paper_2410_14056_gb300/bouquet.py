@@ -117,6 +117,7 @@ EXPORTS = (
     "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
     "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
     "bq_server_destroy", "bq_aesc_estimate_push", "bq_graph_set_eigvecs", "bq_aesc_plan_pilot",
+    "bq_aesc_estimate_shared",
 )
 
 _lock = threading.Lock()
@@ -149,6 +150,8 @@ def load_library(path: str | None = None):
                                          c.POINTER(Sampler), vp, vp, vp, vp]
         L.bq_aesc_estimate.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_aesc_estimate_push.argtypes = [vp, u64, vp, u64, vp, vp, u32, u32, vp, vp, vp, vp]
+        L.bq_aesc_estimate_shared.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp,
+                                              vp, vp]
         L.bq_sync.argtypes = [vp]
         L.bq_strerror.argtypes = [i32]
         L.bq_strerror.restype = c.c_char_p
@@ -460,6 +463,50 @@ def aesc_estimate_push_host(graph: Graph, seed: int, uv: np.ndarray | None, tau:
                                    _hptr(depth, "depth", np.uint32), _hptr(acc, "acc", np.uint64),
                                    _hptr(sc, "sc", np.float64), None))
     return depth, acc, sc
+
+
+def aesc_estimate_shared(graph: Graph, seed: int, uv, tau, nwalks, sampler=None, counts=None,
+                         nused=None, sc=None, stream=None):
+    """Vertex-centric AESC (walks shared per vertex) on device tensors (uv
+    None = all edges); returns (counts, nused, sc).  Waits for the stream
+    once to size its histograms."""
+    import torch
+    L = load_library()
+    k = tau.numel()
+    dev = tau.device
+    if counts is None:
+        counts = torch.empty(4 * k, dtype=torch.int32, device=dev)
+    if nused is None:
+        nused = torch.empty(2 * k, dtype=torch.int32, device=dev)
+    if sc is None:
+        sc = torch.empty(k, dtype=torch.float64, device=dev)
+    _check(L.bq_aesc_estimate_shared(graph.handle, int(seed) & (2**64 - 1), _dptr(uv, "uv"), k,
+                                     _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), _sampler(sampler), 0,
+                                     _dptr(counts, "counts"), _dptr(nused, "nused"), _dptr(sc, "sc", 8),
+                                     _stream_handle(stream)))
+    return counts, nused, sc
+
+
+def aesc_estimate_shared_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.ndarray,
+                              nwalks: np.ndarray, sampler=None):
+    """Vertex-centric AESC through host buffers (BQ_HOST_IO); synchronous.
+    Returns (counts uint32[4k], nused uint32[2k], sc float64[k])."""
+    L = load_library()
+    ta = np.ascontiguousarray(tau, dtype=np.uint32)
+    nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
+    k = ta.size
+    puv = None
+    if uv is not None:
+        uv = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
+        puv = _hptr(uv, "edges", np.uint32)
+    counts = np.zeros(4 * k, np.uint32)
+    nused = np.zeros(2 * k, np.uint32)
+    sc = np.zeros(k, np.float64)
+    _check(L.bq_aesc_estimate_shared(graph.handle, int(seed) & (2**64 - 1), puv, k, _hptr(ta, "tau", np.uint32),
+                                     _hptr(nw, "nwalks", np.uint32), _sampler(sampler), HOST_IO,
+                                     _hptr(counts, "counts", np.uint32), _hptr(nused, "nused", np.uint32),
+                                     _hptr(sc, "sc", np.float64), None))
+    return counts, nused, sc
 
 
 def _query_array(queries):

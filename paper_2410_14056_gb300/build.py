@@ -26,7 +26,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
-UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu", "batch.cu", "tune.cu", "serve.cu"]
+UNITS = ["api.cu", "graph.cu", "walks.cu", "aesc.cu", "noalloc.cu", "batch.cu", "tune.cu", "serve.cu", "shared.cu"]
 HEADERS = ["internal.h", "hash.cuh", "edges.cuh"]
 
 

@@ -666,6 +666,14 @@ int launch_count_w(EL el, const DeviceGraph &g, const QueryInfo *info, const uin
 
 }  // namespace
 
+int launch_canonical_edges(const DeviceGraph &g, uint32_t *uv, cudaStream_t s) {
+    if (g.n == 0) return BQ_OK;
+    count_launches(1);
+    canonical_edges_kernel<<<blocks_for((uint64_t)g.n * 32, kThreads), kThreads, 0, s>>>(g, uv);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
 int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k, const uint32_t *tau,
                 const uint32_t *nwalks, const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
                 cudaStream_t s) {

@@ -150,18 +150,6 @@ bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 // The literal SABA word (walk batches only) runs on the coupled path with
 // t = kSabaT and one group for the whole batch.
 int check_sampler(const bq_sampler *in, Sampler &out, bool allow_saba = false) {
@@ -782,6 +770,7 @@ int bq_sync(void *stream) {
     if (bits & kStatusOverflow) return fail(BQ_EOVERFLOW, "a uint32 counter wrapped or 2 N tau >= 2^32");
     if (bits & kStatusBadIndex) return fail(BQ_EINVAL, "a query had tau = 0 or nwalks = 0 (its estimate is NaN)");
     if (bits & kStatusTimeout) return fail(BQ_ETIMEOUT, "a bounded device wait gave up");
+    if (bits & kStatusRepeated) return fail(BQ_EINVAL, "an edge was queried twice in a vertex-centric estimate");
     return fail(BQ_ECUDA, "unknown device status bits 0x%x", bits);
 }
 

@@ -20,6 +20,7 @@ enum StatusBits : uint32_t {
     kStatusOverflow = 1u << 2,   // a uint32 counter wrapped / plan too large
     kStatusBadIndex = 1u << 3,   // (checked builds) index out of range
     kStatusTimeout = 1u << 4,    // a bounded wait gave up
+    kStatusRepeated = 1u << 5,   // an edge repeated among vertex-centric queries
 };
 
 constexpr uint32_t kNoHub = 0xffffffffu;
@@ -207,6 +208,21 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Makes `dev` the current device for a scope, then restores the previous one.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 // ---- error plumbing (api.cu)
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t err, const char *what);
@@ -307,6 +323,9 @@ struct PilotParams {
 int launch_aesc_moments(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
                         const uint32_t *tau, const uint32_t *nwalks, const Sampler &smp, uint64_t *moments,
                         const PilotParams *pilot, uint32_t *nwalks_out, uint32_t *status, cudaStream_t s);
+// Canonical edge list (edges ordered by lower endpoint, then higher) into
+// uv = device uint32[2m].
+int launch_canonical_edges(const DeviceGraph &g, uint32_t *uv, cudaStream_t s);
 int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
                      const uint32_t *tau, const uint32_t *nwalks, uint32_t push_max, uint32_t *depth_out,
                      uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s);

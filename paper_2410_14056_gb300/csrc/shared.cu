@@ -1,0 +1,441 @@
+// Vertex-centric AESC: the walk loop of TGT+ (Alg. 1) with the walks of a
+// vertex shared by every query edge at that vertex.
+//
+// Every endpoint x of a query edge runs N_x = max nwalks and tau_x = max tau
+// over the query edges at x (walk w < N_x keyed on stream kVertexStream | x).
+// A walk from x standing on x at step l counts a return, kept per (x, l) in a
+// histogram so that each edge weighs the returns by its own tau; a walk from x
+// standing on a query neighbour y of x at step l <= tau of {x, y} adds that
+// step's weight (2 before tau, 1 at tau) to the edge's cross counter.  The
+// neighbour test is one binary search of y in x's row, which every walk of a
+// task shares (L1-resident), and a per-CSR-position query index maps the hit
+// to its edge, so no query list is sorted.
+//
+// Work decomposition (GB300): a task is a bouquet of 32*W walks of one vertex
+// (Alg. 3 with B = 32*W); a persistent grid of warps pulls tasks through the
+// bucket index of the vertices' task prefix.  Returns are counted with a
+// ballot per step and lane; cross hits are combined across the warp with
+// match.any on the edge before one atomic per distinct edge.
+#include <math.h>
+
+#include "edges.cuh"
+#include "hash.cuh"
+#include "internal.h"
+
+namespace bq {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSharedW = 4;                                 // walks per lane
+constexpr uint64_t kVertexStream = 0x2000000000000000ull;  // edge streams stay below
+constexpr uint32_t kNoQuery = 0xffffffffu;
+
+struct SharedQuery {
+    uint32_t u, v;  // normalised endpoints, u < v
+    uint32_t tau, nwalks;
+    uint32_t valid;
+    uint32_t pad;
+};
+
+unsigned blocks_for(uint64_t items, uint64_t per_block) {
+    uint64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffull) b = 0x7fffffffull;
+    return (unsigned)b;
+}
+
+// first index in [lo, hi) whose entry is >= key
+__device__ __forceinline__ int64_t lower_bound_ids(const uint32_t *__restrict__ nbrs, int64_t lo, int64_t hi,
+                                                   uint32_t key) {
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(nbrs + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Validate the queries, take the per-vertex maxima of N and tau, and claim
+// the two CSR positions of each edge in the query index (a second claim of
+// the same position is a repeated edge).
+__global__ void shared_prepare_kernel(DeviceGraph g, const uint32_t *__restrict__ uv, uint64_t k,
+                                      const uint32_t *__restrict__ tau, const uint32_t *__restrict__ nwalks,
+                                      SharedQuery *__restrict__ qinfo, uint32_t *__restrict__ vn,
+                                      uint32_t *__restrict__ vt, uint32_t *__restrict__ qidx, uint32_t *status) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        SharedQuery qi;
+        const uint32_t a = uv[2 * q], b = uv[2 * q + 1];
+        qi.u = a < b ? a : b;
+        qi.v = a < b ? b : a;
+        qi.tau = tau[q];
+        qi.nwalks = nwalks[q];
+        qi.valid = 0;
+        qi.pad = 0;
+        uint32_t bits = 0;
+        if (a >= g.n || b >= g.n || a == b) {
+            bits = kStatusNoEdge;
+        } else {
+            const int64_t lu = g.offsets[qi.u], hu = g.offsets[qi.u + 1];
+            const int64_t lv = g.offsets[qi.v], hv = g.offsets[qi.v + 1];
+            const int64_t puv = lower_bound_ids(g.nbrs, lu, hu, qi.v);
+            const int64_t pvu = lower_bound_ids(g.nbrs, lv, hv, qi.u);
+            if (puv >= hu || g.nbrs[puv] != qi.v || pvu >= hv || g.nbrs[pvu] != qi.u) {
+                bits = kStatusNoEdge;
+            } else if (qi.tau == 0 || qi.nwalks == 0) {
+                bits = kStatusBadIndex;
+            } else if (atomicCAS(qidx + puv, kNoQuery, (uint32_t)q) != kNoQuery) {
+                bits = kStatusRepeated;
+            } else {
+                qidx[pvu] = (uint32_t)q;
+                qi.valid = 1;
+                atomicMax(vn + qi.u, qi.nwalks);
+                atomicMax(vn + qi.v, qi.nwalks);
+                atomicMax(vt + qi.u, qi.tau);
+                atomicMax(vt + qi.v, qi.tau);
+            }
+        }
+        if (bits) atomicOr(status, bits);
+        qinfo[q] = qi;
+    }
+}
+
+__global__ void vertex_tasks_kernel(uint64_t n, const uint32_t *__restrict__ vn, uint32_t bouquet,
+                                    uint32_t *__restrict__ tasks) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        tasks[x] = (vn[x] + bouquet - 1) / bouquet;
+}
+
+template <typename EL, int W, bool COUPLED>
+__global__ void __launch_bounds__(kThreads)
+shared_count_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
+                    const uint32_t *__restrict__ vn, const uint32_t *__restrict__ vt,
+                    const uint64_t *__restrict__ vbegin, const uint32_t *__restrict__ bucket, uint64_t n,
+                    const uint64_t *__restrict__ rbegin, const uint32_t *__restrict__ qidx,
+                    const SharedQuery *__restrict__ qinfo, uint64_t seed, Sampler smp,
+                    unsigned long long *__restrict__ next_task, uint32_t *__restrict__ ret,
+                    uint32_t *__restrict__ cross) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t total = vbegin[n];
+    const uint32_t shift = bucket_shift(total, n);
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(next_task, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        const uint32_t x = (uint32_t)task_edge(vbegin, bucket, n, total, shift, t);
+        const uint64_t k0 = (t - vbegin[x]) * 32ull * W;
+        const uint32_t nx = vn[x], tx = vt[x];
+        const uint64_t stream = kVertexStream | x;
+        const uint64_t rb = rbegin[x];
+        uint64_t st[W], gs[W];
+        bool act[W];
+        if (!COUPLED && (W % 2 == 0)) {
+#pragma unroll
+            for (int j = 0; j < W; j += 2) {
+                const uint64_t kk = k0 + (uint64_t)lane * W + j;
+                walk_key_pair(seed, stream, kk >> 1, st[j], st[j + 1]);
+                act[j] = kk < nx;
+                act[j + 1] = kk + 1 < nx;
+                gs[j] = gs[j + 1] = 0;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const uint64_t kk = COUPLED ? k0 + (uint64_t)j * 32 + lane : k0 + (uint64_t)lane * W + j;
+                st[j] = walk_key(seed, stream, kk);
+                gs[j] = COUPLED ? walk_key(seed, stream | kGroupBit, kk / smp.width) : 0;
+                act[j] = kk < nx;
+            }
+        }
+        uint64_t off0;
+        uint32_t deg0;
+        start_record(offsets, x, off0, deg0);
+        const int64_t row_lo = (int64_t)off0, row_hi = (int64_t)off0 + deg0;
+        uint64_t off[W];
+        uint32_t cur[W], deg[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            cur[j] = x;
+            off[j] = off0;
+            deg[j] = act[j] ? deg0 : 0u;  // inactive walks never move or hit
+        }
+        for (uint32_t l = 1; l <= tx; ++l) {
+            uint32_t returns = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                st[j] += kGolden;
+                if (COUPLED) gs[j] += kGolden;
+                uint32_t key = kNoQuery, w = 0;
+                if (deg[j]) {
+                    const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
+                    el.next(off[j] + kk, cur[j], off[j], deg[j]);
+                    if (cur[j] != x) {
+                        const int64_t p = lower_bound_ids(nbrs, row_lo, row_hi, cur[j]);
+                        if (p < row_hi && __ldg(nbrs + p) == cur[j]) {
+                            const uint32_t q = __ldg(qidx + p);
+                            if (q != kNoQuery) {
+                                const uint32_t tq = qinfo[q].tau;
+                                if (l <= tq) {
+                                    key = 2 * q + (x < cur[j] ? 0u : 1u);
+                                    w = l < tq ? 2u : 1u;
+                                }
+                            }
+                        }
+                    }
+                }
+                returns += __popc(__ballot_sync(0xffffffffu, deg[j] != 0 && cur[j] == x));
+                // lanes hitting the same edge side at this step share one atomic
+                const uint32_t peers = __match_any_sync(0xffffffffu, key);
+                if (key != kNoQuery && lane == (uint32_t)(__ffs(peers) - 1))
+                    atomicAdd(cross + key, w * (uint32_t)__popc(peers));
+            }
+            if (lane == 0 && returns) atomicAdd(ret + rb + (l - 1), returns);
+        }
+    }
+}
+
+// Counters and estimate per query: C_uu and C_vv from the return histograms
+// of u and v weighted by the edge's own tau, C_uv and C_vu from the cross
+// counters; est = s_e + ((C_uu/N_u - C_vu/N_v)/d_u + (C_vv/N_v - C_uv/N_u)/d_v)/2,
+// every operation rounded on its own (_rn intrinsics).
+__global__ void shared_finalize_kernel(const SharedQuery *__restrict__ qinfo, uint64_t k,
+                                       const int64_t *__restrict__ offsets, const uint32_t *__restrict__ vn,
+                                       const uint64_t *__restrict__ rbegin, const uint32_t *__restrict__ ret,
+                                       const uint32_t *__restrict__ cross, uint32_t *__restrict__ counts,
+                                       uint32_t *__restrict__ nused, double *__restrict__ sc, uint32_t *status) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const SharedQuery qi = qinfo[q];
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        if (!qi.valid) {
+            sc[q] = nan;
+            continue;
+        }
+        const uint32_t nu = vn[qi.u], nv = vn[qi.v];
+        if (2ull * (nu > nv ? nu : nv) * qi.tau >= (1ull << 32)) {
+            atomicOr(status, kStatusOverflow);
+            sc[q] = nan;
+            continue;
+        }
+        uint64_t cuu = 0, cvv = 0;
+        const uint32_t *ru = ret + rbegin[qi.u], *rv = ret + rbegin[qi.v];
+        for (uint32_t l = 1; l <= qi.tau; ++l) {
+            const uint32_t w = l < qi.tau ? 2u : 1u;
+            cuu += (uint64_t)w * ru[l - 1];
+            cvv += (uint64_t)w * rv[l - 1];
+        }
+        const uint32_t cuv = cross[2 * q], cvu = cross[2 * q + 1];
+        counts[4 * q + 0] = (uint32_t)cuu;
+        counts[4 * q + 1] = cuv;
+        counts[4 * q + 2] = cvu;
+        counts[4 * q + 3] = (uint32_t)cvv;
+        if (nused) {
+            nused[2 * q] = nu;
+            nused[2 * q + 1] = nv;
+        }
+        const double du = (double)(offsets[qi.u + 1] - offsets[qi.u]);
+        const double dv = (double)(offsets[qi.v + 1] - offsets[qi.v]);
+        const double s = __dadd_rn(__ddiv_rn(1.0, du), __ddiv_rn(1.0, dv));
+        const double fu = (double)nu, fv = (double)nv;
+        const double ruu = __ddiv_rn((double)cuu, fu), ruv = __ddiv_rn((double)cuv, fu);
+        const double rvu = __ddiv_rn((double)cvu, fv), rvv = __ddiv_rn((double)cvv, fv);
+        const double mean =
+            __ddiv_rn(__dadd_rn(__ddiv_rn(__dsub_rn(ruu, rvu), du), __ddiv_rn(__dsub_rn(rvv, ruv), dv)), 2.0);
+        sc[q] = __dadd_rn(s, mean);
+    }
+}
+
+template <typename EL, bool COUPLED>
+int launch_shared_count(EL el, const DeviceGraph &g, const uint32_t *vn, const uint32_t *vt, const uint64_t *vbegin,
+                        const uint32_t *bucket, const uint64_t *rbegin, const uint32_t *qidx,
+                        const SharedQuery *qinfo, uint64_t seed, const Sampler &smp,
+                        unsigned long long *next_task, uint32_t *ret, uint32_t *cross, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto kernel = shared_count_kernel<EL, kSharedW, COUPLED>;
+    BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, g.nbrs, vn, vt, vbegin, bucket, g.n, rbegin, qidx, qinfo,
+                                             seed, smp, next_task, ret, cross);
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+}  // namespace
+
+namespace {
+
+size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+}  // namespace
+
+// Asynchronous on s except for one wait, after the per-vertex plan, that
+// reads the length of the return histograms to size them.
+int launch_aesc_shared(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
+                       const uint32_t *tau, const uint32_t *nwalks, const Sampler &smp, uint32_t *counts,
+                       uint32_t *nused, double *sc, uint32_t *status, cudaStream_t s) {
+    if (k == 0) return BQ_OK;
+    const uint64_t n = g.n;
+    const uint32_t bouquet = 32u * (uint32_t)kSharedW;
+    // scratch: qinfo[k] | vn[n] vt[n] | tasks[n] | vbegin[n + 1] bucket | rbegin[n + 1] |
+    // qidx[nnz] | cross[2k] | next_task | (edges[2k] if all-edges)
+    const size_t b_qinfo = align16(sizeof(SharedQuery) * k);
+    const size_t b_vnt = align16(sizeof(uint32_t) * 2 * n);
+    const size_t b_tasks = align16(sizeof(uint32_t) * n);
+    const size_t b_vbegin = align16(sizeof(uint64_t) * (n + 1) + sizeof(uint32_t) * bucket_count(n));
+    const size_t b_rbegin = align16(sizeof(uint64_t) * (n + 1));
+    const size_t b_qidx = align16(sizeof(uint32_t) * g.nnz);
+    const size_t b_cross = align16(sizeof(uint32_t) * 2 * k);
+    const size_t b_edges = edges_uv ? 0 : align16(sizeof(uint32_t) * 2 * k);
+    const size_t bytes = b_qinfo + b_vnt + b_tasks + b_vbegin + b_rbegin + b_qidx + b_cross + 16 + b_edges;
+    char *buf = nullptr;
+    int rc = scratch_alloc((void **)&buf, bytes, s);
+    if (rc) return rc;
+    char *p = buf;
+    SharedQuery *qinfo = (SharedQuery *)p;
+    p += b_qinfo;
+    uint32_t *vn = (uint32_t *)p;
+    uint32_t *vt = vn + n;
+    p += b_vnt;
+    uint32_t *tasks = (uint32_t *)p;
+    p += b_tasks;
+    uint64_t *vbegin = (uint64_t *)p;
+    uint32_t *bucket = (uint32_t *)(vbegin + n + 1);
+    p += b_vbegin;
+    uint64_t *rbegin = (uint64_t *)p;
+    p += b_rbegin;
+    uint32_t *qidx = (uint32_t *)p;
+    p += b_qidx;
+    uint32_t *cross = (uint32_t *)p;
+    p += b_cross;
+    unsigned long long *next_task = (unsigned long long *)p;
+    p += 16;
+    uint32_t *all_uv = edges_uv ? nullptr : (uint32_t *)p;
+
+    cudaError_t e = cudaMemsetAsync(vn, 0, sizeof(uint32_t) * 2 * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(qidx, 0xff, sizeof(uint32_t) * g.nnz, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cross, 0, sizeof(uint32_t) * 2 * k, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next_task, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        scratch_free(buf, s);
+        return cuda_fail(e, "shared setup");
+    }
+    const uint32_t *uv = edges_uv;
+    uint64_t ret_len = 0;
+    {
+        ProfScope prof(kProfAescAux, s);
+        if (!uv) {
+            rc = launch_canonical_edges(g, all_uv, s);
+            uv = all_uv;
+        }
+        if (rc == BQ_OK) {
+            count_launches(2);
+            shared_prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, qinfo, vn, vt,
+                                                                               qidx, status);
+            vertex_tasks_kernel<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, vn, bouquet, tasks);
+            rc = scan_u32_to_u64(tasks, vbegin, n, s);
+        }
+        if (rc == BQ_OK) {
+            count_launches(1);
+            build_bucket_kernel<<<blocks_for(n, kThreads), kThreads, 0, s>>>(vbegin, n, bucket);
+            rc = scan_u32_to_u64(vt, rbegin, n, s);
+        }
+        if (rc == BQ_OK) {
+            e = cudaMemcpyAsync(&ret_len, rbegin + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "shared plan");
+        }
+    }
+    uint32_t *ret = nullptr;
+    if (rc == BQ_OK) rc = scratch_alloc((void **)&ret, sizeof(uint32_t) * (ret_len + 1), s);
+    if (rc == BQ_OK) {
+        e = cudaMemsetAsync(ret, 0, sizeof(uint32_t) * (ret_len + 1), s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "shared histogram");
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAesc, s);
+        count_launches(1);
+        rc = with_edges(g, [&](auto el) {
+            using EL = decltype(el);
+            return smp.kind == 1 ? launch_shared_count<EL, true>(el, g, vn, vt, vbegin, bucket, rbegin, qidx, qinfo,
+                                                                 seed, smp, next_task, ret, cross, s)
+                                 : launch_shared_count<EL, false>(el, g, vn, vt, vbegin, bucket, rbegin, qidx, qinfo,
+                                                                  seed, smp, next_task, ret, cross, s);
+        });
+    }
+    if (rc == BQ_OK) {
+        ProfScope prof(kProfAescAux, s);
+        count_launches(1);
+        shared_finalize_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(qinfo, k, g.offsets, vn, rbegin, ret,
+                                                                            cross, counts, nused, sc, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "shared_finalize_kernel");
+    }
+    if (ret) scratch_free(ret, s);
+    scratch_free(buf, s);
+    return rc;
+}
+
+}  // namespace bq
+
+extern "C" {
+
+int bq_aesc_estimate_shared(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
+                            const uint32_t *tau_dev, const uint32_t *nwalks_dev, const bq_sampler *sampler,
+                            uint32_t flags, uint32_t *counts_dev, uint32_t *nused_dev, double *sc_dev, void *stream) {
+    using namespace bq;
+    NvtxRange nvtx_range("bq_aesc_estimate_shared");
+    clear_error();
+    if (!g) return fail(BQ_EINVAL, "graph is NULL");
+    if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
+    if (k && (!tau_dev || !nwalks_dev || !counts_dev || !sc_dev))
+        return fail(BQ_EINVAL, "tau, nwalks, counts or sc is NULL");
+    if (!edges_uv_dev && (k != g->nnz / 2 || k != g->m_upper))
+        return fail(BQ_EINVAL, "all-edges estimate needs k = m = %llu (got %llu; %llu edges above the diagonal)",
+                    (unsigned long long)(g->nnz / 2), (unsigned long long)k, (unsigned long long)g->m_upper);
+    Sampler smp;
+    int rc = validate_sampler(sampler, smp);
+    if (rc) return rc;
+    if (k == 0) return BQ_OK;
+    DeviceGuard guard(g->device);
+    uint32_t *status = nullptr;
+    rc = status_word(g->device, &status);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(flags & BQ_HOST_IO))
+        return launch_aesc_shared(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, smp, counts_dev, nused_dev,
+                                  sc_dev, status, s);
+
+    const size_t eb = edges_uv_dev ? sizeof(uint32_t) * 2 * k : 0;
+    const size_t tb = sizeof(uint32_t) * k, cb = sizeof(uint32_t) * 4 * k, scb = sizeof(double) * k;
+    char *buf = nullptr;
+    rc = scratch_alloc((void **)&buf, scb + cb + 4 * tb + eb, s);
+    if (rc) return rc;
+    double *d_sc = (double *)buf;
+    uint32_t *d_counts = (uint32_t *)(buf + scb);
+    uint32_t *d_tau = (uint32_t *)(buf + scb + cb);
+    uint32_t *d_nw = (uint32_t *)(buf + scb + cb + tb);
+    uint32_t *d_nused = (uint32_t *)(buf + scb + cb + 2 * tb);
+    uint32_t *d_uv = edges_uv_dev ? (uint32_t *)(buf + scb + cb + 4 * tb) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(d_tau, tau_dev, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_nw, nwalks_dev, tb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && d_uv) e = cudaMemcpyAsync(d_uv, edges_uv_dev, eb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "host-io upload");
+    if (rc == BQ_OK)
+        rc = launch_aesc_shared(g->view(), seed, d_uv, k, d_tau, d_nw, smp, d_counts, d_nused, d_sc, status, s);
+    if (rc == BQ_OK) {
+        e = cudaMemcpyAsync(counts_dev, d_counts, cb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc_dev, d_sc, scb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && nused_dev)
+            e = cudaMemcpyAsync(nused_dev, d_nused, 2 * tb, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "host-io download");
+    }
+    scratch_free(buf, s);
+    if (rc == BQ_OK) rc = bq_sync(stream);
+    else cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // extern "C"
