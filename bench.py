@@ -437,11 +437,41 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
              "subset_1000_max_abs_diff_vs_16N_2tau": float(ldiff.max()),
              "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(ldiff ** 2))),
              "subset_1000_frac_within_half_eps": float(np.mean(ldiff <= eps / 2))}
+    # vertex-centric estimate: the walks of a vertex serve every edge at it
+    # (N_x, tau_x = maxima over the edges at x), the same plan
+    scounts = torch.empty(4 * tau.size, dtype=torch.int32, device="cuda")
+    snused = torch.empty(2 * tau.size, dtype=torch.int32, device="cuda")
+    bq.aesc_estimate_shared(graph, 5, None, dtau, dnw, counts=scounts, nused=snused, sc=sc)
+    bq.sync()
+    slat = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bq.aesc_estimate_shared(graph, 5, None, dtau, dnw, counts=scounts, nused=snused, sc=sc)
+        e1.record()
+        e1.synchronize()
+        slat.append(e0.elapsed_time(e1))
+    bq.sync()
+    sms = sum(slat) / len(slat)
+    sest = sc.cpu().numpy()
+    uv_all = all_edges(g)
+    vn = np.zeros(g.n, np.float64)
+    vt = np.zeros(g.n, np.float64)
+    for side in (0, 1):
+        np.maximum.at(vn, uv_all[:, side], nw.astype(np.float64))
+        np.maximum.at(vt, uv_all[:, side], tau.astype(np.float64))
+    sdiff = np.abs(sest[pick] - ref)
+    shared = {"edges_per_s": tau.size / (sms / 1e3), "ms_per_estimate": sms,
+              "walk_steps_per_call": float(np.sum(vn * vt)),
+              "foster_residual": abs(float(sest.sum()) - (g.n - 1)) / (g.n - 1),
+              "subset_1000_max_abs_diff_vs_16N_2tau": float(sdiff.max()),
+              "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(sdiff ** 2)))}
     graph.close()
-    cpu_line = aesc_cpu_baseline(g, 5, all_edges(g), tau, nw) if cpu else None
+    cpu_line = aesc_cpu_baseline(g, 5, uv_all, tau, nw) if cpu else None
     return {
         "push_phase": push,
         "pilot_plan": pilot,
+        "shared_walks": shared,
         "cpu_baseline": cpu_line,
         "workload": f"chung-lu n=4M d=10 gamma=2.1 LCC (n={g.n}, m={g.m}), all edges, eps={eps}, "
                     "scheduled plan (uncertified)",
