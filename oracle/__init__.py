@@ -96,7 +96,9 @@ def lib():
                 c.c_uint32, u32p, u64p]
             L.orc_aesc_push_counts.restype = c.c_int
             L.orc_aesc_push_finalize.argtypes = [
-                c.c_uint32, i64p, c.c_uint64, u32p, u32p, u32p, u32p, u64p, f64p]
+                c.c_uint32, i64p, u32p, c.c_uint64, u32p, u32p, u32p, u32p, u64p, f64p]
+            L.orc_push_vector.argtypes = [c.c_uint32, i64p, u32p, c.c_uint32, c.c_uint32, u64p]
+            L.orc_push_vector.restype = c.c_int
             L.orc_aesc_push_finalize.restype = c.c_int
             L.orc_trunc_bound.argtypes = [c.c_double, c.c_double, c.c_double, c.c_uint32]
             L.orc_trunc_bound.restype = c.c_double
@@ -338,10 +340,24 @@ def aesc_estimate(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndar
 PUSH_Q = 1 << 30  # fixed-point scale of the pushed values
 
 
+PUSH_MAX_DEPTH = 8       # deepest push
+PUSH_SUPPORT_MAX = 1024  # largest support per side at depths >= 2
+
+
+def push_vector(g, x: int, depth: int) -> np.ndarray:
+    """r^depth_x as a dense uint64[n] (fixed point, about Q p_depth(y -> x))."""
+    off, nb = _graph_arrays(g)
+    out = np.zeros(g.n, np.uint64)
+    rc = lib().orc_push_vector(g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), int(x), int(depth),
+                               _p(out, ctypes.c_uint64))
+    _check(rc, "push_vector")
+    return out
+
+
 def aesc_push_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
                      push_max: int = 1):
     """(depth uint32[k], acc uint64[4k]): push depth per edge and the
-    fixed-point accumulators A_uu, A_uv, A_vu, A_vv (Alg. 1, depth 0 or 1)."""
+    fixed-point accumulators A_uu, A_uv, A_vu, A_vv (Alg. 1, depth <= 8)."""
     off, nb = _graph_arrays(g)
     q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
     ta = np.ascontiguousarray(tau, dtype=np.uint32)
@@ -357,14 +373,15 @@ def aesc_push_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.n
 
 
 def aesc_push_finalize(g, uv, tau, nwalks, depth, acc) -> np.ndarray:
-    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    off, nb = _graph_arrays(g)
     q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
     ta = np.ascontiguousarray(tau, dtype=np.uint32)
     nw = np.ascontiguousarray(nwalks, dtype=np.uint32)
     dp = np.ascontiguousarray(depth, dtype=np.uint32)
     ac = np.ascontiguousarray(acc, dtype=np.uint64)
     sc = np.zeros(q.shape[0], np.float64)
-    rc = lib().orc_aesc_push_finalize(g.n, _p(off, ctypes.c_int64), q.shape[0], _p(q, ctypes.c_uint32),
+    rc = lib().orc_aesc_push_finalize(g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), q.shape[0],
+                                      _p(q, ctypes.c_uint32),
                                       _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
                                       _p(dp, ctypes.c_uint32), _p(ac, ctypes.c_uint64),
                                       _p(sc, ctypes.c_double))

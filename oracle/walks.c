@@ -700,70 +700,208 @@ int orc_aesc_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
 
 /* Alg. 1 splits each walk term at push depth tau~: the first tau~ levels of
  * p_l(., v_i) are pushed exactly, and walks of tau - tau~ steps carry the
- * rest, each position y adding p_tau~(y -> x) for target x.  Here tau~ is
- * 0 or 1, in fixed point with Q = 2^30:
- *   r_x(y) = Q * [y == x]                         (tau~ = 0)
- *   r_x(y) = floor(Q / d(y)) if y is a neighbour of x, else 0   (tau~ = 1)
- * (a walk from y stands on x one step later with probability 1/d(y) exactly
- * when y is adjacent to x).  tau~ = 1 is taken, as in TGT+'s while loop,
- * when the push volume d(u) + d(v) is below the 2 N walks it replaces, the
- * edge has tau >= 1 and push_max >= 1. */
+ * rest, each position y adding p_tau~(y -> x) for target x.  In fixed point
+ * with Q = 2^30 the pushed vectors of a source x are
+ *   r^0_x = Q e_x,
+ *   r^{j+1}_x(y) = sum over neighbours z of y of floor(r^j_x(z) / d(y))
+ * (a walk from y is on z one step later with probability 1/d(y); the floors
+ * keep every sum exact and order-free), so r^j_x(y) approximates
+ * Q p_j(y -> x) from below; r^1_x(y) = floor(Q / d(y)) on the neighbours of x.
+ * The push of level j - 1 touches the rows of its support: volume
+ * vol_j(x) = sum over j' < j of the degrees of supp r^j'_x (vol_1 = d(x)).
+ * As in TGT+'s while loop, the depth is the largest tau~ <= min(push_max,
+ * tau, 8) such that every level j <= tau~ has vol_j(u) + vol_j(v) < 2 N
+ * (the pushed volume stays below the 2 N walks it replaces) and, from level
+ * 2 on, supports of at most 1024 vertices per side. */
 #define ORC_PUSH_Q 1073741824u
+#define ORC_PUSH_MAX_DEPTH 8u
+#define ORC_PUSH_SUPPORT_MAX 1024u
 
-static uint32_t push_depth_of(const int64_t *offsets, uint32_t u, uint32_t v,
-                              uint32_t tau, uint32_t nwalks, uint32_t push_max)
+/* A sparse vector over the vertices: dense values and the list of nonzero
+ * entries (cleared through the list). */
+typedef struct {
+    uint64_t *val;
+    uint32_t *idx;
+    uint64_t cnt;
+} orc_svec;
+
+static int svec_init(orc_svec *s, uint32_t n)
 {
-    uint64_t vol = (uint64_t)(offsets[u + 1] - offsets[u]) + (uint64_t)(offsets[v + 1] - offsets[v]);
-    return (push_max >= 1 && tau >= 1 && vol < 2ull * nwalks) ? 1u : 0u;
+    s->val = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    s->idx = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    s->cnt = 0;
+    return s->val && s->idx;
 }
 
-static uint64_t push_value(const int64_t *offsets, const uint32_t *nbrs, uint32_t x,
-                           uint32_t y, uint32_t depth)
+static void svec_free(orc_svec *s)
 {
-    int64_t j;
-    if (depth == 0)
-        return y == x ? ORC_PUSH_Q : 0u;
-    for (j = offsets[x]; j < offsets[x + 1]; j++)
-        if (nbrs[j] == y)
-            return ORC_PUSH_Q / (uint32_t)(offsets[y + 1] - offsets[y]);
-    return 0u;
+    free(s->val);
+    free(s->idx);
+}
+
+static void svec_clear(orc_svec *s)
+{
+    uint64_t i;
+    for (i = 0; i < s->cnt; i++)
+        s->val[s->idx[i]] = 0;
+    s->cnt = 0;
+}
+
+static void svec_add(orc_svec *s, uint32_t y, uint64_t c)
+{
+    if (c == 0)
+        return;
+    if (s->val[y] == 0)
+        s->idx[s->cnt++] = y;
+    s->val[y] += c;
+}
+
+/* out = one push of in; returns the volume (sum of the degrees of supp in). */
+static uint64_t push_level(const int64_t *offsets, const uint32_t *nbrs, const orc_svec *in, orc_svec *out)
+{
+    uint64_t i, vol = 0;
+    svec_clear(out);
+    for (i = 0; i < in->cnt; i++) {
+        uint32_t z = in->idx[i];
+        int64_t j;
+        vol += (uint64_t)(offsets[z + 1] - offsets[z]);
+        for (j = offsets[z]; j < offsets[z + 1]; j++) {
+            uint32_t y = nbrs[j];
+            svec_add(out, y, in->val[z] / (uint64_t)(offsets[y + 1] - offsets[y]));
+        }
+    }
+    return vol;
+}
+
+typedef struct {
+    uint32_t levels;                        /* levels computed: 0..levels */
+    uint64_t vol[ORC_PUSH_MAX_DEPTH + 1];   /* vol_j */
+    uint64_t supp[ORC_PUSH_MAX_DEPTH + 1];  /* |supp r^j| */
+    uint64_t at_u[ORC_PUSH_MAX_DEPTH + 1];  /* r^j(u) */
+    uint64_t at_v[ORC_PUSH_MAX_DEPTH + 1];  /* r^j(v) */
+} orc_push_stats;
+
+/* Levels 0..jmax of source x; with `limits`, stopping after a level that no
+ * depth can include (its volume alone reaches two_n, or a level >= 2 with
+ * too large a support).  r^levels_x is left in *a. */
+static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x, uint32_t u, uint32_t v,
+                        uint32_t jmax, int limits, uint64_t two_n, orc_svec *a, orc_svec *b,
+                        orc_push_stats *st)
+{
+    uint32_t j;
+    svec_clear(a);
+    svec_add(a, x, ORC_PUSH_Q);
+    st->levels = 0;
+    st->vol[0] = 0;
+    st->supp[0] = 1;
+    st->at_u[0] = a->val[u];
+    st->at_v[0] = a->val[v];
+    for (j = 1; j <= jmax; j++) {
+        orc_svec t;
+        uint64_t vol = push_level(offsets, nbrs, a, b);
+        t = *a;
+        *a = *b;
+        *b = t;
+        st->levels = j;
+        st->vol[j] = st->vol[j - 1] + vol;
+        st->supp[j] = a->cnt;
+        st->at_u[j] = a->val[u];
+        st->at_v[j] = a->val[v];
+        if (limits && (st->vol[j] >= two_n || (j >= 2 && st->supp[j] > ORC_PUSH_SUPPORT_MAX)))
+            break;
+    }
+}
+
+/* Depth of query {u, v} from both sources' level statistics. */
+static uint32_t push_depth_from(const orc_push_stats *su, const orc_push_stats *sv, uint64_t two_n)
+{
+    uint32_t j, dep = 0;
+    uint32_t top = su->levels < sv->levels ? su->levels : sv->levels;
+    for (j = 1; j <= top; j++) {
+        if (su->vol[j] + sv->vol[j] >= two_n)
+            break;
+        if (j >= 2 && (su->supp[j] > ORC_PUSH_SUPPORT_MAX || sv->supp[j] > ORC_PUSH_SUPPORT_MAX))
+            break;
+        dep = j;
+    }
+    return dep;
+}
+
+static uint32_t depth_cap(uint32_t tau, uint32_t push_max)
+{
+    uint32_t c = push_max < tau ? push_max : tau;
+    return c < ORC_PUSH_MAX_DEPTH ? c : ORC_PUSH_MAX_DEPTH;
+}
+
+/* The pushed vector r^depth_x as a dense array out[n] (test access). */
+int orc_push_vector(uint32_t n, const int64_t *offsets, const uint32_t *nbrs, uint32_t x,
+                    uint32_t depth, uint64_t *out)
+{
+    orc_svec a, b;
+    orc_push_stats st;
+    uint32_t y;
+    if (x >= n || depth > ORC_PUSH_MAX_DEPTH)
+        return ORC_EINVAL;
+    if (!svec_init(&a, n) || !svec_init(&b, n)) {
+        svec_free(&a);
+        svec_free(&b);
+        return ORC_EINVAL;
+    }
+    push_levels(offsets, nbrs, x, x, x, depth, 0, 0, &a, &b, &st);
+    for (y = 0; y < n; y++)
+        out[y] = st.levels == depth ? a.val[y] : 0;
+    svec_free(&a);
+    svec_free(&b);
+    return st.levels == depth ? ORC_OK : ORC_EINVAL;
 }
 
 /* Accumulators for query edge q = {u, v}, u < v: the walks of the plain
  * counters (streams 2e + side, walk index w < nwalks[q]) but tau[q] - tau~
  * steps long; at step l the walk adds w * r_u(cur) and w * r_v(cur) with
- * w = 2 if l + tau~ < tau else 1:
+ * r = r^tau~ and w = 2 if l + tau~ < tau else 1:
  *   acc[4q + 0..3] = A_uu, A_uv (walks from u), A_vu, A_vv (walks from v).
- * depth[q] (may be NULL) receives tau~. */
+ * depth[q] (may be NULL) receives tau~.  push_max <= 8. */
 int orc_aesc_push_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
                          uint64_t seed, uint64_t k, const uint32_t *uv,
                          const uint32_t *tau, const uint32_t *nwalks,
                          uint32_t push_max, uint32_t *depth, uint64_t *acc)
 {
     orc_sampler smp;
+    orc_svec au, bu, av, bv;
     uint64_t *ub;
     uint64_t q;
+    int rc = ORC_OK;
     smp.kind = 0;
     smp.t = 0;
     smp.width = 1;
-    ub = count_upper(n, offsets, nbrs);
-    if (!ub)
+    if (push_max > ORC_PUSH_MAX_DEPTH)
         return ORC_EINVAL;
-    for (q = 0; q < k; q++) {
+    ub = count_upper(n, offsets, nbrs);
+    if (!ub || !svec_init(&au, n) || !svec_init(&bu, n) || !svec_init(&av, n) || !svec_init(&bv, n)) {
+        free(ub);
+        return ORC_EINVAL;
+    }
+    for (q = 0; q < k && rc == ORC_OK; q++) {
         uint32_t a = uv[2 * q], b = uv[2 * q + 1];
         uint32_t u = a < b ? a : b;
         uint32_t v = a < b ? b : a;
         uint64_t e, c[4] = {0, 0, 0, 0};
         uint32_t side, dep;
+        orc_push_stats su, sv;
         if (edge_id_of(n, offsets, nbrs, ub, a, b, &e) != ORC_OK) {
-            free(ub);
-            return ORC_ENOEDGE;
+            rc = ORC_ENOEDGE;
+            break;
         }
         if (tau[q] == 0 || nwalks[q] == 0 || 2ull * nwalks[q] * tau[q] >= 4294967296ull) {
-            free(ub);
-            return ORC_EOVERFLOW;
+            rc = ORC_EOVERFLOW;
+            break;
         }
-        dep = push_depth_of(offsets, u, v, tau[q], nwalks[q], push_max);
+        push_levels(offsets, nbrs, u, u, v, depth_cap(tau[q], push_max), 1, 2ull * nwalks[q], &au, &bu, &su);
+        push_levels(offsets, nbrs, v, u, v, depth_cap(tau[q], push_max), 1, 2ull * nwalks[q], &av, &bv, &sv);
+        dep = push_depth_from(&su, &sv, 2ull * nwalks[q]);
+        /* the vectors at the chosen depth */
+        push_levels(offsets, nbrs, u, u, v, dep, 0, 0, &au, &bu, &su);
+        push_levels(offsets, nbrs, v, u, v, dep, 0, 0, &av, &bv, &sv);
         if (depth)
             depth[q] = dep;
         for (side = 0; side < 2; side++) {
@@ -778,8 +916,8 @@ int orc_aesc_push_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbr
                     uint32_t d = (uint32_t)(offsets[cur + 1] - lo);
                     uint64_t weight = l + dep < tau[q] ? 2u : 1u;
                     cur = nbrs[lo + orc_choose(sample_word(&smp, kw, 0, l, cur), d)];
-                    c[2 * side + 0] += weight * push_value(offsets, nbrs, u, cur, dep);
-                    c[2 * side + 1] += weight * push_value(offsets, nbrs, v, cur, dep);
+                    c[2 * side + 0] += weight * au.val[cur];
+                    c[2 * side + 1] += weight * av.val[cur];
                 }
             }
         }
@@ -789,41 +927,54 @@ int orc_aesc_push_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbr
         acc[4 * q + 3] = c[3];
     }
     free(ub);
-    return ORC_OK;
+    svec_free(&au);
+    svec_free(&bu);
+    svec_free(&av);
+    svec_free(&bv);
+    return rc;
 }
 
 /* Estimate of query edge q from its accumulators:
  *   g(u, v) = (X_u + (A_uu - A_vu) / N) / (2 Q d_u),
- *   X_u = 2Q                                 (tau~ = 0: the l = 0 term),
- *   X_u = 2Q - w_1 floor(Q / d_v)            (tau~ = 1: the l = 0 term and
- *         the l = 1 term of the walks' fixed start, r_u(u) = 0, r_u(v) = Q/d_v)
- * with w_1 = 2 if tau > 1 else 1; g(v, u) likewise; SC = g(u, v) + g(v, u).
- * Each operation rounds once, in this order. */
-int orc_aesc_push_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
+ *   X_u = sum over l = 0..tau~ of w_l (r^l_u(u) - r^l_u(v)),
+ * the series' terms below the push depth and the walks' fixed start, with
+ * w_l = 2 if l < tau else 1 (tau~ = 0: X_u = 2Q; tau~ = 1: X_u = 2Q -
+ * w_1 floor(Q / d_v)); g(v, u) likewise with X_v = sum w_l (r^l_v(v) -
+ * r^l_v(u)); SC = g(u, v) + g(v, u).  Each FP64 operation rounds once, in
+ * this order. */
+int orc_aesc_push_finalize(uint32_t n, const int64_t *offsets, const uint32_t *nbrs, uint64_t k,
                            const uint32_t *uv, const uint32_t *tau, const uint32_t *nwalks,
                            const uint32_t *depth, const uint64_t *acc, double *sc)
 {
+    orc_svec a, b;
     uint64_t q;
+    int rc = ORC_OK;
+    if (!svec_init(&a, n) || !svec_init(&b, n)) {
+        svec_free(&a);
+        svec_free(&b);
+        return ORC_EINVAL;
+    }
     for (q = 0; q < k; q++) {
-        uint32_t a = uv[2 * q], b = uv[2 * q + 1];
-        uint32_t u = a < b ? a : b;
-        uint32_t v = a < b ? b : a;
-        uint32_t du_i, dv_i;
-        int64_t xu, xv;
+        uint32_t x = uv[2 * q], y = uv[2 * q + 1];
+        uint32_t u = x < y ? x : y;
+        uint32_t v = x < y ? y : x;
+        uint32_t l;
+        int64_t xu = 0, xv = 0;
         double du, dv, nw, gu, gv;
-        if (u >= n || v >= n)
-            return ORC_EINVAL;
-        du_i = (uint32_t)(offsets[u + 1] - offsets[u]);
-        dv_i = (uint32_t)(offsets[v + 1] - offsets[v]);
-        xu = 2 * (int64_t)ORC_PUSH_Q;
-        xv = 2 * (int64_t)ORC_PUSH_Q;
-        if (depth[q] == 1) {
-            int64_t w1 = tau[q] > 1 ? 2 : 1;
-            xu -= w1 * (int64_t)(ORC_PUSH_Q / dv_i);
-            xv -= w1 * (int64_t)(ORC_PUSH_Q / du_i);
+        orc_push_stats su, sv;
+        if (u >= n || v >= n || depth[q] > ORC_PUSH_MAX_DEPTH || depth[q] > tau[q]) {
+            rc = ORC_EINVAL;
+            break;
         }
-        du = (double)du_i;
-        dv = (double)dv_i;
+        push_levels(offsets, nbrs, u, u, v, depth[q], 0, 0, &a, &b, &su);
+        push_levels(offsets, nbrs, v, u, v, depth[q], 0, 0, &a, &b, &sv);
+        for (l = 0; l <= depth[q]; l++) {
+            int64_t w = l < tau[q] ? 2 : 1;
+            xu += w * ((int64_t)su.at_u[l] - (int64_t)su.at_v[l]);
+            xv += w * ((int64_t)sv.at_v[l] - (int64_t)sv.at_u[l]);
+        }
+        du = (double)(offsets[u + 1] - offsets[u]);
+        dv = (double)(offsets[v + 1] - offsets[v]);
         nw = (double)nwalks[q];
         gu = ((double)xu + (double)(int64_t)(acc[4 * q + 0] - acc[4 * q + 2]) / nw) /
              (2.0 * (double)ORC_PUSH_Q * du);
@@ -831,7 +982,9 @@ int orc_aesc_push_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
              (2.0 * (double)ORC_PUSH_Q * dv);
         sc[q] = gu + gv;
     }
-    return ORC_OK;
+    svec_free(&a);
+    svec_free(&b);
+    return rc;
 }
 
 

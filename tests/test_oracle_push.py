@@ -130,3 +130,163 @@ def test_eps_contract_with_certified_plan(g, eps):
     _, _, sc = oracle.aesc_push_estimate(g, 11, uv, tau, nw)
     want = exact.sc_pinv(g, uv)
     assert np.max(np.abs(sc - want)) <= eps
+
+
+# ------------------------------------------------------------ push depths >= 2
+
+def star_of_paths():
+    """An irregular graph (degrees 1 to 4) whose walk laws are not symmetric:
+    a hub with four arms of lengths 1..4 and a chord."""
+    from workloads import csr_from_edges
+    u, v = [], []
+    nxt = 1
+    for length in range(1, 5):
+        prev = 0
+        for _ in range(length):
+            u.append(prev)
+            v.append(nxt)
+            prev = nxt
+            nxt += 1
+    u.append(2)
+    v.append(4)
+    return csr_from_edges(nxt, np.array(u), np.array(v), name="star_of_paths")
+
+
+@pytest.mark.parametrize("g", [diamond(), complete(6), cycle(7), prufer_tree(9, 4), gnp_connected(12, 0.4, 5),
+                               star_of_paths()], ids=lambda g: g.name)
+def test_push_vectors_bound_walk_laws(g):
+    """r^j_x(y) lies in [Q p_j(y -> x) - j d_max, Q p_j(y -> x)]: each level
+    loses less than one unit per neighbour to the floors.  (A recurrence run
+    in the other direction, p_j(x -> y), fails on irregular graphs.)"""
+    P = exact.transition(g)
+    dmax = int(g.degrees.max())
+    Pj = np.eye(g.n)
+    for j in range(0, 6):
+        for x in range(g.n):
+            r = oracle.push_vector(g, x, j).astype(np.float64)
+            want = Q * Pj[:, x]
+            assert np.all(r <= want + 1e-6) and np.all(r >= want - j * dmax - 1e-6), (x, j)
+        Pj = Pj @ P
+    # depths 0 and 1 are the closed forms
+    for x in range(g.n):
+        assert np.array_equal(oracle.push_vector(g, x, 0), push_vector(g, x, 0).astype(np.uint64))
+        assert np.array_equal(oracle.push_vector(g, x, 1), push_vector(g, x, 1).astype(np.uint64))
+
+
+def expected_estimate_deep(g, u, v, tau, depth):
+    """E[SC estimate] at any push depth: exact walk laws of the tau - depth
+    step walks, the oracle's pushed vectors, and X = sum over l <= depth of
+    w_l (r^l_u(u) - r^l_u(v))."""
+    u, v = min(u, v), max(u, v)
+    d = g.degrees.astype(np.float64)
+    P = exact.transition(g)
+    w = lambda l: 2.0 if l < tau else 1.0
+    ru = oracle.push_vector(g, u, depth).astype(np.float64)
+    rv = oracle.push_vector(g, v, depth).astype(np.float64)
+    xu = sum(w(l) * (float(oracle.push_vector(g, u, l)[u]) - float(oracle.push_vector(g, u, l)[v]))
+             for l in range(depth + 1))
+    xv = sum(w(l) * (float(oracle.push_vector(g, v, l)[v]) - float(oracle.push_vector(g, v, l)[u]))
+             for l in range(depth + 1))
+    E = {"uu": 0.0, "uv": 0.0, "vu": 0.0, "vv": 0.0}
+    lu, lv = np.eye(g.n)[u], np.eye(g.n)[v]
+    for l in range(1, tau - depth + 1):
+        lu, lv = lu @ P, lv @ P
+        E["uu"] += w(l + depth) * lu @ ru
+        E["uv"] += w(l + depth) * lu @ rv
+        E["vu"] += w(l + depth) * lv @ ru
+        E["vv"] += w(l + depth) * lv @ rv
+    return (xu + E["uu"] - E["vu"]) / (2.0 * Q * d[u]) + (xv + E["vv"] - E["uv"]) / (2.0 * Q * d[v])
+
+
+@pytest.mark.parametrize("g", [diamond(), complete(6), cycle(8), prufer_tree(9, 4), gnp_connected(12, 0.4, 5),
+                               star_of_paths()], ids=lambda g: g.name)
+@pytest.mark.parametrize("depth", [2, 3, 5])
+def test_deep_expectation_is_truncated_series(g, depth):
+    """At every depth the estimator's expectation is the half-weighted series
+    (up to the floors' loss, below 1e-6 here)."""
+    for u, v in all_edges(g).tolist()[:5]:
+        for tau in range(depth, depth + 4):
+            want = exact.truncated_series(g, u, v, tau)
+            assert abs(expected_estimate_deep(g, u, v, tau, depth) - want) < 1e-6, (u, v, tau)
+
+
+def test_deep_estimate_without_walks_is_exact():
+    """tau = depth: no walk is left and the estimate is X alone, equal to the
+    expectation computed from the pushed vectors."""
+    g = gnp_connected(12, 0.4, 5)
+    uv = all_edges(g)
+    for t in (2, 3):
+        tau = np.full(uv.shape[0], t, np.uint32)
+        nw = np.full(uv.shape[0], 60000, np.uint32)  # volume far below 2N: full depth
+        depth, acc, sc = oracle.aesc_push_estimate(g, 1, uv, tau, nw, push_max=t)
+        assert np.all(depth == t) and not acc.any()
+        for (u, v), s in zip(uv.tolist(), sc):
+            assert abs(s - expected_estimate_deep(g, u, v, t, t)) < 1e-12
+            assert abs(s - exact.truncated_series(g, u, v, t)) < 1e-6
+
+
+def support_and_volume(g, x, j):
+    supp = [np.count_nonzero(oracle.push_vector(g, x, i)) for i in range(j + 1)]
+    vol = [0]
+    for i in range(1, j + 1):
+        r = oracle.push_vector(g, x, i - 1)
+        vol.append(vol[-1] + int(g.degrees[r > 0].sum()))
+    return supp, vol
+
+
+def test_depth_rule_general():
+    g = er_with_path(80, 300, 2)
+    uv = all_edges(g)[:60]
+    rng = np.random.default_rng(3)
+    tau = rng.integers(1, 8, uv.shape[0]).astype(np.uint32)
+    nw = rng.integers(1, 400, uv.shape[0]).astype(np.uint32)
+    for push_max in (2, 4, 8):
+        depth, _ = oracle.aesc_push_counts(g, 1, uv, tau, nw, push_max=push_max)
+        for q, (a, b) in enumerate(uv.tolist()):
+            top = min(push_max, int(tau[q]), 8)
+            su, vu = support_and_volume(g, a, top)
+            sv, vv = support_and_volume(g, b, top)
+            want = 0
+            for j in range(1, top + 1):
+                if vu[j] + vv[j] >= 2 * int(nw[q]):
+                    break
+                if j >= 2 and (su[j] > oracle.PUSH_SUPPORT_MAX or sv[j] > oracle.PUSH_SUPPORT_MAX):
+                    break
+                want = j
+            assert depth[q] == want, (q, push_max)
+        if push_max >= 4:
+            assert np.any(depth >= 2) and np.any(depth <= 1)
+
+
+def test_deep_monte_carlo_mean_and_spread():
+    g = gnp_connected(14, 0.45, 7)
+    uv = all_edges(g)[:4]
+    tau = np.full(uv.shape[0], 5, np.uint32)
+    nw = np.full(uv.shape[0], 400, np.uint32)
+    runs = {pm: np.array([oracle.aesc_push_estimate(g, s, uv, tau, nw, push_max=pm)[2] for s in range(40)])
+            for pm in (1, 3)}
+    dep = oracle.aesc_push_counts(g, 0, uv, tau, nw, push_max=3)[0]
+    assert np.all(dep == 3)
+    for i, (u, v) in enumerate(uv.tolist()):
+        e = expected_estimate_deep(g, u, v, 5, 3)
+        x = runs[3][:, i]
+        assert abs(x.mean() - e) < 5 * x.std() / np.sqrt(40) + 1e-9
+    assert runs[3].std(axis=0).mean() < runs[1].std(axis=0).mean()
+
+
+@pytest.mark.parametrize("g,eps", [(complete(8), 0.1), (cycle(10), 0.1), (diamond(), 0.1),
+                                   (gnp_connected(10, 0.5, 3), 0.1)], ids=lambda x: getattr(x, "name", str(x)))
+def test_deep_eps_contract_with_certified_plan(g, eps):
+    uv = all_edges(g)
+    _, l2, lneg = exact.spectrum(g)
+    tau, nw = oracle.plan_certified(g, uv, eps, 0.01, l2, lneg)
+    depth, _, sc = oracle.aesc_push_estimate(g, 11, uv, tau, nw, push_max=8)
+    assert np.max(np.abs(sc - exact.sc_pinv(g, uv))) <= eps
+
+
+def test_push_max_range():
+    g = cycle(6)
+    uv = all_edges(g)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.aesc_push_counts(g, 1, uv, np.full(6, 3, np.uint32), np.full(6, 9, np.uint32), push_max=9)
+    assert ei.value.code == oracle.EINVAL
