@@ -341,7 +341,7 @@ PUSH_Q = 1 << 30  # fixed-point scale of the pushed values
 
 
 PUSH_MAX_DEPTH = 8       # deepest push
-PUSH_SUPPORT_MAX = 1024  # largest support per side at depths >= 2
+PUSH_SUPPORT_MAX = 512   # largest support per side and level at depths >= 2
 
 
 def push_vector(g, x: int, depth: int) -> np.ndarray:

@@ -711,11 +711,12 @@ int orc_aesc_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
  * vol_j(x) = sum over j' < j of the degrees of supp r^j'_x (vol_1 = d(x)).
  * As in TGT+'s while loop, the depth is the largest tau~ <= min(push_max,
  * tau, 8) such that every level j <= tau~ has vol_j(u) + vol_j(v) < 2 N
- * (the pushed volume stays below the 2 N walks it replaces) and, from level
- * 2 on, supports of at most 1024 vertices per side. */
+ * (the pushed volume stays below the 2 N walks it replaces) and, for
+ * tau~ >= 2, every level 1..tau~ has a support of at most 512 vertices per
+ * side. */
 #define ORC_PUSH_Q 1073741824u
 #define ORC_PUSH_MAX_DEPTH 8u
-#define ORC_PUSH_SUPPORT_MAX 1024u
+#define ORC_PUSH_SUPPORT_MAX 512u
 
 /* A sparse vector over the vertices: dense values and the list of nonzero
  * entries (cleared through the list). */
@@ -781,9 +782,9 @@ typedef struct {
     uint64_t at_v[ORC_PUSH_MAX_DEPTH + 1];  /* r^j(v) */
 } orc_push_stats;
 
-/* Levels 0..jmax of source x; with `limits`, stopping after a level that no
- * depth can include (its volume alone reaches two_n, or a level >= 2 with
- * too large a support).  r^levels_x is left in *a. */
+/* Levels 0..jmax of source x; with `limits`, stopping after a level beyond
+ * which no deeper level can be taken (its volume alone reaches two_n, or
+ * its support is above the cap).  r^levels_x is left in *a. */
 static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x, uint32_t u, uint32_t v,
                         uint32_t jmax, int limits, uint64_t two_n, orc_svec *a, orc_svec *b,
                         orc_push_stats *st)
@@ -807,7 +808,7 @@ static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x
         st->supp[j] = a->cnt;
         st->at_u[j] = a->val[u];
         st->at_v[j] = a->val[v];
-        if (limits && (st->vol[j] >= two_n || (j >= 2 && st->supp[j] > ORC_PUSH_SUPPORT_MAX)))
+        if (limits && (st->vol[j] >= two_n || st->supp[j] > ORC_PUSH_SUPPORT_MAX))
             break;
     }
 }

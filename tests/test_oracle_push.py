@@ -250,7 +250,7 @@ def test_depth_rule_general():
             for j in range(1, top + 1):
                 if vu[j] + vv[j] >= 2 * int(nw[q]):
                     break
-                if j >= 2 and (su[j] > oracle.PUSH_SUPPORT_MAX or sv[j] > oracle.PUSH_SUPPORT_MAX):
+                if j >= 2 and max(su[1:j + 1] + sv[1:j + 1]) > oracle.PUSH_SUPPORT_MAX:
                     break
                 want = j
             assert depth[q] == want, (q, push_max)
@@ -290,3 +290,40 @@ def test_push_max_range():
     with pytest.raises(oracle.OracleError) as ei:
         oracle.aesc_push_counts(g, 1, uv, np.full(6, 3, np.uint32), np.full(6, 9, np.uint32), push_max=9)
     assert ei.value.code == oracle.EINVAL
+
+
+def test_support_cap_limits_depth():
+    """Depths >= 2 need every level's support within the cap: a star with 600
+    leaves stops at depth 1 (level 1 holds the 600 leaves); a two-level tree
+    with 30 x 30 grandchildren stops at depth 2 only where level 2 fits."""
+    from workloads import csr_from_edges
+    star = csr_from_edges(601, np.zeros(600, np.int64), np.arange(1, 601), name="star600")
+    uv = all_edges(star)[:5]
+    big = np.full(uv.shape[0], 100000, np.uint32)
+    depth, _ = oracle.aesc_push_counts(star, 1, uv, np.full(uv.shape[0], 4, np.uint32), big, push_max=4)
+    assert np.all(depth == 1)
+    # root 0 -> 30 children -> 30 grandchildren each
+    u, v = [], []
+    nxt = 31
+    for c in range(1, 31):
+        u.append(0)
+        v.append(c)
+        for _ in range(30):
+            u.append(c)
+            v.append(nxt)
+            nxt += 1
+    tree = csr_from_edges(nxt, np.array(u), np.array(v), name="tree30x30")
+    assert np.count_nonzero(oracle.push_vector(tree, 0, 2)) > oracle.PUSH_SUPPORT_MAX or \
+        np.count_nonzero(oracle.push_vector(tree, 1, 2)) > oracle.PUSH_SUPPORT_MAX
+    q = np.array([[0, 1], [1, 31]], np.uint32)
+    depth, _ = oracle.aesc_push_counts(tree, 1, q, np.full(2, 4, np.uint32), np.full(2, 100000, np.uint32),
+                                       push_max=4)
+    for (a, b), dep in zip(q.tolist(), depth.tolist()):
+        s = [max(np.count_nonzero(oracle.push_vector(tree, a, j)), np.count_nonzero(oracle.push_vector(tree, b, j)))
+             for j in range(5)]
+        want = 1
+        for j in range(2, 5):
+            if max(s[1:j + 1]) > oracle.PUSH_SUPPORT_MAX:
+                break
+            want = j
+        assert dep == want and dep < 4
