@@ -479,6 +479,283 @@ __device__ __forceinline__ uint32_t push_set_flags(const uint32_t *keys, const u
     return 0u;
 }
 
+// ---- push depths >= 2: pushed vectors r^j_x (r^0 = Q e_x, r^{j+1}(y) = sum
+// over neighbours z of y of floor(r^j(z) / d_y)), built per query edge by one
+// warp in two shared-memory hash tables, kept as sorted (vertex, value)
+// arrays for the walks' lookups.
+constexpr uint32_t kPushMaxDepth = 8;
+constexpr uint32_t kPushSupportMax = 512;  // support cap per side and level at depths >= 2
+constexpr uint32_t kDeepSlots = 1024;      // hash slots per table (load <= 1/2 up to the cap)
+constexpr int kDeepWarps = 8;              // warps per block of the build kernels
+constexpr uint32_t kDeepEmpty = 0xffffffffu;
+
+struct DeepInfo {
+    uint64_t off;     // r_u's sorted table at tables[off], r_v's at tables[off + su]
+    uint32_t su, sv;  // support sizes at the chosen depth
+    int64_t xu, xv;   // sum over l <= depth of w_l (r^l_u(u) - r^l_u(v)), and for v
+};
+
+struct DeepTable {
+    uint32_t keys[kDeepSlots];
+    uint32_t vals[kDeepSlots];
+    uint32_t count;  // distinct keys
+    uint32_t over;   // count passed the cap (or the table filled)
+};
+
+struct DeepStats {
+    uint64_t vol[2][kPushMaxDepth + 1];
+    uint32_t supp[2][kPushMaxDepth + 1];
+    uint32_t at_u[2][kPushMaxDepth + 1];
+    uint32_t at_v[2][kPushMaxDepth + 1];
+    uint32_t levels[2];
+};
+
+struct DeepWarp {
+    DeepTable t[2];
+    DeepStats st;
+};
+
+__device__ __forceinline__ uint32_t deep_hash(uint32_t y) { return (y * 0x9E3779B1u) >> 22; }  // 10 bits
+
+__device__ void deep_clear(DeepTable *t, uint32_t lane) {
+    for (uint32_t i = lane; i < kDeepSlots; i += 32) {
+        t->keys[i] = kDeepEmpty;
+        t->vals[i] = 0u;
+    }
+    if (lane == 0) {
+        t->count = 0u;
+        t->over = 0u;
+    }
+    __syncwarp();
+}
+
+__device__ void deep_add(DeepTable *t, uint32_t y, uint32_t c) {
+    if (c == 0u) return;
+    uint32_t h = deep_hash(y);
+    for (uint32_t probe = 0; probe < kDeepSlots; ++probe) {
+        const uint32_t prev = atomicCAS(t->keys + h, kDeepEmpty, y);
+        if (prev == kDeepEmpty) {
+            if (atomicAdd(&t->count, 1u) >= kPushSupportMax) t->over = 1u;
+            atomicAdd(t->vals + h, c);
+            return;
+        }
+        if (prev == y) {
+            atomicAdd(t->vals + h, c);
+            return;
+        }
+        h = (h + 1) & (kDeepSlots - 1);
+    }
+    t->over = 1u;
+}
+
+__device__ uint32_t deep_get(const DeepTable *t, uint32_t y) {
+    uint32_t h = deep_hash(y);
+    for (uint32_t probe = 0; probe < kDeepSlots; ++probe) {
+        const uint32_t key = t->keys[h];
+        if (key == y) return t->vals[h];
+        if (key == kDeepEmpty) return 0u;
+        h = (h + 1) & (kDeepSlots - 1);
+    }
+    return 0u;
+}
+
+// out = one push of in; returns the volume (sum of the degrees of supp in),
+// the same in every lane.  Stops adding once out passed the cap (that level
+// is then refused whatever else it would hold).
+__device__ uint64_t deep_push(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
+                              const DeepTable *in, DeepTable *out, uint32_t lane) {
+    deep_clear(out, lane);
+    uint64_t vol = 0;
+    for (uint32_t i = lane; i < kDeepSlots; i += 32) {
+        const uint32_t z = in->keys[i];
+        if (z == kDeepEmpty) continue;
+        const uint32_t r = in->vals[i];
+        const int64_t lo = __ldg(offsets + z), hi = __ldg(offsets + z + 1);
+        vol += (uint64_t)(hi - lo);
+        for (int64_t j = lo; j < hi; ++j) {
+            if (*(volatile uint32_t *)&out->over) break;
+            const uint32_t y = __ldg(nbrs + j);
+            const uint32_t dy = (uint32_t)(__ldg(offsets + y + 1) - __ldg(offsets + y));
+            deep_add(out, y, r / dy);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) vol += __shfl_xor_sync(0xffffffffu, vol, d);
+    __syncwarp();
+    return vol;
+}
+
+// Levels 0..jmax of source x into w->t (final level in t[result]); with
+// limits, stops after a level whose volume reaches two_n or whose support
+// passes the cap.  Records the per-level statistics of `side`.
+__device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs, DeepWarp *w,
+                                uint32_t side, uint32_t x, uint32_t u, uint32_t v, uint32_t jmax, bool limits,
+                                uint64_t two_n, uint32_t lane) {
+    deep_clear(&w->t[0], lane);
+    if (lane == 0) deep_add(&w->t[0], x, kPushQ);
+    __syncwarp();
+    if (lane == 0) {
+        w->st.vol[side][0] = 0;
+        w->st.supp[side][0] = 1;
+        w->st.at_u[side][0] = x == u ? kPushQ : 0u;
+        w->st.at_v[side][0] = x == v ? kPushQ : 0u;
+        w->st.levels[side] = 0;
+    }
+    __syncwarp();
+    uint32_t cur = 0;
+    for (uint32_t j = 1; j <= jmax; ++j) {
+        const uint64_t vol = deep_push(offsets, nbrs, &w->t[cur], &w->t[cur ^ 1], lane);
+        cur ^= 1;
+        const DeepTable *t = &w->t[cur];
+        const uint32_t supp = t->count, over = t->over;
+        const uint32_t au = deep_get(t, u), av = deep_get(t, v);
+        const uint64_t total = w->st.vol[side][j - 1] + vol;
+        __syncwarp();
+        if (lane == 0) {
+            w->st.vol[side][j] = total;
+            w->st.supp[side][j] = supp;
+            w->st.at_u[side][j] = au;
+            w->st.at_v[side][j] = av;
+            w->st.levels[side] = j;
+        }
+        __syncwarp();
+        if (limits && (total >= two_n || over || supp > kPushSupportMax)) break;
+    }
+    return cur;
+}
+
+// Pass 1: for each query at depth 1 with push_max >= 2 and tau >= 2, the
+// deepest level every rule admits (volumes of both sides below 2N, supports
+// within the cap); deeper queries get their depth, X terms, support sizes
+// and walk tasks.
+__global__ void __launch_bounds__(kDeepWarps * 32)
+deep_plan_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs, QueryInfo *__restrict__ info,
+                 uint64_t k, uint32_t push_max, uint32_t bouquet, DeepInfo *__restrict__ deep,
+                 uint32_t *__restrict__ sizes, uint32_t *__restrict__ tasks) {
+    extern __shared__ __align__(16) unsigned char deep_smem[];
+    DeepWarp *w = reinterpret_cast<DeepWarp *>(deep_smem) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = warp; q < k; q += nwarps) {
+        const QueryInfo qi = info[q];
+        uint32_t jmax = push_max < qi.tau ? push_max : qi.tau;
+        if (jmax > kPushMaxDepth) jmax = kPushMaxDepth;
+        if (lane == 0) sizes[q] = 0u;
+        if (!qi.valid || qi.depth != 1 || jmax < 2) continue;
+        const uint64_t two_n = 2ull * qi.nwalks;
+        deep_levels(offsets, nbrs, w, 0, qi.u, qi.u, qi.v, jmax, true, two_n, lane);
+        deep_levels(offsets, nbrs, w, 1, qi.v, qi.u, qi.v, jmax, true, two_n, lane);
+        if (lane == 0) {
+            const DeepStats &st = w->st;
+            const uint32_t top = st.levels[0] < st.levels[1] ? st.levels[0] : st.levels[1];
+            uint32_t dep = 0;
+            for (uint32_t j = 1; j <= top; ++j) {
+                if (st.vol[0][j] + st.vol[1][j] >= two_n) break;
+                if (j >= 2 && (st.supp[0][j] > kPushSupportMax || st.supp[1][j] > kPushSupportMax)) break;
+                dep = j;
+            }
+            if (dep >= 2) {
+                int64_t xu = 0, xv = 0;
+                for (uint32_t l = 0; l <= dep; ++l) {
+                    const int64_t wl = l < qi.tau ? 2 : 1;
+                    xu += wl * ((int64_t)st.at_u[0][l] - (int64_t)st.at_v[0][l]);
+                    xv += wl * ((int64_t)st.at_v[1][l] - (int64_t)st.at_u[1][l]);
+                }
+                DeepInfo di;
+                di.off = 0;
+                di.su = st.supp[0][dep];
+                di.sv = st.supp[1][dep];
+                di.xu = xu;
+                di.xv = xv;
+                deep[q] = di;
+                sizes[q] = di.su + di.sv;
+                info[q].depth = dep;
+                tasks[q] = qi.tau > dep ? 2u * ((qi.nwalks + bouquet - 1) / bouquet) : 0u;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Pass 2: the pushed vectors of each deeper query at its depth, as sorted
+// (vertex << 32 | value) arrays at tables[toff[q]] (r_u, then r_v).
+__global__ void __launch_bounds__(kDeepWarps * 32)
+deep_tables_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
+                   const QueryInfo *__restrict__ info, uint64_t k, const uint64_t *__restrict__ toff,
+                   DeepInfo *__restrict__ deep, unsigned long long *__restrict__ tables) {
+    extern __shared__ __align__(16) unsigned char deep_smem[];
+    DeepWarp *w = reinterpret_cast<DeepWarp *>(deep_smem) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = warp; q < k; q += nwarps) {
+        const QueryInfo qi = info[q];
+        if (!qi.valid || qi.depth < 2) continue;
+        const uint64_t base = toff[q];
+        if (lane == 0) deep[q].off = base;
+        uint64_t at = base;
+        for (uint32_t side = 0; side < 2; ++side) {
+            const uint32_t fin = deep_levels(offsets, nbrs, w, side, side ? qi.v : qi.u, qi.u, qi.v, qi.depth,
+                                             false, 0, lane);
+            const DeepTable *t = &w->t[fin];
+            // compact into the other table's memory, pad to a power of two, sort
+            unsigned long long *arr = reinterpret_cast<unsigned long long *>(&w->t[fin ^ 1]);
+            uint32_t n_out = 0;
+            for (uint32_t base_i = 0; base_i < kDeepSlots; base_i += 32) {
+                const uint32_t i = base_i + lane;
+                const uint32_t key = t->keys[i];
+                const bool has = key != kDeepEmpty;
+                const uint32_t mask = __ballot_sync(0xffffffffu, has);
+                if (has) {
+                    const uint32_t pos = n_out + __popc(mask & ((1u << lane) - 1u));
+                    arr[pos] = ((unsigned long long)key << 32) | t->vals[i];
+                }
+                n_out += __popc(mask);
+            }
+            uint32_t p2 = 1;
+            while (p2 < n_out) p2 <<= 1;
+            for (uint32_t i = n_out + lane; i < p2; i += 32) arr[i] = ~0ull;
+            __syncwarp();
+            for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
+                for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+                    for (uint32_t i = lane; i < p2; i += 32) {
+                        const uint32_t ixj = i ^ jj;
+                        if (ixj > i) {
+                            const unsigned long long a = arr[i], b = arr[ixj];
+                            const bool up = (i & kk) == 0;
+                            if ((a > b) == up) {
+                                arr[i] = b;
+                                arr[ixj] = a;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (uint32_t i = lane; i < n_out; i += 32) tables[at + i] = arr[i];
+            at += n_out;
+            __syncwarp();
+        }
+    }
+}
+
+// r_x(y) from a sorted (vertex << 32 | value) array of `size` entries.
+__device__ __forceinline__ uint64_t deep_value(const unsigned long long *__restrict__ tab, uint32_t size,
+                                               uint32_t y) {
+    uint32_t lo = 0, hi = size;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)(__ldg(tab + mid) >> 32) < y) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < size) {
+        const unsigned long long e = __ldg(tab + lo);
+        if ((uint32_t)(e >> 32) == y) return e & 0xffffffffull;
+    }
+    return 0ull;
+}
+
 // Persistent counting kernel of the push estimator: the tasks, streams and
 // walk indices of aesc_count_kernel (independent sampler), walks of tau -
 // depth steps; at step l a walk adds w r_u(cur) and w r_v(cur), w = 2 if
@@ -489,7 +766,8 @@ __global__ void __launch_bounds__(kThreads, (W <= 4) ? 4 : 1)
 aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
                  const QueryInfo *__restrict__ info, const uint64_t *__restrict__ begin,
                  const uint32_t *__restrict__ bucket, uint64_t k, uint64_t seed,
-                 unsigned long long *__restrict__ next_task, unsigned long long *__restrict__ acc) {
+                 unsigned long long *__restrict__ next_task, unsigned long long *__restrict__ acc,
+                 const DeepInfo *__restrict__ deep, const unsigned long long *__restrict__ tables) {
     __shared__ uint32_t s_keys[kThreads / 32][kPushSetSlots];
     __shared__ uint32_t s_flags[kThreads / 32][kPushSetSlots];
     const uint32_t lane = threadIdx.x & 31;
@@ -513,6 +791,16 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
         const int64_t lo_v = __ldg(offsets + qi.v), hi_v = lo_v + qi.dv;
         // small rows at depth 1: the warp hashes N(u) and N(v) into its set
         const bool use_set = qi.depth == 1 && (uint64_t)qi.du + qi.dv <= kPushSetMaxRows;
+        // depths >= 2: the edge's sorted pushed vectors
+        const unsigned long long *tab_u = nullptr, *tab_v = nullptr;
+        uint32_t size_u = 0, size_v = 0;
+        if (qi.depth >= 2) {
+            const DeepInfo di = deep[q];
+            tab_u = tables + di.off;
+            tab_v = tab_u + di.su;
+            size_u = di.su;
+            size_v = di.sv;
+        }
         if (use_set) {
             for (uint32_t i = lane; i < kPushSetSlots; i += 32) {
                 keys[i] = kPushEmpty;
@@ -553,7 +841,10 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
                 if (deg[j]) {
                     const uint32_t kk = choose(sample_word<false>(st[j], 0ull, cur[j], 0u), deg[j]);
                     el.next(off[j] + kk, cur[j], off[j], deg[j]);
-                    if (use_set) {
+                    if (qi.depth >= 2) {
+                        a_u += weight * deep_value(tab_u, size_u, cur[j]);
+                        a_v += weight * deep_value(tab_v, size_v, cur[j]);
+                    } else if (use_set) {
                         const uint32_t f = push_set_flags(keys, flags, cur[j]);
                         if (f) {
                             const uint64_t r = (uint64_t)(kPushQ / deg[j]);
@@ -580,10 +871,13 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
 }
 
 // g(u, v) = (X_u + (A_uu - A_vu) / N) / (2 Q d_u) with X_u = 2Q, less
-// w_1 floor(Q / d_v) at depth 1 (w_1 = 2 if tau > 1 else 1); SC = g(u, v) +
-// g(v, u); every operation rounded to nearest on its own, in this order.
+// w_1 floor(Q / d_v) at depth 1 (w_1 = 2 if tau > 1 else 1), and at depths
+// >= 2 the sum over l <= depth of w_l (r^l_u(u) - r^l_u(v)) from the build;
+// SC = g(u, v) + g(v, u); every operation rounded to nearest on its own, in
+// this order.
 __global__ void finalize_push_kernel(const QueryInfo *__restrict__ info, uint64_t k,
-                                     const unsigned long long *__restrict__ acc, double *__restrict__ sc) {
+                                     const unsigned long long *__restrict__ acc, const DeepInfo *__restrict__ deep,
+                                     double *__restrict__ sc) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
          q += (uint64_t)gridDim.x * blockDim.x) {
         const QueryInfo qi = info[q];
@@ -593,6 +887,9 @@ __global__ void finalize_push_kernel(const QueryInfo *__restrict__ info, uint64_
             const int64_t w1 = qi.tau > 1 ? 2 : 1;
             xu -= w1 * (int64_t)(kPushQ / qi.dv);
             xv -= w1 * (int64_t)(kPushQ / qi.du);
+        } else if (qi.depth >= 2) {
+            xu = deep[q].xu;
+            xv = deep[q].xv;
         }
         const double du = (double)qi.du, dv = (double)qi.dv, nw = (double)qi.nwalks;
         const double yu = (double)(int64_t)(acc[4 * q + 0] - acc[4 * q + 2]);
@@ -601,6 +898,13 @@ __global__ void finalize_push_kernel(const QueryInfo *__restrict__ info, uint64_
         const double gv = __ddiv_rn(__dadd_rn((double)xv, __ddiv_rn(yv, nw)), __dmul_rn(2.0 * (double)kPushQ, dv));
         sc[q] = __dadd_rn(gu, gv);
     }
+}
+
+// The push depth of every query, once pass 1 of the deeper pushes has run.
+__global__ void push_depth_out_kernel(const QueryInfo *__restrict__ info, uint64_t k, uint32_t *__restrict__ depth) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < k;
+         q += (uint64_t)gridDim.x * blockDim.x)
+        depth[q] = info[q].depth;
 }
 
 unsigned blocks_for(uint64_t items, uint64_t per_block) {
@@ -746,7 +1050,8 @@ namespace {
 
 template <typename EL, int W>
 int launch_push_count(EL el, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
-                      uint64_t seed, unsigned long long *next_task, unsigned long long *acc, cudaStream_t s) {
+                      uint64_t seed, unsigned long long *next_task, unsigned long long *acc, const DeepInfo *deep,
+                      const unsigned long long *tables, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     BQ_CUDA(cudaGetDevice(&dev));
     BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -754,8 +1059,46 @@ int launch_push_count(EL el, const DeviceGraph &g, const QueryInfo *info, const 
     BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
     const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
-    kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, g.nbrs, info, begin, bucket, k, seed, next_task, acc);
+    kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, g.nbrs, info, begin, bucket, k, seed, next_task, acc,
+                                             deep, tables);
     BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
+// Depths >= 2: plan (pass 1), size and allocate the tables (one wait on s),
+// build them (pass 2).  *tables_out is released by the caller.
+int build_deep(const DeviceGraph &g, QueryInfo *info, uint64_t k, uint32_t push_max, uint32_t bouquet,
+               DeepInfo *deep, uint32_t *sizes, uint64_t *toff, uint32_t *tasks,
+               unsigned long long **tables_out, cudaStream_t s) {
+    *tables_out = nullptr;
+    const size_t smem = sizeof(DeepWarp) * kDeepWarps;
+    BQ_CUDA(cudaFuncSetAttribute(deep_plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BQ_CUDA(cudaFuncSetAttribute(deep_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = blocks_for(k, kDeepWarps) < (unsigned)sms ? blocks_for(k, kDeepWarps) : (unsigned)sms;
+    count_launches(1);
+    deep_plan_kernel<<<grid, kDeepWarps * 32, smem, s>>>(g.offsets, g.nbrs, info, k, push_max, bouquet, deep, sizes,
+                                                         tasks);
+    BQ_CUDA(cudaGetLastError());
+    int rc = scan_u32_to_u64(sizes, toff, k, s);
+    if (rc) return rc;
+    uint64_t total = 0;
+    BQ_CUDA(cudaMemcpyAsync(&total, toff + k, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    BQ_CUDA(cudaStreamSynchronize(s));
+    if (total == 0) return BQ_OK;
+    unsigned long long *tables = nullptr;
+    rc = scratch_alloc((void **)&tables, sizeof(unsigned long long) * total, s);
+    if (rc) return rc;
+    count_launches(1);
+    deep_tables_kernel<<<grid, kDeepWarps * 32, smem, s>>>(g.offsets, g.nbrs, info, k, toff, deep, tables);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        scratch_free(tables, s);
+        return cuda_fail(e, "deep_tables_kernel");
+    }
+    *tables_out = tables;
     return BQ_OK;
 }
 
@@ -769,13 +1112,18 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
     if (w != 2 && w != 4 && w != 8) w = 4;
     const uint32_t bouquet = 32u * (uint32_t)w;
     if (k >= kMaxBucketEdges) return fail(BQ_EINVAL, "k = %llu edges in one estimate", (unsigned long long)k);
+    const bool deep_on = push_max >= 2;
     // scratch: info[k] | begin[k + 1] bucket[k + 1] | tasks[k] | next_task |
-    // (edges[2k] if all-edges)
+    // (edges[2k] if all-edges) | (deep[k] sizes[k] toff[k + 1] if push_max >= 2)
     const size_t info_bytes = sizeof(QueryInfo) * k;
     const size_t begin_bytes = sizeof(uint64_t) * (k + 1) + ((sizeof(uint32_t) * bucket_count(k) + 7) & ~(size_t)7);
     const size_t task_bytes = sizeof(uint32_t) * ((k + 1) & ~1ull);
     const size_t edge_bytes = edges_uv ? 0 : sizeof(uint32_t) * 2 * k;
-    const size_t bytes = info_bytes + begin_bytes + task_bytes + 16 + edge_bytes;
+    const size_t deep_bytes = deep_on ? sizeof(DeepInfo) * k : 0;
+    const size_t size_bytes = deep_on ? sizeof(uint32_t) * ((k + 1) & ~1ull) : 0;
+    const size_t toff_bytes = deep_on ? sizeof(uint64_t) * (k + 1) : 0;
+    const size_t head = info_bytes + begin_bytes + task_bytes + 16 + ((edge_bytes + 15) & ~(size_t)15);
+    const size_t bytes = head + deep_bytes + size_bytes + toff_bytes;
     char *buf = nullptr;
     int rc = scratch_alloc((void **)&buf, bytes, s);
     if (rc) return rc;
@@ -784,7 +1132,11 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
     uint32_t *tasks = (uint32_t *)(buf + info_bytes + begin_bytes);
     unsigned long long *next_task = (unsigned long long *)(buf + info_bytes + begin_bytes + task_bytes);
     uint32_t *all_uv = (uint32_t *)(buf + info_bytes + begin_bytes + task_bytes + 16);
+    DeepInfo *deep = deep_on ? (DeepInfo *)(buf + head) : nullptr;
+    uint32_t *sizes = deep_on ? (uint32_t *)(buf + head + deep_bytes) : nullptr;
+    uint64_t *toff = deep_on ? (uint64_t *)(buf + head + deep_bytes + size_bytes) : nullptr;
     unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(acc);
+    unsigned long long *tables = nullptr;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(uint64_t) * 4 * k, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(next_task, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) {
@@ -801,8 +1153,9 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
         }
         count_launches(1);
         prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, push_max, info,
-                                                                    tasks, depth_out, sc, status);
-        rc = scan_u32_to_u64(tasks, begin, k, s);
+                                                                    tasks, nullptr, sc, status);
+        if (deep_on) rc = build_deep(g, info, k, push_max, bouquet, deep, sizes, toff, tasks, &tables, s);
+        if (rc == BQ_OK) rc = scan_u32_to_u64(tasks, begin, k, s);
         if (rc == BQ_OK) {
             count_launches(1);
             build_bucket_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(
@@ -814,18 +1167,20 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
         count_launches(1);
         rc = with_edges(g, [&](auto el) {
             using EL = decltype(el);
-            if (w == 2) return launch_push_count<EL, 2>(el, g, info, begin, k, seed, next_task, acc64, s);
-            if (w == 8) return launch_push_count<EL, 8>(el, g, info, begin, k, seed, next_task, acc64, s);
-            return launch_push_count<EL, 4>(el, g, info, begin, k, seed, next_task, acc64, s);
+            if (w == 2) return launch_push_count<EL, 2>(el, g, info, begin, k, seed, next_task, acc64, deep, tables, s);
+            if (w == 8) return launch_push_count<EL, 8>(el, g, info, begin, k, seed, next_task, acc64, deep, tables, s);
+            return launch_push_count<EL, 4>(el, g, info, begin, k, seed, next_task, acc64, deep, tables, s);
         });
     }
     if (rc == BQ_OK) {
         ProfScope prof(kProfAescAux, s);
-        count_launches(1);
-        finalize_push_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, acc64, sc);
+        count_launches(depth_out ? 2 : 1);
+        finalize_push_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, acc64, deep, sc);
+        if (depth_out) push_depth_out_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(info, k, depth_out);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "finalize_push_kernel");
     }
+    if (tables) scratch_free(tables, s);
     scratch_free(buf, s);
     return rc;
 }

@@ -707,7 +707,7 @@ int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edge
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
-    if (push_max > 1) return fail(BQ_EINVAL, "push_max = %u (0 or 1)", push_max);
+    if (push_max > 8) return fail(BQ_EINVAL, "push_max = %u (at most 8)", push_max);
     if (k && (!tau_dev || !nwalks_dev || !acc_dev || !sc_dev))
         return fail(BQ_EINVAL, "tau, nwalks, acc or sc is NULL");
     if (!edges_uv_dev && (k != g->nnz / 2 || k != g->m_upper))
