@@ -401,12 +401,33 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     dep = depth.cpu().numpy()
     pwork = float(np.sum(2.0 * (tau.astype(np.float64) - dep) * nw))
     pdiff = np.abs(pest[pick] - ref)
+    # the same with pushes up to depth 8 (volume rule, support cap 512 from depth 2)
+    bq.aesc_estimate_push(graph, 5, None, dtau, dnw, 8, depth=depth, acc=acc, sc=sc)
+    bq.sync()
+    dlat = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bq.aesc_estimate_push(graph, 5, None, dtau, dnw, 8, depth=depth, acc=acc, sc=sc)
+        e1.record()
+        e1.synchronize()
+        dlat.append(e0.elapsed_time(e1))
+    bq.sync()
+    dest = sc.cpu().numpy()
+    ddep = depth.cpu().numpy()
+    ddiff = np.abs(dest[pick] - ref)
+    deep = {"push_max": 8, "ms_per_estimate": sum(dlat) / len(dlat),
+            "edges_per_s": tau.size / (sum(dlat) / len(dlat) / 1e3),
+            "depth_histogram": np.bincount(ddep.astype(np.int64), minlength=9).tolist(),
+            "walk_steps_per_call": float(np.sum(2.0 * (tau.astype(np.float64) - ddep) * nw)),
+            "foster_residual": abs(float(dest.sum()) - (g.n - 1)) / (g.n - 1),
+            "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(ddiff ** 2)))}
     push = {"edges_per_s": tau.size / (pms / 1e3), "ms_per_estimate": pms, "walk_steps_per_call": pwork,
             "frac_edges_depth1": float(dep.mean()),
             "foster_residual": abs(float(pest.sum()) - (g.n - 1)) / (g.n - 1),
             "subset_1000_max_abs_diff_vs_16N_2tau": float(pdiff.max()),
             "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(pdiff ** 2))),
-            "plain_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(diff ** 2)))}
+            "plain_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(diff ** 2))), "deeper": deep}
     # the pilot plan: the same tau, N from PILOT_WALKS walks per side (z = PILOT_Z)
     t0 = time.perf_counter()
     ltau, lnw, _ = bq.aesc_plan_pilot(graph, 5, None, eps, sched, PILOT_WALKS, PILOT_Z, moments=False)

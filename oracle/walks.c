@@ -757,21 +757,28 @@ static void svec_add(orc_svec *s, uint32_t y, uint64_t c)
     s->val[y] += c;
 }
 
-/* out = one push of in; returns the volume (sum of the degrees of supp in). */
-static uint64_t push_level(const int64_t *offsets, const uint32_t *nbrs, const orc_svec *in, orc_svec *out)
+/* The volume of pushing in: the sum of the degrees of its support. */
+static uint64_t push_volume(const int64_t *offsets, const orc_svec *in)
 {
     uint64_t i, vol = 0;
+    for (i = 0; i < in->cnt; i++)
+        vol += (uint64_t)(offsets[in->idx[i] + 1] - offsets[in->idx[i]]);
+    return vol;
+}
+
+/* out = one push of in. */
+static void push_level(const int64_t *offsets, const uint32_t *nbrs, const orc_svec *in, orc_svec *out)
+{
+    uint64_t i;
     svec_clear(out);
     for (i = 0; i < in->cnt; i++) {
         uint32_t z = in->idx[i];
         int64_t j;
-        vol += (uint64_t)(offsets[z + 1] - offsets[z]);
         for (j = offsets[z]; j < offsets[z + 1]; j++) {
             uint32_t y = nbrs[j];
             svec_add(out, y, in->val[z] / (uint64_t)(offsets[y + 1] - offsets[y]));
         }
     }
-    return vol;
 }
 
 typedef struct {
@@ -782,9 +789,10 @@ typedef struct {
     uint64_t at_v[ORC_PUSH_MAX_DEPTH + 1];  /* r^j(v) */
 } orc_push_stats;
 
-/* Levels 0..jmax of source x; with `limits`, stopping after a level beyond
- * which no deeper level can be taken (its volume alone reaches two_n, or
- * its support is above the cap).  r^levels_x is left in *a. */
+/* Levels 0..jmax of source x; with `limits`, stopping at a level whose
+ * volume alone reaches two_n (before pushing it) or after one whose support
+ * is above the cap: no deeper level can be taken then.  r^levels_x is left
+ * in *a. */
 static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x, uint32_t u, uint32_t v,
                         uint32_t jmax, int limits, uint64_t two_n, orc_svec *a, orc_svec *b,
                         orc_push_stats *st)
@@ -799,16 +807,21 @@ static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x
     st->at_v[0] = a->val[v];
     for (j = 1; j <= jmax; j++) {
         orc_svec t;
-        uint64_t vol = push_level(offsets, nbrs, a, b);
+        st->vol[j] = st->vol[j - 1] + push_volume(offsets, a);
+        if (limits && st->vol[j] >= two_n) {
+            st->supp[j] = 0;
+            st->levels = j;
+            break;
+        }
+        push_level(offsets, nbrs, a, b);
         t = *a;
         *a = *b;
         *b = t;
         st->levels = j;
-        st->vol[j] = st->vol[j - 1] + vol;
         st->supp[j] = a->cnt;
         st->at_u[j] = a->val[u];
         st->at_v[j] = a->val[v];
-        if (limits && (st->vol[j] >= two_n || st->supp[j] > ORC_PUSH_SUPPORT_MAX))
+        if (limits && st->supp[j] > ORC_PUSH_SUPPORT_MAX)
             break;
     }
 }

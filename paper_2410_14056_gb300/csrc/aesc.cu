@@ -559,19 +559,29 @@ __device__ uint32_t deep_get(const DeepTable *t, uint32_t y) {
     return 0u;
 }
 
-// out = one push of in; returns the volume (sum of the degrees of supp in),
-// the same in every lane.  Stops adding once out passed the cap (that level
-// is then refused whatever else it would hold).
-__device__ uint64_t deep_push(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
-                              const DeepTable *in, DeepTable *out, uint32_t lane) {
-    deep_clear(out, lane);
+// The volume of pushing `in`: the sum of the degrees of its support, the
+// same in every lane.
+__device__ uint64_t deep_volume(const int64_t *__restrict__ offsets, const DeepTable *in, uint32_t lane) {
     uint64_t vol = 0;
+    for (uint32_t i = lane; i < kDeepSlots; i += 32) {
+        const uint32_t z = in->keys[i];
+        if (z != kDeepEmpty) vol += (uint64_t)(__ldg(offsets + z + 1) - __ldg(offsets + z));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) vol += __shfl_xor_sync(0xffffffffu, vol, d);
+    return vol;
+}
+
+// out = one push of in.  Stops adding once out passed the cap (that level
+// is then refused whatever else it would hold).
+__device__ void deep_push(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
+                          const DeepTable *in, DeepTable *out, uint32_t lane) {
+    deep_clear(out, lane);
     for (uint32_t i = lane; i < kDeepSlots; i += 32) {
         const uint32_t z = in->keys[i];
         if (z == kDeepEmpty) continue;
         const uint32_t r = in->vals[i];
         const int64_t lo = __ldg(offsets + z), hi = __ldg(offsets + z + 1);
-        vol += (uint64_t)(hi - lo);
         for (int64_t j = lo; j < hi; ++j) {
             if (*(volatile uint32_t *)&out->over) break;
             const uint32_t y = __ldg(nbrs + j);
@@ -579,15 +589,13 @@ __device__ uint64_t deep_push(const int64_t *__restrict__ offsets, const uint32_
             deep_add(out, y, r / dy);
         }
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) vol += __shfl_xor_sync(0xffffffffu, vol, d);
     __syncwarp();
-    return vol;
 }
 
 // Levels 0..jmax of source x into w->t (final level in t[result]); with
-// limits, stops after a level whose volume reaches two_n or whose support
-// passes the cap.  Records the per-level statistics of `side`.
+// limits, stops at a level whose volume reaches two_n (before pushing it) or
+// after one whose support passes the cap.  Records the per-level statistics
+// of `side`.
 __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs, DeepWarp *w,
                                 uint32_t side, uint32_t x, uint32_t u, uint32_t v, uint32_t jmax, bool limits,
                                 uint64_t two_n, uint32_t lane) {
@@ -604,12 +612,22 @@ __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint3
     __syncwarp();
     uint32_t cur = 0;
     for (uint32_t j = 1; j <= jmax; ++j) {
-        const uint64_t vol = deep_push(offsets, nbrs, &w->t[cur], &w->t[cur ^ 1], lane);
+        const uint64_t total = w->st.vol[side][j - 1] + deep_volume(offsets, &w->t[cur], lane);
+        __syncwarp();
+        if (limits && total >= two_n) {
+            if (lane == 0) {
+                w->st.vol[side][j] = total;
+                w->st.supp[side][j] = 0;
+                w->st.levels[side] = j;
+            }
+            __syncwarp();
+            break;
+        }
+        deep_push(offsets, nbrs, &w->t[cur], &w->t[cur ^ 1], lane);
         cur ^= 1;
         const DeepTable *t = &w->t[cur];
         const uint32_t supp = t->count, over = t->over;
         const uint32_t au = deep_get(t, u), av = deep_get(t, v);
-        const uint64_t total = w->st.vol[side][j - 1] + vol;
         __syncwarp();
         if (lane == 0) {
             w->st.vol[side][j] = total;
@@ -619,7 +637,7 @@ __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint3
             w->st.levels[side] = j;
         }
         __syncwarp();
-        if (limits && (total >= two_n || over || supp > kPushSupportMax)) break;
+        if (limits && (over || supp > kPushSupportMax)) break;
     }
     return cur;
 }
@@ -644,6 +662,22 @@ deep_plan_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restrict
         if (lane == 0) sizes[q] = 0u;
         if (!qi.valid || qi.depth != 1 || jmax < 2) continue;
         const uint64_t two_n = 2ull * qi.nwalks;
+        // level 2 needs both rows within the cap and vol_2(x) = d_x + the sum
+        // of the degrees of N(x) below 2N in total: most edges stop here
+        if (qi.du > kPushSupportMax || qi.dv > kPushSupportMax) continue;
+        uint64_t vol2 = 0;
+        const int64_t lu = __ldg(offsets + qi.u), lv = __ldg(offsets + qi.v);
+        for (uint32_t i = lane; i < qi.du; i += 32) {
+            const uint32_t z = __ldg(nbrs + lu + i);
+            vol2 += (uint64_t)(__ldg(offsets + z + 1) - __ldg(offsets + z));
+        }
+        for (uint32_t i = lane; i < qi.dv; i += 32) {
+            const uint32_t z = __ldg(nbrs + lv + i);
+            vol2 += (uint64_t)(__ldg(offsets + z + 1) - __ldg(offsets + z));
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) vol2 += __shfl_xor_sync(0xffffffffu, vol2, d);
+        if ((uint64_t)qi.du + qi.dv + vol2 >= two_n) continue;
         deep_levels(offsets, nbrs, w, 0, qi.u, qi.u, qi.v, jmax, true, two_n, lane);
         deep_levels(offsets, nbrs, w, 1, qi.v, qi.u, qi.v, jmax, true, two_n, lane);
         if (lane == 0) {
