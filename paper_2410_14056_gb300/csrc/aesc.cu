@@ -867,30 +867,40 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
         }
         uint64_t a_u = 0, a_v = 0;
         const uint32_t steps = qi.tau - qi.depth;
-        for (uint32_t l = 1; l <= steps; ++l) {
-            const uint64_t weight = l + qi.depth < qi.tau ? 2ull : 1ull;
+        // the walk loop with one lookup of the pushed values, chosen per task
+        auto walk = [&](auto lookup) {
+            for (uint32_t l = 1; l <= steps; ++l) {
+                const uint64_t weight = l + qi.depth < qi.tau ? 2ull : 1ull;
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                st[j] += kGolden;
-                if (deg[j]) {
-                    const uint32_t kk = choose(sample_word<false>(st[j], 0ull, cur[j], 0u), deg[j]);
-                    el.next(off[j] + kk, cur[j], off[j], deg[j]);
-                    if (qi.depth >= 2) {
-                        a_u += weight * deep_value(tab_u, size_u, cur[j]);
-                        a_v += weight * deep_value(tab_v, size_v, cur[j]);
-                    } else if (use_set) {
-                        const uint32_t f = push_set_flags(keys, flags, cur[j]);
-                        if (f) {
-                            const uint64_t r = (uint64_t)(kPushQ / deg[j]);
-                            if (f & 1u) a_u += weight * r;
-                            if (f & 2u) a_v += weight * r;
-                        }
-                    } else {
-                        a_u += weight * pushed_value(nbrs, lo_u, hi_u, qi.u, cur[j], deg[j], qi.depth);
-                        a_v += weight * pushed_value(nbrs, lo_v, hi_v, qi.v, cur[j], deg[j], qi.depth);
+                for (int j = 0; j < W; ++j) {
+                    st[j] += kGolden;
+                    if (deg[j]) {
+                        const uint32_t kk = choose(sample_word<false>(st[j], 0ull, cur[j], 0u), deg[j]);
+                        el.next(off[j] + kk, cur[j], off[j], deg[j]);
+                        lookup(cur[j], deg[j], weight);
                     }
                 }
             }
+        };
+        if (qi.depth >= 2) {
+            walk([&](uint32_t y, uint32_t, uint64_t weight) {
+                a_u += weight * deep_value(tab_u, size_u, y);
+                a_v += weight * deep_value(tab_v, size_v, y);
+            });
+        } else if (use_set) {
+            walk([&](uint32_t y, uint32_t dy, uint64_t weight) {
+                const uint32_t f = push_set_flags(keys, flags, y);
+                if (f) {
+                    const uint64_t r = (uint64_t)(kPushQ / dy);
+                    if (f & 1u) a_u += weight * r;
+                    if (f & 2u) a_v += weight * r;
+                }
+            });
+        } else {
+            walk([&](uint32_t y, uint32_t dy, uint64_t weight) {
+                a_u += weight * pushed_value(nbrs, lo_u, hi_u, qi.u, y, dy, qi.depth);
+                a_v += weight * pushed_value(nbrs, lo_v, hi_v, qi.v, y, dy, qi.depth);
+            });
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
