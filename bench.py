@@ -101,14 +101,24 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def walk_kernel_traffic(kernel_file: str):
+WALK_KERNEL_SOURCES = ("walks.cu", "internal.h", "hash.cuh", "edges.cuh")
+
+
+def walk_kernel_digest() -> str:
+    """sha256 (16 hex digits) of the sources the walk kernel is built from."""
+    h = hashlib.sha256()
+    for name in WALK_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2410_14056_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def walk_kernel_traffic():
     """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current kernel sources (else None)."""
     prof = os.path.join(ROOT, "profiles", "walk_hub_kernel_rmat20.md")
-    src = os.path.join(ROOT, "paper_2410_14056_gb300", "csrc", kernel_file)
     if not os.path.exists(prof):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = walk_kernel_digest()
     vals = {}
     for line in open(prof):
         if ":" in line and line.strip().startswith("- "):
@@ -627,7 +637,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     algo_bytes = BYTES_PER_STEP * steps_per_batch
     achieved = algo_bytes / (walk_ms / 1e3) / 1e9
-    traffic = walk_kernel_traffic("walks.cu")
+    traffic = walk_kernel_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "walk_hub_kernel" if bq.get_tuning()["hub_slots"] else "walk_bouquet_kernel",
