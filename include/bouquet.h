@@ -304,27 +304,38 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
 /*
  * AESC with a push phase (Alg. 1: p_l(., v_i) pushed exactly for the first
  * tau~ levels, walks of tau - tau~ steps weighted by p_tau~(x, v_i) instead
- * of hit indicators), for push depth tau~ in {0, 1}.  Depth 1 is taken per
- * edge when push_max = 1, tau >= 1 and d(u) + d(v) < 2 N (TGT+'s test:
- * push while the pushed volume is below the walks it replaces); push_max =
- * 0 keeps depth 0 everywhere.  In fixed point with Q = 2^30:
- *   r_x(y) = Q [y == x] (depth 0), floor(Q / d(y)) if y ~ x else 0 (depth 1);
- * the walks are those of bq_aesc_estimate (streams 2 id + side, walk index,
- * independent sampler), tau - depth steps long; at step l a walk adds
- * w r_u(cur) and w r_v(cur), w = 2 if l + depth < tau else 1, to
+ * of hit indicators), for push depths tau~ from 0 to push_max <= 8.  In
+ * fixed point with Q = 2^30 the pushed vectors of a source x are
+ *   r^0_x = Q e_x,  r^{j+1}_x(y) = sum over neighbours z of y of
+ *                                  floor(r^j_x(z) / d(y))
+ * (so r^1_x(y) = floor(Q / d(y)) on the neighbours of x).  Pushing level j
+ * touches the rows of supp r^{j-1}: vol_j(x) = sum over j' < j of the
+ * degrees of supp r^j'_x (vol_1 = d(x)).  The depth of an edge (TGT+'s test:
+ * push while the pushed volume is below the walks it replaces) is the
+ * largest tau~ <= min(push_max, tau, 8) such that every level j <= tau~ has
+ * vol_j(u) + vol_j(v) < 2 N and, when tau~ >= 2, every level 1..tau~ has at
+ * most 512 vertices in the support of either side; push_max = 0 keeps
+ * depth 0 everywhere.  The walks are those of bq_aesc_estimate (streams
+ * 2 id + side, walk index, independent sampler), tau - depth steps long; at
+ * step l a walk adds w r_u(cur) and w r_v(cur), r = r^depth and w = 2 if
+ * l + depth < tau else 1, to
  *   acc[4q + 0..3] = A_uu, A_uv (walks from u), A_vu, A_vv (walks from v)
  * (uint64; 2 N tau < 2^32 keeps them below 2^62), and
  *   SC = g(u, v) + g(v, u),  g(u, v) = (X_u + (A_uu - A_vu) / N) / (2 Q d_u),
- *   X_u = 2Q at depth 0, 2Q - w_1 floor(Q / d_v) at depth 1 (w_1 = 2 if
- *   tau > 1 else 1), each FP64 operation rounded once in this order.
+ *   X_u = sum over l = 0..depth of w_l (r^l_u(u) - r^l_u(v)), w_l = 2 if
+ *   l < tau else 1 (2Q at depth 0, 2Q - w_1 floor(Q / d_v) at depth 1);
+ *   g(v, u) likewise; each FP64 operation rounded once in this order.
  * Its expectation is the same half-weighted series as bq_aesc_estimate's;
- * depth 1 lowers the variance (a step adds 1/d(y) on every neighbour of u
- * instead of only on u) and saves one step per walk.
+ * deeper pushes lower the variance and shorten the walks.
  *
  * Arguments as bq_aesc_estimate (edges_uv_dev NULL = all edges; BQ_HOST_IO
  * for host buffers), plus depth_dev (k uint32, may be NULL): the depth
- * taken per edge; acc_dev: 4k uint64, overwritten.  Errors: BQ_EINVAL
- * (push_max > 1, NULL buffers), and at bq_sync those of bq_aesc_estimate.
+ * taken per edge; acc_dev: 4k uint64, overwritten.  With push_max >= 2 the
+ * call waits for `stream` once, after planning the depths, to allocate the
+ * pushed vectors of the deeper edges (8 bytes per support vertex, device
+ * memory, released before the call returns its work to the stream).
+ * Errors: BQ_EINVAL (push_max > 8, NULL buffers), BQ_ENOMEM, and at bq_sync
+ * those of bq_aesc_estimate.
  */
 int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev,
                           uint64_t k, const uint32_t *tau_dev, const uint32_t *nwalks_dev,
