@@ -332,8 +332,8 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
  * for host buffers), plus depth_dev (k uint32, may be NULL): the depth
  * taken per edge; acc_dev: 4k uint64, overwritten.  With push_max >= 2 the
  * call waits for `stream` once, after planning the depths, to allocate the
- * pushed vectors of the deeper edges (8 bytes per support vertex, device
- * memory, released before the call returns its work to the stream).
+ * pushed vectors of the deeper edges (8 bytes of device memory per support
+ * vertex, freed in stream order once the estimate has run).
  * Errors: BQ_EINVAL (push_max > 8, NULL buffers), BQ_ENOMEM, and at bq_sync
  * those of bq_aesc_estimate.
  */
