@@ -547,7 +547,17 @@ typedef struct bq_tuning {
                                   kernel, which measured faster (the table's
                                   shared memory takes the L1 capacity that a
                                   bouquet's walks reuse) */
-    uint32_t reserved;
+    uint32_t hub_cluster;      /* graphs created from now on spread a table of
+                                  hub_slots * hub_cluster slots over a thread-
+                                  block cluster of hub_cluster CTAs (2, 4 or
+                                  8), each holding hub_slots of them in its
+                                  shared memory; a walk step reads a hub's slot
+                                  in the owning CTA (distributed shared
+                                  memory).  0 or 1 (default): one CTA holds the
+                                  whole table, which measured faster (on R-MAT
+                                  20 the walk kernel took 14.8 / 21.7 / 30.9 ms
+                                  with clusters of 2 / 4 / 8 against 9.0 ms).
+                                  Never changes a result. */
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

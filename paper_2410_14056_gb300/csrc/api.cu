@@ -26,6 +26,7 @@ std::atomic<int> g_aggregate{0};
 std::atomic<int> g_aesc_walks_per_lane{4};
 std::atomic<int> g_edge_records{1};
 std::atomic<int> g_hub_slots{8192};
+std::atomic<int> g_hub_cluster{1};
 std::atomic<int> g_l2_hints{0};
 std::atomic<int> g_aesc_hub{0};
 }  // namespace
@@ -145,6 +146,7 @@ bool tuning_aggregate_visits() { return g_aggregate.load() != 0; }
 int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
 int tuning_layout() { return g_edge_records.load(); }
 int tuning_hub_slots() { return g_hub_slots.load(); }
+int tuning_hub_cluster() { return g_hub_cluster.load(); }
 bool tuning_l2_hints() { return g_l2_hints.load() != 0; }
 bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
 
@@ -826,6 +828,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->hub_slots = (uint32_t)g_hub_slots.load();
     out->l2_hints = (uint32_t)g_l2_hints.load();
     out->aesc_hub = (uint32_t)g_aesc_hub.load();
+    out->hub_cluster = (uint32_t)g_hub_cluster.load();
     return BQ_OK;
 }
 
@@ -841,6 +844,8 @@ int bq_set_tuning(const bq_tuning *in) {
         return fail(BQ_EINVAL, "hub_slots must be 0 or 1024..%u", kHubSlotsMax);
     if (in->l2_hints > 1) return fail(BQ_EINVAL, "l2_hints must be 0 or 1");
     if (in->aesc_hub > 1) return fail(BQ_EINVAL, "aesc_hub must be 0 or 1");
+    const uint32_t c = in->hub_cluster;
+    if (c != 0 && c != 1 && c != 2 && c != 4 && c != 8) return fail(BQ_EINVAL, "hub_cluster must be 0, 1, 2, 4 or 8");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
@@ -848,6 +853,7 @@ int bq_set_tuning(const bq_tuning *in) {
     g_hub_slots.store((int)in->hub_slots);
     g_l2_hints.store((int)in->l2_hints);
     g_aesc_hub.store((int)in->aesc_hub);
+    g_hub_cluster.store(c < 1 ? 1 : (int)c);
     return BQ_OK;
 }
 

@@ -545,7 +545,8 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
             }
         }
         g->layout = g->d_pk ? 5 : (g->d_edge8 ? 2 : (g->d_edge16 ? 3 : (compact ? 0 : 4)));
-        const uint32_t slots = (uint32_t)tuning_hub_slots();
+        const uint32_t cluster = (uint32_t)tuning_hub_cluster() > 1 ? (uint32_t)tuning_hub_cluster() : 1u;
+        const uint32_t slots = (uint32_t)tuning_hub_slots() * cluster;
         if (slots > 0 && compact && n > 0) {
             unsigned long long *best = nullptr;
             e = cudaMalloc(&best, sizeof(unsigned long long) * slots);
@@ -562,6 +563,7 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
                 goto done;
             }
             g->hub_slots = slots;
+            g->hub_cluster = cluster;
             g->device_bytes += sizeof(uint32_t) * slots;
         }
     }

@@ -74,7 +74,8 @@ struct DeviceGraph {
     // Hub table: slot hub_slot(v, hub_slots) holds the highest-degree
     // vertex hashing there (kNoHub when empty); null if none.
     const uint32_t *hub_tag;
-    uint32_t hub_slots;
+    uint32_t hub_slots;    // slots in all (hub_slot over this count)
+    uint32_t hub_cluster;  // CTAs sharing the table (1: one CTA holds it)
     bool compact() const { return rec8 != nullptr; }
 };
 
@@ -155,6 +156,7 @@ struct bq_graph {
     int layout = 0;  // layout chosen at creation (bq_tuning.layout values)
     uint32_t *d_hub_tag = nullptr;
     uint32_t hub_slots = 0;
+    uint32_t hub_cluster = 1;
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
     uint64_t device_bytes = 0;
@@ -193,6 +195,7 @@ struct bq_graph {
         v.pk_mask = pk_mask;
         v.hub_tag = d_hub_tag;
         v.hub_slots = hub_slots;
+        v.hub_cluster = hub_cluster;
         return v;
     }
 };
@@ -250,6 +253,7 @@ bool tuning_aggregate_visits();
 int tuning_aesc_walks_per_lane();
 int tuning_layout();    // graph layout built at creation (bq_tuning.layout)
 int tuning_hub_slots();  // hub table size built at creation (bq_tuning.hub_slots)
+int tuning_hub_cluster();  // CTAs a created graph's hub table is spread over
 bool tuning_l2_hints(); // L2 eviction policies on the walk kernel's loads
 bool tuning_aesc_hub();  // AESC counting reads hub records from shared memory
 

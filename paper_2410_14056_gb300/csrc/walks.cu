@@ -15,11 +15,15 @@
 // atomic.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "edges.cuh"
 #include "hash.cuh"
 #include "internal.h"
 
 namespace bq {
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -377,6 +381,132 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
     }
 }
 
+// The hub table spread over a thread-block cluster: CTA r of a cluster of C
+// holds slots [r * per, (r + 1) * per) of a table of C * per slots, so a
+// cluster covers C times the hubs of one CTA with the same shared memory per
+// CTA (and so the same L1 left for the walks' gathers).  A step reads its
+// vertex's slot in the owning CTA through distributed shared memory and adds
+// a hub visit there.  The cluster synchronises once the slices are filled
+// and again before any CTA flushes its counts and exits, so no CTA touches
+// the shared memory of a CTA that has left.
+template <typename EL, int W, bool COUPLED>
+__global__ void __launch_bounds__(kHubThreads, 1)
+walk_cluster_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ hub_tag,
+                        uint32_t hub_slots, const uint32_t *__restrict__ sorted_id,
+                        const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr,
+                        uint32_t n_steps, uint64_t seed, Sampler smp, bool visit_start,
+                        uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
+                        unsigned long long *__restrict__ next_chunk) {
+    extern __shared__ __align__(16) unsigned char hub_smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t csize = cluster.num_blocks();
+    const uint32_t rank = cluster.block_rank();
+    const uint32_t per = hub_slots / csize;
+    uint2 *s_rec = reinterpret_cast<uint2 *>(hub_smem);
+    uint32_t *s_tag = reinterpret_cast<uint32_t *>(s_rec + per);
+    uint32_t *s_cnt = s_tag + per;
+    for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) {
+        const uint32_t t = hub_tag[rank * per + i];
+        s_tag[i] = t;
+        s_cnt[i] = 0;
+        uint2 r = make_uint2(0u, 0u);
+        if constexpr (EL::kSplit) {
+            if (t != kNoHub) {
+                uint64_t o;
+                uint32_t d;
+                el.rec_of(t, o, d);
+                r = make_uint2((uint32_t)o, d);
+            }
+        }
+        s_rec[i] = r;
+    }
+    cluster.sync();
+
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t n_valid = *n_valid_ptr;
+    while (true) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(next_chunk, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const uint64_t base = chunk * 32ull * W;
+        if (base >= n_valid) break;
+
+        uint32_t cur[W], id[W], deg[W];
+        uint64_t off[W], st[W], gs[W];
+        uint32_t xw[W];  // the walk's fixed seed (literal SABA word only)
+        bool act[W], moved[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint64_t p = base + (uint64_t)j * 32 + lane;
+            act[j] = p < n_valid;
+            id[j] = 0u;
+            cur[j] = 0u;
+            if (act[j]) {
+                id[j] = sorted_id[p];
+                cur[j] = sorted_start[p];
+            }
+            off[j] = 0;
+            deg[j] = 0;
+            if (act[j]) start_record(offsets, cur[j], off[j], deg[j]);
+            st[j] = walk_key(seed, kBatchStream, id[j]);
+            gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, smp.t == kSabaT ? 0 : id[j] / smp.width)
+                            : 0ull;
+            xw[j] = (uint32_t)st[j];
+            if (act[j]) {
+                if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1)] = cur[j];
+                if (visit_start) {
+                    const uint32_t slot = hub_slot(cur[j], hub_slots);
+                    const uint32_t owner = slot / per, local = slot - owner * per;
+                    if (cluster.map_shared_rank(s_tag, owner)[local] == cur[j])
+                        atomicAdd(cluster.map_shared_rank(s_cnt, owner) + local, 1u);
+                    else
+                        atomicAdd(visits + cur[j], 1u);
+                }
+            }
+        }
+        for (uint32_t l = 1; l <= n_steps; ++l) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                st[j] += kGolden;
+                if (COUPLED) gs[j] += kGolden;
+                moved[j] = deg[j] != 0;
+                if (moved[j]) {
+                    const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t, xw[j]), deg[j]);
+                    if constexpr (EL::kSplit) cur[j] = el.id(off[j] + k);
+                    else el.next(off[j] + k, cur[j], off[j], deg[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                if (!act[j]) continue;
+                const uint32_t slot = hub_slot(cur[j], hub_slots);
+                const uint32_t owner = slot / per, local = slot - owner * per;
+                if (cluster.map_shared_rank(s_tag, owner)[local] == cur[j]) {
+                    atomicAdd(cluster.map_shared_rank(s_cnt, owner) + local, 1u);
+                    if constexpr (EL::kSplit) {
+                        if (moved[j]) {
+                            const uint2 r = cluster.map_shared_rank(s_rec, owner)[local];
+                            off[j] = r.x;
+                            deg[j] = r.y;
+                        }
+                    }
+                } else {
+                    atomicAdd(visits + cur[j], 1u);
+                    if constexpr (EL::kSplit) {
+                        if (moved[j]) el.rec_of(cur[j], off[j], deg[j]);
+                    }
+                }
+                if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1) + l] = cur[j];
+            }
+        }
+    }
+    cluster.sync();
+    for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) {
+        const uint32_t c = s_cnt[i];
+        if (c) atomicAdd(visits + s_tag[i], c);
+    }
+}
+
 unsigned blocks_for(uint64_t items, uint64_t per_block) {
     uint64_t b = (items + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -479,6 +609,65 @@ bool launch_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t
 #undef BQ_HUB
 }
 
+// Launch the cluster hub kernel: clusters of g.hub_cluster CTAs, as many as
+// can be resident at once (the grid is persistent); false (nothing launched)
+// when no such cluster fits.
+template <typename EL, int W, bool COUPLED>
+bool launch_cluster_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst,
+                          const uint32_t *n_valid, uint32_t n_steps, uint64_t seed, const Sampler &smp,
+                          bool visit_start, uint32_t *visits, uint32_t *paths, unsigned long long *next_chunk,
+                          cudaStream_t s) {
+    const uint32_t csize = g.hub_cluster;
+    const size_t smem = (size_t)16 * (g.hub_slots / csize);
+    auto kernel = walk_cluster_hub_kernel<EL, W, COUPLED>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(kHubThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    cfg.gridDim = dim3((unsigned)clusters * csize);
+    ProfScope prof(kProfWalk, s);
+    count_launches(1);
+    if (cudaLaunchKernelEx(&cfg, kernel, el, g.offsets, g.hub_tag, g.hub_slots, sid, sst, n_valid, n_steps, seed, smp,
+                           visit_start, visits, paths, next_chunk) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+template <typename EL>
+bool launch_cluster_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+                        uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
+                        uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
+    const bool c = smp.kind == 1;
+#define BQ_CHUB(WW)                                                                                             \
+    (c ? launch_cluster_hub_w<EL, WW, true>(el, g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, \
+                                            paths, next_chunk, s)                                             \
+       : launch_cluster_hub_w<EL, WW, false>(el, g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, \
+                                             paths, next_chunk, s))
+    if (lanes_w == 1) return BQ_CHUB(1);
+    if (lanes_w == 2) return BQ_CHUB(2);
+    return BQ_CHUB(4);
+#undef BQ_CHUB
+}
+
 // Group the walks by start vertex into (sid, sst); cursor[n] = valid walks.
 int group_by_start(const DeviceGraph &g, const uint32_t *starts, uint64_t n_walks, uint32_t *counts, uint32_t *cursor,
                    uint32_t *sid, uint32_t *sst, uint32_t *status, void *scan_ws, size_t scan_ws_bytes,
@@ -532,6 +721,9 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
         auto *next_chunk = reinterpret_cast<unsigned long long *>(scratch + bouquet_counter_offset(g.n, n_walks));
         BQ_CUDA(cudaMemsetAsync(next_chunk, 0, sizeof(unsigned long long), s));
         const bool launched = with_edges(g, [&](auto el) {
+            if (g.hub_cluster > 1)
+                return launch_cluster_hub(el, g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits,
+                                          paths, next_chunk, lanes_w, s) ? 1 : 0;
             return launch_hub(el, g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths,
                               next_chunk, lanes_w, s) ? 1 : 0;
         });

@@ -142,6 +142,37 @@ def test_every_graph_layout_bit_exact(env, layout, hub_slots):
         bq.set_tuning(**old)
 
 
+@pytest.mark.parametrize("hub_cluster", [2, 4, 8])
+@pytest.mark.parametrize("layout", [1, 2, 5])
+def test_cluster_hub_table_bit_exact(env, layout, hub_cluster):
+    """The hub table spread over a thread-block cluster (distributed shared
+    memory): same visits and paths as the oracle for every sampler, with the
+    start counted, for every lane count."""
+    bq, torch = env
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(layout=layout, hub_slots=2048, hub_cluster=hub_cluster)
+        for name in ("rmat12", "isolated", "cycle10"):
+            g = GRAPHS[name]
+            graph = bq.Graph.from_csr(g)
+            rng = np.random.default_rng(hub_cluster)
+            starts = rng.integers(0, g.n, 30011).astype(np.uint32)
+            st = dev_u32(torch, starts)
+            for sampler in (None, (1, 5, 32), (2, 0, 1)):
+                want_v, want_p = oracle.walk_batch(g, 43, starts, 13, sampler=sampler,
+                                                   include_start=True, want_paths=True)
+                for lanes in (1, 2, 4):
+                    bq.set_tuning(walk_lanes=lanes)
+                    paths = torch.zeros((starts.size, 14), dtype=torch.int32, device="cuda")
+                    vis = bq.walk_batch(graph, 43, st, 13, sampler=sampler, visit_start=True, paths=paths)
+                    bq.sync()
+                    assert np.array_equal(host_u32(vis), want_v), (name, sampler, lanes)
+                    assert np.array_equal(host_u32(paths), want_p), (name, sampler, lanes)
+            graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
 def test_host_io_matches_device(env):
     bq, torch = env
     g = GRAPHS["gnp60"]

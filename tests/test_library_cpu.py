@@ -76,8 +76,17 @@ def test_tuning_roundtrip_and_validation(lib):
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
                                    "layout": old["layout"], "hub_slots": old["hub_slots"],
-                                   "l2_hints": old["l2_hints"], "aesc_hub": old["aesc_hub"]}
+                                   "l2_hints": old["l2_hints"], "aesc_hub": old["aesc_hub"],
+                                   "hub_cluster": old["hub_cluster"]}
         assert old["aesc_hub"] == 0  # off by default
+        for ok in (1, 2, 4, 8):
+            bq.set_tuning(hub_cluster=ok)
+            assert bq.get_tuning()["hub_cluster"] == ok
+        bq.set_tuning(hub_cluster=0)
+        assert bq.get_tuning()["hub_cluster"] == 1  # 0 means one CTA
+        for bad in (3, 16):
+            with pytest.raises(bq.BouquetError):
+                bq.set_tuning(hub_cluster=bad)
         bq.set_tuning(aesc_hub=1)
         assert bq.get_tuning()["aesc_hub"] == 1
         with pytest.raises(bq.BouquetError):
