@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -511,6 +512,57 @@ void plan_scheduled_edge(double s_e, double eps, const bq_schedule &sched, uint3
     if (nw < (double)sched.n_min) nw = (double)sched.n_min;
 }
 
+// Run f(begin, end) over [0, count) on up to 16 host threads (one thread
+// for small counts).
+template <typename F>
+void parallel_ranges(uint64_t count, F &&f) {
+    unsigned threads = std::thread::hardware_concurrency();
+    if (threads < 1) threads = 1;
+    if (threads > 16) threads = 16;
+    if (count < (1u << 16) || threads == 1) {
+        f((uint64_t)0, count);
+        return;
+    }
+    std::vector<std::thread> pool;
+    const uint64_t per = (count + threads - 1) / threads;
+    for (unsigned i = 0; i < threads; ++i) {
+        const uint64_t b = (uint64_t)i * per, e = std::min(count, b + per);
+        if (b >= e) break;
+        pool.emplace_back([&f, b, e] { f(b, e); });
+    }
+    for (auto &t : pool) t.join();
+}
+
+// The canonical pairs {u, v}, u < v, of every edge in row order (the
+// library's edge numbering), built in two parallel passes over the rows;
+// false when the rows are not symmetric.
+bool canonical_pairs_host(const bq_graph *g, std::vector<uint32_t> &canon) {
+    const uint64_t n = g->n;
+    std::vector<uint64_t> start(n + 1, 0);
+    parallel_ranges(n, [&](uint64_t b, uint64_t e) {
+        for (uint64_t u = b; u < e; ++u) {
+            uint64_t c = 0;
+            for (int64_t j = g->h_offsets[u]; j < g->h_offsets[u + 1]; ++j) c += g->h_nbrs[j] > u ? 1 : 0;
+            start[u + 1] = c;
+        }
+    });
+    for (uint64_t u = 0; u < n; ++u) start[u + 1] += start[u];
+    if (start[n] != g->nnz / 2) return false;
+    canon.resize(2 * start[n]);
+    parallel_ranges(n, [&](uint64_t b, uint64_t e) {
+        for (uint64_t u = b; u < e; ++u) {
+            uint64_t p = start[u];
+            for (int64_t j = g->h_offsets[u]; j < g->h_offsets[u + 1]; ++j)
+                if (g->h_nbrs[j] > u) {
+                    canon[2 * p] = (uint32_t)u;
+                    canon[2 * p + 1] = g->h_nbrs[j];
+                    ++p;
+                }
+        }
+    });
+    return true;
+}
+
 }  // namespace bq
 
 extern "C" {
@@ -542,46 +594,71 @@ int bq_aesc_plan(bq_graph *g, const uint32_t *edges_uv, uint64_t k, double eps, 
     const double log_term = plan_mode == BQ_PLAN_CERTIFIED ? log(2.0 * (double)m / delta) : 0.0;
     // all-edges plan: canonical order = rows in order, neighbours above the row
     std::vector<uint32_t> canon;
-    if (!edges_uv) {
-        canon.reserve(2 * m);
-        for (uint32_t u = 0; u < g->n; ++u)
-            for (int64_t j = g->h_offsets[u]; j < g->h_offsets[u + 1]; ++j)
-                if (g->h_nbrs[j] > u) {
-                    canon.push_back(u);
-                    canon.push_back(g->h_nbrs[j]);
-                }
-        if (canon.size() != 2 * k) return fail(BQ_EGRAPH, "graph is not symmetric");
-    }
+    if (!edges_uv && !canonical_pairs_host(g, canon)) return fail(BQ_EGRAPH, "graph is not symmetric");
     const uint32_t *pairs = edges_uv ? edges_uv : canon.data();
-    for (uint64_t q = 0; q < k; ++q) {
-        const uint32_t a = pairs[2 * q], b = pairs[2 * q + 1];
-        if (edges_uv && (a >= g->n || b >= g->n || a == b || find_in_row(g, a, b) < 0))
-            return fail(BQ_ENOEDGE, "query %llu: (%u, %u) is not an edge", (unsigned long long)q, a, b);
-        const double du = (double)(g->h_offsets[a + 1] - g->h_offsets[a]);
-        const double dv = (double)(g->h_offsets[b + 1] - g->h_offsets[b]);
-        const double s_e = 1.0 / du + 1.0 / dv;
-        uint32_t t = 1;
-        double nw = 0.0;
-        if (plan_mode == BQ_PLAN_CERTIFIED) {
-            const uint32_t tau_cap = 1u << 20;
-            while ((g->omega ? trunc_bound_omega(g, a, b, s_e, t) : s_e * trunc_factor(g->lambda2, g->lambda_neg, t)) >
-                   eps / 2.0) {
-                if (t >= tau_cap)
-                    return fail(BQ_EOVERFLOW, "query %llu: truncation length exceeds %u", (unsigned long long)q,
-                                tau_cap);
-                ++t;
+    // per-edge plans on host threads; each range stops at its first failing
+    // query, and the lowest failing query is reported (as a serial loop would)
+    struct PlanError {
+        uint64_t q = UINT64_MAX;
+        int kind = 0;  // 0 not an edge, 1 tau cap, 2 2 N tau >= 2^32
+        uint32_t a = 0, b = 0;
+        double value = 0.0;
+    };
+    const uint32_t tau_cap = 1u << 20;
+    std::mutex err_mutex;
+    PlanError first;
+    parallel_ranges(k, [&](uint64_t begin, uint64_t end) {
+        PlanError err;
+        for (uint64_t q = begin; q < end && err.q == UINT64_MAX; ++q) {
+            const uint32_t a = pairs[2 * q], b = pairs[2 * q + 1];
+            if (edges_uv && (a >= g->n || b >= g->n || a == b || find_in_row(g, a, b) < 0)) {
+                err.q = q;
+                err.kind = 0;
+                err.a = a;
+                err.b = b;
+                break;
             }
-            const double half = (double)t - 0.5;
-            nw = ceil(8.0 * half * half * s_e * s_e * log_term / (eps * eps));
-        } else {
-            plan_scheduled_edge(s_e, eps, *sched, t, nw);
+            const double du = (double)(g->h_offsets[a + 1] - g->h_offsets[a]);
+            const double dv = (double)(g->h_offsets[b + 1] - g->h_offsets[b]);
+            const double s_e = 1.0 / du + 1.0 / dv;
+            uint32_t t = 1;
+            double nw = 0.0;
+            if (plan_mode == BQ_PLAN_CERTIFIED) {
+                while ((g->omega ? trunc_bound_omega(g, a, b, s_e, t)
+                                 : s_e * trunc_factor(g->lambda2, g->lambda_neg, t)) > eps / 2.0) {
+                    if (t >= tau_cap) {
+                        err.q = q;
+                        err.kind = 1;
+                        break;
+                    }
+                    ++t;
+                }
+                if (err.q != UINT64_MAX) break;
+                const double half = (double)t - 0.5;
+                nw = ceil(8.0 * half * half * s_e * s_e * log_term / (eps * eps));
+            } else {
+                plan_scheduled_edge(s_e, eps, *sched, t, nw);
+            }
+            if (nw < 1.0) nw = 1.0;
+            if (nw * 2.0 * (double)t >= 4294967296.0) {
+                err.q = q;
+                err.kind = 2;
+                err.value = nw * 2.0 * (double)t;
+                break;
+            }
+            tau[q] = t;
+            nwalks[q] = (uint32_t)nw;
         }
-        if (nw < 1.0) nw = 1.0;
-        if (nw * 2.0 * (double)t >= 4294967296.0)
-            return fail(BQ_EOVERFLOW, "query %llu: 2 * N * tau = %.3g reaches 2^32", (unsigned long long)q,
-                        nw * 2.0 * (double)t);
-        tau[q] = t;
-        nwalks[q] = (uint32_t)nw;
+        if (err.q != UINT64_MAX) {
+            std::lock_guard<std::mutex> lock(err_mutex);
+            if (err.q < first.q) first = err;
+        }
+    });
+    if (first.q != UINT64_MAX) {
+        const unsigned long long q = (unsigned long long)first.q;
+        if (first.kind == 0) return fail(BQ_ENOEDGE, "query %llu: (%u, %u) is not an edge", q, first.a, first.b);
+        if (first.kind == 1) return fail(BQ_EOVERFLOW, "query %llu: truncation length exceeds %u", q, tau_cap);
+        return fail(BQ_EOVERFLOW, "query %llu: 2 * N * tau = %.3g reaches 2^32", q, first.value);
     }
     return BQ_OK;
 }
@@ -609,15 +686,7 @@ int bq_aesc_plan_pilot(bq_graph *g, uint64_t seed, const uint32_t *edges_uv, uin
             return fail(BQ_EOVERFLOW, "query %llu: 2 * n_pilot * tau reaches 2^32", (unsigned long long)q);
     // explicit pairs (canonical order when edges_uv is NULL)
     std::vector<uint32_t> canon;
-    if (!edges_uv) {
-        canon.reserve(2 * k);
-        for (uint32_t u = 0; u < g->n; ++u)
-            for (int64_t j = g->h_offsets[u]; j < g->h_offsets[u + 1]; ++j)
-                if (g->h_nbrs[j] > u) {
-                    canon.push_back(u);
-                    canon.push_back(g->h_nbrs[j]);
-                }
-    }
+    if (!edges_uv && !canonical_pairs_host(g, canon)) return fail(BQ_EGRAPH, "graph is not symmetric");
     const uint32_t *pairs = edges_uv ? edges_uv : canon.data();
     std::vector<uint32_t> n0(k, n_pilot);
     DeviceGuard guard(g->device);

@@ -179,6 +179,33 @@ def test_scheduled_plan_matches_oracle(env):
         graph.close()
 
 
+def test_large_plan_on_host_threads(env):
+    """Plans of about 1M edges run on host threads: the same arrays as the
+    oracle's, for a subset and for all edges, and of two bad pairs the lower
+    index is the one reported."""
+    bq, torch = env
+    from workloads import chung_lu
+    g = chung_lu(200000, 10.0, 2.1, 8)
+    graph = bq.Graph.from_csr(g)
+    uv = all_edges(g)
+    sched = bq.Schedule(SCHEDULE[0], SCHEDULE[1], SCHEDULE[2], SCHEDULE[3], SCHEDULE[4], 0)
+    otau, onw = oracle.plan_scheduled(g, uv, 0.05, *SCHEDULE)
+    tau, nw = bq.aesc_plan(graph, None, 0.05, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+    assert np.array_equal(tau, otau) and np.array_equal(nw, onw)
+    rev = np.ascontiguousarray(uv[::-1, ::-1])
+    tau, nw = bq.aesc_plan(graph, rev, 0.05, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+    assert np.array_equal(tau, otau[::-1]) and np.array_equal(nw, onw[::-1])
+    bad = rev.copy()
+    row0 = set(g.row(0).tolist())
+    non = next(x for x in range(1, g.n) if x not in row0)
+    bad[uv.shape[0] - 7] = (0, non)
+    bad[uv.shape[0] // 3] = (0, non)
+    with pytest.raises(bq.BouquetError) as ei:
+        bq.aesc_plan(graph, bad, 0.05, 0.01, mode=bq.PLAN_SCHEDULED, schedule=sched)
+    assert ei.value.code == bq.ENOEDGE and f"query {uv.shape[0] // 3}:" in str(ei.value)
+    graph.close()
+
+
 def test_powerlaw_full_size_sampled(env):
     """Chung-Lu n=4M, mean degree 10, exponent 2.1, largest component: all
     edges estimated on the GPU with the scheduled plan at eps=0.05, in the
