@@ -144,7 +144,15 @@ int bq_graph_set_eigvecs(bq_graph *g, uint32_t omega, const double *lambdas, con
                                  top t bits of their random word at the same
                                  (step, vertex): similar walks stay together
                                  (the aim of SABA, Sec. 3.3), each walk still
-                                 an exact random walk */
+                                 an exact random walk.  The walks of a group
+                                 are correlated (at a vertex of degree <=
+                                 2^t the whole group takes the same step), so
+                                 an AESC estimate over N walks has about the
+                                 variance of N / width independent ones: for
+                                 the certified plan's guarantee use width x
+                                 its N (the groups are then the independent
+                                 samples, each group mean bounded like one
+                                 sample) */
 #define BQ_SAMPLER_SABA 2u    /* walk batches only, for comparison: Eq.
                                  select-proposed taken literally, r = X_W xor
                                  h(cur, l) with X_W the walk's fixed 32-bit

@@ -182,3 +182,25 @@ def test_literal_saba_word_is_per_walk_and_not_for_aesc():
     if uv is not None:
         with pytest.raises(oracle.OracleError):
             oracle.aesc_counts(g, 1, uv, np.array([3], np.uint32), np.array([4], np.uint32), sampler=(2, 0, 1))
+
+
+def test_coupled_groups_are_the_independent_samples():
+    """Coupled walks of a group move together where the degree is below 2^t,
+    so an AESC estimate over N coupled walks varies like one over N / width
+    independent walks; with width x N walks the certified plan's eps
+    contract holds again (the groups are the independent samples)."""
+    from workloads import all_edges, complete, diamond
+    g = gnp_connected(12, 0.4, 5)
+    uv = all_edges(g)[:3]
+    tau = np.full(uv.shape[0], 3, np.uint32)
+    nw = np.full(uv.shape[0], 256, np.uint32)
+    ind = np.array([oracle.aesc_estimate(g, s, uv, tau, nw)[1] for s in range(200)])
+    cpl = np.array([oracle.aesc_estimate(g, s, uv, tau, nw, (1, 8, 32))[1] for s in range(200)])
+    ratio = cpl.var(axis=0, ddof=1) / ind.var(axis=0, ddof=1)
+    assert np.all(ratio > 16) and np.all(ratio < 64), ratio
+    for h, eps in ((complete(8), 0.1), (diamond(), 0.1), (gnp_connected(10, 0.5, 3), 0.1)):
+        uv = all_edges(h)
+        _, l2, lneg = exact.spectrum(h)
+        tau, nw = oracle.plan_certified(h, uv, eps, 0.01, l2, lneg)
+        _, sc = oracle.aesc_estimate(h, 7, uv, tau, (nw * 32).astype(np.uint32), (1, 8, 32))
+        assert np.max(np.abs(sc - exact.sc_pinv(h, uv))) <= eps
