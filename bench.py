@@ -305,7 +305,8 @@ def aesc_measure(bq, torch, steps, warmup):
     ms = sum(lat) / len(lat)
     kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
     return {
-        "workload": "er1000_m5000_path, all 5990 edges, eps=0.1, delta=0.01, certified",
+        "workload": f"G(n=1000, m=5000) seed 1 plus a spanning path (m={g.m}), all edges, eps=0.1, "
+                    "delta=0.01, certified plan",
         "edges": int(tau.size), "edges_per_s": tau.size / (ms / 1e3),
         "walk_steps_per_call": steps_per_call,
         "walk_steps_per_s": steps_per_call / (ms / 1e3),
