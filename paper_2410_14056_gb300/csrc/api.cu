@@ -221,7 +221,7 @@ using namespace bq;
 
 extern "C" {
 
-const char *bq_version(void) { return "bouquet-gb300 0.1"; }
+const char *bq_version(void) { return "bouquet-gb300 0.2"; }
 
 const char *bq_last_error(void) { return g_last_error; }
 
