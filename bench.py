@@ -61,6 +61,8 @@ def parse():
                     help="batched workload: use the first N graphs of the 256-graph mix")
     ap.add_argument("--walk-lanes", type=int, default=None)
     ap.add_argument("--aggregate", type=int, default=None)
+    ap.add_argument("--no-relabel", action="store_true",
+                    help="walk the R-MAT graph without its degree-relabelled copy (hashed hub table)")
     return ap.parse_args()
 
 
@@ -101,24 +103,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-WALK_KERNEL_SOURCES = ("walks.cu", "internal.h", "hash.cuh", "edges.cuh")
+# the sources each walk kernel (and the layout it reads) is built from
+WALK_KERNEL_SOURCES = {
+    "walk_hub_kernel": ("walks.cu", "internal.h", "hash.cuh", "edges.cuh"),
+    "walk_relabel_kernel": ("walks.cu", "internal.h", "hash.cuh", "edges.cuh", "graph.cu"),
+}
 
 
-def walk_kernel_digest() -> str:
+def walk_kernel_digest(kernel: str = "walk_hub_kernel") -> str:
     """sha256 (16 hex digits) of the sources the walk kernel is built from."""
     h = hashlib.sha256()
-    for name in WALK_KERNEL_SOURCES:
+    for name in WALK_KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2410_14056_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
-def walk_kernel_traffic():
-    """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
-    prof = os.path.join(ROOT, "profiles", "walk_hub_kernel_rmat20.md")
+def walk_kernel_traffic(kernel: str = "walk_hub_kernel"):
+    """dram bytes per launch from the committed ncu summary of `kernel`, if it
+    was taken on the current kernel sources (else None)."""
+    if kernel not in WALK_KERNEL_SOURCES:
+        return None
+    prof = os.path.join(ROOT, "profiles", f"{kernel}_rmat20.md")
     if not os.path.exists(prof):
         return None
-    digest = walk_kernel_digest()
+    digest = walk_kernel_digest(kernel)
     vals = {}
     for line in open(prof):
         if ":" in line and line.strip().startswith("- "):
@@ -584,7 +592,14 @@ def run_ours(args):
     g = rmat20()
     seed, start_seed = rank_seeds(rank)
     starts = uniform_starts(g, N_WALKS, start_seed)
+    # the walk graph gets the degree-relabelled copy (hubs found by id; measured
+    # 8.81 against 8.96 ms per launch); the other graphs of the run do not
+    relabel_before = bq.get_tuning()["hub_relabel"]
+    bq.set_tuning(hub_relabel=0 if args.no_relabel else 1)
     graph = bq.Graph.from_csr(g)
+    bq.set_tuning(hub_relabel=relabel_before)
+    walk_kernel = ("walk_relabel_kernel" if not args.no_relabel and graph.info()["layout"] == 5
+                   else "walk_hub_kernel" if bq.get_tuning()["hub_slots"] else "walk_bouquet_kernel")
     st = torch.from_numpy(starts.view(np.int32)).cuda()
     visits = torch.zeros(g.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -638,10 +653,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     algo_bytes = BYTES_PER_STEP * steps_per_batch
     achieved = algo_bytes / (walk_ms / 1e3) / 1e9
-    traffic = walk_kernel_traffic()
+    traffic = walk_kernel_traffic(walk_kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "walk_hub_kernel" if bq.get_tuning()["hub_slots"] else "walk_bouquet_kernel",
+                "kernel": walk_kernel,
                 "kernel_ms": walk_ms,
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
@@ -686,6 +701,7 @@ def run_ours(args):
                        "n_walks_per_gpu": N_WALKS, "n_steps": N_STEPS,
                        "starts": "uniform over non-isolated vertices (seeded)",
                        "mode": "BOUQUET, independent sampler", "tuning": bq.get_tuning(),
+                       "walk_kernel": walk_kernel,
                        "autotune": autotune,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (each GPU its own batch)"},

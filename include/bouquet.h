@@ -566,6 +566,17 @@ typedef struct bq_tuning {
                                   20 the walk kernel took 14.8 / 21.7 / 30.9 ms
                                   with clusters of 2 / 4 / 8 against 9.0 ms).
                                   Never changes a result. */
+    uint32_t hub_relabel;      /* 1: graphs created from now on with bit-packed
+                                  ids also get a copy relabelled by degree for
+                                  the walk batch: the highest-degree vertices
+                                  (as many as 12 bytes each fit in hub_slots *
+                                  16 bytes of shared memory, 10,922 by
+                                  default) take internal ids 0.., so a step
+                                  finds a hub by comparing its id, with no
+                                  hash; the others read a 16-byte record
+                                  {row offset, degree, original id}.  Rows
+                                  keep their neighbour order, so results never
+                                  change.  0 (default): no copy. */
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

@@ -61,7 +61,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("walk_lanes", ctypes.c_uint32), ("aggregate_visits", ctypes.c_uint32),
                 ("aesc_lanes", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("hub_slots", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
-                ("aesc_hub", ctypes.c_uint32), ("hub_cluster", ctypes.c_uint32)]
+                ("aesc_hub", ctypes.c_uint32), ("hub_cluster", ctypes.c_uint32),
+                ("hub_relabel", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -674,7 +675,8 @@ def get_tuning() -> dict:
     _check(load_library().bq_get_tuning(ctypes.byref(t)))
     return {"walk_lanes": t.walk_lanes, "aggregate_visits": t.aggregate_visits,
             "aesc_lanes": t.aesc_lanes, "layout": t.layout, "hub_slots": t.hub_slots,
-            "l2_hints": t.l2_hints, "aesc_hub": t.aesc_hub, "hub_cluster": t.hub_cluster}
+            "l2_hints": t.l2_hints, "aesc_hub": t.aesc_hub, "hub_cluster": t.hub_cluster,
+            "hub_relabel": t.hub_relabel}
 
 
 def set_tuning(**kw):
@@ -682,7 +684,7 @@ def set_tuning(**kw):
     cur.update(kw)
     t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]),
                int(cur["layout"]), int(cur["hub_slots"]), int(cur["l2_hints"]), int(cur["aesc_hub"]),
-               int(cur["hub_cluster"]))
+               int(cur["hub_cluster"]), int(cur["hub_relabel"]))
     _check(load_library().bq_set_tuning(ctypes.byref(t)))
 
 

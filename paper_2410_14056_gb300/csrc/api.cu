@@ -28,6 +28,7 @@ std::atomic<int> g_aesc_walks_per_lane{4};
 std::atomic<int> g_edge_records{1};
 std::atomic<int> g_hub_slots{8192};
 std::atomic<int> g_hub_cluster{1};
+std::atomic<int> g_hub_relabel{0};
 std::atomic<int> g_l2_hints{0};
 std::atomic<int> g_aesc_hub{0};
 }  // namespace
@@ -148,6 +149,7 @@ int tuning_aesc_walks_per_lane() { return g_aesc_walks_per_lane.load(); }
 int tuning_layout() { return g_edge_records.load(); }
 int tuning_hub_slots() { return g_hub_slots.load(); }
 int tuning_hub_cluster() { return g_hub_cluster.load(); }
+bool tuning_hub_relabel() { return g_hub_relabel.load() != 0; }
 bool tuning_l2_hints() { return g_l2_hints.load() != 0; }
 bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
 
@@ -326,6 +328,10 @@ int bq_graph_destroy(bq_graph *g) {
     cudaFree(g->d_edge8);
     cudaFree(g->d_edge16);
     cudaFree(g->d_pk);
+    cudaFree(g->d_rl_pk);
+    cudaFree(g->d_rl_rec);
+    cudaFree(g->d_rl_rec8);
+    cudaFree(g->d_rl_new);
     cudaFree(g->d_hub_tag);
     delete g;
     return BQ_OK;
@@ -898,6 +904,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->l2_hints = (uint32_t)g_l2_hints.load();
     out->aesc_hub = (uint32_t)g_aesc_hub.load();
     out->hub_cluster = (uint32_t)g_hub_cluster.load();
+    out->hub_relabel = (uint32_t)g_hub_relabel.load();
     return BQ_OK;
 }
 
@@ -915,6 +922,7 @@ int bq_set_tuning(const bq_tuning *in) {
     if (in->aesc_hub > 1) return fail(BQ_EINVAL, "aesc_hub must be 0 or 1");
     const uint32_t c = in->hub_cluster;
     if (c != 0 && c != 1 && c != 2 && c != 4 && c != 8) return fail(BQ_EINVAL, "hub_cluster must be 0, 1, 2, 4 or 8");
+    if (in->hub_relabel > 1) return fail(BQ_EINVAL, "hub_relabel must be 0 or 1");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
@@ -923,6 +931,7 @@ int bq_set_tuning(const bq_tuning *in) {
     g_l2_hints.store((int)in->l2_hints);
     g_aesc_hub.store((int)in->aesc_hub);
     g_hub_cluster.store(c < 1 ? 1 : (int)c);
+    g_hub_relabel.store((int)in->hub_relabel);
     return BQ_OK;
 }
 

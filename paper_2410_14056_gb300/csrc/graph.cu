@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -301,6 +302,45 @@ __global__ void build_packed_ids_kernel(const uint32_t *__restrict__ nbrs, uint6
     }
 }
 
+// Degree-relabelled copy: the entries of internal row x (original vertex
+// orig[x]) as internal ids, in the original order, at the row's new place.
+// One warp per row.
+__global__ void relabel_rows_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ nbrs,
+                                    const uint32_t *__restrict__ orig, const uint32_t *__restrict__ new_of,
+                                    const int64_t *__restrict__ off_new, uint32_t n, uint32_t *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = warp; x < n; x += nwarps) {
+        const uint32_t v = orig[x];
+        const int64_t lo = off[v], d = off[v + 1] - lo, dst = off_new[x];
+        for (int64_t i = lane; i < d; i += 32) out[dst + i] = new_of[nbrs[lo + i]];
+    }
+}
+
+// rec8[x] = original id | row offset << sh_off | degree << sh_deg of
+// internal vertex x (hubs' degrees need not fit: they are read from rec).
+__global__ void relabel_rec8_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ orig,
+                                    const int64_t *__restrict__ off_new, uint32_t n, uint32_t hubs, uint32_t sh_off,
+                                    uint32_t sh_deg, uint64_t *__restrict__ rec8) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = orig[x];
+        const uint64_t d = x < hubs ? 0ull : (uint64_t)(off[v + 1] - off[v]);
+        rec8[x] = (uint64_t)v | ((uint64_t)off_new[x] << sh_off) | (d << sh_deg);
+    }
+}
+
+// rec[x] = {row offset, degree, original id, 0} of internal vertex x.
+__global__ void relabel_records_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ orig,
+                                       const int64_t *__restrict__ off_new, uint32_t n, uint4 *__restrict__ rec) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = orig[x];
+        rec[x] = make_uint4((uint32_t)off_new[x], (uint32_t)(off[v + 1] - off[v]), v, 0u);
+    }
+}
+
 // Hub table: every vertex with a neighbour bids for slot hash(v); the highest
 // degree wins (ties: the smaller id).  key = degree << 32 | (2^32 - 1 - v).
 __global__ void hub_select_kernel(const int64_t *__restrict__ off, uint32_t n, uint32_t slots,
@@ -353,6 +393,75 @@ int scan_u32_to_u64_ws(const uint32_t *in, uint64_t *out, uint64_t n, void *ws, 
 
 int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
     return scan_ws_impl<uint32_t, uint32_t>(in, out, n, (char *)ws, ws_bytes, s);
+}
+
+// The degree-relabelled copy of a packed-id graph (bq_tuning.hub_relabel):
+// the top H vertices by (degree desc, id asc), H = as many 12-byte hub
+// entries as hub_slots * 16 bytes of shared memory hold, take internal ids
+// 0..H-1 in increasing original id, the others H.. in increasing original id.
+int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cudaStream_t s) {
+    const uint32_t n = g->n;
+    std::vector<int64_t> off(n + 1);
+    BQ_CUDA(cudaMemcpy(off.data(), g->d_offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> cand;
+    for (uint32_t v = 0; v < n; ++v)
+        if (off[v + 1] > off[v]) cand.push_back(v);
+    const uint64_t cap = ((uint64_t)tuning_hub_slots() * 16 - 4) / 12;
+    const uint32_t hubs = (uint32_t)std::min<uint64_t>(cap, cand.size());
+    if (hubs == 0) return BQ_OK;
+    auto deg = [&](uint32_t v) { return off[v + 1] - off[v]; };
+    std::nth_element(cand.begin(), cand.begin() + (hubs - 1), cand.end(), [&](uint32_t a, uint32_t b) {
+        return deg(a) != deg(b) ? deg(a) > deg(b) : a < b;
+    });
+    std::vector<uint8_t> is_hub(n, 0);
+    for (uint32_t i = 0; i < hubs; ++i) is_hub[cand[i]] = 1;
+    std::vector<uint32_t> new_of(n), orig(n);
+    uint32_t next_hub = 0, next_other = hubs;
+    for (uint32_t v = 0; v < n; ++v) {
+        new_of[v] = is_hub[v] ? next_hub++ : next_other++;
+        orig[new_of[v]] = v;
+    }
+    std::vector<int64_t> off_new(n + 1);
+    off_new[0] = 0;
+    for (uint32_t x = 0; x < n; ++x) off_new[x + 1] = off_new[x] + deg(orig[x]);
+    // 8-byte records when id, offset and the largest non-hub degree fit
+    int64_t max_other = 0;
+    for (uint32_t x = hubs; x < n; ++x) max_other = std::max<int64_t>(max_other, deg(orig[x]));
+    const uint32_t b_id = bits_for(n > 0 ? n - 1 : 0), b_off = bits_for(g->nnz), b_deg = bits_for(max_other);
+    if (b_id + b_off + b_deg > 64) return BQ_OK;  // no relabelled copy
+    uint32_t *d_orig = nullptr, *d_tmp = nullptr;
+    int64_t *d_off_new = nullptr;
+    cudaError_t e = cudaMalloc(&g->d_rl_new, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_rl_rec, sizeof(uint4) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_rl_rec8, sizeof(uint64_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_rl_pk, sizeof(uint4) * chunks);
+    if (e == cudaSuccess) e = cudaMalloc(&d_orig, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_off_new, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_tmp, sizeof(uint32_t) * g->nnz);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_rl_new, new_of.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_orig, orig.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_off_new, off_new.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        relabel_rows_kernel<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(g->d_offsets, g->d_nbrs, d_orig,
+                                                                           g->d_rl_new, d_off_new, n, d_tmp);
+        build_packed_ids_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(d_tmp, g->nnz, bits, q, chunks, g->d_rl_pk);
+        relabel_records_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, d_orig, d_off_new, n, g->d_rl_rec);
+        relabel_rec8_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, d_orig, d_off_new, n, hubs, b_id,
+                                                             b_id + b_off, g->d_rl_rec8);
+        e = cudaStreamSynchronize(s);
+    }
+    cudaFree(d_orig);
+    cudaFree(d_off_new);
+    cudaFree(d_tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "degree-relabelled copy");
+    g->rl_hubs = hubs;
+    g->rl_sh_off = b_id;
+    g->rl_sh_deg = b_id + b_off;
+    g->rl_mask_id = b_id >= 32 ? 0xffffffffu : ((1u << b_id) - 1u);
+    g->rl_mask_off = b_off >= 64 ? ~0ull : ((1ull << b_off) - 1ull);
+    g->device_bytes += sizeof(uint32_t) * n + sizeof(uint4) * n + sizeof(uint64_t) * n + sizeof(uint4) * chunks;
+    return BQ_OK;
 }
 
 int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
@@ -511,6 +620,10 @@ int graph_build(bq_graph *g, uint32_t flags, cudaStream_t s) {
                 if (e != cudaSuccess) {
                     rc = cuda_fail(e, "build_packed_ids_kernel");
                     goto done;
+                }
+                if (tuning_hub_relabel() && tuning_hub_slots() > 0) {
+                    rc = build_relabelled(g, bits, q, chunks, s);
+                    if (rc) goto done;
                 }
             }
         }

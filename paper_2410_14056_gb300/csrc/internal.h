@@ -76,6 +76,19 @@ struct DeviceGraph {
     const uint32_t *hub_tag;
     uint32_t hub_slots;    // slots in all (hub_slot over this count)
     uint32_t hub_cluster;  // CTAs sharing the table (1: one CTA holds it)
+    // Degree-relabelled copy for the walk batch (null if not built): internal
+    // id x < rl_hubs are the rl_hubs highest-degree vertices, the others
+    // follow, each group in increasing original id; rows keep the original
+    // neighbour order.  rl_new[v] = internal id of original v; rl_rec[x] =
+    // {row offset, degree, original id, 0}; rl_pk = the rows' internal ids
+    // packed as `pk`.
+    const uint4 *rl_pk;
+    const uint4 *rl_rec;     // hubs' records (read when a block fills its table)
+    const uint64_t *rl_rec8; // every vertex: id | offset << rl_sh_off | degree << rl_sh_deg
+    const uint32_t *rl_new;
+    uint32_t rl_hubs;
+    uint32_t rl_sh_off, rl_sh_deg, rl_mask_id;
+    uint64_t rl_mask_off;
     bool compact() const { return rec8 != nullptr; }
 };
 
@@ -157,6 +170,13 @@ struct bq_graph {
     uint32_t *d_hub_tag = nullptr;
     uint32_t hub_slots = 0;
     uint32_t hub_cluster = 1;
+    uint4 *d_rl_pk = nullptr;
+    uint4 *d_rl_rec = nullptr;
+    uint64_t *d_rl_rec8 = nullptr;
+    uint32_t *d_rl_new = nullptr;
+    uint32_t rl_hubs = 0;
+    uint32_t rl_sh_off = 0, rl_sh_deg = 0, rl_mask_id = 0;
+    uint64_t rl_mask_off = 0;
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
     uint64_t device_bytes = 0;
@@ -196,6 +216,15 @@ struct bq_graph {
         v.hub_tag = d_hub_tag;
         v.hub_slots = hub_slots;
         v.hub_cluster = hub_cluster;
+        v.rl_pk = d_rl_pk;
+        v.rl_rec = d_rl_rec;
+        v.rl_rec8 = d_rl_rec8;
+        v.rl_sh_off = rl_sh_off;
+        v.rl_sh_deg = rl_sh_deg;
+        v.rl_mask_id = rl_mask_id;
+        v.rl_mask_off = rl_mask_off;
+        v.rl_new = d_rl_new;
+        v.rl_hubs = rl_hubs;
         return v;
     }
 };
@@ -254,6 +283,7 @@ int tuning_aesc_walks_per_lane();
 int tuning_layout();    // graph layout built at creation (bq_tuning.layout)
 int tuning_hub_slots();  // hub table size built at creation (bq_tuning.hub_slots)
 int tuning_hub_cluster();  // CTAs a created graph's hub table is spread over
+bool tuning_hub_relabel();  // created packed-id graphs get the degree-relabelled copy
 bool tuning_l2_hints(); // L2 eviction policies on the walk kernel's loads
 bool tuning_aesc_hub();  // AESC counting reads hub records from shared memory
 

@@ -507,6 +507,125 @@ walk_cluster_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32
     }
 }
 
+// The bouquet walk on the degree-relabelled copy: internal ids 0..hubs-1
+// are the highest-degree vertices, so a step finds a hub by comparing its
+// internal id, with no hash and no tag.  Shared memory holds, per hub, its
+// row offset (the next hub's offset ends the row), original id and visit
+// count, 12 bytes; any other vertex's 16-byte record gives its row offset,
+// degree and original id, packed into 8 bytes.  The step word is drawn at the original id, and
+// rows keep their neighbour order, so every walk is the one the plain
+// kernels take.  Visits go to the original ids.
+template <int W, bool COUPLED>
+__global__ void __launch_bounds__(kHubThreads, 1)
+walk_relabel_kernel(EdgesPackedIds el, const uint4 *__restrict__ rl_rec, const uint64_t *__restrict__ rl_rec8,
+                    uint32_t sh_off, uint32_t sh_deg, uint32_t mask_id, uint64_t mask_off,
+                    const uint32_t *__restrict__ rl_new,
+                    uint32_t hubs, const uint32_t *__restrict__ sorted_id, const uint32_t *__restrict__ sorted_start,
+                    const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps, uint64_t seed, Sampler smp,
+                    bool visit_start, uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
+                    unsigned long long *__restrict__ next_chunk) {
+    extern __shared__ __align__(16) unsigned char hub_smem[];
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(hub_smem);  // hubs + 1
+    uint32_t *s_orig = s_off + hubs + 1;
+    uint32_t *s_cnt = s_orig + hubs;
+    for (uint32_t i = threadIdx.x; i < hubs; i += blockDim.x) {
+        const uint4 r = rl_rec[i];
+        s_off[i] = r.x;
+        s_orig[i] = r.z;
+        s_cnt[i] = 0;
+        if (i == hubs - 1) s_off[hubs] = r.x + r.y;
+    }
+    __syncthreads();
+
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t n_valid = *n_valid_ptr;
+    while (true) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(next_chunk, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const uint64_t base = chunk * 32ull * W;
+        if (base >= n_valid) break;
+
+        uint32_t x[W], orig[W], id[W], deg[W];
+        uint64_t off[W], st[W], gs[W];
+        uint32_t xw[W];  // the walk's fixed seed (literal SABA word only)
+        bool act[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint64_t p = base + (uint64_t)j * 32 + lane;
+            act[j] = p < n_valid;
+            id[j] = 0u;
+            orig[j] = 0u;
+            x[j] = 0u;
+            off[j] = 0;
+            deg[j] = 0;
+            if (act[j]) {
+                id[j] = sorted_id[p];
+                orig[j] = sorted_start[p];
+                x[j] = rl_new[orig[j]];
+                if (x[j] < hubs) {
+                    off[j] = s_off[x[j]];
+                    deg[j] = s_off[x[j] + 1] - s_off[x[j]];
+                } else {
+                    const uint64_t w = __ldg(reinterpret_cast<const unsigned long long *>(rl_rec8) + x[j]);
+                    off[j] = (w >> sh_off) & mask_off;
+                    deg[j] = (uint32_t)(w >> sh_deg);
+                }
+            }
+            st[j] = walk_key(seed, kBatchStream, id[j]);
+            gs[j] = COUPLED ? walk_key(seed, kBatchStream | kGroupBit, smp.t == kSabaT ? 0 : id[j] / smp.width)
+                            : 0ull;
+            xw[j] = (uint32_t)st[j];
+            if (act[j]) {
+                if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1)] = orig[j];
+                if (visit_start) {
+                    if (x[j] < hubs) atomicAdd(s_cnt + x[j], 1u);
+                    else atomicAdd(visits + orig[j], 1u);
+                }
+            }
+        }
+        for (uint32_t l = 1; l <= n_steps; ++l) {
+            bool moved[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                st[j] += kGolden;
+                if (COUPLED) gs[j] += kGolden;
+                moved[j] = deg[j] != 0;
+                if (moved[j]) {
+                    const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], orig[j], smp.t, xw[j]), deg[j]);
+                    x[j] = el.id(off[j] + k);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                if (!act[j]) continue;
+                if (x[j] < hubs) {
+                    atomicAdd(s_cnt + x[j], 1u);
+                    if (moved[j]) {
+                        off[j] = s_off[x[j]];
+                        deg[j] = s_off[x[j] + 1] - s_off[x[j]];
+                        orig[j] = s_orig[x[j]];
+                    }
+                } else {
+                    if (moved[j]) {
+                        const uint64_t w = __ldg(reinterpret_cast<const unsigned long long *>(rl_rec8) + x[j]);
+                        off[j] = (w >> sh_off) & mask_off;
+                        deg[j] = (uint32_t)(w >> sh_deg);
+                        orig[j] = (uint32_t)w & mask_id;
+                    }
+                    atomicAdd(visits + orig[j], 1u);
+                }
+                if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1) + l] = orig[j];
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < hubs; i += blockDim.x) {
+        const uint32_t c = s_cnt[i];
+        if (c) atomicAdd(visits + s_orig[i], c);
+    }
+}
+
 unsigned blocks_for(uint64_t items, uint64_t per_block) {
     uint64_t b = (items + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -668,6 +787,50 @@ bool launch_cluster_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const 
 #undef BQ_CHUB
 }
 
+// Launch the relabelled-copy kernel: one persistent block of kHubThreads per
+// SM; false (nothing launched) when the hub arrays do not fit.
+template <int W, bool COUPLED>
+bool launch_relabel_w(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+                      uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
+                      uint32_t *paths, unsigned long long *next_chunk, cudaStream_t s) {
+    const size_t smem = (size_t)12 * g.rl_hubs + 4;
+    auto kernel = walk_relabel_kernel<W, COUPLED>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kHubThreads, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const EdgesPackedIds el{g.rl_pk, nullptr, g.pk_bits, g.pk_q, g.pk_mask};
+    ProfScope prof(kProfWalk, s);
+    count_launches(1);
+    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec, g.rl_rec8, g.rl_sh_off, g.rl_sh_deg, g.rl_mask_id,
+                                                   g.rl_mask_off, g.rl_new, g.rl_hubs, sid, sst, n_valid, n_steps,
+                                                   seed, smp, visit_start, visits, paths, next_chunk);
+    return true;
+}
+
+bool launch_relabel(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+                    uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
+                    uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
+    const bool c = smp.kind == 1;
+#define BQ_RL(WW)                                                                                               \
+    (c ? launch_relabel_w<WW, true>(g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,        \
+                                    next_chunk, s)                                                               \
+       : launch_relabel_w<WW, false>(g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,       \
+                                     next_chunk, s))
+    if (lanes_w == 1) return BQ_RL(1);
+    if (lanes_w == 2) return BQ_RL(2);
+    return BQ_RL(4);
+#undef BQ_RL
+}
+
 // Group the walks by start vertex into (sid, sst); cursor[n] = valid walks.
 int group_by_start(const DeviceGraph &g, const uint32_t *starts, uint64_t n_walks, uint32_t *counts, uint32_t *cursor,
                    uint32_t *sid, uint32_t *sst, uint32_t *status, void *scan_ws, size_t scan_ws_bytes,
@@ -716,6 +879,15 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
         BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         saba_order_kernel<<<sms * 8, 256, 0, s>>>(counts, cursor, g.n, seed, sid);
         BQ_CUDA(cudaGetLastError());
+    }
+    if (g.rl_pk && !checked) {
+        auto *next_chunk = reinterpret_cast<unsigned long long *>(scratch + bouquet_counter_offset(g.n, n_walks));
+        BQ_CUDA(cudaMemsetAsync(next_chunk, 0, sizeof(unsigned long long), s));
+        if (launch_relabel(g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths, next_chunk,
+                           lanes_w, s)) {
+            BQ_CUDA(cudaGetLastError());
+            return BQ_OK;
+        }
     }
     if (g.hub_tag && !checked) {
         auto *next_chunk = reinterpret_cast<unsigned long long *>(scratch + bouquet_counter_offset(g.n, n_walks));

@@ -173,6 +173,40 @@ def test_cluster_hub_table_bit_exact(env, layout, hub_cluster):
         bq.set_tuning(**old)
 
 
+@pytest.mark.parametrize("hub_slots", [1024, 8192])
+def test_degree_relabelled_copy_bit_exact(env, hub_slots):
+    """The walk kernel on the degree-relabelled copy (hubs found by internal
+    id): same visits and paths as the oracle for every sampler and lane
+    count, with the start counted, on graphs with isolated vertices and on
+    graphs whose vertices are all hubs."""
+    bq, torch = env
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(layout=5, hub_slots=hub_slots, hub_relabel=1)
+        for name in ("rmat12", "isolated", "cycle10"):
+            g = GRAPHS[name]
+            graph = bq.Graph.from_csr(g)
+            rng = np.random.default_rng(hub_slots)
+            starts = rng.integers(0, g.n, 30011).astype(np.uint32)
+            st = dev_u32(torch, starts)
+            for sampler in (None, (1, 5, 32), (2, 0, 1)):
+                want_v, want_p = oracle.walk_batch(g, 47, starts, 13, sampler=sampler,
+                                                   include_start=True, want_paths=True)
+                for lanes in (1, 2, 4):
+                    bq.set_tuning(walk_lanes=lanes)
+                    paths = torch.zeros((starts.size, 14), dtype=torch.int32, device="cuda")
+                    vis = bq.walk_batch(graph, 47, st, 13, sampler=sampler, visit_start=True, paths=paths)
+                    bq.sync()
+                    assert np.array_equal(host_u32(vis), want_v), (name, sampler, lanes)
+                    assert np.array_equal(host_u32(paths), want_p), (name, sampler, lanes)
+                vis = bq.walk_batch(graph, 47, st, 13, sampler=sampler)
+                bq.sync()
+                assert np.array_equal(host_u32(vis), oracle.walk_batch(g, 47, starts, 13, sampler=sampler))
+            graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
 def test_host_io_matches_device(env):
     bq, torch = env
     g = GRAPHS["gnp60"]

@@ -77,7 +77,12 @@ def test_tuning_roundtrip_and_validation(lib):
         assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
                                    "layout": old["layout"], "hub_slots": old["hub_slots"],
                                    "l2_hints": old["l2_hints"], "aesc_hub": old["aesc_hub"],
-                                   "hub_cluster": old["hub_cluster"]}
+                                   "hub_cluster": old["hub_cluster"], "hub_relabel": old["hub_relabel"]}
+        bq.set_tuning(hub_relabel=1)
+        assert bq.get_tuning()["hub_relabel"] == 1
+        with pytest.raises(bq.BouquetError):
+            bq.set_tuning(hub_relabel=2)
+        bq.set_tuning(hub_relabel=0)
         assert old["aesc_hub"] == 0  # off by default
         for ok in (1, 2, 4, 8):
             bq.set_tuning(hub_cluster=ok)
