@@ -312,9 +312,11 @@ def aesc_measure(bq, torch, steps, warmup):
     bq.profile_enable(False)
     ms = sum(lat) / len(lat)
     kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
+    naive = aesc_naive_row(bq, torch, graph, dtau, dnw, counts, ms, steps, warmup)
     return {
         "workload": f"G(n=1000, m=5000) seed 1 plus a spanning path (m={g.m}), all edges, eps=0.1, "
                     "delta=0.01, certified plan",
+        "naive": naive,
         "edges": int(tau.size), "edges_per_s": tau.size / (ms / 1e3),
         "walk_steps_per_call": steps_per_call,
         "walk_steps_per_s": steps_per_call / (ms / 1e3),
@@ -323,6 +325,38 @@ def aesc_measure(bq, torch, steps, warmup):
         "count_kernel_ms": kern_ms,
         "count_kernel_gbs": steps_per_call * BYTES_PER_STEP / (kern_ms / 1e3) / 1e9,
     }
+
+
+def aesc_naive_row(bq, torch, graph, dtau, dnw, counts, bouquet_ms, steps, warmup):
+    """The same all-edges estimate with one walk per thread (BQ_AESC_NAIVE):
+    Alg. 2 per walk against the bouquets of Alg. 3, at the same eps and plan.
+    Its counters must equal the bouquet kernel's (checked here)."""
+    ncounts = torch.empty_like(counts)
+    nsc = torch.empty(dtau.numel(), dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        bq.aesc_estimate(graph, 5, None, dtau, dnw, counts=ncounts, sc=nsc, naive=True)
+    bq.sync()
+    bq.profile_read()
+    bq.profile_enable(True)
+    lat = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bq.aesc_estimate(graph, 5, None, dtau, dnw, counts=ncounts, sc=nsc, naive=True)
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    bq.sync()
+    prof = bq.profile_read()
+    bq.profile_enable(False)
+    # the timed bouquet estimate left its counters in `counts`
+    if not torch.equal(ncounts, counts):
+        raise RuntimeError("naive and bouquet AESC counters differ")
+    ms = sum(lat) / len(lat)
+    return {"ms_per_estimate": ms, "edges_per_s": dtau.numel() / (ms / 1e3),
+            "count_kernel_ms": prof["aesc_ms"] / max(prof["aesc_launches"], 1),
+            "bouquet_speedup": ms / bouquet_ms, "counters_equal_bouquet": True,
+            "kernel": "aesc_naive_kernel: one walk per thread, plain CSR, per-walk atomics"}
 
 
 POWERLAW_SCHEDULE = dict(tau_scale=2.0, tau_add=2, tau_max=64, n_scale=9.0, n_min=32)
@@ -391,6 +425,7 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     ms = sum(lat) / len(lat)
     kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
     est = sc.cpu().numpy()
+    naive = aesc_naive_row(bq, torch, graph, dtau, dnw, counts, ms, max(2, steps - 1), 1)
     foster = abs(float(est.sum()) - (g.n - 1)) / (g.n - 1)
     # re-estimate 1000 edges with 16 x N and 2 x tau (independent seed)
     rng = np.random.default_rng(7)
@@ -509,6 +544,7 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     graph.close()
     cpu_line = aesc_cpu_baseline(g, 5, uv_all, tau, nw) if cpu else None
     return {
+        "naive": naive,
         "push_phase": push,
         "pilot_plan": pilot,
         "shared_walks": shared,
@@ -598,8 +634,9 @@ def run_ours(args):
     bq.set_tuning(hub_relabel=0 if args.no_relabel else 1)
     graph = bq.Graph.from_csr(g)
     bq.set_tuning(hub_relabel=relabel_before)
-    walk_kernel = ("walk_relabel_kernel" if not args.no_relabel and graph.info()["layout"] == 5
-                   else "walk_hub_kernel" if bq.get_tuning()["hub_slots"] else "walk_bouquet_kernel")
+    ginfo = graph.info()
+    if not args.no_relabel and not ginfo["relabel_hubs"]:
+        raise RuntimeError("the degree-relabelled copy of the walk graph was not built")
     st = torch.from_numpy(starts.view(np.int32)).cuda()
     visits = torch.zeros(g.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -642,6 +679,13 @@ def run_ours(args):
         total_ms, prof = timed(bq.MODE_BOUQUET, args.steps, args.warmup)
     ms_per_step = total_ms / args.steps
     steps_per_batch = N_WALKS * N_STEPS
+    # the walk kernel that ran, as the library counted its launches
+    launched = {k: v for k, v in prof["walk_kernels"].items() if v}
+    if len(launched) != 1 or sum(launched.values()) != args.steps:
+        raise RuntimeError(f"expected one walk kernel launch per step, the library reports {launched}")
+    walk_kernel = f"walk_{next(iter(launched))}_kernel"
+    if not args.no_relabel and walk_kernel != "walk_relabel_kernel":
+        raise RuntimeError(f"the relabelled-copy kernel did not run ({launched})")
     value = whole_job_rate(world, steps_per_batch, ms_per_step / 1e3)
     walk_ms = prof["walk_ms"] / max(prof["walk_launches"], 1)
     group_ms = prof["group_ms"] / max(prof["group_launches"], 1)
@@ -702,6 +746,10 @@ def run_ours(args):
                        "starts": "uniform over non-isolated vertices (seeded)",
                        "mode": "BOUQUET, independent sampler", "tuning": bq.get_tuning(),
                        "walk_kernel": walk_kernel,
+                       "walk_kernel_source": "library launch counts (bq_profile.walk_kernel_launches)",
+                       "walk_graph": {k: ginfo[k] for k in ("layout", "hub_slots", "packed_bits", "relabel_hubs",
+                                                            "relabel_bits_id", "relabel_bits_off",
+                                                            "relabel_bits_deg")},
                        "autotune": autotune,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world} (each GPU its own batch)"},

@@ -94,6 +94,19 @@ typedef struct bq_graph_info_t {
     double lambda_neg;
     int32_t layout;        /* device layout built (bq_tuning.layout value, never 1) */
     int32_t reserved;
+    /* What the walk batch's kernels will use on this graph (set at creation):
+     * hub_slots      slots of the hashed hub table (0: none);
+     * packed_bits    bits per packed neighbour id (0: ids not packed);
+     * relabel_hubs   vertices the kernel on the degree-relabelled copy serves
+     *                from shared memory (0: no relabelled copy was built);
+     * relabel_bits_* field widths of the copy's 8-byte vertex records
+     *                {original id, row offset, degree} (0 without a copy). */
+    uint32_t hub_slots;
+    uint32_t packed_bits;
+    uint32_t relabel_hubs;
+    uint32_t relabel_bits_id;
+    uint32_t relabel_bits_off;
+    uint32_t relabel_bits_deg;
 } bq_graph_info_t;
 
 /* Fill *info (host struct).  May copy the CSR to the host once to find the
@@ -301,8 +314,17 @@ int bq_aesc_plan_pilot(bq_graph *g, uint64_t seed, const uint32_t *edges_uv, uin
  * reports BQ_ENOEDGE; 2 nwalks tau >= 2^32 gets NaN and BQ_EOVERFLOW.
  * Results depend only on (seed, graph, the pair, its tau and nwalks,
  * sampler): not on the other queried edges.  sampler NULL = independent.
+ * flags: BQ_HOST_IO (host buffers), BQ_AESC_NAIVE (the plain form, below).
  * Scratch comes from the stream-ordered pool.
+ *
+ * BQ_AESC_NAIVE runs the same walks one per thread (Alg. 2 for each walk of
+ * Alg. 1's loop: walks in edge, side, walk order on the plain CSR, a
+ * neighbour id and the neighbour's vertex record read per step, each walk's
+ * hits added with its own atomics), instead of bouquets of 32 x lanes walks
+ * of one start advanced in lockstep by a warp (Alg. 3).  The counters and
+ * estimates are the same integers and doubles; only the speed differs.
  */
+#define BQ_AESC_NAIVE 0x4u
 int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev,
                      uint64_t k, const uint32_t *tau_dev, const uint32_t *nwalks_dev,
                      const bq_sampler *sampler, uint32_t flags, uint32_t *counts_dev,
@@ -604,7 +626,7 @@ int bq_autotune_aesc(const bq_aesc_query *queries, uint32_t n_queries, const bq_
  * on the caller's stream (no extra synchronisation) and counts every kernel
  * it launches.  bq_profile_read waits for the recorded events, returns the
  * summed device time per kernel group since the previous read, and resets
- * the sums.  Counting launches is always on.
+ * the sums and the launch counts.  Counting launches is always on.
  */
 typedef struct bq_profile {
     double walk_ms;          /* walk kernels (bouquet or naive) */
@@ -616,7 +638,16 @@ typedef struct bq_profile {
     double aesc_aux_ms;      /* AESC edge preparation, task scan, finalize */
     uint64_t aesc_aux_launches;
     uint64_t kernel_launches; /* every kernel the library launched */
+    /* walk-batch kernel launches by kind, indexed by BQ_WALK_KERNEL_*
+     * (counted whether or not timing is enabled) */
+    uint64_t walk_kernel_launches[8];
 } bq_profile;
+
+#define BQ_WALK_KERNEL_NAIVE 0       /* one walk per thread (BQ_MODE_NAIVE) */
+#define BQ_WALK_KERNEL_BOUQUET 1     /* bouquets, plain records */
+#define BQ_WALK_KERNEL_HUB 2         /* bouquets, hashed hub table in shared memory */
+#define BQ_WALK_KERNEL_CLUSTER_HUB 3 /* bouquets, hub table over a CTA cluster */
+#define BQ_WALK_KERNEL_RELABEL 4     /* bouquets on the degree-relabelled copy */
 
 int bq_profile_enable(int enable);
 int bq_profile_read(bq_profile *out);

@@ -38,6 +38,7 @@ MODE_NAIVE = 0
 MODE_BOUQUET = 1
 VISIT_START = 0x1
 HOST_IO = 0x2
+AESC_NAIVE = 0x4
 
 SAMPLER_IND = 0
 SAMPLER_COUPLED = 1
@@ -72,7 +73,10 @@ class GraphInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("has_spectrum", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("lambda2", ctypes.c_double),
                 ("lambda_neg", ctypes.c_double), ("layout", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("hub_slots", ctypes.c_uint32),
+                ("packed_bits", ctypes.c_uint32), ("relabel_hubs", ctypes.c_uint32),
+                ("relabel_bits_id", ctypes.c_uint32), ("relabel_bits_off", ctypes.c_uint32),
+                ("relabel_bits_deg", ctypes.c_uint32)]
 
 
 class Profile(ctypes.Structure):
@@ -80,7 +84,12 @@ class Profile(ctypes.Structure):
                 ("group_ms", ctypes.c_double), ("group_launches", ctypes.c_uint64),
                 ("aesc_ms", ctypes.c_double), ("aesc_launches", ctypes.c_uint64),
                 ("aesc_aux_ms", ctypes.c_double), ("aesc_aux_launches", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64),
+                ("walk_kernel_launches", ctypes.c_uint64 * 8)]
+
+
+# indices of Profile.walk_kernel_launches (BQ_WALK_KERNEL_*)
+WALK_KERNELS = ("naive", "bouquet", "hub", "cluster_hub", "relabel")
 
 
 class AescQuery(ctypes.Structure):
@@ -388,8 +397,9 @@ def aesc_plan_pilot(graph: Graph, seed: int, uv: np.ndarray | None, eps: float, 
 
 
 def aesc_estimate(graph: Graph, seed: int, uv, tau, nwalks, sampler=None, counts=None,
-                  sc=None, stream=None):
-    """Enqueue an AESC estimate on device tensors; returns (counts, sc)."""
+                  sc=None, stream=None, naive: bool = False):
+    """Enqueue an AESC estimate on device tensors; returns (counts, sc).
+    naive=True runs the same walks one per thread (BQ_AESC_NAIVE)."""
     import torch
     L = load_library()
     k = tau.numel()
@@ -399,14 +409,16 @@ def aesc_estimate(graph: Graph, seed: int, uv, tau, nwalks, sampler=None, counts
     if sc is None:
         sc = torch.empty(k, dtype=torch.float64, device=dev)
     _check(L.bq_aesc_estimate(graph.handle, int(seed) & (2**64 - 1), _dptr(uv, "edges"), k,
-                              _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), _sampler(sampler), 0,
+                              _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), _sampler(sampler),
+                              AESC_NAIVE if naive else 0,
                               _dptr(counts, "counts"), _dptr(sc, "sc", 8), _stream_handle(stream)))
     return counts, sc
 
 
 def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.ndarray,
-                       nwalks: np.ndarray, sampler=None, stream=None):
-    """AESC estimate on host arrays; returns (counts uint32[4k], sc float64[k])."""
+                       nwalks: np.ndarray, sampler=None, stream=None, naive: bool = False):
+    """AESC estimate on host arrays; returns (counts uint32[4k], sc float64[k]).
+    naive=True runs the same walks one per thread (BQ_AESC_NAIVE)."""
     L = load_library()
     tau = np.ascontiguousarray(tau, dtype=np.uint32)
     nwalks = np.ascontiguousarray(nwalks, dtype=np.uint32)
@@ -419,7 +431,8 @@ def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.n
     sc = np.zeros(k, np.float64)
     _check(L.bq_aesc_estimate(graph.handle, int(seed) & (2**64 - 1), puv, k,
                               _hptr(tau, "tau", np.uint32), _hptr(nwalks, "nwalks", np.uint32),
-                              _sampler(sampler), HOST_IO, _hptr(counts, "counts", np.uint32),
+                              _sampler(sampler), HOST_IO | (AESC_NAIVE if naive else 0),
+                              _hptr(counts, "counts", np.uint32),
                               _hptr(sc, "sc", np.float64), _stream_handle(stream)))
     return counts, sc
 
@@ -698,7 +711,9 @@ def profile_read() -> dict:
     previous read; waits for the recorded events."""
     p = Profile()
     _check(load_library().bq_profile_read(ctypes.byref(p)))
-    return {name: getattr(p, name) for name, _ in Profile._fields_}
+    out = {name: getattr(p, name) for name, _ in Profile._fields_ if name != "walk_kernel_launches"}
+    out["walk_kernels"] = {k: int(p.walk_kernel_launches[i]) for i, k in enumerate(WALK_KERNELS)}
+    return out
 
 
 def version() -> str:

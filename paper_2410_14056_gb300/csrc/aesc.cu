@@ -268,6 +268,71 @@ aesc_count_kernel(EL el, const int64_t *__restrict__ offsets, const QueryInfo *_
     }
 }
 
+// The naive form of the same estimate (Alg. 2 per walk inside Alg. 1's walk
+// loop): one walk per thread, walks in edge, side, walk order, on the plain
+// CSR (a 4-byte neighbour id and the neighbour's vertex record per step), no
+// bouquets, no task queue and no hub table.  Walk t of the flat order is
+// walk w of side s of query q with begin[q] <= t < begin[q + 1], s = 1 when
+// t - begin[q] >= N_q; it takes the same stream 2 e + s, walk index w and
+// sampler as the bouquet kernel, so the counters are the same integers.  A
+// walk with hits adds them to its side's two counters with its own atomics.
+template <typename RL, bool COUPLED>
+__global__ void __launch_bounds__(kThreads)
+aesc_naive_kernel(RL rl, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
+                  const QueryInfo *__restrict__ info, const uint64_t *__restrict__ begin,
+                  const uint32_t *__restrict__ bucket, uint64_t k, uint64_t seed, Sampler smp,
+                  uint32_t *__restrict__ counts) {
+    const uint64_t total = begin[k];
+    const uint32_t shift = bucket_shift(total, k);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = task_edge(begin, bucket, k, total, shift, t);
+        const QueryInfo qi = info[q];
+        const uint64_t local = t - begin[q];
+        const uint32_t side = local >= qi.nwalks ? 1u : 0u;
+        const uint64_t w = local - (side ? qi.nwalks : 0u);
+        const uint64_t stream = 2 * qi.edge + side;
+        uint32_t cur = side ? qi.v : qi.u;
+        uint64_t st = walk_key(seed, stream, w);
+        uint64_t gs = COUPLED ? walk_key(seed, stream | kGroupBit, w / smp.width) : 0ull;
+        uint64_t off;
+        uint32_t deg;
+        start_record(offsets, cur, off, deg);
+        uint32_t hit_u = 0, hit_v = 0;
+        for (uint32_t l = 1; l <= qi.tau; ++l) {
+            st += kGolden;
+            if (COUPLED) gs += kGolden;
+            if (deg) {
+                cur = nbrs[off + choose(sample_word<COUPLED>(st, gs, cur, smp.t), deg)];
+                rl.load(cur, off, deg);
+                const uint32_t weight = l < qi.tau ? 2u : 1u;
+                hit_u += cur == qi.u ? weight : 0u;
+                hit_v += cur == qi.v ? weight : 0u;
+            }
+        }
+        if (hit_u) atomicAdd(counts + 4 * q + 2 * side + 0, hit_u);
+        if (hit_v) atomicAdd(counts + 4 * q + 2 * side + 1, hit_v);
+    }
+}
+
+struct NaiveRec8 {
+    const uint2 *rec;
+    __device__ __forceinline__ void load(uint32_t v, uint64_t &off, uint32_t &deg) const {
+        const uint2 r = __ldg(rec + v);
+        off = r.x;
+        deg = r.y;
+    }
+};
+
+struct NaiveRec16 {
+    const uint4 *rec;
+    __device__ __forceinline__ void load(uint32_t v, uint64_t &off, uint32_t &deg) const {
+        const uint4 r = __ldg(rec + v);
+        off = ((uint64_t)r.y << 32) | r.x;
+        deg = r.z;
+    }
+};
+
 // Pilot sample of the scheduled plan: the first nwalks walks of each side,
 // i.e. the estimator's own walks (same streams, walk indices and sampler),
 // each scored by a = its weighted hits of u and b = its weighted hits of v.
@@ -1022,13 +1087,38 @@ int launch_canonical_edges(const DeviceGraph &g, uint32_t *uv, cudaStream_t s) {
     return BQ_OK;
 }
 
+// One walk per thread over the flat walk order (grid-stride, a grid of SMs x
+// resident blocks).
+template <typename RL>
+int launch_naive_count(RL rl, const DeviceGraph &g, const QueryInfo *info, const uint64_t *begin, uint64_t k,
+                       uint64_t seed, const Sampler &smp, uint32_t *counts, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    BQ_CUDA(cudaGetDevice(&dev));
+    BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint32_t *bucket = reinterpret_cast<const uint32_t *>(begin + k + 1);
+    if (smp.kind == 1) {
+        auto kernel = aesc_naive_kernel<RL, true>;
+        BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+        kernel<<<sms * (per_sm < 1 ? 1 : per_sm), kThreads, 0, s>>>(rl, g.offsets, g.nbrs, info, begin, bucket, k,
+                                                                    seed, smp, counts);
+    } else {
+        auto kernel = aesc_naive_kernel<RL, false>;
+        BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+        kernel<<<sms * (per_sm < 1 ? 1 : per_sm), kThreads, 0, s>>>(rl, g.offsets, g.nbrs, info, begin, bucket, k,
+                                                                    seed, smp, counts);
+    }
+    BQ_CUDA(cudaGetLastError());
+    return BQ_OK;
+}
+
 int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k, const uint32_t *tau,
-                const uint32_t *nwalks, const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
-                cudaStream_t s) {
+                const uint32_t *nwalks, const Sampler &smp, bool naive, uint32_t *counts, double *sc,
+                uint32_t *status, cudaStream_t s) {
     if (k == 0) return BQ_OK;
     int w = tuning_aesc_walks_per_lane();
     if (w != 2 && w != 4 && w != 8) w = 4;
-    const uint32_t bouquet = 32u * (uint32_t)w;
+    // the naive kernel's work items are single walks: 2 N per edge
+    const uint32_t bouquet = naive ? 1u : 32u * (uint32_t)w;
     if (k >= kMaxBucketEdges) return fail(BQ_EINVAL, "k = %llu edges in one estimate", (unsigned long long)k);
     // scratch: info[k] | begin[k + 1] bucket[k + 1] | tasks[k] | next_task |
     // (edges[2k] if all-edges)
@@ -1072,9 +1162,13 @@ int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, u
     if (rc == BQ_OK) {
         ProfScope prof(kProfAesc, s);
         count_launches(1);
-        rc = with_edges(g, [&](auto el) {
-            return launch_count_w(el, g, info, begin, k, seed, smp, next_task, counts, w, s);
-        });
+        if (naive)
+            rc = g.compact() ? launch_naive_count(NaiveRec8{g.rec8}, g, info, begin, k, seed, smp, counts, s)
+                             : launch_naive_count(NaiveRec16{g.rec16}, g, info, begin, k, seed, smp, counts, s);
+        else
+            rc = with_edges(g, [&](auto el) {
+                return launch_count_w(el, g, info, begin, k, seed, smp, next_task, counts, w, s);
+            });
     }
     if (rc == BQ_OK) {
         ProfScope prof(kProfAescAux, s);

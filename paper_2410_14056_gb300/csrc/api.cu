@@ -111,6 +111,7 @@ std::vector<cudaEvent_t> g_prof_free_events;
 double g_prof_ms[4] = {0, 0, 0, 0};
 uint64_t g_prof_count[4] = {0, 0, 0, 0};
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_walk_kernels[8];
 
 cudaEvent_t take_event() {
     std::lock_guard<std::mutex> lock(g_prof_mutex);
@@ -140,6 +141,9 @@ ProfScope::~ProfScope() {
 }
 
 void count_launches(unsigned n) { g_launches.fetch_add(n); }
+void count_walk_kernel(int kind) {
+    if (kind >= 0 && kind < 8) g_walk_kernels[kind].fetch_add(1);
+}
 
 int validate_sampler(const bq_sampler *in, Sampler &out);
 
@@ -357,6 +361,14 @@ int bq_graph_info(bq_graph *g, bq_graph_info_t *info) {
     info->lambda2 = g->lambda2;
     info->lambda_neg = g->lambda_neg;
     info->layout = g->layout;
+    info->hub_slots = g->d_hub_tag ? g->hub_slots * g->hub_cluster : 0;
+    info->packed_bits = g->d_pk ? g->pk_bits : 0;
+    if (g->d_rl_pk) {
+        info->relabel_hubs = g->rl_hubs;
+        info->relabel_bits_id = g->rl_sh_off;
+        info->relabel_bits_off = g->rl_sh_deg - g->rl_sh_off;
+        info->relabel_bits_deg = g->rl_bits_deg;
+    }
     return BQ_OK;
 }
 
@@ -733,7 +745,8 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
     bq::NvtxRange nvtx_range("bq_aesc_estimate");
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
-    if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
+    if (flags & ~(BQ_HOST_IO | BQ_AESC_NAIVE)) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
+    const bool naive = (flags & BQ_AESC_NAIVE) != 0;
     if (k && (!tau_dev || !nwalks_dev || !counts_dev || !sc_dev))
         return fail(BQ_EINVAL, "tau, nwalks, counts or sc is NULL");
     if (!edges_uv_dev && (k != g->nnz / 2 || k != g->m_upper))
@@ -749,7 +762,8 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (!(flags & BQ_HOST_IO))
-        return launch_aesc(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, smp, counts_dev, sc_dev, status, s);
+        return launch_aesc(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, smp, naive, counts_dev, sc_dev,
+                           status, s);
 
     const size_t eb = edges_uv_dev ? sizeof(uint32_t) * 2 * k : 0;
     const size_t tb = sizeof(uint32_t) * k, cb = sizeof(uint32_t) * 4 * k, scb = sizeof(double) * k;
@@ -765,7 +779,7 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_nw, nwalks_dev, tb, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && d_uv) e = cudaMemcpyAsync(d_uv, edges_uv_dev, eb, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) rc = cuda_fail(e, "host-io upload");
-    if (rc == BQ_OK) rc = launch_aesc(g->view(), seed, d_uv, k, d_tau, d_nw, smp, d_counts, d_sc, status, s);
+    if (rc == BQ_OK) rc = launch_aesc(g->view(), seed, d_uv, k, d_tau, d_nw, smp, naive, d_counts, d_sc, status, s);
     if (rc == BQ_OK) {
         e = cudaMemcpyAsync(counts_dev, d_counts, cb, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc_dev, d_sc, scb, cudaMemcpyDeviceToHost, s);
@@ -886,6 +900,7 @@ int bq_profile_read(bq_profile *out) {
     out->aesc_aux_ms = g_prof_ms[kProfAescAux];
     out->aesc_aux_launches = g_prof_count[kProfAescAux];
     out->kernel_launches = g_launches.exchange(0);
+    for (int i = 0; i < 8; ++i) out->walk_kernel_launches[i] = g_walk_kernels[i].exchange(0);
     for (int i = 0; i < 4; ++i) {
         g_prof_ms[i] = 0.0;
         g_prof_count[i] = 0;

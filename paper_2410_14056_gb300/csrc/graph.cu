@@ -460,6 +460,7 @@ int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cu
     g->rl_sh_deg = b_id + b_off;
     g->rl_mask_id = b_id >= 32 ? 0xffffffffu : ((1u << b_id) - 1u);
     g->rl_mask_off = b_off >= 64 ? ~0ull : ((1ull << b_off) - 1ull);
+    g->rl_bits_deg = b_deg;
     g->device_bytes += sizeof(uint32_t) * n + sizeof(uint4) * n + sizeof(uint64_t) * n + sizeof(uint4) * chunks;
     return BQ_OK;
 }

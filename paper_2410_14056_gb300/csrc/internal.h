@@ -175,7 +175,7 @@ struct bq_graph {
     uint64_t *d_rl_rec8 = nullptr;
     uint32_t *d_rl_new = nullptr;
     uint32_t rl_hubs = 0;
-    uint32_t rl_sh_off = 0, rl_sh_deg = 0, rl_mask_id = 0;
+    uint32_t rl_sh_off = 0, rl_sh_deg = 0, rl_mask_id = 0, rl_bits_deg = 0;
     uint64_t rl_mask_off = 0;
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
@@ -298,6 +298,7 @@ struct ProfScope {
     ~ProfScope();
 };
 void count_launches(unsigned n);
+void count_walk_kernel(int kind);  // BQ_WALK_KERNEL_* of a walk-batch launch
 
 // ---- graph.cu
 // Validate a device CSR and build records / edge numbering.  Synchronous on s.
@@ -340,9 +341,10 @@ int serve_prepare_many(const ServeMany &L, uint32_t bouquet, cudaStream_t s);
 int serve_finalize_many(const ServeMany &L, cudaStream_t s);
 
 // ---- aesc.cu
+// naive: one walk per thread on the plain CSR (BQ_AESC_NAIVE), else bouquets
 int launch_aesc(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv,
                 uint64_t k, const uint32_t *tau, const uint32_t *nwalks,
-                const Sampler &smp, uint32_t *counts, double *sc, uint32_t *status,
+                const Sampler &smp, bool naive, uint32_t *counts, double *sc, uint32_t *status,
                 cudaStream_t s);
 // Pilot of the scheduled plan: per query and side the sums of a, b, a^2,
 // b^2, a b over the first nwalks[q] walks (a, b = one walk's weighted hits of

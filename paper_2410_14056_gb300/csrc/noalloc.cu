@@ -55,6 +55,7 @@ extern "C" int bq_walk_batch_noalloc(const bq_graph *g, uint64_t seed, const uin
                                      uint32_t n_steps, const bq_sampler *sampler, uint32_t flags,
                                      uint32_t *visits_dev, uint32_t *paths_dev, void *stream) {
     bq::NvtxRange nvtx_range("bq_walk_batch_noalloc");
+    clear_error();
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (flags & ~BQ_VISIT_START)
         return fail(BQ_EINVAL, "bq_walk_batch_noalloc takes device buffers only (flags 0x%x)", flags);
@@ -65,13 +66,13 @@ extern "C" int bq_walk_batch_noalloc(const bq_graph *g, uint64_t seed, const uin
     Sampler smp;
     int rc = validate_sampler(sampler, smp, true);
     if (rc) return rc;
+    if (n_walks == 0) return BQ_OK;  // nothing to run, whatever the graph's size
     const size_t need = walk_batch_scratch_bytes(g->n, n_walks);
     if (need > kStaticScratchBytes)
         return fail(BQ_EINVAL,
                     "bq_walk_batch_noalloc needs %zu bytes of scratch for n = %u and %llu walks; its static "
                     "scratch holds %zu bytes (use bq_walk_batch, or split the batch)",
                     need, g->n, (unsigned long long)n_walks, kStaticScratchBytes);
-    if (n_walks == 0) return BQ_OK;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != g->device) {

@@ -640,6 +640,7 @@ int launch_naive(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *sta
     const unsigned grid = blocks_for(n_walks, kThreads);
     ProfScope prof(kProfWalk, s);
     count_launches(1);
+    count_walk_kernel(BQ_WALK_KERNEL_NAIVE);
     if (smp.kind == 1)
         walk_naive_kernel<RL, true><<<grid, kThreads, 0, s>>>(rl, g.nbrs, g.n, starts, n_walks, n_steps, seed,
                                                               smp, visit_start, checked, visits, paths, status);
@@ -657,6 +658,7 @@ void launch_bouquet_w(EL el, const DeviceGraph &g, const uint32_t *sid, const ui
     const unsigned grid = blocks_for(n_walks, (uint64_t)kThreads * W);
     ProfScope prof(kProfWalk, s);
     count_launches(1);
+    count_walk_kernel(BQ_WALK_KERNEL_BOUQUET);
     if (smp.kind == 1)
         walk_bouquet_kernel<EL, W, true><<<grid, kThreads, 0, s>>>(el, g.offsets, sid, sst, n_valid, n_steps, seed,
                                                                    smp, visit_start, checked, agg, visits, paths,
@@ -706,6 +708,7 @@ bool launch_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32
     }
     ProfScope prof(kProfWalk, s);
     count_launches(1);
+    count_walk_kernel(BQ_WALK_KERNEL_HUB);
     kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.offsets, g.hub_tag, g.hub_slots, sid, sst, n_valid, n_steps,
                                                    seed, smp, visit_start, visits, paths, next_chunk,
                                                    tuning_l2_hints());
@@ -768,6 +771,7 @@ bool launch_cluster_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, cons
         cudaGetLastError();
         return false;
     }
+    count_walk_kernel(BQ_WALK_KERNEL_CLUSTER_HUB);
     return true;
 }
 
@@ -810,6 +814,7 @@ bool launch_relabel_w(const DeviceGraph &g, const uint32_t *sid, const uint32_t 
     const EdgesPackedIds el{g.rl_pk, nullptr, g.pk_bits, g.pk_q, g.pk_mask};
     ProfScope prof(kProfWalk, s);
     count_launches(1);
+    count_walk_kernel(BQ_WALK_KERNEL_RELABEL);
     kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec, g.rl_rec8, g.rl_sh_off, g.rl_sh_deg, g.rl_mask_id,
                                                    g.rl_mask_off, g.rl_new, g.rl_hubs, sid, sst, n_valid, n_steps,
                                                    seed, smp, visit_start, visits, paths, next_chunk);

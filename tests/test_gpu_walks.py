@@ -278,6 +278,70 @@ def test_full_size_rmat_batch(env):
     assert np.array_equal(vh, host_u32(vb))
 
 
+def test_full_size_relabelled_batch_matches_oracle(env):
+    """The kernel the bench times, in the bench's configuration: R-MAT scale
+    20 (edge factor 16) with its degree-relabelled copy, 2^24 uniform starts,
+    64 steps, for 1, 2 and 4 walks per lane.  The copy's 8-byte records pack
+    the original id, row offset and degree at the widths this graph needs
+    (20, 25 and 9 bits), so this is the size at which those fields are
+    exercised.  Visits equal the hashed-hub kernel's and the naive kernel's
+    on the plain graph, sum to 2^30, equal the histogram of every path, and
+    3000 sampled walks (half starting on a hub of the copy, half not) equal
+    the oracle's replay of the same walk ids row for row."""
+    bq, torch = env
+    g = rmat20()
+    n_walks, n_steps = 1 << 24, 64
+    starts = uniform_starts(g, n_walks, 21)
+    st = dev_u32(torch, starts)
+    plain = bq.Graph.from_csr(g)
+    vh = bq.walk_batch(plain, 2024, st, n_steps, mode=bq.MODE_BOUQUET)
+    vn = bq.walk_batch(plain, 2024, st, n_steps, mode=bq.MODE_NAIVE)
+    bq.sync()
+    assert torch.equal(vh, vn)
+    plain.close()
+    old = bq.get_tuning()
+    try:
+        bq.set_tuning(hub_relabel=1)
+        graph = bq.Graph.from_csr(g)
+    finally:
+        bq.set_tuning(**old)
+    info = graph.info()
+    assert info["relabel_hubs"] == 10922
+    assert (info["relabel_bits_id"], info["relabel_bits_off"], info["relabel_bits_deg"]) == (20, 25, 9)
+    deg = np.diff(g.offsets)
+    order = np.lexsort((np.arange(g.n), -deg))  # degree descending, then id
+    is_hub = np.zeros(g.n, bool)
+    is_hub[order[:info["relabel_hubs"]]] = True
+    rng = np.random.default_rng(6)
+    hub_ids = np.flatnonzero(is_hub[starts])
+    other_ids = np.flatnonzero(~is_hub[starts])
+    ids = np.sort(np.concatenate([rng.choice(hub_ids, 1500, replace=False),
+                                  rng.choice(other_ids, 1500, replace=False)])).astype(np.uint64)
+    want = oracle.walk_paths_by_id(g, 2024, ids, starts[ids.astype(np.int64)], n_steps)
+    tids = torch.from_numpy(ids.astype(np.int64)).cuda()
+    paths = torch.empty((n_walks, n_steps + 1), dtype=torch.int32, device="cuda")
+    try:
+        for lanes in (1, 2, 4):
+            bq.set_tuning(walk_lanes=lanes)
+            bq.profile_read()
+            vr = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_BOUQUET)
+            paths.fill_(-1)
+            vp = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_BOUQUET, paths=paths)
+            bq.sync()
+            assert bq.profile_read()["walk_kernels"]["relabel"] == 2, lanes
+            assert torch.equal(vr, vh), lanes
+            assert torch.equal(vp, vh), lanes
+            assert int(vr.to(torch.int64).sum()) == n_walks * n_steps
+            hist = torch.bincount(paths[:, 1:].reshape(-1), minlength=g.n)
+            assert torch.equal(hist.to(torch.int32), vr), lanes
+            assert torch.equal(paths[:, 0], st), lanes
+            assert np.array_equal(host_u32(paths[tids]), want), lanes
+    finally:
+        bq.set_tuning(**old)
+        del paths
+        graph.close()
+
+
 def test_literal_saba_word_orders_buckets_and_is_refused_by_aesc(env):
     """The literal SABA sampler: the same paths as the oracle in both modes
     (the bucket ordering by seed changes no result), and AESC calls refuse
