@@ -63,7 +63,8 @@ class Tuning(ctypes.Structure):
                 ("aesc_lanes", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("hub_slots", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
                 ("aesc_hub", ctypes.c_uint32), ("hub_cluster", ctypes.c_uint32),
-                ("hub_relabel", ctypes.c_uint32)]
+                ("hub_relabel", ctypes.c_uint32), ("walk_counted", ctypes.c_uint32),
+                ("counted_hubs", ctypes.c_uint32), ("counted_bits", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -89,7 +90,7 @@ class Profile(ctypes.Structure):
 
 
 # indices of Profile.walk_kernel_launches (BQ_WALK_KERNEL_*)
-WALK_KERNELS = ("naive", "bouquet", "hub", "cluster_hub", "relabel")
+WALK_KERNELS = ("naive", "bouquet", "hub", "cluster_hub", "relabel", "counted")
 
 
 class AescQuery(ctypes.Structure):
@@ -686,18 +687,16 @@ def sync(stream=None):
 def get_tuning() -> dict:
     t = Tuning()
     _check(load_library().bq_get_tuning(ctypes.byref(t)))
-    return {"walk_lanes": t.walk_lanes, "aggregate_visits": t.aggregate_visits,
-            "aesc_lanes": t.aesc_lanes, "layout": t.layout, "hub_slots": t.hub_slots,
-            "l2_hints": t.l2_hints, "aesc_hub": t.aesc_hub, "hub_cluster": t.hub_cluster,
-            "hub_relabel": t.hub_relabel}
+    return {name: int(getattr(t, name)) for name, _ in Tuning._fields_}
 
 
 def set_tuning(**kw):
     cur = get_tuning()
+    unknown = set(kw) - set(cur)
+    if unknown:
+        raise ValueError(f"unknown tuning fields {sorted(unknown)}")
     cur.update(kw)
-    t = Tuning(int(cur["walk_lanes"]), int(cur["aggregate_visits"]), int(cur["aesc_lanes"]),
-               int(cur["layout"]), int(cur["hub_slots"]), int(cur["l2_hints"]), int(cur["aesc_hub"]),
-               int(cur["hub_cluster"]), int(cur["hub_relabel"]))
+    t = Tuning(*(int(cur[name]) for name, _ in Tuning._fields_))
     _check(load_library().bq_set_tuning(ctypes.byref(t)))
 
 

@@ -319,14 +319,17 @@ __global__ void relabel_rows_kernel(const int64_t *__restrict__ off, const uint3
 }
 
 // rec8[x] = original id | row offset << sh_off | degree << sh_deg of
-// internal vertex x (hubs' degrees need not fit: they are read from rec).
+// internal vertex x; a degree that needs more than deg_bits bits (only the
+// first internal ids, which the kernels serve from shared memory) is stored
+// as 0.
 __global__ void relabel_rec8_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ orig,
-                                    const int64_t *__restrict__ off_new, uint32_t n, uint32_t hubs, uint32_t sh_off,
-                                    uint32_t sh_deg, uint64_t *__restrict__ rec8) {
+                                    const int64_t *__restrict__ off_new, uint32_t n, uint32_t deg_bits,
+                                    uint32_t sh_off, uint32_t sh_deg, uint64_t *__restrict__ rec8) {
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = orig[x];
-        const uint64_t d = x < hubs ? 0ull : (uint64_t)(off[v + 1] - off[v]);
+        uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+        if ((d >> deg_bits) != 0) d = 0;
         rec8[x] = (uint64_t)v | ((uint64_t)off_new[x] << sh_off) | (d << sh_deg);
     }
 }
@@ -396,39 +399,39 @@ int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t 
 }
 
 // The degree-relabelled copy of a packed-id graph (bq_tuning.hub_relabel):
-// the top H vertices by (degree desc, id asc), H = as many 12-byte hub
-// entries as hub_slots * 16 bytes of shared memory hold, take internal ids
-// 0..H-1 in increasing original id, the others H.. in increasing original id.
+// internal ids follow (degree desc, original id asc), vertices without
+// neighbours last, so every prefix 0..H-1 holds the H highest-degree
+// vertices.  The walk kernels serve such a prefix from shared memory: the
+// plain relabel kernel the first rl_hubs (as many 12-byte entries as
+// hub_slots * 16 bytes of shared memory hold), the counted kernel as many
+// 8-byte entries as fit, at least rl_fit (the vertices whose degree does
+// not fit the records' degree field).
 int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cudaStream_t s) {
     const uint32_t n = g->n;
     std::vector<int64_t> off(n + 1);
     BQ_CUDA(cudaMemcpy(off.data(), g->d_offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
-    std::vector<uint32_t> cand;
-    for (uint32_t v = 0; v < n; ++v)
-        if (off[v + 1] > off[v]) cand.push_back(v);
-    const uint64_t cap = ((uint64_t)tuning_hub_slots() * 16 - 4) / 12;
-    const uint32_t hubs = (uint32_t)std::min<uint64_t>(cap, cand.size());
-    if (hubs == 0) return BQ_OK;
     auto deg = [&](uint32_t v) { return off[v + 1] - off[v]; };
-    std::nth_element(cand.begin(), cand.begin() + (hubs - 1), cand.end(), [&](uint32_t a, uint32_t b) {
+    std::vector<uint32_t> orig(n);
+    for (uint32_t v = 0; v < n; ++v) orig[v] = v;
+    std::sort(orig.begin(), orig.end(), [&](uint32_t a, uint32_t b) {
         return deg(a) != deg(b) ? deg(a) > deg(b) : a < b;
     });
-    std::vector<uint8_t> is_hub(n, 0);
-    for (uint32_t i = 0; i < hubs; ++i) is_hub[cand[i]] = 1;
-    std::vector<uint32_t> new_of(n), orig(n);
-    uint32_t next_hub = 0, next_other = hubs;
-    for (uint32_t v = 0; v < n; ++v) {
-        new_of[v] = is_hub[v] ? next_hub++ : next_other++;
-        orig[new_of[v]] = v;
-    }
+    uint32_t live = 0;
+    while (live < n && deg(orig[live]) > 0) ++live;
+    const uint64_t cap = ((uint64_t)tuning_hub_slots() * 16 - 4) / 12;
+    const uint32_t hubs = (uint32_t)std::min<uint64_t>(cap, live);
+    if (hubs == 0) return BQ_OK;
+    std::vector<uint32_t> new_of(n);
+    for (uint32_t x = 0; x < n; ++x) new_of[orig[x]] = x;
     std::vector<int64_t> off_new(n + 1);
     off_new[0] = 0;
     for (uint32_t x = 0; x < n; ++x) off_new[x + 1] = off_new[x] + deg(orig[x]);
     // 8-byte records when id, offset and the largest non-hub degree fit
-    int64_t max_other = 0;
-    for (uint32_t x = hubs; x < n; ++x) max_other = std::max<int64_t>(max_other, deg(orig[x]));
+    const int64_t max_other = hubs < n ? deg(orig[hubs]) : 0;
     const uint32_t b_id = bits_for(n > 0 ? n - 1 : 0), b_off = bits_for(g->nnz), b_deg = bits_for(max_other);
     if (b_id + b_off + b_deg > 64) return BQ_OK;  // no relabelled copy
+    uint32_t fit = 0;  // first internal id whose degree fits b_deg bits
+    while (fit < n && (deg(orig[fit]) >> b_deg) != 0) ++fit;
     uint32_t *d_orig = nullptr, *d_tmp = nullptr;
     int64_t *d_off_new = nullptr;
     cudaError_t e = cudaMalloc(&g->d_rl_new, sizeof(uint32_t) * n);
@@ -447,7 +450,7 @@ int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cu
                                                                            g->d_rl_new, d_off_new, n, d_tmp);
         build_packed_ids_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(d_tmp, g->nnz, bits, q, chunks, g->d_rl_pk);
         relabel_records_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, d_orig, d_off_new, n, g->d_rl_rec);
-        relabel_rec8_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, d_orig, d_off_new, n, hubs, b_id,
+        relabel_rec8_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->d_offsets, d_orig, d_off_new, n, b_deg, b_id,
                                                              b_id + b_off, g->d_rl_rec8);
         e = cudaStreamSynchronize(s);
     }
@@ -461,6 +464,8 @@ int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cu
     g->rl_mask_id = b_id >= 32 ? 0xffffffffu : ((1u << b_id) - 1u);
     g->rl_mask_off = b_off >= 64 ? ~0ull : ((1ull << b_off) - 1ull);
     g->rl_bits_deg = b_deg;
+    g->rl_live = live;
+    g->rl_fit = fit;
     g->device_bytes += sizeof(uint32_t) * n + sizeof(uint4) * n + sizeof(uint64_t) * n + sizeof(uint4) * chunks;
     return BQ_OK;
 }

@@ -26,6 +26,7 @@ enum StatusBits : uint32_t {
 constexpr uint32_t kNoHub = 0xffffffffu;
 constexpr uint32_t kHubHash = 0x9E3779B1u;
 constexpr uint32_t kHubSlotsMax = 13312;  // 16 B per slot: 208 KiB of shared memory
+constexpr uint32_t kCountedHubsMax = 28000;  // 8 B per hub: at most 219 KiB of shared memory
 
 // Hub-table slot of vertex v: the high half of (v * kHubHash mod 2^32) * slots.
 __host__ __device__ __forceinline__ uint32_t hub_slot(uint32_t v, uint32_t slots) {
@@ -77,17 +78,19 @@ struct DeviceGraph {
     uint32_t hub_slots;    // slots in all (hub_slot over this count)
     uint32_t hub_cluster;  // CTAs sharing the table (1: one CTA holds it)
     // Degree-relabelled copy for the walk batch (null if not built): internal
-    // id x < rl_hubs are the rl_hubs highest-degree vertices, the others
-    // follow, each group in increasing original id; rows keep the original
-    // neighbour order.  rl_new[v] = internal id of original v; rl_rec[x] =
-    // {row offset, degree, original id, 0}; rl_pk = the rows' internal ids
-    // packed as `pk`.
+    // ids follow (degree desc, original id asc), vertices without neighbours
+    // last, so internal ids x < H are the H highest-degree vertices for any
+    // H; rows keep the original neighbour order.  rl_new[v] = internal id of
+    // original v; rl_rec[x] = {row offset, degree, original id, 0}; rl_pk =
+    // the rows' internal ids packed as `pk`.
     const uint4 *rl_pk;
     const uint4 *rl_rec;     // hubs' records (read when a block fills its table)
     const uint64_t *rl_rec8; // every vertex: id | offset << rl_sh_off | degree << rl_sh_deg
+                             // (degree 0 for x < rl_fit, whose degree needs more bits)
     const uint32_t *rl_new;
-    uint32_t rl_hubs;
-    uint32_t rl_sh_off, rl_sh_deg, rl_mask_id;
+    uint32_t rl_hubs;        // hubs of the plain relabel kernel (12 B each)
+    uint32_t rl_sh_off, rl_sh_deg, rl_mask_id, rl_bits_deg;
+    uint32_t rl_live, rl_fit;
     uint64_t rl_mask_off;
     bool compact() const { return rec8 != nullptr; }
 };
@@ -176,6 +179,8 @@ struct bq_graph {
     uint32_t *d_rl_new = nullptr;
     uint32_t rl_hubs = 0;
     uint32_t rl_sh_off = 0, rl_sh_deg = 0, rl_mask_id = 0, rl_bits_deg = 0;
+    uint32_t rl_live = 0;  // internal ids below this have neighbours
+    uint32_t rl_fit = 0;   // internal ids from here on have their degree in rl_rec8
     uint64_t rl_mask_off = 0;
     uint32_t min_degree = 0, max_degree = 0;
     uint64_t m_upper = 0;  // entries v > u over all rows u (= m when symmetric)
@@ -225,6 +230,9 @@ struct bq_graph {
         v.rl_mask_off = rl_mask_off;
         v.rl_new = d_rl_new;
         v.rl_hubs = rl_hubs;
+        v.rl_bits_deg = rl_bits_deg;
+        v.rl_live = rl_live;
+        v.rl_fit = rl_fit;
         return v;
     }
 };
@@ -286,6 +294,9 @@ int tuning_hub_cluster();  // CTAs a created graph's hub table is spread over
 bool tuning_hub_relabel();  // created packed-id graphs get the degree-relabelled copy
 bool tuning_l2_hints(); // L2 eviction policies on the walk kernel's loads
 bool tuning_aesc_hub();  // AESC counting reads hub records from shared memory
+int tuning_walk_counted();      // relabelled copy: 0 plain kernel, 1 counted records, 2 + chunk loads skip L1
+uint32_t tuning_counted_hubs(); // counted kernel's shared-memory hubs (0: hub_slots * 16 bytes' worth)
+uint32_t tuning_counted_bits(); // cap on the counted kernel's count-field width (0: none)
 
 // Profiling (api.cu): event brackets around kernel groups while enabled, and
 // a count of every kernel launch.
@@ -318,7 +329,7 @@ int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *start
                       uint32_t *paths, uint32_t *status, cudaStream_t s);
 
 // Bouquet walk batch in a caller-provided scratch region (no allocation).
-size_t walk_batch_scratch_bytes(uint32_t n, uint64_t n_walks);
+size_t walk_batch_scratch_bytes(const DeviceGraph &g, uint64_t n_walks);
 int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
                          uint32_t n_steps, const Sampler &smp, bool visit_start, uint32_t *visits, uint32_t *paths,
                          uint32_t *status, void *scratch, size_t scratch_bytes, cudaStream_t s);
