@@ -107,7 +107,7 @@ def measured_peaks():
 WALK_KERNEL_SOURCES = {
     "walk_hub_kernel": ("walks.cu", "internal.h", "hash.cuh", "edges.cuh"),
     "walk_relabel_kernel": ("walks.cu", "internal.h", "hash.cuh", "edges.cuh", "graph.cu"),
-    "walk_counted_kernel": ("walks.cu", "internal.h", "hash.cuh", "edges.cuh", "graph.cu"),
+    "walk_relabel8_kernel": ("walks.cu", "internal.h", "hash.cuh", "edges.cuh", "graph.cu"),
 }
 
 
@@ -685,7 +685,7 @@ def run_ours(args):
     if len(launched) != 1 or sum(launched.values()) != args.steps:
         raise RuntimeError(f"expected one walk kernel launch per step, the library reports {launched}")
     walk_kernel = f"walk_{next(iter(launched))}_kernel"
-    if not args.no_relabel and walk_kernel not in ("walk_relabel_kernel", "walk_counted_kernel"):
+    if not args.no_relabel and walk_kernel not in ("walk_relabel_kernel", "walk_relabel8_kernel"):
         raise RuntimeError(f"no kernel on the relabelled copy ran ({launched})")
     value = whole_job_rate(world, steps_per_batch, ms_per_step / 1e3)
     walk_ms = prof["walk_ms"] / max(prof["walk_launches"], 1)

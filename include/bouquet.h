@@ -599,33 +599,28 @@ typedef struct bq_tuning {
                                   {row offset, degree, original id}.  Rows
                                   keep their neighbour order, so results never
                                   change.  0 (default): no copy. */
-    uint32_t walk_counted;     /* the walk kernel on the relabelled copy:
-                                  1 (default): counted records: each visit of
-                                  a vertex outside shared memory is one 64-bit
-                                  atomic add on a per-call copy of its 8-byte
-                                  record, which returns the record and counts
-                                  the visit in its spare top bits (a count
-                                  that wraps adds 2^bits to the visits); the
-                                  shared-memory hubs hold {original id, row
-                                  offset, count} in 8 bytes the same way;
-                                  2: counted records, hubs as 12-byte
-                                  entries (row offset, original id and a
-                                  32-bit counter);
-                                  3: 8-byte hub words, and a record load
-                                  plus a visit atomic for the others;
-                                  0: the plain relabel kernel (12-byte hubs,
-                                  record load plus visit atomic).  Never
-                                  changes a result. */
-    uint32_t counted_hubs;     /* hubs (highest-degree vertices) the counted
-                                  kernel serves from shared memory, 8 bytes
-                                  each: 0 (default) = as many as hub_slots *
-                                  16 bytes hold; at most 28000 */
-    uint32_t counted_bits;     /* cap on the width of the counted kernel's
-                                  count fields, 1..31 (0, default: every
-                                  spare bit of the record, up to 31).  A
-                                  narrower field only wraps more often, each
-                                  wrap one more atomic; for tests of the
-                                  wrap path.  Never changes a result. */
+    uint32_t relabel_hub8;     /* the walk kernel on the relabelled copy:
+                                  1 (default): 8-byte shared-memory hubs
+                                  (a 32-bit row offset and one 32-bit word
+                                  {original id | count}: a step to a hub is
+                                  one 32-bit shared-memory atomic that
+                                  returns the id and counts the visit; a
+                                  count that wraps adds 2^bits to the
+                                  visits), so 1.5x the hubs fit in the same
+                                  shared memory (16,383 instead of 10,922);
+                                  0: the 12-byte entries of the plain relabel
+                                  kernel.  Never changes a result. */
+    uint32_t hub8_hubs;        /* hubs of the 8-byte kernel: 0 (default) = as
+                                  many as the 12-byte kernel's shared memory
+                                  holds; at most 28000 (fewer than the
+                                  vertices whose degree needs more than the
+                                  records' degree field falls back to the
+                                  12-byte kernel) */
+    uint32_t hub8_count_bits;  /* cap on the width of the 8-byte hubs' count
+                                  field, 1..31 (0, default: every bit above
+                                  the id).  A narrower field only wraps more
+                                  often, each wrap one more atomic; for tests
+                                  of the wrap path.  Never changes a result. */
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);
@@ -675,7 +670,7 @@ typedef struct bq_profile {
 #define BQ_WALK_KERNEL_HUB 2         /* bouquets, hashed hub table in shared memory */
 #define BQ_WALK_KERNEL_CLUSTER_HUB 3 /* bouquets, hub table over a CTA cluster */
 #define BQ_WALK_KERNEL_RELABEL 4     /* bouquets on the degree-relabelled copy */
-#define BQ_WALK_KERNEL_COUNTED 5     /* the same with counted records (bq_tuning.walk_counted) */
+#define BQ_WALK_KERNEL_RELABEL8 5    /* the same with 8-byte hubs (bq_tuning.relabel_hub8) */
 
 int bq_profile_enable(int enable);
 int bq_profile_read(bq_profile *out);

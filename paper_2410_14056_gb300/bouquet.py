@@ -63,8 +63,8 @@ class Tuning(ctypes.Structure):
                 ("aesc_lanes", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("hub_slots", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
                 ("aesc_hub", ctypes.c_uint32), ("hub_cluster", ctypes.c_uint32),
-                ("hub_relabel", ctypes.c_uint32), ("walk_counted", ctypes.c_uint32),
-                ("counted_hubs", ctypes.c_uint32), ("counted_bits", ctypes.c_uint32)]
+                ("hub_relabel", ctypes.c_uint32), ("relabel_hub8", ctypes.c_uint32),
+                ("hub8_hubs", ctypes.c_uint32), ("hub8_count_bits", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -90,7 +90,7 @@ class Profile(ctypes.Structure):
 
 
 # indices of Profile.walk_kernel_launches (BQ_WALK_KERNEL_*)
-WALK_KERNELS = ("naive", "bouquet", "hub", "cluster_hub", "relabel", "counted")
+WALK_KERNELS = ("naive", "bouquet", "hub", "cluster_hub", "relabel", "relabel8")
 
 
 class AescQuery(ctypes.Structure):

@@ -31,9 +31,9 @@ std::atomic<int> g_hub_cluster{1};
 std::atomic<int> g_hub_relabel{0};
 std::atomic<int> g_l2_hints{0};
 std::atomic<int> g_aesc_hub{0};
-std::atomic<int> g_walk_counted{1};
-std::atomic<int> g_counted_hubs{0};
-std::atomic<int> g_counted_bits{0};
+std::atomic<int> g_relabel_hub8{1};
+std::atomic<int> g_hub8_hubs{0};
+std::atomic<int> g_hub8_count_bits{0};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -159,9 +159,9 @@ int tuning_hub_cluster() { return g_hub_cluster.load(); }
 bool tuning_hub_relabel() { return g_hub_relabel.load() != 0; }
 bool tuning_l2_hints() { return g_l2_hints.load() != 0; }
 bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
-int tuning_walk_counted() { return g_walk_counted.load(); }
-uint32_t tuning_counted_hubs() { return (uint32_t)g_counted_hubs.load(); }
-uint32_t tuning_counted_bits() { return (uint32_t)g_counted_bits.load(); }
+bool tuning_relabel_hub8() { return g_relabel_hub8.load() != 0; }
+uint32_t tuning_hub8_hubs() { return (uint32_t)g_hub8_hubs.load(); }
+uint32_t tuning_hub8_count_bits() { return (uint32_t)g_hub8_count_bits.load(); }
 
 namespace {
 
@@ -926,9 +926,9 @@ int bq_get_tuning(bq_tuning *out) {
     out->aesc_hub = (uint32_t)g_aesc_hub.load();
     out->hub_cluster = (uint32_t)g_hub_cluster.load();
     out->hub_relabel = (uint32_t)g_hub_relabel.load();
-    out->walk_counted = (uint32_t)g_walk_counted.load();
-    out->counted_hubs = (uint32_t)g_counted_hubs.load();
-    out->counted_bits = (uint32_t)g_counted_bits.load();
+    out->relabel_hub8 = (uint32_t)g_relabel_hub8.load();
+    out->hub8_hubs = (uint32_t)g_hub8_hubs.load();
+    out->hub8_count_bits = (uint32_t)g_hub8_count_bits.load();
     return BQ_OK;
 }
 
@@ -947,10 +947,9 @@ int bq_set_tuning(const bq_tuning *in) {
     const uint32_t c = in->hub_cluster;
     if (c != 0 && c != 1 && c != 2 && c != 4 && c != 8) return fail(BQ_EINVAL, "hub_cluster must be 0, 1, 2, 4 or 8");
     if (in->hub_relabel > 1) return fail(BQ_EINVAL, "hub_relabel must be 0 or 1");
-    if (in->walk_counted > 6) return fail(BQ_EINVAL, "walk_counted must be 0..6");
-    if (in->counted_hubs > kCountedHubsMax)
-        return fail(BQ_EINVAL, "counted_hubs must be at most %u", kCountedHubsMax);
-    if (in->counted_bits > 31) return fail(BQ_EINVAL, "counted_bits must be 0..31");
+    if (in->relabel_hub8 > 1) return fail(BQ_EINVAL, "relabel_hub8 must be 0 or 1");
+    if (in->hub8_hubs > kHub8Max) return fail(BQ_EINVAL, "hub8_hubs must be at most %u", kHub8Max);
+    if (in->hub8_count_bits > 31) return fail(BQ_EINVAL, "hub8_count_bits must be 0..31");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
@@ -960,9 +959,9 @@ int bq_set_tuning(const bq_tuning *in) {
     g_aesc_hub.store((int)in->aesc_hub);
     g_hub_cluster.store(c < 1 ? 1 : (int)c);
     g_hub_relabel.store((int)in->hub_relabel);
-    g_walk_counted.store((int)in->walk_counted);
-    g_counted_hubs.store((int)in->counted_hubs);
-    g_counted_bits.store((int)in->counted_bits);
+    g_relabel_hub8.store((int)in->relabel_hub8);
+    g_hub8_hubs.store((int)in->hub8_hubs);
+    g_hub8_count_bits.store((int)in->hub8_count_bits);
     return BQ_OK;
 }
 

@@ -403,9 +403,12 @@ int scan_u32_ws(const uint32_t *in, uint32_t *out, uint64_t n, void *ws, size_t 
 // neighbours last, so every prefix 0..H-1 holds the H highest-degree
 // vertices.  The walk kernels serve such a prefix from shared memory: the
 // plain relabel kernel the first rl_hubs (as many 12-byte entries as
-// hub_slots * 16 bytes of shared memory hold), the counted kernel as many
-// 8-byte entries as fit, at least rl_fit (the vertices whose degree does
-// not fit the records' degree field).
+// hub_slots * 16 bytes of shared memory hold), the 8-byte-hub kernel as many
+// 8-byte entries as fit in the same bytes, at least rl_fit (the vertices
+// whose degree does not fit the records' degree field).  The degree order
+// also puts the records of the most visited non-hubs side by side (8.54
+// against 8.83 ms per R-MAT 20 batch for the plain relabel kernel, against
+// the earlier order by original id).
 int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cudaStream_t s) {
     const uint32_t n = g->n;
     std::vector<int64_t> off(n + 1);

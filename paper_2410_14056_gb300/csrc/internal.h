@@ -26,7 +26,7 @@ enum StatusBits : uint32_t {
 constexpr uint32_t kNoHub = 0xffffffffu;
 constexpr uint32_t kHubHash = 0x9E3779B1u;
 constexpr uint32_t kHubSlotsMax = 13312;  // 16 B per slot: 208 KiB of shared memory
-constexpr uint32_t kCountedHubsMax = 28000;  // 8 B per hub: at most 219 KiB of shared memory
+constexpr uint32_t kHub8Max = 28000;  // 8 B per hub: at most 219 KiB of shared memory
 
 // Hub-table slot of vertex v: the high half of (v * kHubHash mod 2^32) * slots.
 __host__ __device__ __forceinline__ uint32_t hub_slot(uint32_t v, uint32_t slots) {
@@ -294,9 +294,9 @@ int tuning_hub_cluster();  // CTAs a created graph's hub table is spread over
 bool tuning_hub_relabel();  // created packed-id graphs get the degree-relabelled copy
 bool tuning_l2_hints(); // L2 eviction policies on the walk kernel's loads
 bool tuning_aesc_hub();  // AESC counting reads hub records from shared memory
-int tuning_walk_counted();      // relabelled copy: 0 plain kernel, 1 counted records, 2 + chunk loads skip L1
-uint32_t tuning_counted_hubs(); // counted kernel's shared-memory hubs (0: hub_slots * 16 bytes' worth)
-uint32_t tuning_counted_bits(); // cap on the counted kernel's count-field width (0: none)
+bool tuning_relabel_hub8();      // relabelled copy: 8-byte hubs (else the 12-byte relabel kernel)
+uint32_t tuning_hub8_hubs();       // their number (0: what the 12-byte kernel's shared memory holds)
+uint32_t tuning_hub8_count_bits(); // cap on their count-field width (0: every bit above the id)
 
 // Profiling (api.cu): event brackets around kernel groups while enabled, and
 // a count of every kernel launch.
@@ -329,7 +329,7 @@ int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *start
                       uint32_t *paths, uint32_t *status, cudaStream_t s);
 
 // Bouquet walk batch in a caller-provided scratch region (no allocation).
-size_t walk_batch_scratch_bytes(const DeviceGraph &g, uint64_t n_walks);
+size_t walk_batch_scratch_bytes(uint32_t n, uint64_t n_walks);
 int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
                          uint32_t n_steps, const Sampler &smp, bool visit_start, uint32_t *visits, uint32_t *paths,
                          uint32_t *status, void *scratch, size_t scratch_bytes, cudaStream_t s);

@@ -67,7 +67,7 @@ extern "C" int bq_walk_batch_noalloc(const bq_graph *g, uint64_t seed, const uin
     int rc = validate_sampler(sampler, smp, true);
     if (rc) return rc;
     if (n_walks == 0) return BQ_OK;  // nothing to run, whatever the graph's size
-    const size_t need = walk_batch_scratch_bytes(g->view(), n_walks);
+    const size_t need = walk_batch_scratch_bytes(g->n, n_walks);
     if (need > kStaticScratchBytes)
         return fail(BQ_EINVAL,
                     "bq_walk_batch_noalloc needs %zu bytes of scratch for n = %u and %llu walks; its static "

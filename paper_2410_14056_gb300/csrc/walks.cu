@@ -626,139 +626,51 @@ walk_relabel_kernel(EdgesPackedIds el, const uint4 *__restrict__ rl_rec, const u
     }
 }
 
-// The bouquet walk on the degree-relabelled copy with counted records.  The
-// plain relabel kernel spends, on a step to a vertex outside shared memory,
-// a record load and a separate visit atomic, each a random 32-byte sector in
-// L2; here both are one operation: the call works on its own copy of the
-// 8-byte records {original id | row offset | degree | count}, and a step
-// adds 1 to the count field with a 64-bit atomic that returns the record.
-// The count field holds the top bits the record does not use; when an add
-// wraps it (the returned count is all ones) the walker adds 2^bits to the
-// vertex's visits, so no visit is lost.  The hubs (internal ids below
-// `hubs`, the highest-degree vertices) live in shared memory as 8-byte words
-// {original id | row offset | count}; a step to a hub is one shared-memory
-// atomic plus the next hub's offset for the degree.  At the end each block
-// adds its hub counts to the visits and counted_flush_kernel adds the
-// records' counts.  Paths and visits are those of the plain kernels.
-struct CountedFields {
-    uint32_t sh_off;        // bits of the original id
-    uint32_t sh_deg;        // + bits of the row offset: a hub word's count starts here
-    uint32_t sh_cnt;        // + bits of the degree: a record's count starts here
+// The bouquet walk on the degree-relabelled copy with 8-byte shared-memory
+// hubs.  Internal ids follow the degree order, so the first `hubs` of them
+// are the highest-degree vertices, the number chosen at launch from the
+// shared memory the plain relabel kernel's 12-byte entries take (16,383
+// instead of 10,922 on R-MAT scale 20: 57 % of the visits instead of 49 %).
+// A hub keeps its row offset (32 bits; the next hub's offset ends its row)
+// and one 32-bit word {original id | count << cnt_shift}: a step to a hub is
+// one 32-bit shared-memory atomic add of 1 << cnt_shift, which returns the
+// original id and counts the visit.  The count field holds the bits above
+// the id; when an add wraps it (the returned count is all ones) the walker
+// adds 2^(32 - cnt_shift) to the vertex's visits, so no visit is lost.  Any
+// other vertex reads its 8-byte record and adds its visit in L2, as in the
+// plain kernel.  Each block adds its hub counts to the visits at the end.
+// Paths and visits are those of every other walk kernel.
+struct Hub8Fields {
+    uint32_t sh_off;     // bits of the original id in a record
+    uint32_t sh_deg;     // + bits of the row offset
     uint32_t mask_id;
     uint64_t mask_off;
     uint32_t mask_deg;
-    uint32_t cnt_bits;      // width of a record's count field (<= 31)
-    uint32_t hub_cnt_bits;  // width of a hub word's count field (<= 31)
-    uint32_t hubs;
+    uint32_t hubs;       // internal ids below this are served from shared memory
+    uint32_t cnt_shift;  // a hub word's count field is bits [cnt_shift, 32)
     uint32_t n;
     uint64_t nnz;
-    uint32_t hub_pk_shift;  // packed hub words: the count field is bits [shift, 32)
 };
 
-// VAR selects the variants: bit 0 keeps the hubs as 8-byte words
-// {original id | row offset | count} (64-bit shared atomics); bit 2 keeps
-// them as a 32-bit row offset and a 32-bit word {original id | count} (8
-// bytes, 32-bit shared atomics); neither: 12 bytes (row offset, original id
-// and a 32-bit counter in three arrays).  Bit 1 counts the other vertices in
-// their records (else a record load plus a visit atomic).
-template <int W, bool COUPLED, int VAR>
+template <int W, bool COUPLED>
 __global__ void __launch_bounds__(kHubThreads, 1)
-walk_counted_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, unsigned long long *__restrict__ rec_cnt,
-                    CountedFields f, const uint32_t *__restrict__ rl_new, const uint32_t *__restrict__ sorted_id,
-                    const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr,
-                    uint32_t n_steps, uint64_t seed, Sampler smp, bool visit_start, uint32_t *__restrict__ visits,
-                    uint32_t *__restrict__ paths, unsigned long long *__restrict__ next_chunk) {
-    constexpr bool kHubWords = (VAR & 1) != 0, kRecCount = (VAR & 2) != 0, kHubPacked = (VAR & 4) != 0;
+walk_hub8_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, Hub8Fields f,
+                 const uint32_t *__restrict__ rl_new, const uint32_t *__restrict__ sorted_id,
+                 const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps,
+                 uint64_t seed, Sampler smp, bool visit_start, uint32_t *__restrict__ visits,
+                 uint32_t *__restrict__ paths, unsigned long long *__restrict__ next_chunk) {
     extern __shared__ __align__(16) unsigned char hub_smem[];
-    unsigned long long *s_hub = reinterpret_cast<unsigned long long *>(hub_smem);  // hubs + 1 words
-    uint32_t *s_off = reinterpret_cast<uint32_t *>(hub_smem);                       // or: hubs + 1
-    uint32_t *s_orig = s_off + f.hubs + 1;                                           //     hubs (id | count)
-    uint32_t *s_cnt = s_orig + f.hubs;                                               //     hubs
-    const uint64_t keep = (uint64_t)f.mask_id | (f.mask_off << f.sh_off);
-    // packed hubs: count in bits [hub_pk_shift, 32) of the id word
-    const uint32_t pk_one = 1u << (f.hub_pk_shift & 31);
-    const uint32_t pk_cmask = kHubPacked ? (0xffffffffu >> f.hub_pk_shift) : 0u;
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(hub_smem);  // hubs + 1 row offsets
+    uint32_t *s_idc = s_off + f.hubs + 1;                      // hubs words {id | count}
     for (uint32_t i = threadIdx.x; i < f.hubs; i += blockDim.x) {
         const uint64_t w = __ldg(rl_rec8 + i);
-        if constexpr (kHubWords) {
-            s_hub[i] = w & keep;
-        } else if constexpr (kHubPacked) {
-            s_off[i] = (uint32_t)((w >> f.sh_off) & f.mask_off);
-            s_orig[i] = (uint32_t)w & f.mask_id;
-        } else {
-            s_off[i] = (uint32_t)((w >> f.sh_off) & f.mask_off);
-            s_orig[i] = (uint32_t)w & f.mask_id;
-            s_cnt[i] = 0;
-        }
+        s_off[i] = (uint32_t)((w >> f.sh_off) & f.mask_off);
+        s_idc[i] = (uint32_t)w & f.mask_id;
     }
-    if (threadIdx.x == 0) {  // the row end of the last hub
-        const uint64_t end = f.hubs < f.n ? (__ldg(rl_rec8 + f.hubs) >> f.sh_off) & f.mask_off : f.nnz;
-        if constexpr (kHubWords) s_hub[f.hubs] = end << f.sh_off;
-        else s_off[f.hubs] = (uint32_t)end;
-    }
+    if (threadIdx.x == 0)  // the row end of the last hub
+        s_off[f.hubs] = (uint32_t)(f.hubs < f.n ? (__ldg(rl_rec8 + f.hubs) >> f.sh_off) & f.mask_off : f.nnz);
     __syncthreads();
-    const unsigned long long hub_one = 1ull << f.sh_deg, rec_one = 1ull << f.sh_cnt;
-    const uint32_t hub_cmask = (1u << f.hub_cnt_bits) - 1u, rec_cmask = (1u << f.cnt_bits) - 1u;
-
-    // a visit of hub x: count it, and (when the walk moved there) load its
-    // original id, row offset and degree
-    auto hub_visit = [&](uint32_t x, bool load, uint32_t &orig, uint64_t &off, uint32_t &deg) {
-        if constexpr (kHubWords) {
-            const unsigned long long w = atomicAdd(s_hub + x, hub_one);
-            if (((uint32_t)(w >> f.sh_deg) & hub_cmask) == hub_cmask)
-                atomicAdd(visits + ((uint32_t)w & f.mask_id), hub_cmask + 1u);
-            if (load) {
-                orig = (uint32_t)w & f.mask_id;
-                off = (w >> f.sh_off) & f.mask_off;
-                deg = (uint32_t)(((s_hub[x + 1] >> f.sh_off) & f.mask_off) - off);
-            }
-        } else if constexpr (kHubPacked) {
-            const uint32_t w = atomicAdd(s_orig + x, pk_one);
-            if ((w >> f.hub_pk_shift) == pk_cmask) atomicAdd(visits + (w & f.mask_id), pk_cmask + 1u);
-            if (load) {
-                orig = w & f.mask_id;
-                off = s_off[x];
-                deg = s_off[x + 1] - s_off[x];
-            }
-        } else {
-            atomicAdd(s_cnt + x, 1u);
-            if (load) {
-                orig = s_orig[x];
-                off = s_off[x];
-                deg = s_off[x + 1] - s_off[x];
-            }
-        }
-    };
-    auto hub_peek = [&](uint32_t x, uint64_t &off, uint32_t &deg) {
-        if constexpr (kHubWords) {
-            off = (s_hub[x] >> f.sh_off) & f.mask_off;
-            deg = (uint32_t)(((s_hub[x + 1] >> f.sh_off) & f.mask_off) - off);
-        } else {
-            off = s_off[x];
-            deg = s_off[x + 1] - s_off[x];
-        }
-    };
-    // a visit of another vertex x
-    auto rec_visit = [&](uint32_t x, bool load, uint32_t &orig, uint64_t &off, uint32_t &deg) {
-        if constexpr (kRecCount) {
-            const unsigned long long w = atomicAdd(rec_cnt + x, rec_one);
-            if (((uint32_t)(w >> f.sh_cnt) & rec_cmask) == rec_cmask)
-                atomicAdd(visits + ((uint32_t)w & f.mask_id), rec_cmask + 1u);
-            if (load) {
-                orig = (uint32_t)w & f.mask_id;
-                off = (w >> f.sh_off) & f.mask_off;
-                deg = (uint32_t)(w >> f.sh_deg) & f.mask_deg;
-            }
-        } else {
-            if (load) {
-                const uint64_t w = __ldg(rl_rec8 + x);
-                orig = (uint32_t)w & f.mask_id;
-                off = (w >> f.sh_off) & f.mask_off;
-                deg = (uint32_t)(w >> f.sh_deg) & f.mask_deg;
-            }
-            atomicAdd(visits + orig, 1u);
-        }
-    };
+    const uint32_t one = 1u << f.cnt_shift, cmask = 0xffffffffu >> f.cnt_shift;
 
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t n_valid = *n_valid_ptr;
@@ -769,8 +681,8 @@ walk_counted_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, uns
         const uint64_t base = chunk * 32ull * W;
         if (base >= n_valid) break;
 
-        uint32_t x[W], orig[W], id[W], deg[W];
-        uint64_t off[W], st[W], gs[W];
+        uint32_t x[W], orig[W], id[W], deg[W], off[W];
+        uint64_t st[W], gs[W];
         uint32_t xw[W];  // the walk's fixed seed (literal SABA word only)
         bool act[W];
 #pragma unroll
@@ -780,24 +692,24 @@ walk_counted_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, uns
             id[j] = 0u;
             orig[j] = 0u;
             x[j] = 0u;
-            off[j] = 0;
-            deg[j] = 0;
+            off[j] = 0u;
+            deg[j] = 0u;
             if (act[j]) {
                 id[j] = sorted_id[p];
                 orig[j] = sorted_start[p];
                 x[j] = rl_new[orig[j]];
-                uint32_t o = orig[j];
                 if (x[j] < f.hubs) {
-                    if (visit_start) hub_visit(x[j], true, o, off[j], deg[j]);
-                    else hub_peek(x[j], off[j], deg[j]);
-                } else {
                     if (visit_start) {
-                        rec_visit(x[j], true, o, off[j], deg[j]);
-                    } else {
-                        const uint64_t w = __ldg(rl_rec8 + x[j]);
-                        off[j] = (w >> f.sh_off) & f.mask_off;
-                        deg[j] = (uint32_t)(w >> f.sh_deg) & f.mask_deg;
+                        const uint32_t w = atomicAdd(s_idc + x[j], one);
+                        if ((w >> f.cnt_shift) == cmask) atomicAdd(visits + orig[j], cmask + 1u);
                     }
+                    off[j] = s_off[x[j]];
+                    deg[j] = s_off[x[j] + 1] - off[j];
+                } else {
+                    const uint64_t w = __ldg(rl_rec8 + x[j]);
+                    off[j] = (uint32_t)((w >> f.sh_off) & f.mask_off);
+                    deg[j] = (uint32_t)(w >> f.sh_deg) & f.mask_deg;
+                    if (visit_start) atomicAdd(visits + orig[j], 1u);
                 }
             }
             st[j] = walk_key(seed, kBatchStream, id[j]);
@@ -815,43 +727,37 @@ walk_counted_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, uns
                 moved[j] = deg[j] != 0;
                 if (moved[j]) {
                     const uint32_t k = choose(sample_word<COUPLED>(st[j], gs[j], orig[j], smp.t, xw[j]), deg[j]);
-                    x[j] = el.id(off[j] + k);
+                    x[j] = el.id((uint64_t)off[j] + k);
                 }
             }
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 if (!act[j]) continue;
-                if (x[j] < f.hubs) hub_visit(x[j], moved[j], orig[j], off[j], deg[j]);
-                else rec_visit(x[j], moved[j], orig[j], off[j], deg[j]);
+                if (x[j] < f.hubs) {
+                    const uint32_t w = atomicAdd(s_idc + x[j], one);
+                    if ((w >> f.cnt_shift) == cmask) atomicAdd(visits + (w & f.mask_id), cmask + 1u);
+                    if (moved[j]) {
+                        orig[j] = w & f.mask_id;
+                        off[j] = s_off[x[j]];
+                        deg[j] = s_off[x[j] + 1] - off[j];
+                    }
+                } else {
+                    if (moved[j]) {
+                        const uint64_t w = __ldg(rl_rec8 + x[j]);
+                        orig[j] = (uint32_t)w & f.mask_id;
+                        off[j] = (uint32_t)((w >> f.sh_off) & f.mask_off);
+                        deg[j] = (uint32_t)(w >> f.sh_deg) & f.mask_deg;
+                    }
+                    atomicAdd(visits + orig[j], 1u);
+                }
                 if (paths) paths[(uint64_t)id[j] * ((uint64_t)n_steps + 1) + l] = orig[j];
             }
         }
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < f.hubs; i += blockDim.x) {
-        if constexpr (kHubWords) {
-            const unsigned long long w = s_hub[i];
-            const uint32_t c = (uint32_t)(w >> f.sh_deg) & hub_cmask;
-            if (c) atomicAdd(visits + ((uint32_t)w & f.mask_id), c);
-        } else if constexpr (kHubPacked) {
-            const uint32_t w = s_orig[i];
-            if (w >> f.hub_pk_shift) atomicAdd(visits + (w & f.mask_id), w >> f.hub_pk_shift);
-        } else {
-            const uint32_t c = s_cnt[i];
-            if (c) atomicAdd(visits + s_orig[i], c);
-        }
-    }
-}
-
-// The counts left in the records of internal ids [from, n) go to visits.
-__global__ void counted_flush_kernel(const unsigned long long *__restrict__ rec_cnt, uint32_t from, CountedFields f,
-                                     uint32_t *__restrict__ visits) {
-    const uint32_t rec_cmask = (1u << f.cnt_bits) - 1u;
-    for (uint64_t x = from + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < f.n;
-         x += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long w = rec_cnt[x];
-        const uint32_t c = (uint32_t)(w >> f.sh_cnt) & rec_cmask;
-        if (c) atomicAdd(visits + ((uint32_t)w & f.mask_id), c);
+        const uint32_t w = s_idc[i];
+        if (w >> f.cnt_shift) atomicAdd(visits + (w & f.mask_id), w >> f.cnt_shift);
     }
 }
 
@@ -1065,43 +971,41 @@ bool launch_relabel(const DeviceGraph &g, const uint32_t *sid, const uint32_t *s
 #undef BQ_RL
 }
 
-// The counted kernel's fields on this graph, and whether it can run: the
-// hubs must cover every vertex whose degree the records do not hold, and
-// both count fields need at least kMinCountBits bits.
+// The 8-byte-hub kernel's fields on this graph, and whether it can run: the
+// hubs must cover every vertex whose degree the records do not hold, row
+// offsets must fit 32 bits, and a hub word needs at least kMinCountBits
+// count bits above the id.
 constexpr uint32_t kMinCountBits = 8;
 
-bool counted_fields(const DeviceGraph &g, CountedFields &f, uint32_t hub_bytes) {
-    if (!g.rl_pk || !g.rl_rec8) return false;
-    uint32_t hubs = tuning_counted_hubs();
+bool hub8_fields(const DeviceGraph &g, Hub8Fields &f) {
+    if (!g.rl_pk || !g.rl_rec8 || g.nnz >= (1ull << 32) || g.rl_sh_off >= 32) return false;
+    uint32_t hubs = tuning_hub8_hubs();
     if (hubs == 0)  // as many as the plain relabel kernel's shared memory holds
-        hubs = (uint32_t)(((size_t)12 * g.rl_hubs + 4 - (hub_bytes == 8 ? 8 : 4)) / hub_bytes);
+        hubs = (uint32_t)(((size_t)12 * g.rl_hubs + 4 - 4) / 8);
     if (hubs > g.rl_live) hubs = g.rl_live;
     if (hubs < g.rl_fit) return false;
+    const uint32_t cap = tuning_hub8_count_bits();
+    uint32_t bits = 32 - g.rl_sh_off;
+    if (bits < kMinCountBits && !cap) return false;
+    if (cap && cap < bits) bits = cap;
     f.sh_off = g.rl_sh_off;
     f.sh_deg = g.rl_sh_deg;
-    f.sh_cnt = g.rl_sh_deg + g.rl_bits_deg;
-    if (f.sh_cnt + kMinCountBits > 64 || f.sh_deg + kMinCountBits > 64) return false;
     f.mask_id = g.rl_mask_id;
     f.mask_off = g.rl_mask_off;
     f.mask_deg = g.rl_bits_deg >= 32 ? 0xffffffffu : ((1u << g.rl_bits_deg) - 1u);
-    const uint32_t cap = tuning_counted_bits() ? tuning_counted_bits() : 31u;
-    f.cnt_bits = std::min<uint32_t>(64 - f.sh_cnt, cap);
-    f.hub_cnt_bits = std::min<uint32_t>(64 - f.sh_deg, cap);
-    f.hub_pk_shift = f.sh_off >= 32 ? 32u : 32u - std::min<uint32_t>(32 - f.sh_off, cap);
     f.hubs = hubs;
+    f.cnt_shift = 32 - bits;
     f.n = g.n;
     f.nnz = g.nnz;
     return true;
 }
 
-template <int W, bool COUPLED, int VAR>
-bool launch_counted_w(const DeviceGraph &g, const CountedFields &f, unsigned long long *rec_cnt, const uint32_t *sid,
-                      const uint32_t *sst, const uint32_t *n_valid, uint32_t n_steps, uint64_t seed, const Sampler &smp,
-                      bool visit_start, uint32_t *visits, uint32_t *paths, unsigned long long *next_chunk,
-                      cudaStream_t s) {
-    const size_t smem = (VAR & 1) ? (size_t)8 * (f.hubs + 1) : (VAR & 4) ? (size_t)8 * f.hubs + 4
-                                                                            : (size_t)12 * f.hubs + 4;
-    auto kernel = walk_counted_kernel<W, COUPLED, VAR>;
+template <int W, bool COUPLED>
+bool launch_hub8_w(const DeviceGraph &g, const Hub8Fields &f, const uint32_t *sid, const uint32_t *sst,
+                   const uint32_t *n_valid, uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start,
+                   uint32_t *visits, uint32_t *paths, unsigned long long *next_chunk, cudaStream_t s) {
+    const size_t smem = (size_t)8 * f.hubs + 4;
+    auto kernel = walk_hub8_kernel<W, COUPLED>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -1115,49 +1019,29 @@ bool launch_counted_w(const DeviceGraph &g, const CountedFields &f, unsigned lon
         return false;
     }
     const EdgesPackedIds el{g.rl_pk, nullptr, g.pk_bits, g.pk_q, g.pk_mask};
-    if ((VAR & 2) &&
-        cudaMemcpyAsync(rec_cnt, g.rl_rec8, sizeof(uint64_t) * g.n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
     ProfScope prof(kProfWalk, s);
-    count_launches((VAR & 2) ? 2 : 1);
-    count_walk_kernel(BQ_WALK_KERNEL_COUNTED);
-    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec8, rec_cnt, f, g.rl_new, sid, sst, n_valid, n_steps,
-                                                   seed, smp, visit_start, visits, paths, next_chunk);
-    if (VAR & 2) counted_flush_kernel<<<blocks_for(g.n - f.hubs, 256), 256, 0, s>>>(rec_cnt, f.hubs, f, visits);
+    count_launches(1);
+    count_walk_kernel(BQ_WALK_KERNEL_RELABEL8);
+    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec8, f, g.rl_new, sid, sst, n_valid, n_steps, seed, smp,
+                                                   visit_start, visits, paths, next_chunk);
     return true;
 }
 
-bool launch_counted(const DeviceGraph &g, unsigned long long *rec_cnt, const uint32_t *sid, const uint32_t *sst,
-                    const uint32_t *n_valid, uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start,
-                    uint32_t *visits, uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
-    // walk_counted -> VAR: 1 -> 3, 2 -> 2, 3 -> 1, 4 -> 4, 5 -> 6, 6 -> 0
-    static const int kVar[7] = {-1, 3, 2, 1, 4, 6, 0};
-    const int mode = tuning_walk_counted();
-    if (mode <= 0 || mode > 6) return false;
-    const int var = kVar[mode];
-    CountedFields f;
-    if (!counted_fields(g, f, (var & 5) ? 8u : 12u)) return false;
-    // packed hub words need room for their count next to the id
-    if ((var & 4) && (f.sh_off >= 32 || (f.sh_off + kMinCountBits > 32 && !tuning_counted_bits()))) return false;
+bool launch_hub8(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+                 uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
+                 uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
+    Hub8Fields f;
+    if (!tuning_relabel_hub8() || !hub8_fields(g, f)) return false;
     const bool c = smp.kind == 1;
-#define BQ_CNT(WW, VV)                                                                                          \
-    (c ? launch_counted_w<WW, true, VV>(g, f, rec_cnt, sid, sst, n_valid, n_steps, seed, smp, visit_start,      \
-                                        visits, paths, next_chunk, s)                                            \
-       : launch_counted_w<WW, false, VV>(g, f, rec_cnt, sid, sst, n_valid, n_steps, seed, smp, visit_start,     \
-                                         visits, paths, next_chunk, s))
-#define BQ_CNT_W(VV) (lanes_w == 1 ? BQ_CNT(1, VV) : lanes_w == 2 ? BQ_CNT(2, VV) : BQ_CNT(4, VV))
-    switch (var) {
-    case 0: return BQ_CNT_W(0);
-    case 1: return BQ_CNT_W(1);
-    case 2: return BQ_CNT_W(2);
-    case 4: return BQ_CNT_W(4);
-    case 6: return BQ_CNT_W(6);
-    default: return BQ_CNT_W(3);
-    }
-#undef BQ_CNT_W
-#undef BQ_CNT
+#define BQ_H8(WW)                                                                                               \
+    (c ? launch_hub8_w<WW, true>(g, f, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,       \
+                                 next_chunk, s)                                                                   \
+       : launch_hub8_w<WW, false>(g, f, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,      \
+                                  next_chunk, s))
+    if (lanes_w == 1) return BQ_H8(1);
+    if (lanes_w == 2) return BQ_H8(2);
+    return BQ_H8(4);
+#undef BQ_H8
 }
 
 // Group the walks by start vertex into (sid, sst); cursor[n] = valid walks.
@@ -1177,20 +1061,13 @@ int group_by_start(const DeviceGraph &g, const uint32_t *starts, uint64_t n_walk
     return BQ_OK;
 }
 
-// counts[n] | cursor[n + 1] | sorted ids | sorted starts | chunk counter |
-// (with the relabelled copy) the counted records, 8 bytes per vertex
+// counts[n] | cursor[n + 1] | sorted ids | sorted starts | chunk counter
 size_t bouquet_counter_offset(uint32_t n, uint64_t n_walks) {
     return (sizeof(uint32_t) * (2 * (size_t)n + 1 + 2 * (size_t)n_walks) + 15) & ~(size_t)15;
 }
 
-size_t bouquet_records_offset(uint32_t n, uint64_t n_walks) {
+size_t bouquet_arrays_bytes(uint32_t n, uint64_t n_walks) {
     return (bouquet_counter_offset(n, n_walks) + 16 + 255) & ~(size_t)255;
-}
-
-size_t bouquet_arrays_bytes(const DeviceGraph &g, uint64_t n_walks) {
-    size_t b = bouquet_records_offset(g.n, n_walks);
-    if (g.rl_pk) b += (sizeof(uint64_t) * (size_t)g.n + 255) & ~(size_t)255;
-    return b;
 }
 
 // The bouquet walk batch in `scratch` (counts[n] | cursor[n + 1] | sorted
@@ -1219,9 +1096,8 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
     if (g.rl_pk && !checked) {
         auto *next_chunk = reinterpret_cast<unsigned long long *>(scratch + bouquet_counter_offset(g.n, n_walks));
         BQ_CUDA(cudaMemsetAsync(next_chunk, 0, sizeof(unsigned long long), s));
-        auto *rec_cnt = reinterpret_cast<unsigned long long *>(scratch + bouquet_records_offset(g.n, n_walks));
-        if (launch_counted(g, rec_cnt, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths,
-                           next_chunk, lanes_w, s)) {
+        if (launch_hub8(g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths, next_chunk,
+                        lanes_w, s)) {
             BQ_CUDA(cudaGetLastError());
             return BQ_OK;
         }
@@ -1257,16 +1133,16 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
 
 }  // namespace
 
-size_t walk_batch_scratch_bytes(const DeviceGraph &g, uint64_t n_walks) {
-    return bouquet_arrays_bytes(g, n_walks) + scan_u32_ws_bytes(g.n);
+size_t walk_batch_scratch_bytes(uint32_t n, uint64_t n_walks) {
+    return bouquet_arrays_bytes(n, n_walks) + scan_u32_ws_bytes(n);
 }
 
 int launch_walk_batch_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint64_t n_walks,
                          uint32_t n_steps, const Sampler &smp, bool visit_start, uint32_t *visits, uint32_t *paths,
                          uint32_t *status, void *scratch, size_t scratch_bytes, cudaStream_t s) {
     if (n_walks == 0) return BQ_OK;
-    if (walk_batch_scratch_bytes(g, n_walks) > scratch_bytes) return fail(BQ_EINVAL, "scratch too small");
-    const size_t arrays = bouquet_arrays_bytes(g, n_walks);
+    if (walk_batch_scratch_bytes(g.n, n_walks) > scratch_bytes) return fail(BQ_EINVAL, "scratch too small");
+    const size_t arrays = bouquet_arrays_bytes(g.n, n_walks);
     char *base = (char *)scratch;
     return bouquet_in(g, seed, starts, n_walks, n_steps, smp, visit_start, visits, paths, status, base, base + arrays,
                       scratch_bytes - arrays, s);
@@ -1286,7 +1162,7 @@ int launch_walk_batch(const DeviceGraph &g, uint64_t seed, const uint32_t *start
                             paths, status, s);
     }
     char *buf = nullptr;
-    int rc = scratch_alloc((void **)&buf, bouquet_arrays_bytes(g, n_walks), s);
+    int rc = scratch_alloc((void **)&buf, bouquet_arrays_bytes(g.n, n_walks), s);
     if (rc) return rc;
     rc = bouquet_in(g, seed, starts, n_walks, n_steps, smp, visit_start, visits, paths, status, buf, nullptr, 0, s);
     scratch_free(buf, s);

@@ -173,24 +173,24 @@ def test_cluster_hub_table_bit_exact(env, layout, hub_cluster):
         bq.set_tuning(**old)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6])
-@pytest.mark.parametrize("counted_bits", [0, 1, 3])
-@pytest.mark.parametrize("counted_hubs", [0, 700, 2500])
-def test_counted_records_bit_exact(env, counted_hubs, counted_bits, mode):
-    """The counted-record kernel on the relabelled copy of an R-MAT scale 14
-    graph (hub_slots 1024: 1365 plain hubs, the rest in 8-byte records):
-    visits and paths equal the oracle's for every sampler and lane count,
-    with the start counted, for several shared-memory hub counts and with
-    the count fields narrowed to 1 and 3 bits, so that counts wrap on almost
-    every visit (each wrap adds 2^bits to the visits)."""
+@pytest.mark.parametrize("count_bits", [0, 1, 3])
+@pytest.mark.parametrize("hub8_hubs", [0, 700, 2500])
+def test_hub8_kernel_bit_exact(env, hub8_hubs, count_bits):
+    """The 8-byte-hub kernel on the relabelled copy of an R-MAT scale 14
+    graph (hub_slots 1024: 1365 hubs of 12 bytes, 2047 of 8 bytes by
+    default; every vertex of degree >= 64 must be a hub): visits and paths
+    equal the oracle's for two samplers and every lane count, with the start
+    counted, for several hub counts and with the hubs' count field narrowed
+    to 1 and 3 bits, so that counts wrap every 2 or 8 visits (each wrap adds
+    2^bits to the visits)."""
     bq, torch = env
     old = bq.get_tuning()
     g = rmat(14, 8, seed=7)
     try:
         bq.set_tuning(layout=5, hub_slots=1024, hub_relabel=1)
         graph = bq.Graph.from_csr(g)
-        bq.set_tuning(walk_counted=mode, counted_hubs=counted_hubs, counted_bits=counted_bits)
-        rng = np.random.default_rng(counted_hubs + counted_bits)
+        bq.set_tuning(relabel_hub8=1, hub8_hubs=hub8_hubs, hub8_count_bits=count_bits)
+        rng = np.random.default_rng(hub8_hubs + count_bits)
         starts = rng.integers(0, g.n, 40009).astype(np.uint32)  # isolated starts included
         st = dev_u32(torch, starts)
         for sampler in (None, (1, 5, 32)):
@@ -202,9 +202,16 @@ def test_counted_records_bit_exact(env, counted_hubs, counted_bits, mode):
                 paths = torch.zeros((starts.size, 12), dtype=torch.int32, device="cuda")
                 vis = bq.walk_batch(graph, 51, st, 11, sampler=sampler, visit_start=True, paths=paths)
                 bq.sync()
-                assert bq.profile_read()["walk_kernels"]["counted"] == 1
+                assert bq.profile_read()["walk_kernels"]["relabel8"] == 1
                 assert np.array_equal(host_u32(vis), want_v), (sampler, lanes)
                 assert np.array_equal(host_u32(paths), want_p), (sampler, lanes)
+        # too few hubs to cover the high-degree vertices: the 12-byte kernel runs
+        bq.set_tuning(hub8_hubs=100)
+        bq.profile_read()
+        vis = bq.walk_batch(graph, 51, st, 11, visit_start=True)
+        bq.sync()
+        assert bq.profile_read()["walk_kernels"]["relabel"] == 1
+        assert np.array_equal(host_u32(vis), oracle.walk_batch(g, 51, starts, 11, include_start=True))
         graph.close()
     finally:
         bq.set_tuning(**old)
@@ -229,14 +236,13 @@ def test_degree_relabelled_copy_bit_exact(env, hub_slots):
             for sampler in (None, (1, 5, 32), (2, 0, 1)):
                 want_v, want_p = oracle.walk_batch(g, 47, starts, 13, sampler=sampler,
                                                    include_start=True, want_paths=True)
-                for lanes, counted in ((1, 0), (2, 0), (4, 0), (1, 1), (2, 1), (4, 1), (4, 2), (2, 3), (1, 4),
-                                       (2, 4), (4, 4), (4, 5), (2, 6)):
-                    bq.set_tuning(walk_lanes=lanes, walk_counted=counted)
+                for lanes, hub8 in ((1, 0), (2, 0), (4, 0), (1, 1), (2, 1), (4, 1)):
+                    bq.set_tuning(walk_lanes=lanes, relabel_hub8=hub8)
                     paths = torch.zeros((starts.size, 14), dtype=torch.int32, device="cuda")
                     vis = bq.walk_batch(graph, 47, st, 13, sampler=sampler, visit_start=True, paths=paths)
                     bq.sync()
-                    assert np.array_equal(host_u32(vis), want_v), (name, sampler, lanes, counted)
-                    assert np.array_equal(host_u32(paths), want_p), (name, sampler, lanes, counted)
+                    assert np.array_equal(host_u32(vis), want_v), (name, sampler, lanes, hub8)
+                    assert np.array_equal(host_u32(paths), want_p), (name, sampler, lanes, hub8)
                 vis = bq.walk_batch(graph, 47, st, 13, sampler=sampler)
                 bq.sync()
                 assert np.array_equal(host_u32(vis), oracle.walk_batch(g, 47, starts, 13, sampler=sampler))
@@ -358,18 +364,18 @@ def test_full_size_relabelled_batch_matches_oracle(env):
     want = oracle.walk_paths_by_id(g, 2024, ids, starts[ids.astype(np.int64)], n_steps)
     tids = torch.from_numpy(ids.astype(np.int64)).cuda()
     paths = torch.empty((n_walks, n_steps + 1), dtype=torch.int32, device="cuda")
-    kernel = {0: "relabel", 1: "counted", 2: "counted", 3: "counted", 4: "counted", 5: "counted", 6: "counted"}
+    kernel = {0: "relabel", 1: "relabel8"}
     try:
-        for counted in (1, 0, 2, 3, 4, 5, 6):
+        for hub8 in (1, 0):
             for lanes in (1, 2, 4):
-                bq.set_tuning(walk_lanes=lanes, walk_counted=counted)
+                bq.set_tuning(walk_lanes=lanes, relabel_hub8=hub8)
                 bq.profile_read()
                 vr = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_BOUQUET)
                 paths.fill_(-1)
                 vp = bq.walk_batch(graph, 2024, st, n_steps, mode=bq.MODE_BOUQUET, paths=paths)
                 bq.sync()
-                case = (counted, lanes)
-                assert bq.profile_read()["walk_kernels"][kernel[counted]] == 2, case
+                case = (hub8, lanes)
+                assert bq.profile_read()["walk_kernels"][kernel[hub8]] == 2, case
                 assert torch.equal(vr, vh), case
                 assert torch.equal(vp, vh), case
                 assert int(vr.to(torch.int64).sum()) == n_walks * n_steps

@@ -74,10 +74,16 @@ def test_tuning_roundtrip_and_validation(lib):
     old = bq.get_tuning()
     try:
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
-        assert bq.get_tuning() == {"walk_lanes": 2, "aggregate_visits": 1, "aesc_lanes": 8,
-                                   "layout": old["layout"], "hub_slots": old["hub_slots"],
-                                   "l2_hints": old["l2_hints"], "aesc_hub": old["aesc_hub"],
-                                   "hub_cluster": old["hub_cluster"], "hub_relabel": old["hub_relabel"]}
+        assert bq.get_tuning() == dict(old, walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
+        assert (old["relabel_hub8"], old["hub8_hubs"], old["hub8_count_bits"]) == (1, 0, 0)  # defaults
+        bq.set_tuning(relabel_hub8=0, hub8_hubs=28000, hub8_count_bits=31)
+        assert bq.get_tuning()["hub8_hubs"] == 28000
+        for bad in (dict(relabel_hub8=2), dict(hub8_hubs=28001), dict(hub8_count_bits=32)):
+            with pytest.raises(bq.BouquetError):
+                bq.set_tuning(**bad)
+        with pytest.raises(ValueError):
+            bq.set_tuning(no_such_knob=1)
+        bq.set_tuning(relabel_hub8=1, hub8_hubs=0, hub8_count_bits=0)
         bq.set_tuning(hub_relabel=1)
         assert bq.get_tuning()["hub_relabel"] == 1
         with pytest.raises(bq.BouquetError):

@@ -96,7 +96,7 @@ def test_noalloc_relabelled_copy_matches_oracle_twice(env):
             assert np.array_equal(host_u32(vis), want_v), f"visits differ from the oracle on call {call}"
             assert np.array_equal(host_u32(paths), want_p), f"paths differ from the oracle on call {call}"
         launched = bq.profile_read()["walk_kernels"]
-        assert launched["relabel"] + launched["counted"] == 2, launched
+        assert launched["relabel"] + launched["relabel8"] == 2, launched
         graph.close()
     finally:
         bq.set_tuning(**old)
