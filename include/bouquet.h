@@ -218,7 +218,7 @@ int bq_walk_batch(const bq_graph *g, uint64_t seed, const uint32_t *starts_dev,
  * buffers only (flags: BQ_VISIT_START; BQ_HOST_IO is rejected).  Its scratch
  * is a fixed 32 MiB array in the library's device memory, held by every
  * device that loads the library's module until the process exits; a batch
- * needs 4 * (2 n + 1 + 2 n_walks) bytes plus a small scan workspace, and a
+ * needs about 4 * (2 n + 1 + 2 n_walks) bytes plus a small scan workspace, and a
  * larger request fails with BQ_EINVAL and a message giving both sizes.  The
  * first call on a device looks up the array's device address (make it before
  * any stream capture).  All calls share the array: calls whose work overlaps

@@ -107,15 +107,13 @@ __global__ void hist_starts_kernel(const uint32_t *__restrict__ starts, uint64_t
 // placed in its bucket (order inside a bucket is unspecified and does not
 // change any result).
 __global__ void scatter_starts_kernel(const uint32_t *__restrict__ starts, uint64_t n_walks, uint32_t n,
-                                      uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted_id,
-                                      uint32_t *__restrict__ sorted_start) {
+                                      uint32_t *__restrict__ cursor, uint2 *__restrict__ sorted) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_walks;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t s = starts[i];
         if (s >= n) continue;
         const uint32_t pos = atomicAdd(cursor + s, 1u);
-        sorted_id[pos] = (uint32_t)i;
-        sorted_start[pos] = s;
+        sorted[pos] = make_uint2((uint32_t)i, s);  // one 8-byte store
     }
 }
 
@@ -129,7 +127,7 @@ constexpr uint32_t kSabaRun = 1024;
 
 __global__ void __launch_bounds__(256)
 saba_order_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ cursor, uint32_t n,
-                  uint64_t seed, uint32_t *__restrict__ sorted_id) {
+                  uint64_t seed, uint2 *__restrict__ sorted) {
     __shared__ uint32_t s_key[kSabaRun];
     __shared__ uint32_t s_id[kSabaRun];
     for (uint32_t v = blockIdx.x; v < n; v += gridDim.x) {
@@ -142,7 +140,7 @@ saba_order_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restric
             while (m < len) m <<= 1;
             for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
                 if (i < len) {
-                    const uint32_t id = sorted_id[lo + i];
+                    const uint32_t id = sorted[lo + i].x;
                     s_id[i] = id;
                     s_key[i] = (uint32_t)walk_key(seed, kBatchStream, id);
                 } else {
@@ -170,7 +168,7 @@ saba_order_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restric
                     __syncthreads();
                 }
             }
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sorted_id[lo + i] = s_id[i];
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) sorted[lo + i].x = s_id[i];
             __syncthreads();
         }
     }
@@ -188,8 +186,7 @@ saba_order_kernel(const uint32_t *__restrict__ counts, const uint32_t *__restric
 // visit increments (match + popc) before one atomic.
 template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kThreads)
-walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ sorted_id,
-                    const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr,
+walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint2 *__restrict__ sorted, const uint32_t *__restrict__ n_valid_ptr,
                     uint32_t n_steps, uint64_t seed, Sampler smp, bool visit_start, bool checked, bool agg,
                     uint32_t *__restrict__ visits, uint32_t *__restrict__ paths, uint32_t *status) {
     const uint32_t lane = threadIdx.x & 31;
@@ -207,8 +204,9 @@ walk_bouquet_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *
         const uint64_t p = base + (uint64_t)j * 32 + lane;
         act[j] = p < n_valid;
         amask[j] = __ballot_sync(0xffffffffu, act[j]);
-        id[j] = act[j] ? sorted_id[p] : 0u;
-        cur[j] = act[j] ? sorted_start[p] : 0u;
+        const uint2 ws = act[j] ? sorted[p] : make_uint2(0u, 0u);
+        id[j] = ws.x;
+        cur[j] = ws.y;
         off[j] = 0;
         deg[j] = 0;
         if (act[j]) start_record(offsets, cur[j], off[j], deg[j]);
@@ -269,7 +267,7 @@ constexpr int kHubThreads = 1024;
 template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kHubThreads, 1)
 walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ hub_tag, uint32_t hub_slots,
-                const uint32_t *__restrict__ sorted_id, const uint32_t *__restrict__ sorted_start,
+                const uint2 *__restrict__ sorted,
                 const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps, uint64_t seed, Sampler smp,
                 bool visit_start, uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
                 unsigned long long *__restrict__ next_chunk, bool l2_hints) {
@@ -317,8 +315,9 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
             id[j] = 0u;
             cur[j] = 0u;
             if (act[j]) {
-                id[j] = l2_hints ? ldg_pol(sorted_id + p, pol_stream) : sorted_id[p];
-                cur[j] = l2_hints ? ldg_pol(sorted_start + p, pol_stream) : sorted_start[p];
+                const uint2 ws = l2_hints ? ldg_pol(sorted + p, pol_stream) : sorted[p];
+                id[j] = ws.x;
+                cur[j] = ws.y;
             }
             off[j] = 0;
             deg[j] = 0;
@@ -392,8 +391,7 @@ walk_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__re
 template <typename EL, int W, bool COUPLED>
 __global__ void __launch_bounds__(kHubThreads, 1)
 walk_cluster_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ hub_tag,
-                        uint32_t hub_slots, const uint32_t *__restrict__ sorted_id,
-                        const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr,
+                        uint32_t hub_slots, const uint2 *__restrict__ sorted, const uint32_t *__restrict__ n_valid_ptr,
                         uint32_t n_steps, uint64_t seed, Sampler smp, bool visit_start,
                         uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
                         unsigned long long *__restrict__ next_chunk) {
@@ -442,8 +440,9 @@ walk_cluster_hub_kernel(EL el, const int64_t *__restrict__ offsets, const uint32
             id[j] = 0u;
             cur[j] = 0u;
             if (act[j]) {
-                id[j] = sorted_id[p];
-                cur[j] = sorted_start[p];
+                const uint2 ws = sorted[p];
+                id[j] = ws.x;
+                cur[j] = ws.y;
             }
             off[j] = 0;
             deg[j] = 0;
@@ -520,7 +519,7 @@ __global__ void __launch_bounds__(kHubThreads, 1)
 walk_relabel_kernel(EdgesPackedIds el, const uint4 *__restrict__ rl_rec, const uint64_t *__restrict__ rl_rec8,
                     uint32_t sh_off, uint32_t sh_deg, uint32_t mask_id, uint64_t mask_off,
                     const uint32_t *__restrict__ rl_new,
-                    uint32_t hubs, const uint32_t *__restrict__ sorted_id, const uint32_t *__restrict__ sorted_start,
+                    uint32_t hubs, const uint2 *__restrict__ sorted,
                     const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps, uint64_t seed, Sampler smp,
                     bool visit_start, uint32_t *__restrict__ visits, uint32_t *__restrict__ paths,
                     unsigned long long *__restrict__ next_chunk) {
@@ -560,8 +559,9 @@ walk_relabel_kernel(EdgesPackedIds el, const uint4 *__restrict__ rl_rec, const u
             off[j] = 0;
             deg[j] = 0;
             if (act[j]) {
-                id[j] = sorted_id[p];
-                orig[j] = sorted_start[p];
+                const uint2 ws = sorted[p];
+                id[j] = ws.x;
+                orig[j] = ws.y;
                 x[j] = rl_new[orig[j]];
                 if (x[j] < hubs) {
                     off[j] = s_off[x[j]];
@@ -654,9 +654,8 @@ struct Hub8Fields {
 
 template <int W, bool COUPLED>
 __global__ void __launch_bounds__(kHubThreads, 1)
-walk_hub8_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, Hub8Fields f,
-                 const uint32_t *__restrict__ rl_new, const uint32_t *__restrict__ sorted_id,
-                 const uint32_t *__restrict__ sorted_start, const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps,
+walk_relabel8_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, Hub8Fields f,
+                 const uint32_t *__restrict__ rl_new, const uint2 *__restrict__ sorted, const uint32_t *__restrict__ n_valid_ptr, uint32_t n_steps,
                  uint64_t seed, Sampler smp, bool visit_start, uint32_t *__restrict__ visits,
                  uint32_t *__restrict__ paths, unsigned long long *__restrict__ next_chunk) {
     extern __shared__ __align__(16) unsigned char hub_smem[];
@@ -695,8 +694,9 @@ walk_hub8_kernel(EdgesPackedIds el, const uint64_t *__restrict__ rl_rec8, Hub8Fi
             off[j] = 0u;
             deg[j] = 0u;
             if (act[j]) {
-                id[j] = sorted_id[p];
-                orig[j] = sorted_start[p];
+                const uint2 ws = sorted[p];
+                id[j] = ws.x;
+                orig[j] = ws.y;
                 x[j] = rl_new[orig[j]];
                 if (x[j] < f.hubs) {
                     if (visit_start) {
@@ -787,7 +787,7 @@ int launch_naive(RL rl, const DeviceGraph &g, uint64_t seed, const uint32_t *sta
 }
 
 template <typename EL, int W>
-void launch_bouquet_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+void launch_bouquet_w(EL el, const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                       uint64_t n_walks, uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start,
                       bool checked, bool agg, uint32_t *visits, uint32_t *paths, uint32_t *status, cudaStream_t s) {
     const unsigned grid = blocks_for(n_walks, (uint64_t)kThreads * W);
@@ -795,28 +795,28 @@ void launch_bouquet_w(EL el, const DeviceGraph &g, const uint32_t *sid, const ui
     count_launches(1);
     count_walk_kernel(BQ_WALK_KERNEL_BOUQUET);
     if (smp.kind == 1)
-        walk_bouquet_kernel<EL, W, true><<<grid, kThreads, 0, s>>>(el, g.offsets, sid, sst, n_valid, n_steps, seed,
+        walk_bouquet_kernel<EL, W, true><<<grid, kThreads, 0, s>>>(el, g.offsets, sorted, n_valid, n_steps, seed,
                                                                    smp, visit_start, checked, agg, visits, paths,
                                                                    status);
     else
-        walk_bouquet_kernel<EL, W, false><<<grid, kThreads, 0, s>>>(el, g.offsets, sid, sst, n_valid, n_steps, seed,
+        walk_bouquet_kernel<EL, W, false><<<grid, kThreads, 0, s>>>(el, g.offsets, sorted, n_valid, n_steps, seed,
                                                                     smp, visit_start, checked, agg, visits, paths,
                                                                     status);
 }
 
 template <typename EL>
-void launch_bouquet_any(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst,
+void launch_bouquet_any(EL el, const DeviceGraph &g, const uint2 *sorted,
                         const uint32_t *n_valid, uint64_t n_walks, uint32_t n_steps, uint64_t seed,
                         const Sampler &smp, bool visit_start, bool checked, bool agg, uint32_t *visits,
                         uint32_t *paths, uint32_t *status, int lanes_w, cudaStream_t s) {
     switch (lanes_w) {
-    case 1: launch_bouquet_w<EL, 1>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+    case 1: launch_bouquet_w<EL, 1>(el, g, sorted, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
                                     visits, paths, status, s); break;
-    case 2: launch_bouquet_w<EL, 2>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+    case 2: launch_bouquet_w<EL, 2>(el, g, sorted, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
                                     visits, paths, status, s); break;
-    case 8: launch_bouquet_w<EL, 8>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+    case 8: launch_bouquet_w<EL, 8>(el, g, sorted, n_valid, n_walks, n_steps, seed, smp, visit_start, checked, agg,
                                     visits, paths, status, s); break;
-    default: launch_bouquet_w<EL, 4>(el, g, sid, sst, n_valid, n_walks, n_steps, seed, smp, visit_start, checked,
+    default: launch_bouquet_w<EL, 4>(el, g, sorted, n_valid, n_walks, n_steps, seed, smp, visit_start, checked,
                                      agg, visits, paths, status, s); break;
     }
 }
@@ -824,7 +824,7 @@ void launch_bouquet_any(EL el, const DeviceGraph &g, const uint32_t *sid, const 
 // Launch the hub kernel; returns false (nothing launched) when a block of
 // kHubThreads with the table does not fit on an SM.
 template <typename EL, int W, bool COUPLED>
-bool launch_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+bool launch_hub_w(EL el, const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                   uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                   uint32_t *paths, unsigned long long *next_chunk, cudaStream_t s) {
     const size_t smem = (size_t)16 * g.hub_slots;
@@ -844,21 +844,21 @@ bool launch_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32
     ProfScope prof(kProfWalk, s);
     count_launches(1);
     count_walk_kernel(BQ_WALK_KERNEL_HUB);
-    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.offsets, g.hub_tag, g.hub_slots, sid, sst, n_valid, n_steps,
+    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.offsets, g.hub_tag, g.hub_slots, sorted, n_valid, n_steps,
                                                    seed, smp, visit_start, visits, paths, next_chunk,
                                                    tuning_l2_hints());
     return true;
 }
 
 template <typename EL>
-bool launch_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+bool launch_hub(EL el, const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                 uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                 uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
     const bool c = smp.kind == 1;
 #define BQ_HUB(WW)                                                                                                 \
-    (c ? launch_hub_w<EL, WW, true>(el, g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,   \
+    (c ? launch_hub_w<EL, WW, true>(el, g, sorted, n_valid, n_steps, seed, smp, visit_start, visits, paths,   \
                                     next_chunk, s)                                                             \
-       : launch_hub_w<EL, WW, false>(el, g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,  \
+       : launch_hub_w<EL, WW, false>(el, g, sorted, n_valid, n_steps, seed, smp, visit_start, visits, paths,  \
                                      next_chunk, s))
     if (lanes_w == 1) return BQ_HUB(1);
     if (lanes_w == 2) return BQ_HUB(2);
@@ -870,7 +870,7 @@ bool launch_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t
 // can be resident at once (the grid is persistent); false (nothing launched)
 // when no such cluster fits.
 template <typename EL, int W, bool COUPLED>
-bool launch_cluster_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst,
+bool launch_cluster_hub_w(EL el, const DeviceGraph &g, const uint2 *sorted,
                           const uint32_t *n_valid, uint32_t n_steps, uint64_t seed, const Sampler &smp,
                           bool visit_start, uint32_t *visits, uint32_t *paths, unsigned long long *next_chunk,
                           cudaStream_t s) {
@@ -901,7 +901,7 @@ bool launch_cluster_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, cons
     cfg.gridDim = dim3((unsigned)clusters * csize);
     ProfScope prof(kProfWalk, s);
     count_launches(1);
-    if (cudaLaunchKernelEx(&cfg, kernel, el, g.offsets, g.hub_tag, g.hub_slots, sid, sst, n_valid, n_steps, seed, smp,
+    if (cudaLaunchKernelEx(&cfg, kernel, el, g.offsets, g.hub_tag, g.hub_slots, sorted, n_valid, n_steps, seed, smp,
                            visit_start, visits, paths, next_chunk) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -911,14 +911,14 @@ bool launch_cluster_hub_w(EL el, const DeviceGraph &g, const uint32_t *sid, cons
 }
 
 template <typename EL>
-bool launch_cluster_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+bool launch_cluster_hub(EL el, const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                         uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                         uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
     const bool c = smp.kind == 1;
 #define BQ_CHUB(WW)                                                                                             \
-    (c ? launch_cluster_hub_w<EL, WW, true>(el, g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, \
+    (c ? launch_cluster_hub_w<EL, WW, true>(el, g, sorted, n_valid, n_steps, seed, smp, visit_start, visits, \
                                             paths, next_chunk, s)                                             \
-       : launch_cluster_hub_w<EL, WW, false>(el, g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, \
+       : launch_cluster_hub_w<EL, WW, false>(el, g, sorted, n_valid, n_steps, seed, smp, visit_start, visits, \
                                              paths, next_chunk, s))
     if (lanes_w == 1) return BQ_CHUB(1);
     if (lanes_w == 2) return BQ_CHUB(2);
@@ -929,7 +929,7 @@ bool launch_cluster_hub(EL el, const DeviceGraph &g, const uint32_t *sid, const 
 // Launch the relabelled-copy kernel: one persistent block of kHubThreads per
 // SM; false (nothing launched) when the hub arrays do not fit.
 template <int W, bool COUPLED>
-bool launch_relabel_w(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+bool launch_relabel_w(const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                       uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                       uint32_t *paths, unsigned long long *next_chunk, cudaStream_t s) {
     const size_t smem = (size_t)12 * g.rl_hubs + 4;
@@ -951,19 +951,19 @@ bool launch_relabel_w(const DeviceGraph &g, const uint32_t *sid, const uint32_t 
     count_launches(1);
     count_walk_kernel(BQ_WALK_KERNEL_RELABEL);
     kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec, g.rl_rec8, g.rl_sh_off, g.rl_sh_deg, g.rl_mask_id,
-                                                   g.rl_mask_off, g.rl_new, g.rl_hubs, sid, sst, n_valid, n_steps,
+                                                   g.rl_mask_off, g.rl_new, g.rl_hubs, sorted, n_valid, n_steps,
                                                    seed, smp, visit_start, visits, paths, next_chunk);
     return true;
 }
 
-bool launch_relabel(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+bool launch_relabel(const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                     uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                     uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
     const bool c = smp.kind == 1;
 #define BQ_RL(WW)                                                                                               \
-    (c ? launch_relabel_w<WW, true>(g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,        \
+    (c ? launch_relabel_w<WW, true>(g, sorted, n_valid, n_steps, seed, smp, visit_start, visits, paths,        \
                                     next_chunk, s)                                                               \
-       : launch_relabel_w<WW, false>(g, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,       \
+       : launch_relabel_w<WW, false>(g, sorted, n_valid, n_steps, seed, smp, visit_start, visits, paths,       \
                                      next_chunk, s))
     if (lanes_w == 1) return BQ_RL(1);
     if (lanes_w == 2) return BQ_RL(2);
@@ -1001,11 +1001,11 @@ bool hub8_fields(const DeviceGraph &g, Hub8Fields &f) {
 }
 
 template <int W, bool COUPLED>
-bool launch_hub8_w(const DeviceGraph &g, const Hub8Fields &f, const uint32_t *sid, const uint32_t *sst,
+bool launch_hub8_w(const DeviceGraph &g, const Hub8Fields &f, const uint2 *sorted,
                    const uint32_t *n_valid, uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start,
                    uint32_t *visits, uint32_t *paths, unsigned long long *next_chunk, cudaStream_t s) {
     const size_t smem = (size_t)8 * f.hubs + 4;
-    auto kernel = walk_hub8_kernel<W, COUPLED>;
+    auto kernel = walk_relabel8_kernel<W, COUPLED>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -1022,21 +1022,21 @@ bool launch_hub8_w(const DeviceGraph &g, const Hub8Fields &f, const uint32_t *si
     ProfScope prof(kProfWalk, s);
     count_launches(1);
     count_walk_kernel(BQ_WALK_KERNEL_RELABEL8);
-    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec8, f, g.rl_new, sid, sst, n_valid, n_steps, seed, smp,
+    kernel<<<sms * per_sm, kHubThreads, smem, s>>>(el, g.rl_rec8, f, g.rl_new, sorted, n_valid, n_steps, seed, smp,
                                                    visit_start, visits, paths, next_chunk);
     return true;
 }
 
-bool launch_hub8(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst, const uint32_t *n_valid,
+bool launch_hub8(const DeviceGraph &g, const uint2 *sorted, const uint32_t *n_valid,
                  uint32_t n_steps, uint64_t seed, const Sampler &smp, bool visit_start, uint32_t *visits,
                  uint32_t *paths, unsigned long long *next_chunk, int lanes_w, cudaStream_t s) {
     Hub8Fields f;
     if (!tuning_relabel_hub8() || !hub8_fields(g, f)) return false;
     const bool c = smp.kind == 1;
 #define BQ_H8(WW)                                                                                               \
-    (c ? launch_hub8_w<WW, true>(g, f, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,       \
+    (c ? launch_hub8_w<WW, true>(g, f, sorted, n_valid, n_steps, seed, smp, visit_start, visits, paths,       \
                                  next_chunk, s)                                                                   \
-       : launch_hub8_w<WW, false>(g, f, sid, sst, n_valid, n_steps, seed, smp, visit_start, visits, paths,      \
+       : launch_hub8_w<WW, false>(g, f, sorted, n_valid, n_steps, seed, smp, visit_start, visits, paths,      \
                                   next_chunk, s))
     if (lanes_w == 1) return BQ_H8(1);
     if (lanes_w == 2) return BQ_H8(2);
@@ -1044,9 +1044,10 @@ bool launch_hub8(const DeviceGraph &g, const uint32_t *sid, const uint32_t *sst,
 #undef BQ_H8
 }
 
-// Group the walks by start vertex into (sid, sst); cursor[n] = valid walks.
+// Group the walks by start vertex into `sorted` (walk id, start) pairs;
+// cursor[n] = valid walks.
 int group_by_start(const DeviceGraph &g, const uint32_t *starts, uint64_t n_walks, uint32_t *counts, uint32_t *cursor,
-                   uint32_t *sid, uint32_t *sst, uint32_t *status, void *scan_ws, size_t scan_ws_bytes,
+                   uint2 *sorted, uint32_t *status, void *scan_ws, size_t scan_ws_bytes,
                    cudaStream_t s) {
     BQ_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * g.n, s));
     const unsigned grid = blocks_for(n_walks, kThreads * 4);
@@ -1056,14 +1057,17 @@ int group_by_start(const DeviceGraph &g, const uint32_t *starts, uint64_t n_walk
     const int rc = scan_ws ? scan_u32_ws(counts, cursor, g.n, scan_ws, scan_ws_bytes, s)
                            : scan_u32(counts, cursor, g.n, s);
     if (rc) return rc;
-    scatter_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, cursor, sid, sst);
+    scatter_starts_kernel<<<grid, kThreads, 0, s>>>(starts, n_walks, g.n, cursor, sorted);
     BQ_CUDA(cudaGetLastError());
     return BQ_OK;
 }
 
-// counts[n] | cursor[n + 1] | sorted ids | sorted starts | chunk counter
+// counts[n] | cursor[n + 1] | (8-byte aligned) sorted (id, start) pairs |
+// chunk counter
+size_t bouquet_pairs_offset(uint32_t n) { return (sizeof(uint32_t) * (2 * (size_t)n + 1) + 7) & ~(size_t)7; }
+
 size_t bouquet_counter_offset(uint32_t n, uint64_t n_walks) {
-    return (sizeof(uint32_t) * (2 * (size_t)n + 1 + 2 * (size_t)n_walks) + 15) & ~(size_t)15;
+    return (bouquet_pairs_offset(n) + sizeof(uint2) * (size_t)n_walks + 15) & ~(size_t)15;
 }
 
 size_t bouquet_arrays_bytes(uint32_t n, uint64_t n_walks) {
@@ -1081,8 +1085,9 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
     const int lanes_w = tuning_walks_per_lane();
     const bool agg = tuning_aggregate_visits();
     const size_t n = g.n;
-    uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n, *sid = cursor + n + 1, *sst = sid + n_walks;
-    int rc = group_by_start(g, starts, n_walks, counts, cursor, sid, sst, status, scan_ws, scan_ws_bytes, s);
+    uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n;
+    uint2 *sorted = reinterpret_cast<uint2 *>(scratch + bouquet_pairs_offset(g.n));
+    int rc = group_by_start(g, starts, n_walks, counts, cursor, sorted, status, scan_ws, scan_ws_bytes, s);
     if (rc) return rc;
     if (smp.kind == 1 && smp.t == kSabaT) {
         ProfScope prof(kProfGroup, s);
@@ -1090,18 +1095,18 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
         int dev = 0, sms = 0;
         BQ_CUDA(cudaGetDevice(&dev));
         BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        saba_order_kernel<<<sms * 8, 256, 0, s>>>(counts, cursor, g.n, seed, sid);
+        saba_order_kernel<<<sms * 8, 256, 0, s>>>(counts, cursor, g.n, seed, sorted);
         BQ_CUDA(cudaGetLastError());
     }
     if (g.rl_pk && !checked) {
         auto *next_chunk = reinterpret_cast<unsigned long long *>(scratch + bouquet_counter_offset(g.n, n_walks));
         BQ_CUDA(cudaMemsetAsync(next_chunk, 0, sizeof(unsigned long long), s));
-        if (launch_hub8(g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths, next_chunk,
+        if (launch_hub8(g, sorted, cursor + n, n_steps, seed, smp, visit_start, visits, paths, next_chunk,
                         lanes_w, s)) {
             BQ_CUDA(cudaGetLastError());
             return BQ_OK;
         }
-        if (launch_relabel(g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths, next_chunk,
+        if (launch_relabel(g, sorted, cursor + n, n_steps, seed, smp, visit_start, visits, paths, next_chunk,
                            lanes_w, s)) {
             BQ_CUDA(cudaGetLastError());
             return BQ_OK;
@@ -1112,9 +1117,9 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
         BQ_CUDA(cudaMemsetAsync(next_chunk, 0, sizeof(unsigned long long), s));
         const bool launched = with_edges(g, [&](auto el) {
             if (g.hub_cluster > 1)
-                return launch_cluster_hub(el, g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits,
+                return launch_cluster_hub(el, g, sorted, cursor + n, n_steps, seed, smp, visit_start, visits,
                                           paths, next_chunk, lanes_w, s) ? 1 : 0;
-            return launch_hub(el, g, sid, sst, cursor + n, n_steps, seed, smp, visit_start, visits, paths,
+            return launch_hub(el, g, sorted, cursor + n, n_steps, seed, smp, visit_start, visits, paths,
                               next_chunk, lanes_w, s) ? 1 : 0;
         });
         if (launched) {
@@ -1123,7 +1128,7 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
         }
     }
     rc = with_edges(g, [&](auto el) {
-        launch_bouquet_any(el, g, sid, sst, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked, agg,
+        launch_bouquet_any(el, g, sorted, cursor + n, n_walks, n_steps, seed, smp, visit_start, checked, agg,
                            visits, paths, status, lanes_w, s);
         return BQ_OK;
     });
