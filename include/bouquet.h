@@ -675,6 +675,19 @@ typedef struct bq_profile {
 int bq_profile_enable(int enable);
 int bq_profile_read(bq_profile *out);
 
+/*
+ * Read-bandwidth probe for roofline ceilings (the paper has no counterpart):
+ * times, with CUDA events on `stream` (synchronised), one launch of a
+ * persistent kernel that reads the device buffer buf_dev (16-byte aligned,
+ * `bytes` long, contents arbitrary and unchanged) `reps` times with
+ * coalesced 16-byte loads that bypass L1, after one warm-up launch; *gbs =
+ * bytes * reps / time.  A buffer well below the L2 size (129 MB) measures
+ * the L2 read ceiling, one well above it the HBM read ceiling.  Allocates 16
+ * bytes of stream-ordered scratch.  Errors: BQ_EINVAL (NULL, misaligned,
+ * bytes < 16, reps = 0), BQ_ECUDA.
+ */
+int bq_profile_read_bandwidth(const void *buf_dev, uint64_t bytes, uint32_t reps, void *stream, double *gbs);
+
 /* ------------------------------------------------------------ errors */
 /* Wait for `stream`, then read and clear the status word of the current
  * device: BQ_OK, or the code of the first error a kernel recorded since the

@@ -128,7 +128,7 @@ EXPORTS = (
     "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
     "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
     "bq_server_destroy", "bq_aesc_estimate_push", "bq_graph_set_eigvecs", "bq_aesc_plan_pilot",
-    "bq_aesc_estimate_shared",
+    "bq_aesc_estimate_shared", "bq_profile_read_bandwidth",
 )
 
 _lock = threading.Lock()
@@ -187,6 +187,7 @@ def load_library(path: str | None = None):
         L.bq_server_destroy.argtypes = [vp]
         L.bq_profile_enable.argtypes = [i32]
         L.bq_profile_read.argtypes = [c.POINTER(Profile)]
+        L.bq_profile_read_bandwidth.argtypes = [vp, u64, u32, vp, c.POINTER(f64)]
         for name in EXPORTS:
             if name not in ("bq_strerror", "bq_last_error", "bq_version"):
                 getattr(L, name).restype = i32
@@ -713,6 +714,19 @@ def profile_read() -> dict:
     out = {name: getattr(p, name) for name, _ in Profile._fields_ if name != "walk_kernel_launches"}
     out["walk_kernels"] = {k: int(p.walk_kernel_launches[i]) for i, k in enumerate(WALK_KERNELS)}
     return out
+
+
+def read_bandwidth(buf, reps: int = 20, stream=None) -> float:
+    """GB/s of `reps` coalesced reads of the CUDA tensor `buf` in one launch
+    (bq_profile_read_bandwidth): an L2 ceiling for a buffer well below the
+    L2 size, an HBM one for a buffer well above it."""
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    out = ctypes.c_double()
+    _check(load_library().bq_profile_read_bandwidth(ctypes.c_void_p(buf.data_ptr()),
+                                                    buf.numel() * buf.element_size(), int(reps),
+                                                    _stream_handle(stream), ctypes.byref(out)))
+    return out.value
 
 
 def version() -> str:
