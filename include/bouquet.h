@@ -344,8 +344,10 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
  * push while the pushed volume is below the walks it replaces) is the
  * largest tau~ <= min(push_max, tau, 8) such that every level j <= tau~ has
  * vol_j(u) + vol_j(v) < 2 N and, when tau~ >= 2, every level 1..tau~ has at
- * most 512 vertices in the support of either side; push_max = 0 keeps
- * depth 0 everywhere.  The walks are those of bq_aesc_estimate (streams
+ * most support_cap vertices in the support of either side (a planner
+ * parameter the paper does not have: 1..512, bounded by the size of the
+ * device's pushed-vector tables; 512 is the usual value); push_max = 0
+ * keeps depth 0 everywhere.  The walks are those of bq_aesc_estimate (streams
  * 2 id + side, walk index, independent sampler), tau - depth steps long; at
  * step l a walk adds w r_u(cur) and w r_v(cur), r = r^depth and w = 2 if
  * l + depth < tau else 1, to
@@ -364,13 +366,13 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
  * call waits for `stream` once, after planning the depths, to allocate the
  * pushed vectors of the deeper edges (8 bytes of device memory per support
  * vertex, freed in stream order once the estimate has run).
- * Errors: BQ_EINVAL (push_max > 8, NULL buffers), BQ_ENOMEM, and at bq_sync
- * those of bq_aesc_estimate.
+ * Errors: BQ_EINVAL (push_max > 8, support_cap outside 1..512, NULL
+ * buffers), BQ_ENOMEM, and at bq_sync those of bq_aesc_estimate.
  */
 int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev,
                           uint64_t k, const uint32_t *tau_dev, const uint32_t *nwalks_dev,
-                          uint32_t push_max, uint32_t flags, uint32_t *depth_dev,
-                          uint64_t *acc_dev, double *sc_dev, void *stream);
+                          uint32_t push_max, uint32_t support_cap, uint32_t flags,
+                          uint32_t *depth_dev, uint64_t *acc_dev, double *sc_dev, void *stream);
 
 /* ----------------------------------------------- bq_aesc_estimate_shared */
 /*

@@ -93,7 +93,7 @@ def lib():
             L.orc_aesc_finalize.restype = c.c_int
             L.orc_aesc_push_counts.argtypes = [
                 c.c_uint32, i64p, u32p, c.c_uint64, c.c_uint64, u32p, u32p, u32p,
-                c.c_uint32, u32p, u64p]
+                c.c_uint32, c.c_uint32, u32p, u64p]
             L.orc_aesc_push_counts.restype = c.c_int
             L.orc_aesc_push_finalize.argtypes = [
                 c.c_uint32, i64p, u32p, c.c_uint64, u32p, u32p, u32p, u32p, u64p, f64p]
@@ -341,7 +341,9 @@ PUSH_Q = 1 << 30  # fixed-point scale of the pushed values
 
 
 PUSH_MAX_DEPTH = 8       # deepest push
-PUSH_SUPPORT_MAX = 512   # largest support per side and level at depths >= 2
+# The planner's usual support cap at push depths >= 2 (largest support per
+# side and level); a parameter of aesc_push_counts, not part of TGT+'s rule.
+PUSH_SUPPORT_CAP = 512
 
 
 def push_vector(g, x: int, depth: int) -> np.ndarray:
@@ -355,9 +357,11 @@ def push_vector(g, x: int, depth: int) -> np.ndarray:
 
 
 def aesc_push_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.ndarray,
-                     push_max: int = 1):
+                     push_max: int = 1, support_cap: int = PUSH_SUPPORT_CAP):
     """(depth uint32[k], acc uint64[4k]): push depth per edge and the
-    fixed-point accumulators A_uu, A_uv, A_vu, A_vv (Alg. 1, depth <= 8)."""
+    fixed-point accumulators A_uu, A_uv, A_vu, A_vv (Alg. 1, depth <= 8).
+    support_cap: largest support per side and level admitted at depths >= 2
+    (a planner parameter; 0 = no cap, TGT+'s volume rule alone)."""
     off, nb = _graph_arrays(g)
     q = np.ascontiguousarray(uv, dtype=np.uint32).reshape(-1, 2)
     ta = np.ascontiguousarray(tau, dtype=np.uint32)
@@ -367,7 +371,7 @@ def aesc_push_counts(g, seed: int, uv: np.ndarray, tau: np.ndarray, nwalks: np.n
     rc = lib().orc_aesc_push_counts(
         g.n, _p(off, ctypes.c_int64), _p(nb, ctypes.c_uint32), seed, q.shape[0],
         _p(q, ctypes.c_uint32), _p(ta, ctypes.c_uint32), _p(nw, ctypes.c_uint32),
-        int(push_max), _p(depth, ctypes.c_uint32), _p(acc, ctypes.c_uint64))
+        int(push_max), int(support_cap), _p(depth, ctypes.c_uint32), _p(acc, ctypes.c_uint64))
     _check(rc, "aesc_push_counts")
     return depth, acc
 
@@ -389,9 +393,9 @@ def aesc_push_finalize(g, uv, tau, nwalks, depth, acc) -> np.ndarray:
     return sc
 
 
-def aesc_push_estimate(g, seed: int, uv, tau, nwalks, push_max: int = 1):
+def aesc_push_estimate(g, seed: int, uv, tau, nwalks, push_max: int = 1, support_cap: int = PUSH_SUPPORT_CAP):
     """(depth, acc, sc) of the push-phase estimator."""
-    depth, acc = aesc_push_counts(g, seed, uv, tau, nwalks, push_max)
+    depth, acc = aesc_push_counts(g, seed, uv, tau, nwalks, push_max, support_cap)
     return depth, acc, aesc_push_finalize(g, uv, tau, nwalks, depth, acc)
 
 

@@ -711,12 +711,12 @@ int orc_aesc_finalize(uint32_t n, const int64_t *offsets, uint64_t k,
  * vol_j(x) = sum over j' < j of the degrees of supp r^j'_x (vol_1 = d(x)).
  * As in TGT+'s while loop, the depth is the largest tau~ <= min(push_max,
  * tau, 8) such that every level j <= tau~ has vol_j(u) + vol_j(v) < 2 N
- * (the pushed volume stays below the 2 N walks it replaces) and, for
- * tau~ >= 2, every level 1..tau~ has a support of at most 512 vertices per
+ * (the pushed volume stays below the 2 N walks it replaces) and, when a
+ * support cap is given (a planner parameter, not part of TGT+'s rule), for
+ * tau~ >= 2 every level 1..tau~ has a support of at most `cap` vertices per
  * side. */
 #define ORC_PUSH_Q 1073741824u
 #define ORC_PUSH_MAX_DEPTH 8u
-#define ORC_PUSH_SUPPORT_MAX 512u
 
 /* A sparse vector over the vertices: dense values and the list of nonzero
  * entries (cleared through the list). */
@@ -791,10 +791,10 @@ typedef struct {
 
 /* Levels 0..jmax of source x; with `limits`, stopping at a level whose
  * volume alone reaches two_n (before pushing it) or after one whose support
- * is above the cap: no deeper level can be taken then.  r^levels_x is left
- * in *a. */
+ * is above the cap (cap 0: none): no deeper level can be taken then.
+ * r^levels_x is left in *a. */
 static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x, uint32_t u, uint32_t v,
-                        uint32_t jmax, int limits, uint64_t two_n, orc_svec *a, orc_svec *b,
+                        uint32_t jmax, int limits, uint64_t two_n, uint32_t cap, orc_svec *a, orc_svec *b,
                         orc_push_stats *st)
 {
     uint32_t j;
@@ -821,20 +821,21 @@ static void push_levels(const int64_t *offsets, const uint32_t *nbrs, uint32_t x
         st->supp[j] = a->cnt;
         st->at_u[j] = a->val[u];
         st->at_v[j] = a->val[v];
-        if (limits && st->supp[j] > ORC_PUSH_SUPPORT_MAX)
+        if (limits && cap && st->supp[j] > cap)
             break;
     }
 }
 
 /* Depth of query {u, v} from both sources' level statistics. */
-static uint32_t push_depth_from(const orc_push_stats *su, const orc_push_stats *sv, uint64_t two_n)
+static uint32_t push_depth_from(const orc_push_stats *su, const orc_push_stats *sv, uint64_t two_n,
+                                uint32_t cap)
 {
     uint32_t j, dep = 0;
     uint32_t top = su->levels < sv->levels ? su->levels : sv->levels;
     for (j = 1; j <= top; j++) {
         if (su->vol[j] + sv->vol[j] >= two_n)
             break;
-        if (j >= 2 && (su->supp[j] > ORC_PUSH_SUPPORT_MAX || sv->supp[j] > ORC_PUSH_SUPPORT_MAX))
+        if (j >= 2 && cap && (su->supp[j] > cap || sv->supp[j] > cap))
             break;
         dep = j;
     }
@@ -861,7 +862,7 @@ int orc_push_vector(uint32_t n, const int64_t *offsets, const uint32_t *nbrs, ui
         svec_free(&b);
         return ORC_EINVAL;
     }
-    push_levels(offsets, nbrs, x, x, x, depth, 0, 0, &a, &b, &st);
+    push_levels(offsets, nbrs, x, x, x, depth, 0, 0, 0, &a, &b, &st);
     for (y = 0; y < n; y++)
         out[y] = st.levels == depth ? a.val[y] : 0;
     svec_free(&a);
@@ -874,11 +875,12 @@ int orc_push_vector(uint32_t n, const int64_t *offsets, const uint32_t *nbrs, ui
  * steps long; at step l the walk adds w * r_u(cur) and w * r_v(cur) with
  * r = r^tau~ and w = 2 if l + tau~ < tau else 1:
  *   acc[4q + 0..3] = A_uu, A_uv (walks from u), A_vu, A_vv (walks from v).
- * depth[q] (may be NULL) receives tau~.  push_max <= 8. */
+ * depth[q] (may be NULL) receives tau~.  push_max <= 8; support_cap = the
+ * largest support per side and level admitted at depths >= 2 (0: no cap). */
 int orc_aesc_push_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbrs,
                          uint64_t seed, uint64_t k, const uint32_t *uv,
                          const uint32_t *tau, const uint32_t *nwalks,
-                         uint32_t push_max, uint32_t *depth, uint64_t *acc)
+                         uint32_t push_max, uint32_t support_cap, uint32_t *depth, uint64_t *acc)
 {
     orc_sampler smp;
     orc_svec au, bu, av, bv;
@@ -910,12 +912,14 @@ int orc_aesc_push_counts(uint32_t n, const int64_t *offsets, const uint32_t *nbr
             rc = ORC_EOVERFLOW;
             break;
         }
-        push_levels(offsets, nbrs, u, u, v, depth_cap(tau[q], push_max), 1, 2ull * nwalks[q], &au, &bu, &su);
-        push_levels(offsets, nbrs, v, u, v, depth_cap(tau[q], push_max), 1, 2ull * nwalks[q], &av, &bv, &sv);
-        dep = push_depth_from(&su, &sv, 2ull * nwalks[q]);
+        push_levels(offsets, nbrs, u, u, v, depth_cap(tau[q], push_max), 1, 2ull * nwalks[q], support_cap, &au,
+                    &bu, &su);
+        push_levels(offsets, nbrs, v, u, v, depth_cap(tau[q], push_max), 1, 2ull * nwalks[q], support_cap, &av,
+                    &bv, &sv);
+        dep = push_depth_from(&su, &sv, 2ull * nwalks[q], support_cap);
         /* the vectors at the chosen depth */
-        push_levels(offsets, nbrs, u, u, v, dep, 0, 0, &au, &bu, &su);
-        push_levels(offsets, nbrs, v, u, v, dep, 0, 0, &av, &bv, &sv);
+        push_levels(offsets, nbrs, u, u, v, dep, 0, 0, 0, &au, &bu, &su);
+        push_levels(offsets, nbrs, v, u, v, dep, 0, 0, 0, &av, &bv, &sv);
         if (depth)
             depth[q] = dep;
         for (side = 0; side < 2; side++) {
@@ -980,8 +984,8 @@ int orc_aesc_push_finalize(uint32_t n, const int64_t *offsets, const uint32_t *n
             rc = ORC_EINVAL;
             break;
         }
-        push_levels(offsets, nbrs, u, u, v, depth[q], 0, 0, &a, &b, &su);
-        push_levels(offsets, nbrs, v, u, v, depth[q], 0, 0, &a, &b, &sv);
+        push_levels(offsets, nbrs, u, u, v, depth[q], 0, 0, 0, &a, &b, &su);
+        push_levels(offsets, nbrs, v, u, v, depth[q], 0, 0, 0, &a, &b, &sv);
         for (l = 0; l <= depth[q]; l++) {
             int64_t w = l < tau[q] ? 2 : 1;
             xu += w * ((int64_t)su.at_u[l] - (int64_t)su.at_v[l]);

@@ -160,7 +160,7 @@ def load_library(path: str | None = None):
         L.bq_aesc_plan_pilot.argtypes = [vp, u64, vp, u64, f64, c.POINTER(Schedule), u32, f64,
                                          c.POINTER(Sampler), vp, vp, vp, vp]
         L.bq_aesc_estimate.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp, vp]
-        L.bq_aesc_estimate_push.argtypes = [vp, u64, vp, u64, vp, vp, u32, u32, vp, vp, vp, vp]
+        L.bq_aesc_estimate_push.argtypes = [vp, u64, vp, u64, vp, vp, u32, u32, u32, vp, vp, vp, vp]
         L.bq_aesc_estimate_shared.argtypes = [vp, u64, vp, u64, vp, vp, c.POINTER(Sampler), u32, vp, vp,
                                               vp, vp]
         L.bq_sync.argtypes = [vp]
@@ -439,8 +439,11 @@ def aesc_estimate_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.n
     return counts, sc
 
 
+PUSH_SUPPORT_CAP = 512  # the usual support cap at push depths >= 2 (at most 512)
+
+
 def aesc_estimate_push(graph: Graph, seed: int, uv, tau, nwalks, push_max: int = 1,
-                       depth=None, acc=None, sc=None, stream=None):
+                       depth=None, acc=None, sc=None, stream=None, support_cap: int = PUSH_SUPPORT_CAP):
     """Push-phase AESC on device tensors (uv None = all edges); returns
     (depth, acc, sc) with acc the 4k uint64 fixed-point accumulators."""
     import torch
@@ -454,14 +457,15 @@ def aesc_estimate_push(graph: Graph, seed: int, uv, tau, nwalks, push_max: int =
     if sc is None:
         sc = torch.empty(k, dtype=torch.float64, device=dev)
     _check(L.bq_aesc_estimate_push(graph.handle, int(seed) & (2**64 - 1), _dptr(uv, "uv"), k,
-                                   _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), int(push_max), 0,
+                                   _dptr(tau, "tau"), _dptr(nwalks, "nwalks"), int(push_max),
+                                   int(support_cap), 0,
                                    _dptr(depth, "depth"), _dptr(acc, "acc", 8), _dptr(sc, "sc", 8),
                                    _stream_handle(stream)))
     return depth, acc, sc
 
 
 def aesc_estimate_push_host(graph: Graph, seed: int, uv: np.ndarray | None, tau: np.ndarray,
-                            nwalks: np.ndarray, push_max: int = 1):
+                            nwalks: np.ndarray, push_max: int = 1, support_cap: int = PUSH_SUPPORT_CAP):
     """Push-phase AESC through host buffers (BQ_HOST_IO); synchronous."""
     L = load_library()
     ta = np.ascontiguousarray(tau, dtype=np.uint32)
@@ -475,7 +479,7 @@ def aesc_estimate_push_host(graph: Graph, seed: int, uv: np.ndarray | None, tau:
     acc = np.zeros(4 * k, np.uint64)
     sc = np.zeros(k, np.float64)
     _check(L.bq_aesc_estimate_push(graph.handle, int(seed) & (2**64 - 1), puv, k, _hptr(ta, "tau", np.uint32),
-                                   _hptr(nw, "nwalks", np.uint32), int(push_max), HOST_IO,
+                                   _hptr(nw, "nwalks", np.uint32), int(push_max), int(support_cap), HOST_IO,
                                    _hptr(depth, "depth", np.uint32), _hptr(acc, "acc", np.uint64),
                                    _hptr(sc, "sc", np.float64), None))
     return depth, acc, sc

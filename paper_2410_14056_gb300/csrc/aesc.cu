@@ -549,7 +549,7 @@ __device__ __forceinline__ uint32_t push_set_flags(const uint32_t *keys, const u
 // warp in two shared-memory hash tables, kept as sorted (vertex, value)
 // arrays for the walks' lookups.
 constexpr uint32_t kPushMaxDepth = 8;
-constexpr uint32_t kPushSupportMax = 512;  // support cap per side and level at depths >= 2
+constexpr uint32_t kPushSupportMax = kPushSupportCapMax;  // largest support cap per side and level
 constexpr uint32_t kDeepSlots = 1024;      // hash slots per table (load <= 1/2 up to the cap)
 constexpr int kDeepWarps = 8;              // warps per block of the build kernels
 constexpr uint32_t kDeepEmpty = 0xffffffffu;
@@ -594,13 +594,13 @@ __device__ void deep_clear(DeepTable *t, uint32_t lane) {
     __syncwarp();
 }
 
-__device__ void deep_add(DeepTable *t, uint32_t y, uint32_t c) {
+__device__ void deep_add(DeepTable *t, uint32_t y, uint32_t c, uint32_t cap) {
     if (c == 0u) return;
     uint32_t h = deep_hash(y);
     for (uint32_t probe = 0; probe < kDeepSlots; ++probe) {
         const uint32_t prev = atomicCAS(t->keys + h, kDeepEmpty, y);
         if (prev == kDeepEmpty) {
-            if (atomicAdd(&t->count, 1u) >= kPushSupportMax) t->over = 1u;
+            if (atomicAdd(&t->count, 1u) >= cap) t->over = 1u;
             atomicAdd(t->vals + h, c);
             return;
         }
@@ -640,7 +640,7 @@ __device__ uint64_t deep_volume(const int64_t *__restrict__ offsets, const DeepT
 // out = one push of in.  Stops adding once out passed the cap (that level
 // is then refused whatever else it would hold).
 __device__ void deep_push(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
-                          const DeepTable *in, DeepTable *out, uint32_t lane) {
+                          const DeepTable *in, DeepTable *out, uint32_t cap, uint32_t lane) {
     deep_clear(out, lane);
     for (uint32_t i = lane; i < kDeepSlots; i += 32) {
         const uint32_t z = in->keys[i];
@@ -651,7 +651,7 @@ __device__ void deep_push(const int64_t *__restrict__ offsets, const uint32_t *_
             if (*(volatile uint32_t *)&out->over) break;
             const uint32_t y = __ldg(nbrs + j);
             const uint32_t dy = (uint32_t)(__ldg(offsets + y + 1) - __ldg(offsets + y));
-            deep_add(out, y, r / dy);
+            deep_add(out, y, r / dy, cap);
         }
     }
     __syncwarp();
@@ -659,13 +659,14 @@ __device__ void deep_push(const int64_t *__restrict__ offsets, const uint32_t *_
 
 // Levels 0..jmax of source x into w->t (final level in t[result]); with
 // limits, stops at a level whose volume reaches two_n (before pushing it) or
-// after one whose support passes the cap.  Records the per-level statistics
-// of `side`.
+// after one whose support passes the cap (<= kPushSupportMax, which keeps
+// the tables at most half full).  Records the per-level statistics of
+// `side`.
 __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs, DeepWarp *w,
                                 uint32_t side, uint32_t x, uint32_t u, uint32_t v, uint32_t jmax, bool limits,
-                                uint64_t two_n, uint32_t lane) {
+                                uint64_t two_n, uint32_t cap, uint32_t lane) {
     deep_clear(&w->t[0], lane);
-    if (lane == 0) deep_add(&w->t[0], x, kPushQ);
+    if (lane == 0) deep_add(&w->t[0], x, kPushQ, cap);
     __syncwarp();
     if (lane == 0) {
         w->st.vol[side][0] = 0;
@@ -688,7 +689,7 @@ __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint3
             __syncwarp();
             break;
         }
-        deep_push(offsets, nbrs, &w->t[cur], &w->t[cur ^ 1], lane);
+        deep_push(offsets, nbrs, &w->t[cur], &w->t[cur ^ 1], cap, lane);
         cur ^= 1;
         const DeepTable *t = &w->t[cur];
         const uint32_t supp = t->count, over = t->over;
@@ -702,7 +703,7 @@ __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint3
             w->st.levels[side] = j;
         }
         __syncwarp();
-        if (limits && (over || supp > kPushSupportMax)) break;
+        if (limits && (over || supp > cap)) break;
     }
     return cur;
 }
@@ -713,7 +714,7 @@ __device__ uint32_t deep_levels(const int64_t *__restrict__ offsets, const uint3
 // and walk tasks.
 __global__ void __launch_bounds__(kDeepWarps * 32)
 deep_plan_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs, QueryInfo *__restrict__ info,
-                 uint64_t k, uint32_t push_max, uint32_t bouquet, DeepInfo *__restrict__ deep,
+                 uint64_t k, uint32_t push_max, uint32_t cap, uint32_t bouquet, DeepInfo *__restrict__ deep,
                  uint32_t *__restrict__ sizes, uint32_t *__restrict__ tasks) {
     extern __shared__ __align__(16) unsigned char deep_smem[];
     DeepWarp *w = reinterpret_cast<DeepWarp *>(deep_smem) + (threadIdx.x >> 5);
@@ -729,7 +730,7 @@ deep_plan_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restrict
         const uint64_t two_n = 2ull * qi.nwalks;
         // level 2 needs both rows within the cap and vol_2(x) = d_x + the sum
         // of the degrees of N(x) below 2N in total: most edges stop here
-        if (qi.du > kPushSupportMax || qi.dv > kPushSupportMax) continue;
+        if (qi.du > cap || qi.dv > cap) continue;
         uint64_t vol2 = 0;
         const int64_t lu = __ldg(offsets + qi.u), lv = __ldg(offsets + qi.v);
         for (uint32_t i = lane; i < qi.du; i += 32) {
@@ -743,15 +744,15 @@ deep_plan_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restrict
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) vol2 += __shfl_xor_sync(0xffffffffu, vol2, d);
         if ((uint64_t)qi.du + qi.dv + vol2 >= two_n) continue;
-        deep_levels(offsets, nbrs, w, 0, qi.u, qi.u, qi.v, jmax, true, two_n, lane);
-        deep_levels(offsets, nbrs, w, 1, qi.v, qi.u, qi.v, jmax, true, two_n, lane);
+        deep_levels(offsets, nbrs, w, 0, qi.u, qi.u, qi.v, jmax, true, two_n, cap, lane);
+        deep_levels(offsets, nbrs, w, 1, qi.v, qi.u, qi.v, jmax, true, two_n, cap, lane);
         if (lane == 0) {
             const DeepStats &st = w->st;
             const uint32_t top = st.levels[0] < st.levels[1] ? st.levels[0] : st.levels[1];
             uint32_t dep = 0;
             for (uint32_t j = 1; j <= top; ++j) {
                 if (st.vol[0][j] + st.vol[1][j] >= two_n) break;
-                if (j >= 2 && (st.supp[0][j] > kPushSupportMax || st.supp[1][j] > kPushSupportMax)) break;
+                if (j >= 2 && (st.supp[0][j] > cap || st.supp[1][j] > cap)) break;
                 dep = j;
             }
             if (dep >= 2) {
@@ -795,8 +796,9 @@ deep_tables_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restri
         if (lane == 0) deep[q].off = base;
         uint64_t at = base;
         for (uint32_t side = 0; side < 2; ++side) {
+            // every level up to the depth passed the planner's cap in pass 1
             const uint32_t fin = deep_levels(offsets, nbrs, w, side, side ? qi.v : qi.u, qi.u, qi.v, qi.depth,
-                                             false, 0, lane);
+                                             false, 0, kPushSupportMax, lane);
             const DeepTable *t = &w->t[fin];
             // compact into the other table's memory, pad to a power of two, sort
             unsigned long long *arr = reinterpret_cast<unsigned long long *>(&w->t[fin ^ 1]);
@@ -1205,8 +1207,8 @@ int launch_push_count(EL el, const DeviceGraph &g, const QueryInfo *info, const 
 
 // Depths >= 2: plan (pass 1), size and allocate the tables (one wait on s),
 // build them (pass 2).  *tables_out is released by the caller.
-int build_deep(const DeviceGraph &g, QueryInfo *info, uint64_t k, uint32_t push_max, uint32_t bouquet,
-               DeepInfo *deep, uint32_t *sizes, uint64_t *toff, uint32_t *tasks,
+int build_deep(const DeviceGraph &g, QueryInfo *info, uint64_t k, uint32_t push_max, uint32_t cap,
+               uint32_t bouquet, DeepInfo *deep, uint32_t *sizes, uint64_t *toff, uint32_t *tasks,
                unsigned long long **tables_out, cudaStream_t s) {
     *tables_out = nullptr;
     const size_t smem = sizeof(DeepWarp) * kDeepWarps;
@@ -1217,8 +1219,8 @@ int build_deep(const DeviceGraph &g, QueryInfo *info, uint64_t k, uint32_t push_
     BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned grid = blocks_for(k, kDeepWarps) < (unsigned)sms ? blocks_for(k, kDeepWarps) : (unsigned)sms;
     count_launches(1);
-    deep_plan_kernel<<<grid, kDeepWarps * 32, smem, s>>>(g.offsets, g.nbrs, info, k, push_max, bouquet, deep, sizes,
-                                                         tasks);
+    deep_plan_kernel<<<grid, kDeepWarps * 32, smem, s>>>(g.offsets, g.nbrs, info, k, push_max, cap, bouquet, deep,
+                                                         sizes, tasks);
     BQ_CUDA(cudaGetLastError());
     int rc = scan_u32_to_u64(sizes, toff, k, s);
     if (rc) return rc;
@@ -1243,8 +1245,8 @@ int build_deep(const DeviceGraph &g, QueryInfo *info, uint64_t k, uint32_t push_
 }  // namespace
 
 int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k, const uint32_t *tau,
-                     const uint32_t *nwalks, uint32_t push_max, uint32_t *depth_out, uint64_t *acc, double *sc,
-                     uint32_t *status, cudaStream_t s) {
+                     const uint32_t *nwalks, uint32_t push_max, uint32_t support_cap, uint32_t *depth_out,
+                     uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s) {
     if (k == 0) return BQ_OK;
     int w = tuning_aesc_walks_per_lane();
     if (w != 2 && w != 4 && w != 8) w = 4;
@@ -1292,7 +1294,8 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
         count_launches(1);
         prepare_kernel<<<blocks_for(k, kThreads), kThreads, 0, s>>>(g, uv, k, tau, nwalks, bouquet, push_max, info,
                                                                     tasks, nullptr, sc, status);
-        if (deep_on) rc = build_deep(g, info, k, push_max, bouquet, deep, sizes, toff, tasks, &tables, s);
+        if (deep_on)
+            rc = build_deep(g, info, k, push_max, support_cap, bouquet, deep, sizes, toff, tasks, &tables, s);
         if (rc == BQ_OK) rc = scan_u32_to_u64(tasks, begin, k, s);
         if (rc == BQ_OK) {
             count_launches(1);

@@ -798,13 +798,17 @@ int bq_aesc_estimate(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_
 }
 
 int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edges_uv_dev, uint64_t k,
-                          const uint32_t *tau_dev, const uint32_t *nwalks_dev, uint32_t push_max, uint32_t flags,
-                          uint32_t *depth_dev, uint64_t *acc_dev, double *sc_dev, void *stream) {
+                          const uint32_t *tau_dev, const uint32_t *nwalks_dev, uint32_t push_max,
+                          uint32_t support_cap, uint32_t flags, uint32_t *depth_dev, uint64_t *acc_dev,
+                          double *sc_dev, void *stream) {
     bq::NvtxRange nvtx_range("bq_aesc_estimate_push");
     g_last_error[0] = 0;
     if (!g) return fail(BQ_EINVAL, "graph is NULL");
     if (flags & ~BQ_HOST_IO) return fail(BQ_EINVAL, "unknown AESC flags 0x%x", flags);
     if (push_max > 8) return fail(BQ_EINVAL, "push_max = %u (at most 8)", push_max);
+    if (support_cap == 0 || support_cap > kPushSupportCapMax)
+        return fail(BQ_EINVAL, "support_cap = %u (1..%u: the pushed-vector tables hold %u vertices per side)",
+                    support_cap, kPushSupportCapMax, kPushSupportCapMax);
     if (k && (!tau_dev || !nwalks_dev || !acc_dev || !sc_dev))
         return fail(BQ_EINVAL, "tau, nwalks, acc or sc is NULL");
     if (!edges_uv_dev && (k != g->nnz / 2 || k != g->m_upper))
@@ -817,7 +821,8 @@ int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edge
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (!(flags & BQ_HOST_IO))
-        return launch_aesc_push(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, push_max, depth_dev, acc_dev,
+        return launch_aesc_push(g->view(), seed, edges_uv_dev, k, tau_dev, nwalks_dev, push_max, support_cap,
+                                depth_dev, acc_dev,
                                 sc_dev, status, s);
 
     const size_t eb = edges_uv_dev ? sizeof(uint32_t) * 2 * k : 0;
@@ -836,7 +841,8 @@ int bq_aesc_estimate_push(const bq_graph *g, uint64_t seed, const uint32_t *edge
     if (e == cudaSuccess && d_uv) e = cudaMemcpyAsync(d_uv, edges_uv_dev, eb, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) rc = cuda_fail(e, "host-io upload");
     if (rc == BQ_OK)
-        rc = launch_aesc_push(g->view(), seed, d_uv, k, d_tau, d_nw, push_max, d_depth, d_acc, d_sc, status, s);
+        rc = launch_aesc_push(g->view(), seed, d_uv, k, d_tau, d_nw, push_max, support_cap, d_depth, d_acc, d_sc,
+                              status, s);
     if (rc == BQ_OK) {
         e = cudaMemcpyAsync(acc_dev, d_acc, ab, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc_dev, d_sc, scb, cudaMemcpyDeviceToHost, s);

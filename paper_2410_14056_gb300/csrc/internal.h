@@ -373,8 +373,11 @@ int launch_aesc_moments(const DeviceGraph &g, uint64_t seed, const uint32_t *edg
 // Canonical edge list (edges ordered by lower endpoint, then higher) into
 // uv = device uint32[2m].
 int launch_canonical_edges(const DeviceGraph &g, uint32_t *uv, cudaStream_t s);
+// support_cap: 1..kPushSupportCapMax, the largest support per side and level
+// admitted at push depths >= 2
+constexpr uint32_t kPushSupportCapMax = 512;
 int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_uv, uint64_t k,
-                     const uint32_t *tau, const uint32_t *nwalks, uint32_t push_max, uint32_t *depth_out,
-                     uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s);
+                     const uint32_t *tau, const uint32_t *nwalks, uint32_t push_max, uint32_t support_cap,
+                     uint32_t *depth_out, uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s);
 
 }  // namespace bq

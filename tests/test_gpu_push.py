@@ -28,9 +28,10 @@ def same_bits(a, b):
     return np.array_equal(np.asarray(a, np.float64).view(np.uint64), np.asarray(b, np.float64).view(np.uint64))
 
 
-def check(bq, graph, g, seed, uv, tau, nw, push_max):
-    depth, acc, sc = bq.aesc_estimate_push_host(graph, seed, uv, tau, nw, push_max)
-    od, oa, osc = oracle.aesc_push_estimate(g, seed, uv if uv is not None else all_edges(g), tau, nw, push_max)
+def check(bq, graph, g, seed, uv, tau, nw, push_max, cap=512):
+    depth, acc, sc = bq.aesc_estimate_push_host(graph, seed, uv, tau, nw, push_max, support_cap=cap)
+    od, oa, osc = oracle.aesc_push_estimate(g, seed, uv if uv is not None else all_edges(g), tau, nw, push_max,
+                                            support_cap=cap)
     assert np.array_equal(depth, od)
     assert np.array_equal(acc, oa)
     assert same_bits(sc, osc)
@@ -122,6 +123,10 @@ def test_errors(env):
     with pytest.raises(bq.BouquetError) as ei:
         bq.aesc_estimate_push_host(graph, 1, uv, tau, nw, push_max=9)
     assert ei.value.code == bq.EINVAL
+    for cap in (0, 513):  # the device tables hold 512 vertices per side and level
+        with pytest.raises(bq.BouquetError) as ei:
+            bq.aesc_estimate_push_host(graph, 1, uv, tau, nw, push_max=4, support_cap=cap)
+        assert ei.value.code == bq.EINVAL and "support_cap" in str(ei.value)
     row0 = set(g.row(0).tolist())
     non = next(x for x in range(1, g.n) if x not in row0)
     bad = np.array([[0, non]], np.uint32)
@@ -230,3 +235,24 @@ def test_deep_device_tensors_and_power_law(env):
     assert np.array_equal(depth[pick], od)
     assert np.array_equal(acc[pick], oa.reshape(-1, 4))
     assert same_bits(sc[pick], osc)
+
+
+@pytest.mark.parametrize("cap", [1, 8, 64, 200, 512])
+def test_deep_support_cap_parameter(env, cap):
+    """The support cap is a plan parameter both sides receive: depths,
+    accumulators and estimates equal the oracle's for every cap, and a
+    smaller cap never deepens a push."""
+    bq, torch = env
+    g = er_with_path(1000, 5000, 1)
+    graph = bq.Graph.from_csr(g)
+    rng = np.random.default_rng(9)
+    uv_all = all_edges(g)
+    uv = uv_all[rng.choice(uv_all.shape[0], 300, replace=False)]
+    tau, nw = oracle.plan_scheduled(g, uv, 0.05, *SCHED)
+    nw *= 10
+    tau[::3] += 3
+    depth = check(bq, graph, g, 31, uv, tau, nw, 8, cap)
+    full = oracle.aesc_push_counts(g, 31, uv, tau, nw, 8, support_cap=512)[0]
+    assert np.all(depth <= full)
+    if cap >= 64:
+        assert depth.max() >= 2

@@ -54,7 +54,7 @@ def test_argument_errors_without_device(lib):
     assert lib.bq_graph_create(3, None, None, 0, None, None) == bq.EINVAL
     assert lib.bq_walk_batch(None, 0, None, 0, 1, 0, None, 0, None, None, None) == bq.EINVAL
     assert lib.bq_aesc_plan(None, None, 0, 0.1, 0.01, 0, None, None, None) == bq.EINVAL
-    assert lib.bq_aesc_estimate_push(None, 0, None, 0, None, None, 1, 0, None, None, None, None) == bq.EINVAL
+    assert lib.bq_aesc_estimate_push(None, 0, None, 0, None, None, 1, 512, 0, None, None, None, None) == bq.EINVAL
     assert lib.bq_graph_destroy(None) == bq.OK
 
 

@@ -250,7 +250,7 @@ def test_depth_rule_general():
             for j in range(1, top + 1):
                 if vu[j] + vv[j] >= 2 * int(nw[q]):
                     break
-                if j >= 2 and max(su[1:j + 1] + sv[1:j + 1]) > oracle.PUSH_SUPPORT_MAX:
+                if j >= 2 and max(su[1:j + 1] + sv[1:j + 1]) > oracle.PUSH_SUPPORT_CAP:
                     break
                 want = j
             assert depth[q] == want, (q, push_max)
@@ -313,8 +313,8 @@ def test_support_cap_limits_depth():
             v.append(nxt)
             nxt += 1
     tree = csr_from_edges(nxt, np.array(u), np.array(v), name="tree30x30")
-    assert np.count_nonzero(oracle.push_vector(tree, 0, 2)) > oracle.PUSH_SUPPORT_MAX or \
-        np.count_nonzero(oracle.push_vector(tree, 1, 2)) > oracle.PUSH_SUPPORT_MAX
+    assert np.count_nonzero(oracle.push_vector(tree, 0, 2)) > oracle.PUSH_SUPPORT_CAP or \
+        np.count_nonzero(oracle.push_vector(tree, 1, 2)) > oracle.PUSH_SUPPORT_CAP
     q = np.array([[0, 1], [1, 31]], np.uint32)
     depth, _ = oracle.aesc_push_counts(tree, 1, q, np.full(2, 4, np.uint32), np.full(2, 100000, np.uint32),
                                        push_max=4)
@@ -323,7 +323,45 @@ def test_support_cap_limits_depth():
              for j in range(5)]
         want = 1
         for j in range(2, 5):
-            if max(s[1:j + 1]) > oracle.PUSH_SUPPORT_MAX:
+            if max(s[1:j + 1]) > oracle.PUSH_SUPPORT_CAP:
                 break
             want = j
         assert dep == want and dep < 4
+
+
+@pytest.mark.parametrize("cap", [0, 1, 3, 40, 512])
+def test_support_cap_is_a_planner_parameter(cap):
+    """The cap is a parameter of the depth rule (0: none, TGT+'s volume rule
+    alone).  Without it the 600-leaf star goes as deep as the volumes allow;
+    every cap gives the depth recomputed from supports and volumes, and the
+    estimator keeps its expectation at whatever depth is taken."""
+    g = er_with_path(60, 200, 4)
+    uv = all_edges(g)[:40]
+    rng = np.random.default_rng(cap + 1)
+    tau = rng.integers(2, 7, uv.shape[0]).astype(np.uint32)
+    nw = rng.integers(50, 3000, uv.shape[0]).astype(np.uint32)
+    depth, _ = oracle.aesc_push_counts(g, 1, uv, tau, nw, push_max=8, support_cap=cap)
+    for q, (a, b) in enumerate(uv.tolist()):
+        top = min(8, int(tau[q]))
+        su, vu = support_and_volume(g, a, top)
+        sv, vv = support_and_volume(g, b, top)
+        want = 0
+        for j in range(1, top + 1):
+            if vu[j] + vv[j] >= 2 * int(nw[q]):
+                break
+            if j >= 2 and cap and max(su[1:j + 1] + sv[1:j + 1]) > cap:
+                break
+            want = j
+        assert depth[q] == want, (q, cap)
+    if cap in (1, 3):
+        assert depth.max() <= 1 or cap == 3
+    from workloads import csr_from_edges
+    star = csr_from_edges(601, np.zeros(600, np.int64), np.arange(1, 601), name="star600")
+    suv = all_edges(star)[:3]
+    sd, _ = oracle.aesc_push_counts(star, 1, suv, np.full(3, 4, np.uint32), np.full(3, 100000, np.uint32),
+                                    push_max=4, support_cap=cap)
+    assert np.all(sd == (4 if cap == 0 else 1)), sd
+    # the expectation at the depth taken is still the half-weighted series
+    for (u, v), dep, t in list(zip(uv.tolist(), depth.tolist(), tau.tolist()))[:6]:
+        if dep >= 2:
+            assert abs(expected_estimate_deep(g, u, v, t, dep) - exact.truncated_series(g, u, v, t)) < 1e-6
