@@ -6,9 +6,11 @@ library with ``paper_2410_14056_gb300.build.build()``.
 """
 
 from .bouquet import (  # noqa: F401
-    BORROW, DEVICE_PTRS, EBUSY, EGRAPH, EINVAL, ENOEDGE, ENOMEM, EOVERFLOW, ETIMEOUT, HOST_IO, HOST_PTRS,
-    MODE_BOUQUET, MODE_NAIVE, OK, PLAN_CERTIFIED, PLAN_SCHEDULED, REQUIRE_CONNECTED,
-    SAMPLER_COUPLED, SAMPLER_IND, SAMPLER_SABA, SKIP_VALIDATE, VISIT_START, Batch, BouquetError, Graph, Sampler,
-    Schedule, Server, ServerConfig, aesc_estimate, aesc_estimate_push, aesc_estimate_push_host, aesc_estimate_shared, aesc_estimate_shared_host, autotune_aesc, autotune_walks, profile_enable, profile_read, aesc_estimate_host, aesc_plan, aesc_plan_pilot, get_tuning, load_library,
-    set_tuning, sync, version, walk_batch, walk_batch_host,
+    AESC_NAIVE, BORROW, DEVICE_PTRS, EBUSY, ECUDA, EGRAPH, EINVAL, ENOEDGE, ENOMEM, EOVERFLOW, ETIMEOUT, HOST_IO,
+    HOST_PTRS, MODE_BOUQUET, MODE_NAIVE, OK, PLAN_CERTIFIED, PLAN_SCHEDULED, PUSH_SUPPORT_CAP, REQUIRE_CONNECTED,
+    SAMPLER_COUPLED, SAMPLER_IND, SAMPLER_SABA, SKIP_VALIDATE, VISIT_START, WALK_KERNELS, Batch, BouquetError, Graph,
+    Sampler, Schedule, Server, ServerConfig, aesc_estimate, aesc_estimate_host, aesc_estimate_push,
+    aesc_estimate_push_host, aesc_estimate_shared, aesc_estimate_shared_host, aesc_plan, aesc_plan_pilot,
+    autotune_aesc, autotune_walks, get_tuning, load_library, profile_enable, profile_read, read_bandwidth,
+    set_tuning, sync, version, walk_batch, walk_batch_host, walk_batch_noalloc,
 )
