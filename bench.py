@@ -389,6 +389,74 @@ def aesc_cpu_baseline(g, seed, uv, tau, nw, n_edges=100_000):
                       f"C oracle counters on {cores} threads, {dt:.1f} s"}
 
 
+def aesc_equal_accuracy(bq, torch, graph, tau, nw, ltau, lnw):
+    """The AESC estimators compared at equal accuracy on all edges of the
+    power-law graph.  Accuracy is the noise variance: the mean over edges of
+    (est_seed_a - est_seed_b)^2 / 2 for two independent seeds, free of the
+    truncation bias (the same Ŝ_tau for every variant) and of any reference.
+    Each variant's walk counts are scaled by var_variant / var_plain (its
+    variance per walk relative to the plain estimator's; variance falls as
+    1/N), so all reach the plain estimator's variance; the table gives the
+    time of one estimate at the scaled plan and the variance re-measured
+    there."""
+    import numpy as np
+    k = tau.size
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+
+    def run(kind, t_h, n_h, seed):
+        dt, dn = dev(t_h), dev(n_h)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if kind == "plain" or kind == "pilot":
+            _, sc = bq.aesc_estimate(graph, seed, None, dt, dn)
+        elif kind == "push1":
+            _, _, sc = bq.aesc_estimate_push(graph, seed, None, dt, dn, 1)
+        elif kind == "push8":
+            _, _, sc = bq.aesc_estimate_push(graph, seed, None, dt, dn, 8)
+        else:
+            _, _, sc = bq.aesc_estimate_shared(graph, seed, None, dt, dn)
+        e1.record()
+        e1.synchronize()
+        bq.sync()
+        return e0.elapsed_time(e1), sc.cpu().numpy()
+
+    def measure(kind, t_h, n_h):
+        run(kind, t_h, n_h, 105)  # warm-up
+        ms, a = run(kind, t_h, n_h, 105)
+        _, b = run(kind, t_h, n_h, 106)
+        return ms, float(np.mean((a - b) ** 2) / 2.0)
+
+    def scaled(n_h, t_h, factor):
+        lim = (2**32 - 1) // (2 * t_h.astype(np.uint64) + 2)
+        return np.minimum(np.maximum(np.ceil(n_h.astype(np.float64) * factor), 1), lim).astype(np.uint32)
+
+    plans = {"plain": (tau, nw), "push1": (tau, nw), "push8": (tau, nw), "shared": (tau, nw), "pilot": (ltau, lnw)}
+    base = {kind: measure(kind, *plan) for kind, plan in plans.items()}
+    var0 = base["plain"][1]
+    rows = {}
+    for kind, (t_h, n_h) in plans.items():
+        ms_b, var_b = base[kind]
+        factor = var_b / var0
+        walks_b = float(np.sum(n_h, dtype=np.float64))
+        if kind == "plain":
+            ms_s, var_s, n_s = ms_b, var_b, n_h
+        else:
+            n_s = scaled(n_h, t_h, factor)
+            ms_s, var_s = measure(kind, t_h, n_s)
+        rows[kind] = {"ms_at_plan": ms_b, "noise_var_at_plan": var_b, "n_scale": factor,
+                      "ms_at_equal_accuracy": ms_s, "noise_var_at_equal_accuracy": var_s,
+                      "edges_per_s_at_equal_accuracy": k / (ms_s / 1e3),
+                      "walks_per_side_mean": float(np.sum(n_s, dtype=np.float64)) / k,
+                      "walks_per_side_mean_at_plan": walks_b / k}
+    best = min(rows, key=lambda r: rows[r]["ms_at_equal_accuracy"])
+    return {"target_noise_var": var0, "variants": rows, "fastest_at_equal_accuracy": best,
+            "note": "noise variance = mean over all edges of (est(seed 105) - est(seed 106))^2 / 2; "
+                    "plain/push/shared use the scheduled plan, pilot its own plan; N scaled per variant"}
+
+
 def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
     """AESC on the power-law graph (Chung-Lu n = 4M, mean degree 10,
     exponent 2.1, largest component), all edges at eps = 0.05 with the
@@ -544,10 +612,12 @@ def aesc_powerlaw(bq, torch, steps, warmup, cpu=False):
               "foster_residual": abs(float(sest.sum()) - (g.n - 1)) / (g.n - 1),
               "subset_1000_max_abs_diff_vs_16N_2tau": float(sdiff.max()),
               "subset_1000_rms_diff_vs_16N_2tau": float(np.sqrt(np.mean(sdiff ** 2)))}
+    equal = aesc_equal_accuracy(bq, torch, graph, tau, nw, ltau, lnw)
     graph.close()
     cpu_line = aesc_cpu_baseline(g, 5, uv_all, tau, nw) if cpu else None
     return {
         "naive": naive,
+        "equal_accuracy": equal,
         "push_phase": push,
         "pilot_plan": pilot,
         "shared_walks": shared,
