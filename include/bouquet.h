@@ -436,6 +436,24 @@ int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_s
                     bq_batch **out);
 
 /*
+ * A batch of vertex-centric estimates: each query is estimated as by
+ * bq_aesc_estimate_shared on it alone (the walks of each endpoint serve every
+ * query edge at it; counts_dev receives C_uu, C_uv, C_vu, C_vv, sc_dev the
+ * estimates, bit-identical to a single call), and one persistent launch runs
+ * the vertex tasks of all queries.  Queries must be distinct edges within
+ * each query (a repeated edge gives BQ_EINVAL at bq_sync).  Creation runs
+ * each query's per-vertex plan once to size its return histograms (sum over
+ * the endpoints x of tau_x = the largest tau at x): later runs may change the
+ * plans' contents as long as no vertex's largest tau grows past what it was
+ * at creation (else that query's estimates are NaN and bq_sync returns
+ * BQ_EINVAL).  Device memory: about 32 B per vertex and 4 B per CSR entry of
+ * each query's graph, 32 B per queried edge, 4 B per histogram entry.  Run
+ * with bq_batch_run, release with bq_batch_destroy.  Synchronous.
+ */
+int bq_batch_create_shared(const bq_aesc_query *queries, uint32_t n_queries, const bq_sampler *sampler,
+                           bq_batch **out);
+
+/*
  * Run the batch on `stream`: kernel launches only (no allocation, no host
  * copy, no synchronisation), so the call can be captured into a CUDA graph
  * and the graph replayed.  Errors (a pair that is not an edge, tau = 0,

@@ -128,7 +128,7 @@ EXPORTS = (
     "bq_batch_size", "bq_batch_destroy", "bq_autotune_walks", "bq_autotune_aesc",
     "bq_server_create", "bq_server_submit", "bq_server_wait", "bq_server_stats_get",
     "bq_server_destroy", "bq_aesc_estimate_push", "bq_graph_set_eigvecs", "bq_aesc_plan_pilot",
-    "bq_aesc_estimate_shared", "bq_profile_read_bandwidth",
+    "bq_aesc_estimate_shared", "bq_profile_read_bandwidth", "bq_batch_create_shared",
 )
 
 _lock = threading.Lock()
@@ -173,6 +173,7 @@ def load_library(path: str | None = None):
         L.bq_set_tuning.argtypes = [c.POINTER(Tuning)]
         L.bq_walk_batch_noalloc.argtypes = [vp, u64, vp, u64, u32, c.POINTER(Sampler), u32, vp, vp, vp]
         L.bq_batch_create.argtypes = [c.POINTER(AescQuery), u32, c.POINTER(Sampler), c.POINTER(vp)]
+        L.bq_batch_create_shared.argtypes = [c.POINTER(AescQuery), u32, c.POINTER(Sampler), c.POINTER(vp)]
         L.bq_batch_run.argtypes = [vp, vp]
         L.bq_batch_size.argtypes = [vp, c.POINTER(u64)]
         L.bq_batch_destroy.argtypes = [vp]
@@ -585,14 +586,17 @@ class Batch:
 
     `queries` is a list of dicts with keys graph, seed, tau, nwalks (device
     uint32 tensors) and optionally uv (device pairs; None = all edges),
-    counts, sc (outputs, allocated when absent).  run() only launches
-    kernels, so it may be captured in a CUDA graph."""
+    counts, sc (outputs, allocated when absent).  shared=True estimates each
+    query with walks shared per vertex (bq_batch_create_shared: the results
+    of aesc_estimate_shared).  run() only launches kernels, so it may be
+    captured in a CUDA graph."""
 
-    def __init__(self, queries, sampler=None):
+    def __init__(self, queries, sampler=None, shared: bool = False):
         L = load_library()
         arr, self._keep, self.outputs = _query_array(queries)
         self._h = ctypes.c_void_p()
-        _check(L.bq_batch_create(arr, len(queries), _sampler(sampler), ctypes.byref(self._h)))
+        create = L.bq_batch_create_shared if shared else L.bq_batch_create
+        _check(create(arr, len(queries), _sampler(sampler), ctypes.byref(self._h)))
 
     def run(self, stream=None):
         _check(load_library().bq_batch_run(self._h, _stream_handle(stream)))

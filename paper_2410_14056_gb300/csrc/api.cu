@@ -874,6 +874,9 @@ int bq_sync(void *stream) {
     if (bits & kStatusBadIndex) return fail(BQ_EINVAL, "a query had tau = 0 or nwalks = 0 (its estimate is NaN)");
     if (bits & kStatusTimeout) return fail(BQ_ETIMEOUT, "a bounded device wait gave up");
     if (bits & kStatusRepeated) return fail(BQ_EINVAL, "an edge was queried twice in a vertex-centric estimate");
+    if (bits & kStatusPlanGrew)
+        return fail(BQ_EINVAL, "a vertex-centric batch's plan needs longer return histograms than at its creation "
+                               "(a vertex's largest tau grew; its estimates are NaN)");
     return fail(BQ_ECUDA, "unknown device status bits 0x%x", bits);
 }
 

@@ -10,6 +10,7 @@
 // bq_batch_run launches kernels only, so it can be captured in a CUDA graph.
 #include <math.h>
 
+#include <new>
 #include <vector>
 
 #include "edges.cuh"
@@ -368,6 +369,7 @@ struct bq_batch {
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
     uint32_t *status = nullptr;
+    bq::SharedBatch *shared = nullptr;  // vertex-centric batch (bq_batch_create_shared)
 };
 
 using namespace bq;
@@ -396,6 +398,7 @@ void launch_batch_count(const bq_batch *b, cudaStream_t s) {
 
 void free_batch(bq_batch *b) {
     if (!b) return;
+    if (b->shared) shared_batch_free(b->shared);
     cudaFree(b->d_qd);
     cudaFree(b->d_ebase);
     cudaFree(b->d_info);
@@ -509,6 +512,30 @@ int bq_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const bq_s
     return BQ_OK;
 }
 
+int bq_batch_create_shared(const bq_aesc_query *queries, uint32_t n_queries, const bq_sampler *sampler,
+                           bq_batch **out) {
+    bq::NvtxRange nvtx_range("bq_batch_create_shared");
+    clear_error();
+    if (!out) return fail(BQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_queries == 0 || !queries) return fail(BQ_EINVAL, "a batch needs at least one query");
+    Sampler smp;
+    int rc = validate_sampler(sampler, smp);
+    if (rc) return rc;
+    bq_batch *b = new (std::nothrow) bq_batch();
+    if (!b) return fail(BQ_ENOMEM, "host allocation failed");
+    BQ_CUDA(cudaGetDevice(&b->device));
+    b->nq = n_queries;
+    b->smp = smp;
+    rc = shared_batch_create(queries, n_queries, smp, &b->shared, &b->edges);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return BQ_OK;
+}
+
 int bq_batch_run(bq_batch *b, void *stream) {
     bq::NvtxRange nvtx_range("bq_batch_run");
     if (!b) return fail(BQ_EINVAL, "batch is NULL");
@@ -517,6 +544,11 @@ int bq_batch_run(bq_batch *b, void *stream) {
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != b->device) cudaSetDevice(b->device);
+    if (b->shared) {
+        const int rc = shared_batch_run(b->shared, s);
+        if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+        return rc;
+    }
     const uint32_t bouquet = 32u * (uint32_t)b->lanes;
     int rc = BQ_OK;
     cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s);

@@ -21,6 +21,7 @@ enum StatusBits : uint32_t {
     kStatusBadIndex = 1u << 3,   // (checked builds) index out of range
     kStatusTimeout = 1u << 4,    // a bounded wait gave up
     kStatusRepeated = 1u << 5,   // an edge repeated among vertex-centric queries
+    kStatusPlanGrew = 1u << 6,   // a shared batch's plan outgrew its histograms
 };
 
 constexpr uint32_t kNoHub = 0xffffffffu;
@@ -350,6 +351,13 @@ int serve_iterate(const ServeItem *d_items, uint32_t n_items, uint64_t total_ite
 // prepare + task scan, or finalize, of up to kServeMany requests in one launch each
 int serve_prepare_many(const ServeMany &L, uint32_t bouquet, cudaStream_t s);
 int serve_finalize_many(const ServeMany &L, cudaStream_t s);
+
+// ---- shared.cu: batches of vertex-centric estimates (bq_batch_create_shared)
+struct SharedBatch;
+int shared_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const Sampler &smp, SharedBatch **out,
+                        uint64_t *edges);
+int shared_batch_run(SharedBatch *b, cudaStream_t s);
+void shared_batch_free(SharedBatch *b);
 
 // ---- aesc.cu
 // naive: one walk per thread on the plain CSR (BQ_AESC_NAIVE), else bouquets
