@@ -968,6 +968,40 @@ def batched_measure(bq, torch, mix_count, steps, warmup, small_n=20_000):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     batch.close()
 
+    # the same queries with walks shared per vertex (bq_batch_create_shared)
+    sbatch = bq.Batch(queries, shared=True)
+    sstream = torch.cuda.Stream()
+    with torch.cuda.stream(sstream):
+        sbatch.run(sstream)
+    torch.cuda.synchronize()
+    scg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(scg, stream=sstream):
+        sbatch.run(sstream)
+    for _ in range(max(1, warmup)):
+        scg.replay()
+    torch.cuda.synchronize()
+    slat = []
+    for k in range(steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        scg.replay()
+        e1.record()
+        e1.synchronize()
+        slat.append(e0.elapsed_time(e1))
+    bq.sync()
+    q0 = queries[0]
+    c1, _, _ = bq.aesc_estimate_shared(q0["graph"], q0["seed"], None, q0["tau"], q0["nwalks"])
+    bq.sync()
+    if not torch.equal(c1, sbatch.outputs[0][0]):
+        raise RuntimeError("shared batch differs from a single vertex-centric call")
+    s_ms = sum(slat) / len(slat)
+    shared_row = {"ms_per_step": s_ms, "edges_per_s": edges / (s_ms / 1e3), "speedup_vs_plain_batch": ms / s_ms,
+                  "note": "the vertex-centric estimator at the same plan (each edge gets at least its N walks "
+                          "per side, so its variance is lower; see aesc_powerlaw.equal_accuracy)"}
+    sbatch.close()
+    del scg
+
     small = [i for i, (g, _) in enumerate(mix) if g.n <= small_n]
     by_size = None
     if small:
@@ -995,6 +1029,7 @@ def batched_measure(bq, torch, mix_count, steps, warmup, small_n=20_000):
         "p99_ms": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))],
         "sequential_one_call_per_graph_ms": seq_ms, "batching_speedup": seq_ms / ms,
         "small_graphs": by_size,
+        "shared_walks": shared_row,
         "autotuned_aesc_lanes": best, "autotune_ms": tune_ms,
         "roofline": {"bound": "l2", "achieved": achieved, "unit": "GB/s", "kernel": "batch_count_kernel",
                      "kernel_ms": kern_ms, "peak_hbm": peak, "frac_hbm": achieved / peak,
