@@ -316,10 +316,43 @@ def aesc_measure(bq, torch, steps, warmup):
     ms = sum(lat) / len(lat)
     kern_ms = prof["aesc_ms"] / max(prof["aesc_launches"], 1)
     naive = aesc_naive_row(bq, torch, graph, dtau, dnw, counts, ms, steps, warmup)
+    # exact SC = effective resistance from the Laplacian's pseudoinverse (numpy, FP64)
+    from workloads import all_edges
+    uv = all_edges(g).astype(np.int64)
+    lp = np.linalg.pinv(np.diag(A.sum(axis=1)) - A)
+    exact = lp[uv[:, 0], uv[:, 0]] + lp[uv[:, 1], uv[:, 1]] - 2.0 * lp[uv[:, 0], uv[:, 1]]
+    plain_err = float(np.max(np.abs(sc.cpu().numpy() - exact)))
+    # the same certified plan with walks shared per vertex: every edge keeps at
+    # least its N walks per side, so the same eps guarantee holds
+    scounts = torch.empty_like(counts)
+    ssc = torch.empty_like(sc)
+    for _ in range(warmup):
+        bq.aesc_estimate_shared(graph, 5, None, dtau, dnw, counts=scounts, sc=ssc)
+    bq.sync()
+    slat = []
+    for _ in range(steps):
+        ev0.record()
+        bq.aesc_estimate_shared(graph, 5, None, dtau, dnw, counts=scounts, sc=ssc)
+        ev1.record()
+        ev1.synchronize()
+        slat.append(ev0.elapsed_time(ev1))
+    bq.sync()
+    s_ms = sum(slat) / len(slat)
+    nvert = np.zeros(g.n)
+    tvert = np.zeros(g.n)
+    for side in (0, 1):
+        np.maximum.at(nvert, uv[:, side], nw.astype(np.float64))
+        np.maximum.at(tvert, uv[:, side], tau.astype(np.float64))
+    shared = {"ms_per_estimate": s_ms, "edges_per_s": tau.size / (s_ms / 1e3),
+              "walk_steps_per_call": float(np.sum(nvert * tvert)),
+              "max_abs_error_vs_exact": float(np.max(np.abs(ssc.cpu().numpy() - exact))),
+              "speedup_vs_per_edge": ms / s_ms}
     return {
         "workload": f"G(n=1000, m=5000) seed 1 plus a spanning path (m={g.m}), all edges, eps=0.1, "
                     "delta=0.01, certified plan",
         "naive": naive,
+        "shared_walks": shared,
+        "max_abs_error_vs_exact": plain_err,
         "edges": int(tau.size), "edges_per_s": tau.size / (ms / 1e3),
         "walk_steps_per_call": steps_per_call,
         "walk_steps_per_s": steps_per_call / (ms / 1e3),
