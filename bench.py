@@ -797,8 +797,13 @@ def run_ours(args):
     group_ms = prof["group_ms"] / max(prof["group_launches"], 1)
     launches = prof["kernel_launches"]
 
+    bouquet_visits = visits.clone()  # the last timed batch
     naive_ms, _ = timed(bq.MODE_NAIVE, max(3, args.steps // 2), 1)
     naive_ms /= max(3, args.steps // 2)
+    if not torch.equal(visits, bouquet_visits):
+        raise RuntimeError("the naive and bouquet walk kernels gave different visit counts")
+    if int(bouquet_visits.to(torch.int64).sum()) != N_WALKS * N_STEPS:
+        raise RuntimeError("the visit counts do not sum to walks x steps")
 
     peak, peak_kind = measured_peaks()
     algo_bytes = BYTES_PER_STEP * steps_per_batch
@@ -873,7 +878,8 @@ def run_ours(args):
             "grouping_ms_per_step": group_ms,
             "naive": {"value": whole_job_rate(world, steps_per_batch, naive_ms / 1e3), "unit": "walk-steps/s",
                       "ms_per_step": naive_ms,
-                      "bouquet_speedup": naive_ms / ms_per_step},
+                      "bouquet_speedup": naive_ms / ms_per_step,
+                      "visits_equal_bouquet": True},
             "samplers": samplers,
             "aesc": aesc,
             "aesc_powerlaw": aesc_pl,
