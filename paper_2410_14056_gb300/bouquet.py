@@ -64,7 +64,8 @@ class Tuning(ctypes.Structure):
                 ("hub_slots", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
                 ("aesc_hub", ctypes.c_uint32), ("hub_cluster", ctypes.c_uint32),
                 ("hub_relabel", ctypes.c_uint32), ("relabel_hub8", ctypes.c_uint32),
-                ("hub8_hubs", ctypes.c_uint32), ("hub8_count_bits", ctypes.c_uint32)]
+                ("hub8_hubs", ctypes.c_uint32), ("hub8_count_bits", ctypes.c_uint32),
+                ("shared_lanes", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):

@@ -34,6 +34,7 @@ std::atomic<int> g_aesc_hub{0};
 std::atomic<int> g_relabel_hub8{1};
 std::atomic<int> g_hub8_hubs{0};
 std::atomic<int> g_hub8_count_bits{0};
+std::atomic<int> g_shared_lanes{2};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -162,6 +163,7 @@ bool tuning_aesc_hub() { return g_aesc_hub.load() != 0; }
 bool tuning_relabel_hub8() { return g_relabel_hub8.load() != 0; }
 uint32_t tuning_hub8_hubs() { return (uint32_t)g_hub8_hubs.load(); }
 uint32_t tuning_hub8_count_bits() { return (uint32_t)g_hub8_count_bits.load(); }
+int tuning_shared_lanes() { return g_shared_lanes.load(); }
 
 namespace {
 
@@ -938,6 +940,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->relabel_hub8 = (uint32_t)g_relabel_hub8.load();
     out->hub8_hubs = (uint32_t)g_hub8_hubs.load();
     out->hub8_count_bits = (uint32_t)g_hub8_count_bits.load();
+    out->shared_lanes = (uint32_t)g_shared_lanes.load();
     return BQ_OK;
 }
 
@@ -959,6 +962,8 @@ int bq_set_tuning(const bq_tuning *in) {
     if (in->relabel_hub8 > 1) return fail(BQ_EINVAL, "relabel_hub8 must be 0 or 1");
     if (in->hub8_hubs > kHub8Max) return fail(BQ_EINVAL, "hub8_hubs must be at most %u", kHub8Max);
     if (in->hub8_count_bits > 31) return fail(BQ_EINVAL, "hub8_count_bits must be 0..31");
+    if (in->shared_lanes != 2 && in->shared_lanes != 4 && in->shared_lanes != 8)
+        return fail(BQ_EINVAL, "shared_lanes must be 2, 4 or 8");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
@@ -971,6 +976,7 @@ int bq_set_tuning(const bq_tuning *in) {
     g_relabel_hub8.store((int)in->relabel_hub8);
     g_hub8_hubs.store((int)in->hub8_hubs);
     g_hub8_count_bits.store((int)in->hub8_count_bits);
+    g_shared_lanes.store((int)in->shared_lanes);
     return BQ_OK;
 }
 

@@ -29,7 +29,7 @@ namespace bq {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSharedW = 4;                                 // walks per lane
+constexpr int kSharedW = 2;                                 // walks per lane (coupled sampler)
 constexpr uint64_t kVertexStream = 0x2000000000000000ull;  // edge streams stay below
 constexpr uint32_t kNoQuery = 0xffffffffu;
 
@@ -181,9 +181,12 @@ __device__ __forceinline__ void run_vertex_task(const EL &el, const int64_t *__r
             }
             returns += __popc(__ballot_sync(0xffffffffu, deg[j] != 0 && cur[j] == x));
             // lanes hitting the same edge side at this step share one atomic
-            const uint32_t peers = __match_any_sync(0xffffffffu, key);
-            if (key != kNoQuery && lane == (uint32_t)(__ffs(peers) - 1))
-                atomicAdd(cross + key, w * (uint32_t)__popc(peers));
+            // (the match is skipped when no lane hit a query neighbour)
+            if (__any_sync(0xffffffffu, key != kNoQuery)) {
+                const uint32_t peers = __match_any_sync(0xffffffffu, key);
+                if (key != kNoQuery && lane == (uint32_t)(__ffs(peers) - 1))
+                    atomicAdd(cross + key, w * (uint32_t)__popc(peers));
+            }
         }
         if (lane == 0 && returns && rb + (l - 1) < ret_cap) atomicAdd(ret + rb + (l - 1), returns);
     }
@@ -269,7 +272,15 @@ __global__ void shared_finalize_kernel(const SharedQuery *__restrict__ qinfo, ui
     }
 }
 
-template <typename EL, bool COUPLED>
+// Walks per lane of the vertex-centric kernels (bq_tuning.shared_lanes; the
+// coupled sampler keeps kSharedW): never changes a result, the walks of a
+// vertex are the same whatever their grouping.
+int shared_walks_per_lane(const Sampler &smp) {
+    const int w = tuning_shared_lanes();
+    return smp.kind == 1 || (w != 2 && w != 4 && w != 8) ? kSharedW : w;
+}
+
+template <typename EL, int W, bool COUPLED>
 int launch_shared_count(EL el, const DeviceGraph &g, const uint32_t *vn, const uint32_t *vt, const uint64_t *vbegin,
                         const uint32_t *bucket, const uint64_t *rbegin, uint64_t ret_cap, const uint32_t *qidx,
                         const SharedQuery *qinfo, uint64_t seed, const Sampler &smp,
@@ -277,7 +288,7 @@ int launch_shared_count(EL el, const DeviceGraph &g, const uint32_t *vn, const u
     int dev = 0, sms = 0, per_sm = 0;
     BQ_CUDA(cudaGetDevice(&dev));
     BQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    auto kernel = shared_count_kernel<EL, kSharedW, COUPLED>;
+    auto kernel = shared_count_kernel<EL, W, COUPLED>;
     BQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
     kernel<<<sms * per_sm, kThreads, 0, s>>>(el, g.offsets, g.nbrs, vn, vt, vbegin, bucket, g.n, rbegin, ret_cap,
@@ -301,7 +312,8 @@ int launch_aesc_shared(const DeviceGraph &g, uint64_t seed, const uint32_t *edge
                        uint32_t *nused, double *sc, uint32_t *status, cudaStream_t s) {
     if (k == 0) return BQ_OK;
     const uint64_t n = g.n;
-    const uint32_t bouquet = 32u * (uint32_t)kSharedW;
+    const int lanes_w = shared_walks_per_lane(smp);
+    const uint32_t bouquet = 32u * (uint32_t)lanes_w;
     // scratch: qinfo[k] | vn[n] vt[n] | tasks[n] | vbegin[n + 1] bucket | rbegin[n + 1] |
     // qidx[nnz] | cross[2k] | next_task | (edges[2k] if all-edges)
     const size_t b_qinfo = align16(sizeof(SharedQuery) * k);
@@ -382,10 +394,17 @@ int launch_aesc_shared(const DeviceGraph &g, uint64_t seed, const uint32_t *edge
         count_launches(1);
         rc = with_edges(g, [&](auto el) {
             using EL = decltype(el);
-            return smp.kind == 1 ? launch_shared_count<EL, true>(el, g, vn, vt, vbegin, bucket, rbegin, ret_len + 1,
-                                                                 qidx, qinfo, seed, smp, next_task, ret, cross, s)
-                                 : launch_shared_count<EL, false>(el, g, vn, vt, vbegin, bucket, rbegin, ret_len + 1,
-                                                                  qidx, qinfo, seed, smp, next_task, ret, cross, s);
+            if (smp.kind == 1)
+                return launch_shared_count<EL, kSharedW, true>(el, g, vn, vt, vbegin, bucket, rbegin, ret_len + 1,
+                                                               qidx, qinfo, seed, smp, next_task, ret, cross, s);
+            if (lanes_w == 4)
+                return launch_shared_count<EL, 4, false>(el, g, vn, vt, vbegin, bucket, rbegin, ret_len + 1, qidx,
+                                                         qinfo, seed, smp, next_task, ret, cross, s);
+            if (lanes_w == 8)
+                return launch_shared_count<EL, 8, false>(el, g, vn, vt, vbegin, bucket, rbegin, ret_len + 1, qidx,
+                                                         qinfo, seed, smp, next_task, ret, cross, s);
+            return launch_shared_count<EL, 2, false>(el, g, vn, vt, vbegin, bucket, rbegin, ret_len + 1, qidx,
+                                                     qinfo, seed, smp, next_task, ret, cross, s);
         });
     }
     if (rc == BQ_OK) {
@@ -503,6 +522,7 @@ struct SharedBatchQuery {
 struct SharedBatch {
     int device = 0;
     Sampler smp{0, 0, 1};
+    int lanes = kSharedW;  // walks per lane, fixed at creation
     uint64_t edges = 0;
     int grid = 0;
     std::vector<SharedBatchQuery> q;
@@ -528,14 +548,14 @@ void shared_batch_free_impl(SharedBatch *b) {
 // The per-vertex plan of one query on s (the first half of a single call):
 // validation, walk counts and lengths, vertex task prefix and bucket index,
 // histogram offsets; zeroes the return histograms it will fill.
-int shared_plan(const SharedBatchQuery &q, uint32_t *status, cudaStream_t s) {
+int shared_plan(const SharedBatchQuery &q, uint32_t lanes, uint32_t *status, cudaStream_t s) {
     const uint64_t n = q.g.n;
     cudaError_t e = cudaMemsetAsync(q.vn, 0, sizeof(uint32_t) * 2 * n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(q.qidx, 0xff, sizeof(uint32_t) * q.g.nnz, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(q.cross, 0, sizeof(uint32_t) * 2 * q.k, s);
     if (e == cudaSuccess && q.ret) e = cudaMemsetAsync(q.ret, 0, sizeof(uint32_t) * q.ret_cap, s);
     if (e != cudaSuccess) return cuda_fail(e, "shared batch setup");
-    const uint32_t bouquet = 32u * (uint32_t)kSharedW;
+    const uint32_t bouquet = 32u * lanes;
     count_launches(3);
     shared_prepare_kernel<<<blocks_for(q.k, kThreads), kThreads, 0, s>>>(q.g, q.uv, q.k, q.tau, q.nwalks, q.qinfo,
                                                                          q.vn, q.vt, q.qidx, status);
@@ -568,6 +588,7 @@ int shared_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const 
     if (!b) return fail(BQ_ENOMEM, "host allocation failed");
     b->device = dev;
     b->smp = smp;
+    b->lanes = shared_walks_per_lane(smp);
     b->q.resize(n_queries);
     int rc = status_word(dev, &b->status);
     uint32_t *plan_status = nullptr;  // the plan run at creation reports nothing to bq_sync
@@ -634,7 +655,7 @@ int shared_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const 
             q.uv = q.own_uv;
         }
         // one plan now sizes the return histograms: sum over vertices of tau_x
-        if (rc == BQ_OK) rc = shared_plan(q, plan_status, 0);
+        if (rc == BQ_OK) rc = shared_plan(q, (uint32_t)b->lanes, plan_status, 0);
         uint64_t ret_len = 0;
         if (rc == BQ_OK && (cudaMemcpy(&ret_len, q.rbegin + n, sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess))
             rc = fail(BQ_ECUDA, "query %u: reading the plan", i);
@@ -678,8 +699,10 @@ int shared_batch_create(const bq_aesc_query *queries, uint32_t n_queries, const 
                                                 : cuda_fail(e, "shared batch create");
     }
     if (rc == BQ_OK) {
-        const bool c = smp.kind == 1;
-        rc = c ? shared_batch_grid<kSharedW, true>(&b->grid) : shared_batch_grid<kSharedW, false>(&b->grid);
+        rc = smp.kind == 1   ? shared_batch_grid<kSharedW, true>(&b->grid)
+             : b->lanes == 4 ? shared_batch_grid<4, false>(&b->grid)
+             : b->lanes == 8 ? shared_batch_grid<8, false>(&b->grid)
+                             : shared_batch_grid<2, false>(&b->grid);
     }
     if (rc) {
         shared_batch_free_impl(b);
@@ -697,7 +720,7 @@ int shared_batch_run(SharedBatch *b, cudaStream_t s) {
         ProfScope prof(kProfAescAux, s);
         for (const SharedBatchQuery &q : b->q) {
             if (q.k == 0) continue;
-            const int rc = shared_plan(q, b->status, s);
+            const int rc = shared_plan(q, (uint32_t)b->lanes, b->status, s);
             if (rc) return rc;
         }
         count_launches(1);
@@ -706,12 +729,15 @@ int shared_batch_run(SharedBatch *b, cudaStream_t s) {
     {
         ProfScope prof(kProfAesc, s);
         count_launches(1);
+        const SharedQueryDesc *qd = b->d_qd;
         if (b->smp.kind == 1)
-            shared_batch_count_kernel<kSharedW, true><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_qbase, nq, b->smp,
-                                                                                  b->d_next);
+            shared_batch_count_kernel<kSharedW, true><<<b->grid, kThreads, 0, s>>>(qd, b->d_qbase, nq, b->smp, b->d_next);
+        else if (b->lanes == 4)
+            shared_batch_count_kernel<4, false><<<b->grid, kThreads, 0, s>>>(qd, b->d_qbase, nq, b->smp, b->d_next);
+        else if (b->lanes == 8)
+            shared_batch_count_kernel<8, false><<<b->grid, kThreads, 0, s>>>(qd, b->d_qbase, nq, b->smp, b->d_next);
         else
-            shared_batch_count_kernel<kSharedW, false><<<b->grid, kThreads, 0, s>>>(b->d_qd, b->d_qbase, nq, b->smp,
-                                                                                   b->d_next);
+            shared_batch_count_kernel<2, false><<<b->grid, kThreads, 0, s>>>(qd, b->d_qbase, nq, b->smp, b->d_next);
         BQ_CUDA(cudaGetLastError());
     }
     ProfScope prof(kProfAescAux, s);

@@ -67,12 +67,15 @@ def make_queries(bq, torch, rng):
     return graphs, queries, host
 
 
-@pytest.mark.parametrize("sampler", [None, (1, 5, 32)])
-def test_shared_batch_matches_oracle_and_single(env, sampler):
+@pytest.mark.parametrize("sampler,lanes", [(None, 2), (None, 8), ((1, 5, 32), 2)])
+def test_shared_batch_matches_oracle_and_single(env, sampler, lanes):
     bq, torch = env
     rng = np.random.default_rng(13)
     graphs, queries, host = make_queries(bq, torch, rng)
+    old = bq.get_tuning()
+    bq.set_tuning(shared_lanes=lanes)  # kept by the batch from its creation
     batch = bq.Batch(queries, sampler=sampler, shared=True)
+    bq.set_tuning(**old)
     assert batch.size() == sum(h[3].size for h in host)
     for _ in range(2):  # outputs are overwritten, not accumulated
         batch.run()

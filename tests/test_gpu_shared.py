@@ -67,7 +67,9 @@ def test_layouts_never_change_results(env, layout):
     try:
         bq.set_tuning(layout=layout)
         graph = bq.Graph.from_csr(g)
-        check(bq, graph, g, 5, uv, tau, nw)
+        for lanes in (2, 4, 8):  # walks per lane: the task grouping, never a result
+            bq.set_tuning(shared_lanes=lanes)
+            check(bq, graph, g, 5, uv, tau, nw)
         graph.close()
     finally:
         bq.set_tuning(**old)

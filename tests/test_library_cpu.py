@@ -75,7 +75,10 @@ def test_tuning_roundtrip_and_validation(lib):
     try:
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == dict(old, walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
-        assert (old["relabel_hub8"], old["hub8_hubs"], old["hub8_count_bits"]) == (1, 0, 0)  # defaults
+        assert (old["relabel_hub8"], old["hub8_hubs"], old["hub8_count_bits"], old["shared_lanes"]) == (1, 0, 0, 2)
+        for bad in (dict(shared_lanes=3), dict(shared_lanes=0)):
+            with pytest.raises(bq.BouquetError):
+                bq.set_tuning(**bad)
         bq.set_tuning(relabel_hub8=0, hub8_hubs=28000, hub8_count_bits=31)
         assert bq.get_tuning()["hub8_hubs"] == 28000
         for bad in (dict(relabel_hub8=2), dict(hub8_hubs=28001), dict(hub8_count_bits=32)):
