@@ -1226,7 +1226,8 @@ def serving_measure(bq, torch, sat_requests, load_seconds, warmup, max_requests=
                       "iterations": st1["iterations"] - st0["iterations"],
                       "count_kernel_ms": kern_ms,
                       "worker_s": {k: st1[f"worker_{k}_s"] - st0[f"worker_{k}_s"]
-                                   for k in ("admit", "launch", "complete", "idle")}}
+                                   for k in ("admit", "launch", "complete", "idle")},
+                      "planner_s": st1["planner_s"] - st0["planner_s"]}
         loads = []
         for f in SERVE_LOADS:
             rate = f * sat_rps

@@ -496,7 +496,13 @@ typedef struct bq_server_config {
     double n_scale;
     uint32_t n_min;
     uint32_t planner_threads;     /* threads planning submitted requests (0: half the
-                                     host cores, at most 8) */
+                                     host cores, at most 8); a request of 32768 pairs
+                                     or more is planned by up to 4 threads */
+    uint32_t reserved;
+    uint64_t pinned_arena_bytes;  /* page-locked host memory taken at creation for the
+                                     requests' input and output images (0: 256 MiB), so
+                                     that requests do not wait for page locking; more is
+                                     page-locked on demand past it */
 } bq_server_config;
 
 typedef struct bq_server_stats {
@@ -511,6 +517,9 @@ typedef struct bq_server_stats {
      * launching iterations (including waits for a free descriptor slot),
      * completing requests (waits for results, copies, frees), and idle */
     double worker_admit_s, worker_launch_s, worker_complete_s, worker_idle_s;
+    /* the planner threads' time: planning every request (summed over the
+     * threads), and the longest planning of one request */
+    double planner_s, planner_max_ms;
 } bq_server_stats;
 
 /* Start a server over graphs (all on the current device, nnz < 2^32; they

@@ -106,7 +106,8 @@ class ServerConfig(ctypes.Structure):
                 ("max_pending", ctypes.c_uint32), ("tasks_per_iteration", ctypes.c_uint64),
                 ("tau_scale", ctypes.c_double), ("tau_add", ctypes.c_uint32),
                 ("tau_max", ctypes.c_uint32), ("n_scale", ctypes.c_double),
-                ("n_min", ctypes.c_uint32), ("planner_threads", ctypes.c_uint32)]
+                ("n_min", ctypes.c_uint32), ("planner_threads", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("pinned_arena_bytes", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -117,7 +118,8 @@ class ServerStats(ctypes.Structure):
                 ("uptime_s", ctypes.c_double), ("inflight", ctypes.c_uint32),
                 ("pending", ctypes.c_uint32), ("worker_admit_s", ctypes.c_double),
                 ("worker_launch_s", ctypes.c_double), ("worker_complete_s", ctypes.c_double),
-                ("worker_idle_s", ctypes.c_double)]
+                ("worker_idle_s", ctypes.c_double), ("planner_s", ctypes.c_double),
+                ("planner_max_ms", ctypes.c_double)]
 
 
 # every symbol include/bouquet.h declares

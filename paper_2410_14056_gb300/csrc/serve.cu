@@ -117,13 +117,28 @@ size_t request_bytes(uint64_t k) { return layout_of(k).total; }
 // from 4 KiB), so that results come back by asynchronous DMA.  Blocks are
 // allocated on the worker thread and returned by waiters.
 struct PinnedPool {
+    // Blocks come from per-size-class free lists, then from one page-locked
+    // arena allocated when the server starts (so that a request does not wait
+    // for page locking), then from cudaMallocHost.
     std::mutex mu;
     std::unordered_map<size_t, std::vector<char *>> free;
     std::vector<char *> all;
+    char *arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
     static size_t size_class(size_t bytes) {
         size_t c = 4096;
         while (c < bytes) c <<= 1;
         return c;
+    }
+    int reserve(size_t bytes) {
+        if (bytes == 0) return BQ_OK;
+        if (cudaMallocHost((void **)&arena, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            arena = nullptr;
+            return fail(BQ_ENOMEM, "cannot page-lock %zu bytes of host memory for the server", bytes);
+        }
+        arena_size = bytes;
+        return BQ_OK;
     }
     char *get(size_t bytes, size_t &cap) {
         cap = size_class(bytes);
@@ -133,6 +148,11 @@ struct PinnedPool {
             if (!v.empty()) {
                 char *p = v.back();
                 v.pop_back();
+                return p;
+            }
+            if (arena && arena_used + cap <= arena_size) {
+                char *p = arena + arena_used;
+                arena_used += cap;
                 return p;
             }
         }
@@ -152,6 +172,9 @@ struct PinnedPool {
     }
     void release() {
         for (char *p : all) cudaFreeHost(p);
+        if (arena) cudaFreeHost(arena);
+        arena = nullptr;
+        arena_size = arena_used = 0;
         all.clear();
         free.clear();
     }
@@ -199,6 +222,7 @@ struct bq_server {
     uint64_t submitted = 0, completed = 0, failed = 0, edges_completed = 0, iterations = 0;
     double walk_steps = 0;
     double t_admit = 0, t_launch = 0, t_complete = 0, t_idle = 0;  // worker seconds per phase
+    double t_plan = 0, t_plan_max = 0;  // planner seconds: all requests, the longest one
     std::vector<double> latencies_ms;
 };
 
@@ -227,6 +251,75 @@ void give_event(bq_server *srv, cudaEvent_t &e) {
     e = nullptr;
 }
 
+// Plan pairs [lo, hi) of a request: tau and N per pair from the endpoint
+// degrees (the scheduled plan), the bouquet tasks and walk steps summed.
+// Returns the index of the first pair that cannot be planned (hi if none),
+// with its code and message.
+struct PlanPart {
+    uint64_t bad = 0;
+    int code = BQ_OK;
+    std::string msg;
+    uint64_t tasks = 0;
+    double steps = 0.0;
+};
+
+void plan_range(const bq_graph *g, const uint32_t *edges_uv, uint64_t lo, uint64_t hi, double eps,
+                const bq_schedule &sched, uint32_t bouquet, uint32_t *tau, uint32_t *nw, PlanPart &out) {
+    const int64_t *off = g->h_offsets.data();
+    out.bad = hi;
+    // the endpoints' offsets are random reads into an array of up to
+    // several hundred MB: request them kAhead pairs before they are used
+    constexpr uint64_t kAhead = 32;
+    for (uint64_t i = lo; i < hi && i < lo + kAhead; ++i) {
+        if (edges_uv[2 * i] < g->n) __builtin_prefetch(off + edges_uv[2 * i]);
+        if (edges_uv[2 * i + 1] < g->n) __builtin_prefetch(off + edges_uv[2 * i + 1]);
+    }
+    char buf[160];
+    for (uint64_t i = lo; i < hi; ++i) {
+        if (i + kAhead < hi) {
+            const uint32_t pa = edges_uv[2 * (i + kAhead)], pb = edges_uv[2 * (i + kAhead) + 1];
+            if (pa < g->n) __builtin_prefetch(off + pa);
+            if (pb < g->n) __builtin_prefetch(off + pb);
+        }
+        const uint32_t a = edges_uv[2 * i], b = edges_uv[2 * i + 1];
+        int64_t da = 0, db = 0;
+        if (a < g->n && b < g->n && a != b) {
+            da = off[a + 1] - off[a];
+            db = off[b + 1] - off[b];
+        }
+        if (da == 0 || db == 0) {
+            snprintf(buf, sizeof buf, "pair %llu: (%u, %u) is not an edge", (unsigned long long)i, a, b);
+            out.bad = i;
+            out.code = BQ_ENOEDGE;
+            out.msg = buf;
+            return;
+        }
+        const double s_e = 1.0 / (double)da + 1.0 / (double)db;
+        uint32_t t = 1;
+        double n = 0.0;
+        plan_scheduled_edge(s_e, eps, sched, t, n);
+        if (n < 1.0) n = 1.0;
+        if (n * 2.0 * (double)t >= 4294967296.0) {
+            snprintf(buf, sizeof buf, "pair %llu: 2 N tau = %.3g reaches 2^32", (unsigned long long)i,
+                     n * 2.0 * (double)t);
+            out.bad = i;
+            out.code = BQ_EOVERFLOW;
+            out.msg = buf;
+            return;
+        }
+        tau[i] = t;
+        nw[i] = (uint32_t)n;
+        out.tasks += 2ull * ((nw[i] + bouquet - 1) / bouquet);
+        out.steps += 2.0 * (double)nw[i] * (double)t;
+    }
+}
+
+// Requests with at least kPlanSplit pairs are planned by up to kPlanThreads
+// threads, one contiguous range each; the error reported is always that of
+// the lowest failing pair, as in one pass.
+constexpr uint64_t kPlanSplit = 32768;
+constexpr unsigned kPlanThreads = 4;
+
 // Plan one request on the host (a planner thread, no lock): fill tau and N
 // per edge of its input image from the endpoint degrees (the scheduled
 // plan), count its bouquet tasks and walk steps.  A pair with an endpoint of
@@ -242,30 +335,31 @@ int plan_request(bq_server *srv, Request &r) {
     const uint32_t *edges_uv = r.h_uv();
     const bq_schedule sched{srv->cfg.tau_scale, srv->cfg.tau_add, srv->cfg.tau_max,
                             srv->cfg.n_scale,   srv->cfg.n_min,   0};
-    const int64_t *off = g->h_offsets.data();
     const uint32_t bouquet = bouquet_of(srv);
     uint32_t *tau = r.h_tau(), *nw = r.h_nw();
+    unsigned parts = 1;
+    if (r.k >= kPlanSplit)
+        parts = (unsigned)std::min<uint64_t>(kPlanThreads, r.k / (kPlanSplit / 2));
+    std::vector<PlanPart> out(parts);
+    const uint64_t per = (r.k + parts - 1) / parts;
+    auto run = [&](unsigned i) {
+        const uint64_t lo = std::min<uint64_t>(r.k, (uint64_t)i * per), hi = std::min<uint64_t>(r.k, lo + per);
+        plan_range(g, edges_uv, lo, hi, r.eps, sched, bouquet, tau, nw, out[i]);
+    };
+    if (parts == 1) {
+        run(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (unsigned i = 1; i < parts; ++i) pool.emplace_back(run, i);
+        run(0);
+        for (auto &t : pool) t.join();
+    }
     r.tasks_total = 0;
     r.walk_steps = 0;
-    for (uint64_t i = 0; i < r.k; ++i) {
-        const uint32_t a = edges_uv[2 * i], b = edges_uv[2 * i + 1];
-        if (a >= g->n || b >= g->n || a == b)
-            return fail(BQ_ENOEDGE, "pair %llu: (%u, %u) is not an edge", (unsigned long long)i, a, b);
-        const int64_t da = off[a + 1] - off[a], db = off[b + 1] - off[b];
-        if (da == 0 || db == 0)
-            return fail(BQ_ENOEDGE, "pair %llu: (%u, %u) is not an edge", (unsigned long long)i, a, b);
-        const double s_e = 1.0 / (double)da + 1.0 / (double)db;
-        uint32_t t = 1;
-        double n = 0.0;
-        plan_scheduled_edge(s_e, r.eps, sched, t, n);
-        if (n < 1.0) n = 1.0;
-        if (n * 2.0 * (double)t >= 4294967296.0)
-            return fail(BQ_EOVERFLOW, "pair %llu: 2 N tau = %.3g reaches 2^32", (unsigned long long)i,
-                        n * 2.0 * (double)t);
-        tau[i] = t;
-        nw[i] = (uint32_t)n;
-        r.tasks_total += 2ull * ((nw[i] + bouquet - 1) / bouquet);
-        r.walk_steps += 2.0 * (double)nw[i] * (double)t;
+    for (const PlanPart &p : out) {  // parts in pair order: the first error is the lowest pair's
+        if (p.code != BQ_OK) return fail(p.code, "%s", p.msg.c_str());
+        r.tasks_total += p.tasks;
+        r.walk_steps += p.steps;
     }
     return BQ_OK;
 }
@@ -521,11 +615,15 @@ void planner_main(bq_server *srv) {
             ++srv->planning;
         }
         clear_error();
+        const auto t0 = Clock::now();
         const int rc = plan_request(srv, *r);
+        const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
         const std::string msg = rc != BQ_OK ? std::string(bq_last_error()) : std::string();
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             --srv->planning;
+            srv->t_plan += dt;
+            if (dt > srv->t_plan_max) srv->t_plan_max = dt;
             if (rc == BQ_OK) {
                 srv->pending.push_back(r);
             } else {
@@ -688,6 +786,7 @@ int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server
     if (!c.max_inflight) c.max_inflight = 256;
     if (!c.max_pending) c.max_pending = 65536;
     if (!c.tasks_per_iteration) c.tasks_per_iteration = 1ull << 16;
+    if (!c.pinned_arena_bytes) c.pinned_arena_bytes = 256ull << 20;
     if (c.max_inflight > (1u << 20)) return fail(BQ_EINVAL, "max_inflight %u is above 2^20", c.max_inflight);
     if (c.tau_max < 1 || !(c.tau_scale >= 0.0) || !(c.n_scale >= 0.0)) return fail(BQ_EINVAL, "bad schedule");
     // the planner reads host copies of the graphs: take them now, before the
@@ -719,7 +818,8 @@ int bq_server_create(bq_graph *const *graphs, uint32_t n_graphs, const bq_server
     {
         // the stream-ordered pool keeps freed request memory (set once per device)
         uint32_t *unused = nullptr;
-        const int rc = status_word(dev, &unused);
+        int rc = status_word(dev, &unused);
+        if (rc == BQ_OK) rc = srv->pinned.reserve(c.pinned_arena_bytes);
         if (rc) {
             server_free(srv);
             return rc;
@@ -823,6 +923,8 @@ int bq_server_stats_get(bq_server *srv, bq_server_stats *out) {
         out->worker_launch_s = srv->t_launch;
         out->worker_complete_s = srv->t_complete;
         out->worker_idle_s = srv->t_idle;
+        out->planner_s = srv->t_plan;
+        out->planner_max_ms = srv->t_plan_max * 1e3;
         lat = srv->latencies_ms;
     }
     out->p50_ms = percentile(lat, 0.50);
