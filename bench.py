@@ -798,6 +798,21 @@ def run_ours(args):
     launches = prof["kernel_launches"]
 
     bouquet_visits = visits.clone()  # the last timed batch
+    # the same kernel on the walks in input order (no grouping by start)
+    bq.set_tuning(group_walks=0)
+    ug_steps = max(3, args.steps // 2)
+    ug_total, ug_prof = timed(bq.MODE_BOUQUET, ug_steps, 1)
+    bq.set_tuning(group_walks=1)
+    if not torch.equal(visits, bouquet_visits):
+        raise RuntimeError("grouped and ungrouped walk batches gave different visit counts")
+    ungrouped = {"ms_per_step": ug_total / ug_steps,
+                 "walk_kernel_ms": ug_prof["walk_ms"] / max(ug_prof["walk_launches"], 1),
+                 "pairs_ms": ug_prof["group_ms"] / max(ug_prof["group_launches"], 1),
+                 "note": "bq_tuning.group_walks = 0: the same walk kernel on the walks in input order; "
+                         "the grouped step's walk kernel and grouping times are walk_kernel_ms_grouped and "
+                         "grouping_ms_per_step"}
+    ungrouped["walk_kernel_ms_grouped"] = walk_ms
+    ungrouped["grouping_gain_in_walk_kernel"] = ungrouped["walk_kernel_ms"] / walk_ms
     naive_ms, _ = timed(bq.MODE_NAIVE, max(3, args.steps // 2), 1)
     naive_ms /= max(3, args.steps // 2)
     if not torch.equal(visits, bouquet_visits):
@@ -876,6 +891,7 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps,
             "clocks": clocks.summary(),
             "grouping_ms_per_step": group_ms,
+            "ungrouped": ungrouped,
             "naive": {"value": whole_job_rate(world, steps_per_batch, naive_ms / 1e3), "unit": "walk-steps/s",
                       "ms_per_step": naive_ms,
                       "bouquet_speedup": naive_ms / ms_per_step,

@@ -657,6 +657,13 @@ typedef struct bq_tuning {
                                   4M-vertex power-law AESC 2 / 4 / 8 measured
                                   464 / 481 / 578 ms.  Never changes a
                                   result. */
+    uint32_t group_walks;      /* 1 (default): a BOUQUET walk batch groups its
+                                  walks by start vertex (Alg. 3's bouquets)
+                                  before the walk kernel; 0: the same kernel
+                                  runs the walks in input order (only the
+                                  walks with a start < n are kept), to
+                                  measure what the grouping buys.  Never
+                                  changes a result. */
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

@@ -35,6 +35,7 @@ std::atomic<int> g_relabel_hub8{1};
 std::atomic<int> g_hub8_hubs{0};
 std::atomic<int> g_hub8_count_bits{0};
 std::atomic<int> g_shared_lanes{2};
+std::atomic<int> g_group_walks{1};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -164,6 +165,7 @@ bool tuning_relabel_hub8() { return g_relabel_hub8.load() != 0; }
 uint32_t tuning_hub8_hubs() { return (uint32_t)g_hub8_hubs.load(); }
 uint32_t tuning_hub8_count_bits() { return (uint32_t)g_hub8_count_bits.load(); }
 int tuning_shared_lanes() { return g_shared_lanes.load(); }
+bool tuning_group_walks() { return g_group_walks.load() != 0; }
 
 namespace {
 
@@ -941,6 +943,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->hub8_hubs = (uint32_t)g_hub8_hubs.load();
     out->hub8_count_bits = (uint32_t)g_hub8_count_bits.load();
     out->shared_lanes = (uint32_t)g_shared_lanes.load();
+    out->group_walks = (uint32_t)g_group_walks.load();
     return BQ_OK;
 }
 
@@ -964,6 +967,7 @@ int bq_set_tuning(const bq_tuning *in) {
     if (in->hub8_count_bits > 31) return fail(BQ_EINVAL, "hub8_count_bits must be 0..31");
     if (in->shared_lanes != 2 && in->shared_lanes != 4 && in->shared_lanes != 8)
         return fail(BQ_EINVAL, "shared_lanes must be 2, 4 or 8");
+    if (in->group_walks > 1) return fail(BQ_EINVAL, "group_walks must be 0 or 1");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
@@ -977,6 +981,7 @@ int bq_set_tuning(const bq_tuning *in) {
     g_hub8_hubs.store((int)in->hub8_hubs);
     g_hub8_count_bits.store((int)in->hub8_count_bits);
     g_shared_lanes.store((int)in->shared_lanes);
+    g_group_walks.store((int)in->group_walks);
     return BQ_OK;
 }
 

@@ -117,6 +117,42 @@ __global__ void scatter_starts_kernel(const uint32_t *__restrict__ starts, uint6
     }
 }
 
+// Without grouping (bq_tuning.group_walks = 0): the valid walks' (walk id,
+// start) pairs in input order within each block's tile of kPairTile walks
+// (one atomic per tile reserves its slots), their number in *n_valid;
+// starts >= n are skipped and reported.  The order of the tiles follows the
+// schedule; no result depends on it.
+constexpr int kPairTile = 1024;  // = the block size
+
+__global__ void __launch_bounds__(kPairTile)
+pairs_in_order_kernel(const uint32_t *__restrict__ starts, uint64_t n_walks, uint32_t n,
+                      uint32_t *__restrict__ n_valid, uint2 *__restrict__ sorted, uint32_t *status) {
+    __shared__ uint32_t s_warp[kPairTile / 32];
+    __shared__ uint32_t s_base;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t tile = blockIdx.x * (uint64_t)kPairTile; tile < n_walks; tile += (uint64_t)gridDim.x * kPairTile) {
+        const uint64_t i = tile + threadIdx.x;
+        const uint32_t s = i < n_walks ? starts[i] : 0u;
+        const bool valid = i < n_walks && s < n;
+        if (i < n_walks && !valid) atomicOr(status, kStatusBadStart);
+        const uint32_t mask = __ballot_sync(0xffffffffu, valid);
+        if (lane == 0) s_warp[warp] = (uint32_t)__popc(mask);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // the tile's warps in order, then one atomic
+            uint32_t acc = 0;
+            for (int w = 0; w < kPairTile / 32; ++w) {
+                const uint32_t c = s_warp[w];
+                s_warp[w] = acc;
+                acc += c;
+            }
+            s_base = acc ? atomicAdd(n_valid, acc) : 0u;
+        }
+        __syncthreads();
+        if (valid) sorted[s_base + s_warp[warp] + __popc(mask & ((1u << lane) - 1u))] = make_uint2((uint32_t)i, s);
+        __syncthreads();
+    }
+}
+
 // The paper's SABA arrangement for the literal SABA word: inside each start
 // vertex's bucket, walks ordered by their seed X_W (the low 32 bits of the
 // walk key; ties by id), so that a bouquet holds walks whose seeds, and so
@@ -1087,9 +1123,20 @@ int bouquet_in(const DeviceGraph &g, uint64_t seed, const uint32_t *starts, uint
     const size_t n = g.n;
     uint32_t *counts = (uint32_t *)scratch, *cursor = counts + n;
     uint2 *sorted = reinterpret_cast<uint2 *>(scratch + bouquet_pairs_offset(g.n));
-    int rc = group_by_start(g, starts, n_walks, counts, cursor, sorted, status, scan_ws, scan_ws_bytes, s);
+    const bool grouped = tuning_group_walks();
+    int rc = BQ_OK;
+    if (grouped) {
+        rc = group_by_start(g, starts, n_walks, counts, cursor, sorted, status, scan_ws, scan_ws_bytes, s);
+    } else {  // the same kernels on the walks in input order (cursor[n] = valid walks)
+        BQ_CUDA(cudaMemsetAsync(cursor + n, 0, sizeof(uint32_t), s));
+        ProfScope prof(kProfGroup, s);
+        count_launches(1);
+        pairs_in_order_kernel<<<blocks_for(n_walks, kPairTile), kPairTile, 0, s>>>(starts, n_walks, g.n, cursor + n,
+                                                                                     sorted, status);
+        BQ_CUDA(cudaGetLastError());
+    }
     if (rc) return rc;
-    if (smp.kind == 1 && smp.t == kSabaT) {
+    if (grouped && smp.kind == 1 && smp.t == kSabaT) {
         ProfScope prof(kProfGroup, s);
         count_launches(1);
         int dev = 0, sms = 0;

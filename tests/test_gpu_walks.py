@@ -251,6 +251,50 @@ def test_degree_relabelled_copy_bit_exact(env, hub_slots):
         bq.set_tuning(**old)
 
 
+@pytest.mark.parametrize("tuning,kind", [(dict(hub_slots=0, layout=0), "bouquet"),
+                                         (dict(hub_slots=1024, layout=5), "hub"),
+                                         (dict(hub_slots=1024, layout=5, hub_relabel=1, relabel_hub8=0), "relabel"),
+                                         (dict(hub_slots=1024, layout=5, hub_relabel=1, relabel_hub8=1), "relabel8")],
+                         ids=["bouquet", "hub", "relabel", "relabel8"])
+def test_ungrouped_walks_bit_exact(env, tuning, kind):
+    """group_walks = 0: the bouquet kernels run the walks in input order
+    (no grouping by start); visits and paths are those of the oracle, and
+    starts >= n are skipped and reported as in the grouped path."""
+    bq, torch = env
+    old = bq.get_tuning()
+    g = rmat(12, 8, seed=2)
+    try:
+        bq.set_tuning(**tuning)
+        graph = bq.Graph.from_csr(g)
+        bq.set_tuning(group_walks=0)
+        rng = np.random.default_rng(17)
+        starts = rng.integers(0, g.n, 50021).astype(np.uint32)
+        for lanes in (1, 4):
+            bq.set_tuning(walk_lanes=lanes)
+            want_v, want_p = oracle.walk_batch(g, 61, starts, 12, include_start=True, want_paths=True)
+            paths = torch.zeros((starts.size, 13), dtype=torch.int32, device="cuda")
+            bq.profile_read()
+            vis = bq.walk_batch(graph, 61, dev_u32(torch, starts), 12, visit_start=True, paths=paths)
+            bq.sync()
+            assert bq.profile_read()["walk_kernels"][kind] == 1
+            assert np.array_equal(host_u32(vis), want_v), lanes
+            assert np.array_equal(host_u32(paths), want_p), lanes
+        bad = starts.copy()
+        bad[::997] = g.n + 3
+        vis = bq.walk_batch(graph, 61, dev_u32(torch, bad), 12)
+        with pytest.raises(bq.BouquetError) as ei:
+            bq.sync()
+        assert ei.value.code == bq.EINVAL
+        keep = bad < g.n
+        ids = np.flatnonzero(keep).astype(np.uint64)
+        p = oracle.walk_paths_by_id(g, 61, ids, bad[keep], 12)
+        want = np.bincount(p[:, 1:].reshape(-1).astype(np.int64), minlength=g.n)
+        assert np.array_equal(host_u32(vis).astype(np.int64), want)
+        graph.close()
+    finally:
+        bq.set_tuning(**old)
+
+
 def test_host_io_matches_device(env):
     bq, torch = env
     g = GRAPHS["gnp60"]
