@@ -58,6 +58,20 @@ __device__ __forceinline__ int64_t lower_bound_ids(const uint32_t *__restrict__ 
     return lo;
 }
 
+// Position of `key` in the sorted row[0, n), n >= 1: the largest i with
+// row[i] <= key (0 if none), so the key is in the row iff row[i] == key.
+// The trip count depends on n alone, which every lane of a vertex task
+// shares (all lanes walk from the same start), so the loop never diverges.
+__device__ __forceinline__ uint32_t last_le_row(const uint32_t *__restrict__ row, uint32_t n, uint32_t key) {
+    uint32_t base = 0;
+    while (n > 1) {
+        const uint32_t half = n >> 1;
+        if (__ldg(row + base + half) <= key) base += half;
+        n -= half;
+    }
+    return base;
+}
+
 // Validate the queries, take the per-vertex maxima of N and tau, and claim
 // the two CSR positions of each edge in the query index (a second claim of
 // the same position is a repeated edge).
@@ -146,7 +160,8 @@ __device__ __forceinline__ void run_vertex_task(const EL &el, const int64_t *__r
     uint64_t off0;
     uint32_t deg0;
     start_record(offsets, x, off0, deg0);
-    const int64_t row_lo = (int64_t)off0, row_hi = (int64_t)off0 + deg0;
+    const uint32_t *__restrict__ row = nbrs + off0;  // the start's row and its query index
+    const uint32_t *__restrict__ qrow = qidx + off0;
     uint64_t off[W];
     uint32_t cur[W], deg[W];
 #pragma unroll
@@ -163,12 +178,20 @@ __device__ __forceinline__ void run_vertex_task(const EL &el, const int64_t *__r
             if (COUPLED) gs[j] += kGolden;
             uint32_t key = kNoQuery, w = 0;
             if (deg[j]) {
+                const bool from_x = cur[j] == x;
                 const uint32_t kk = choose(sample_word<COUPLED>(st[j], gs[j], cur[j], smp.t), deg[j]);
                 el.next(off[j] + kk, cur[j], off[j], deg[j]);
                 if (cur[j] != x) {
-                    const int64_t p = lower_bound_ids(nbrs, row_lo, row_hi, cur[j]);
-                    if (p < row_hi && __ldg(nbrs + p) == cur[j]) {
-                        const uint32_t q = __ldg(qidx + p);
+                    // a step taken from x lands on position kk of x's row;
+                    // any other step searches the row for the new vertex
+                    uint32_t p = kk;
+                    bool in_row = from_x;
+                    if (!from_x) {
+                        p = last_le_row(row, deg0, cur[j]);
+                        in_row = __ldg(row + p) == cur[j];
+                    }
+                    if (in_row) {
+                        const uint32_t q = __ldg(qrow + p);
                         if (q != kNoQuery) {
                             const uint32_t tq = qinfo[q].tau;
                             if (l <= tq) {
