@@ -503,11 +503,10 @@ constexpr uint32_t kPushQ = 1u << 30;  // fixed-point scale of the pushed values
 // a neighbour of x: a walk from y stands on x one step later with
 // probability 1/d_y exactly then).  The row of x is searched in the plain
 // CSR ids; every walk of a task searches the same two rows, which stay in L1.
-__device__ __forceinline__ uint64_t pushed_value(const uint32_t *__restrict__ nbrs, int64_t lo, int64_t hi,
-                                                 uint32_t x, uint32_t y, uint32_t dy, uint32_t depth) {
+__device__ __forceinline__ uint64_t pushed_value(const uint32_t *__restrict__ row, uint32_t d, uint32_t x,
+                                                 uint32_t y, uint32_t dy, uint32_t depth) {
     if (depth == 0) return y == x ? (uint64_t)kPushQ : 0ull;
-    const int64_t p = lower_bound_row(nbrs, lo, hi, y);
-    return (p < hi && __ldg(nbrs + p) == y) ? (uint64_t)(kPushQ / dy) : 0ull;
+    return __ldg(row + last_le_row(row, d, y)) == y ? (uint64_t)(kPushQ / dy) : 0ull;  // d >= 1: x has an edge
 }
 
 // Per-warp shared-memory set of N(u) and N(v) for a depth-1 task with small
@@ -841,20 +840,20 @@ deep_tables_kernel(const int64_t *__restrict__ offsets, const uint32_t *__restri
     }
 }
 
-// r_x(y) from a sorted (vertex << 32 | value) array of `size` entries.
+// r_x(y) from a sorted (vertex << 32 | value) array of `size` entries: the
+// last entry whose vertex is <= y, found in a trip count that depends on the
+// size alone (all lanes of a task search the same table).
 __device__ __forceinline__ uint64_t deep_value(const unsigned long long *__restrict__ tab, uint32_t size,
                                                uint32_t y) {
-    uint32_t lo = 0, hi = size;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if ((uint32_t)(__ldg(tab + mid) >> 32) < y) lo = mid + 1;
-        else hi = mid;
+    if (size == 0) return 0ull;
+    uint32_t base = 0;
+    while (size > 1) {
+        const uint32_t half = size >> 1;
+        if ((uint32_t)(__ldg(tab + base + half) >> 32) <= y) base += half;
+        size -= half;
     }
-    if (lo < size) {
-        const unsigned long long e = __ldg(tab + lo);
-        if ((uint32_t)(e >> 32) == y) return e & 0xffffffffull;
-    }
-    return 0ull;
+    const unsigned long long e = __ldg(tab + base);
+    return (uint32_t)(e >> 32) == y ? (e & 0xffffffffull) : 0ull;
 }
 
 // Persistent counting kernel of the push estimator: the tasks, streams and
@@ -888,8 +887,9 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
         const uint64_t stream = 2 * qi.edge + side;
         const uint32_t start = side ? qi.v : qi.u;
         const uint64_t k0 = (local >> 1) * 32ull * W;
-        const int64_t lo_u = __ldg(offsets + qi.u), hi_u = lo_u + qi.du;
-        const int64_t lo_v = __ldg(offsets + qi.v), hi_v = lo_v + qi.dv;
+        const int64_t lo_u = __ldg(offsets + qi.u), lo_v = __ldg(offsets + qi.v);
+        const uint32_t *__restrict__ row_u = nbrs + lo_u;
+        const uint32_t *__restrict__ row_v = nbrs + lo_v;
         // small rows at depth 1: the warp hashes N(u) and N(v) into its set
         const bool use_set = qi.depth == 1 && (uint64_t)qi.du + qi.dv <= kPushSetMaxRows;
         // depths >= 2: the edge's sorted pushed vectors
@@ -908,8 +908,8 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
                 flags[i] = 0u;
             }
             __syncwarp();
-            for (uint32_t i = lane; i < qi.du; i += 32) push_set_insert(keys, flags, __ldg(nbrs + lo_u + i), 1u);
-            for (uint32_t i = lane; i < qi.dv; i += 32) push_set_insert(keys, flags, __ldg(nbrs + lo_v + i), 2u);
+            for (uint32_t i = lane; i < qi.du; i += 32) push_set_insert(keys, flags, __ldg(row_u + i), 1u);
+            for (uint32_t i = lane; i < qi.dv; i += 32) push_set_insert(keys, flags, __ldg(row_v + i), 2u);
             __syncwarp();
         }
 
@@ -965,8 +965,8 @@ aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__r
             });
         } else {
             walk([&](uint32_t y, uint32_t dy, uint64_t weight) {
-                a_u += weight * pushed_value(nbrs, lo_u, hi_u, qi.u, y, dy, qi.depth);
-                a_v += weight * pushed_value(nbrs, lo_v, hi_v, qi.v, y, dy, qi.depth);
+                a_u += weight * pushed_value(row_u, qi.du, qi.u, y, dy, qi.depth);
+                a_v += weight * pushed_value(row_v, qi.dv, qi.v, y, dy, qi.depth);
             });
         }
 #pragma unroll

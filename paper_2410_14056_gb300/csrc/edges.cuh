@@ -71,6 +71,21 @@ __device__ __forceinline__ void start_record(const int64_t *__restrict__ offsets
     deg = (uint32_t)(hi - lo);
 }
 
+// Position of `key` in the sorted row[0, n), n >= 1: the largest i with
+// row[i] <= key (0 if none), so the key is in the row iff row[i] == key.
+// The trip count depends on n alone; the counting kernels search rows that
+// every lane of a task shares (the task's start, or its edge's endpoints),
+// so the loop never diverges.
+__device__ __forceinline__ uint32_t last_le_row(const uint32_t *__restrict__ row, uint32_t n, uint32_t key) {
+    uint32_t base = 0;
+    while (n > 1) {
+        const uint32_t half = n >> 1;
+        if (__ldg(row + base + half) <= key) base += half;
+        n -= half;
+    }
+    return base;
+}
+
 // Neighbour ids bit-packed q per 16-byte chunk (one aligned vector load), then
 // the neighbour's 8-byte vertex record.  Shrinks the array a step reads at
 // random so that more of it stays in L2.

@@ -414,11 +414,20 @@ int build_relabelled(bq_graph *g, uint32_t bits, uint32_t q, uint64_t chunks, cu
     std::vector<int64_t> off(n + 1);
     BQ_CUDA(cudaMemcpy(off.data(), g->d_offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
     auto deg = [&](uint32_t v) { return off[v + 1] - off[v]; };
+    // internal order: degree descending, ids ascending within a degree (a
+    // stable counting sort over the degrees, linear in n + max degree)
+    int64_t max_deg = 0;
+    for (uint32_t v = 0; v < n; ++v) max_deg = std::max(max_deg, deg(v));
+    std::vector<uint64_t> first((size_t)max_deg + 1, 0);
+    for (uint32_t v = 0; v < n; ++v) ++first[(size_t)deg(v)];
+    uint64_t pos = 0;
+    for (int64_t d = max_deg; d >= 0; --d) {
+        const uint64_t c = first[(size_t)d];
+        first[(size_t)d] = pos;
+        pos += c;
+    }
     std::vector<uint32_t> orig(n);
-    for (uint32_t v = 0; v < n; ++v) orig[v] = v;
-    std::sort(orig.begin(), orig.end(), [&](uint32_t a, uint32_t b) {
-        return deg(a) != deg(b) ? deg(a) > deg(b) : a < b;
-    });
+    for (uint32_t v = 0; v < n; ++v) orig[first[(size_t)deg(v)]++] = v;
     uint32_t live = 0;
     while (live < n && deg(orig[live]) > 0) ++live;
     const uint64_t cap = ((uint64_t)tuning_hub_slots() * 16 - 4) / 12;

@@ -58,20 +58,6 @@ __device__ __forceinline__ int64_t lower_bound_ids(const uint32_t *__restrict__ 
     return lo;
 }
 
-// Position of `key` in the sorted row[0, n), n >= 1: the largest i with
-// row[i] <= key (0 if none), so the key is in the row iff row[i] == key.
-// The trip count depends on n alone, which every lane of a vertex task
-// shares (all lanes walk from the same start), so the loop never diverges.
-__device__ __forceinline__ uint32_t last_le_row(const uint32_t *__restrict__ row, uint32_t n, uint32_t key) {
-    uint32_t base = 0;
-    while (n > 1) {
-        const uint32_t half = n >> 1;
-        if (__ldg(row + base + half) <= key) base += half;
-        n -= half;
-    }
-    return base;
-}
-
 // Validate the queries, take the per-vertex maxima of N and tau, and claim
 // the two CSR positions of each edge in the query index (a second claim of
 // the same position is a repeated edge).
