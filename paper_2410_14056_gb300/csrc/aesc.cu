@@ -861,8 +861,17 @@ __device__ __forceinline__ uint64_t deep_value(const unsigned long long *__restr
 // depth steps; at step l a walk adds w r_u(cur) and w r_v(cur), w = 2 if
 // l + depth < tau else 1, to 64-bit fixed-point accumulators
 // acc[4q + 2 side + {0, 1}] (A_uu, A_uv from u; A_vu, A_vv from v).
+// Resident blocks per SM the push kernel is compiled for.  It waits on
+// dependent loads, so occupancy pays: 6 blocks (40 registers) at 2 walks per
+// lane and 5 (48) at 4 were measured 16 % and 4-9 % faster than 4 blocks, and 8
+// blocks (32 registers, spilling) slower than 6.
+template <int W>
+constexpr int push_min_blocks() {
+    return W <= 2 ? 6 : (W <= 4 ? 5 : 1);
+}
+
 template <typename EL, int W>
-__global__ void __launch_bounds__(kThreads, (W <= 4) ? 4 : 1)
+__global__ void __launch_bounds__(kThreads, push_min_blocks<W>())
 aesc_push_kernel(EL el, const int64_t *__restrict__ offsets, const uint32_t *__restrict__ nbrs,
                  const QueryInfo *__restrict__ info, const uint64_t *__restrict__ begin,
                  const uint32_t *__restrict__ bucket, uint64_t k, uint64_t seed,
