@@ -664,6 +664,12 @@ typedef struct bq_tuning {
                                   walks with a start < n are kept), to
                                   measure what the grouping buys.  Never
                                   changes a result. */
+    uint32_t push_lanes;       /* walks per lane of the push-phase counting
+                                  kernel (bq_aesc_estimate_push): 2
+                                  (default), 4 or 8.  On the 4M-vertex
+                                  power-law AESC at depth <= 1, 2 / 4
+                                  measured 820 / 955 ms.  Never changes a
+                                  result. */
 } bq_tuning;
 
 int bq_get_tuning(bq_tuning *out);

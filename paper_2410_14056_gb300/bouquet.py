@@ -65,7 +65,8 @@ class Tuning(ctypes.Structure):
                 ("aesc_hub", ctypes.c_uint32), ("hub_cluster", ctypes.c_uint32),
                 ("hub_relabel", ctypes.c_uint32), ("relabel_hub8", ctypes.c_uint32),
                 ("hub8_hubs", ctypes.c_uint32), ("hub8_count_bits", ctypes.c_uint32),
-                ("shared_lanes", ctypes.c_uint32), ("group_walks", ctypes.c_uint32)]
+                ("shared_lanes", ctypes.c_uint32), ("group_walks", ctypes.c_uint32),
+                ("push_lanes", ctypes.c_uint32)]
 
 
 class GraphInfo(ctypes.Structure):

@@ -1257,8 +1257,8 @@ int launch_aesc_push(const DeviceGraph &g, uint64_t seed, const uint32_t *edges_
                      const uint32_t *nwalks, uint32_t push_max, uint32_t support_cap, uint32_t *depth_out,
                      uint64_t *acc, double *sc, uint32_t *status, cudaStream_t s) {
     if (k == 0) return BQ_OK;
-    int w = tuning_aesc_walks_per_lane();
-    if (w != 2 && w != 4 && w != 8) w = 4;
+    int w = tuning_push_walks_per_lane();
+    if (w != 2 && w != 4 && w != 8) w = 2;
     const uint32_t bouquet = 32u * (uint32_t)w;
     if (k >= kMaxBucketEdges) return fail(BQ_EINVAL, "k = %llu edges in one estimate", (unsigned long long)k);
     const bool deep_on = push_max >= 2;

@@ -36,6 +36,7 @@ std::atomic<int> g_hub8_hubs{0};
 std::atomic<int> g_hub8_count_bits{0};
 std::atomic<int> g_shared_lanes{2};
 std::atomic<int> g_group_walks{1};
+std::atomic<int> g_push_lanes{2};
 }  // namespace
 
 int fail(int code, const char *fmt, ...) {
@@ -166,6 +167,7 @@ uint32_t tuning_hub8_hubs() { return (uint32_t)g_hub8_hubs.load(); }
 uint32_t tuning_hub8_count_bits() { return (uint32_t)g_hub8_count_bits.load(); }
 int tuning_shared_lanes() { return g_shared_lanes.load(); }
 bool tuning_group_walks() { return g_group_walks.load() != 0; }
+int tuning_push_walks_per_lane() { return g_push_lanes.load(); }
 
 namespace {
 
@@ -944,6 +946,7 @@ int bq_get_tuning(bq_tuning *out) {
     out->hub8_count_bits = (uint32_t)g_hub8_count_bits.load();
     out->shared_lanes = (uint32_t)g_shared_lanes.load();
     out->group_walks = (uint32_t)g_group_walks.load();
+    out->push_lanes = (uint32_t)g_push_lanes.load();
     return BQ_OK;
 }
 
@@ -968,6 +971,8 @@ int bq_set_tuning(const bq_tuning *in) {
     if (in->shared_lanes != 2 && in->shared_lanes != 4 && in->shared_lanes != 8)
         return fail(BQ_EINVAL, "shared_lanes must be 2, 4 or 8");
     if (in->group_walks > 1) return fail(BQ_EINVAL, "group_walks must be 0 or 1");
+    if (in->push_lanes != 2 && in->push_lanes != 4 && in->push_lanes != 8)
+        return fail(BQ_EINVAL, "push_lanes must be 2, 4 or 8");
     g_walks_per_lane.store((int)w);
     g_aggregate.store((int)in->aggregate_visits);
     g_aesc_walks_per_lane.store((int)a);
@@ -982,6 +987,7 @@ int bq_set_tuning(const bq_tuning *in) {
     g_hub8_count_bits.store((int)in->hub8_count_bits);
     g_shared_lanes.store((int)in->shared_lanes);
     g_group_walks.store((int)in->group_walks);
+    g_push_lanes.store((int)in->push_lanes);
     return BQ_OK;
 }
 

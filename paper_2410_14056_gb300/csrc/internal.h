@@ -299,6 +299,7 @@ bool tuning_relabel_hub8();      // relabelled copy: 8-byte hubs (else the 12-by
 uint32_t tuning_hub8_hubs();       // their number (0: what the 12-byte kernel's shared memory holds)
 uint32_t tuning_hub8_count_bits(); // cap on their count-field width (0: every bit above the id)
 int tuning_shared_lanes();         // walks per lane of the vertex-centric kernels (2, 4, 8)
+int tuning_push_walks_per_lane();  // walks per lane of the push-phase counting kernel
 bool tuning_group_walks();         // walk batches group their walks by start vertex (bouquets)
 
 // Profiling (api.cu): event brackets around kernel groups while enabled, and

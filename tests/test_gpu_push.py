@@ -87,7 +87,7 @@ def test_layouts_and_lanes_never_change_results(env, layout):
         bq.set_tuning(layout=layout)
         graph = bq.Graph.from_csr(g)
         for lanes in (2, 4, 8):
-            bq.set_tuning(aesc_lanes=lanes)
+            bq.set_tuning(push_lanes=lanes)
             depth, acc, sc = bq.aesc_estimate_push_host(graph, 5, uv, tau, nw, 1)
             assert np.array_equal(depth, want[0]) and np.array_equal(acc, want[1]) and same_bits(sc, want[2]), lanes
         graph.close()
@@ -183,7 +183,7 @@ def test_deep_layouts_and_lanes(env, layout):
         bq.set_tuning(layout=layout)
         graph = bq.Graph.from_csr(g)
         for lanes in (2, 4, 8):
-            bq.set_tuning(aesc_lanes=lanes)
+            bq.set_tuning(push_lanes=lanes)
             depth, acc, sc = bq.aesc_estimate_push_host(graph, 5, uv, tau, nw, 3)
             assert np.array_equal(depth, want[0]) and np.array_equal(acc, want[1]) and same_bits(sc, want[2]), lanes
         graph.close()

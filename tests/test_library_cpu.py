@@ -76,7 +76,11 @@ def test_tuning_roundtrip_and_validation(lib):
         bq.set_tuning(walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert bq.get_tuning() == dict(old, walk_lanes=2, aggregate_visits=1, aesc_lanes=8)
         assert (old["relabel_hub8"], old["hub8_hubs"], old["hub8_count_bits"], old["shared_lanes"]) == (1, 0, 0, 2)
-        for bad in (dict(shared_lanes=3), dict(shared_lanes=0)):
+        assert (old["group_walks"], old["push_lanes"]) == (1, 2)
+        for ok in (4, 8, 2):
+            bq.set_tuning(push_lanes=ok)
+            assert bq.get_tuning()["push_lanes"] == ok
+        for bad in (dict(shared_lanes=3), dict(shared_lanes=0), dict(push_lanes=1), dict(push_lanes=0)):
             with pytest.raises(bq.BouquetError):
                 bq.set_tuning(**bad)
         bq.set_tuning(relabel_hub8=0, hub8_hubs=28000, hub8_count_bits=31)
