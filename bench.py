@@ -1186,11 +1186,11 @@ def serve_run(srv, reqs, arrivals):
         t0 = time.perf_counter()
         for req, at in zip(reqs, arrivals):
             t_sched = t0 + at
-            while True:
-                dt = t_sched - time.perf_counter()
-                if dt <= 0:
-                    break
-                time.sleep(dt if dt > 2e-3 else 0)
+            # sleep to the arrival (no spinning: a spinning main thread holds
+            # the GIL that the submitting threads need)
+            dt = t_sched - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
             futs.append(pool.submit(submit, req, t_sched))
         lat = []
         for f in futs:
