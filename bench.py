@@ -1134,6 +1134,9 @@ SERVE_LOADS = (0.5, 0.8, 1.0)
 SERVE_SATURATION_REQUESTS = 2000
 SERVE_LOAD_SECONDS = 3.0
 SERVE_SUBMITTERS = 12
+SERVE_WAITERS = 128
+# page-locked arena for request images: a 2000-request burst holds about 1 GB
+SERVE_ARENA_BYTES = 2 << 30
 
 
 def serving_graphs(bq, torch):
@@ -1169,34 +1172,46 @@ def serving_requests(dgs, count, rng, gen):
     return out
 
 
-def serve_run(srv, reqs, arrivals):
-    """Submit reqs at the given offsets (s) from a pool of submitting threads
-    (each plans on its own thread), then wait for all.  Returns the
-    latencies (arrival -> results on the host, ms) and the wall time from
-    the first arrival to the last completion."""
+def serve_run(srv, reqs, arrivals, prompt=True):
+    """Submit reqs at the given offsets (s) from a pool of submitting threads.
+    prompt: wait for each request as soon as it is submitted, from a pool of
+    waiting threads (a prompt client: a request's page-locked image returns to
+    the server's pool when its results are read); else wait for all after the
+    last submission (a burst: the waiting threads would slow the submitting
+    ones).  Returns the latencies (arrival -> results ready on the host, ms)
+    and the wall time from the first arrival to the last completion."""
     import concurrent.futures as cf
+    lat = [0.0] * len(reqs)
 
     def submit(req, t_sched):
         t_start = time.perf_counter()
         rid = srv.submit(*req)
         return rid, (t_start - t_sched) * 1e3
 
-    futs = []
-    with cf.ThreadPoolExecutor(SERVE_SUBMITTERS) as pool:
+    def wait(i, fut):
+        rid, queued_ms = fut.result()
+        _, _, server_ms = srv.wait(rid, timeout=600)
+        lat[i] = queued_ms + server_ms
+
+    with cf.ThreadPoolExecutor(SERVE_SUBMITTERS) as pool, cf.ThreadPoolExecutor(SERVE_WAITERS) as waiters:
         t0 = time.perf_counter()
-        for req, at in zip(reqs, arrivals):
+        subs, done = [], []
+        for i, (req, at) in enumerate(zip(reqs, arrivals)):
             t_sched = t0 + at
             # sleep to the arrival (no spinning: a spinning main thread holds
             # the GIL that the submitting threads need)
             dt = t_sched - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            futs.append(pool.submit(submit, req, t_sched))
-        lat = []
-        for f in futs:
-            rid, queued_ms = f.result()
-            _, _, server_ms = srv.wait(rid, timeout=600)
-            lat.append(queued_ms + server_ms)
+            f = pool.submit(submit, req, t_sched)
+            if prompt:
+                done.append(waiters.submit(wait, i, f))
+            else:
+                subs.append(f)
+        for i, f in enumerate(subs):
+            wait(i, f)
+        for d in done:
+            d.result()
         t_end = time.perf_counter()
     return lat, t_end - t0
 
@@ -1218,6 +1233,7 @@ def serving_measure(bq, torch, sat_requests, load_seconds, warmup, max_requests=
     gen = torch.Generator(device="cuda")
     gen.manual_seed(910)
     cfg = bq.ServerConfig(device_budget_bytes=4 << 30, max_inflight=256, max_pending=65536,
+                          pinned_arena_bytes=SERVE_ARENA_BYTES,
                           tasks_per_iteration=1 << 16, **POWERLAW_SCHEDULE)
     with bq.Server(graphs, cfg) as srv:
         # warm-up: a few requests through the whole path
@@ -1228,7 +1244,7 @@ def serving_measure(bq, torch, sat_requests, load_seconds, warmup, max_requests=
         st0 = srv.stats()
         bq.profile_read()
         bq.profile_enable(True)
-        lat, wall = serve_run(srv, sat_reqs, [0.0] * len(sat_reqs))
+        lat, wall = serve_run(srv, sat_reqs, [0.0] * len(sat_reqs), prompt=False)
         prof = bq.profile_read()
         bq.profile_enable(False)
         st1 = srv.stats()
@@ -1268,7 +1284,9 @@ def serving_measure(bq, torch, sat_requests, load_seconds, warmup, max_requests=
         "graphs": [{"name": d.name, "n": d.n, "m": d.m} for d in dgs],
         "resident_graph_bytes": resident,
         "server": {"device_budget_bytes": cfg.device_budget_bytes, "max_inflight": cfg.max_inflight,
-                   "tasks_per_iteration": cfg.tasks_per_iteration, "submitting_threads": SERVE_SUBMITTERS},
+                   "tasks_per_iteration": cfg.tasks_per_iteration, "pinned_arena_bytes": cfg.pinned_arena_bytes,
+                   "submitting_threads": SERVE_SUBMITTERS,
+                   "waiting_threads": f"{SERVE_WAITERS} (Poisson loads wait for each request at once; the burst after its last submission)"},
         "saturation": saturation, "loads": loads,
         "p50_ms": {str(l["offered"]): l["p50_ms"] for l in loads},
         "p99_ms": {str(l["offered"]): l["p99_ms"] for l in loads},

@@ -520,6 +520,11 @@ typedef struct bq_server_stats {
     /* the planner threads' time: planning every request (summed over the
      * threads), and the longest planning of one request */
     double planner_s, planner_max_ms;
+    /* page-locked blocks for request images that had to come from
+     * cudaMallocHost because the free lists and the arena (cfg
+     * pinned_arena_bytes) had none left, and the seconds those calls took */
+    uint64_t pinned_fallbacks;
+    double pinned_fallback_s;
 } bq_server_stats;
 
 /* Start a server over graphs (all on the current device, nnz < 2^32; they

@@ -120,7 +120,8 @@ class ServerStats(ctypes.Structure):
                 ("pending", ctypes.c_uint32), ("worker_admit_s", ctypes.c_double),
                 ("worker_launch_s", ctypes.c_double), ("worker_complete_s", ctypes.c_double),
                 ("worker_idle_s", ctypes.c_double), ("planner_s", ctypes.c_double),
-                ("planner_max_ms", ctypes.c_double)]
+                ("planner_max_ms", ctypes.c_double), ("pinned_fallbacks", ctypes.c_uint64),
+                ("pinned_fallback_s", ctypes.c_double)]
 
 
 # every symbol include/bouquet.h declares

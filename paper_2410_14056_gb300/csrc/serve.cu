@@ -125,6 +125,8 @@ struct PinnedPool {
     std::vector<char *> all;
     char *arena = nullptr;
     size_t arena_size = 0, arena_used = 0;
+    uint64_t fallbacks = 0;  // blocks from cudaMallocHost after the arena ran out
+    double fallback_s = 0;   // and the time those calls took
     static size_t size_class(size_t bytes) {
         size_t c = 4096;
         while (c < bytes) c <<= 1;
@@ -157,12 +159,16 @@ struct PinnedPool {
             }
         }
         char *p = nullptr;
+        const auto t0 = std::chrono::steady_clock::now();
         if (cudaMallocHost((void **)&p, cap) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         std::lock_guard<std::mutex> lk(mu);
         all.push_back(p);
+        ++fallbacks;
+        fallback_s += dt;
         return p;
     }
     void put(char *p, size_t cap) {
@@ -925,6 +931,11 @@ int bq_server_stats_get(bq_server *srv, bq_server_stats *out) {
         out->worker_idle_s = srv->t_idle;
         out->planner_s = srv->t_plan;
         out->planner_max_ms = srv->t_plan_max * 1e3;
+        {
+            std::lock_guard<std::mutex> plk(srv->pinned.mu);
+            out->pinned_fallbacks = srv->pinned.fallbacks;
+            out->pinned_fallback_s = srv->pinned.fallback_s;
+        }
         lat = srv->latencies_ms;
     }
     out->p50_ms = percentile(lat, 0.50);
