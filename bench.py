@@ -144,7 +144,9 @@ def walk_kernel_traffic(kernel: str = "walk_hub_kernel"):
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 25 ms) while the timed region runs; entering
+    waits (at most 3 s) for the first sample, so that a short timed region is
+    still covered."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -159,12 +161,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
+            return self
+        t_end = time.perf_counter() + 3.0
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+            time.sleep(0.005)
         return self
 
     def _read(self):
