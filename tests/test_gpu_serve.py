@@ -97,6 +97,26 @@ def test_alone_equals_mixed_and_single_call(env):
     assert same_bits(sc.cpu().numpy(), sc_alone)
 
 
+def test_pinned_fallbacks_counted(env):
+    """Request images that find the page-locked arena full are page-locked on
+    demand and counted in the stats, with unchanged results; with the default
+    arena and results read as they come, small requests need none."""
+    bq, hosts, graphs = env
+    rng = np.random.default_rng(21)
+    reqs = requests(hosts, rng, 12)
+    with bq.Server(graphs, pinned_arena_bytes=4096, **SCHED) as srv:
+        ids = [srv.submit(*r) for r in reqs]
+        results = [srv.wait(rid, timeout=120, counts=True) for rid in ids]
+        st = srv.stats()
+    assert st["pinned_fallbacks"] >= 1 and st["pinned_fallback_s"] >= 0.0
+    for req, (sc, counts, _) in zip(reqs, results):
+        check_against_oracle(hosts, req, sc, counts)
+    with bq.Server(graphs, **SCHED) as srv:
+        for r in reqs:
+            srv.wait(srv.submit(*r), timeout=120)
+        assert srv.stats()["pinned_fallbacks"] == 0
+
+
 def test_empty_and_failed_requests(env):
     bq, hosts, graphs = env
     uv_ok = all_edges(hosts[0])[:5]
