@@ -295,6 +295,28 @@ def test_ungrouped_walks_bit_exact(env, tuning, kind):
         bq.set_tuning(**old)
 
 
+def test_grouping_with_skewed_starts(env):
+    """Grouping by start vertex with skewed starts: thousands of walks on a few
+    start vertices beside uniform ones.  The batch equals the oracle, also
+    with the literal SABA word, which reorders each start's walks after
+    grouping."""
+    bq, torch = env
+    g = GRAPHS["rmat12"]
+    graph = bq.Graph.from_csr(g)
+    rng = np.random.default_rng(31)
+    starts = np.concatenate([rng.integers(0, 200, 20000), rng.integers(0, g.n, 15000),
+                             np.full(9000, 4000)]).astype(np.uint32)
+    rng.shuffle(starts)
+    st = dev_u32(torch, starts)
+    for sampler in (None, (2, 0, 1)):
+        want_v, want_p = oracle.walk_batch(g, 19, starts, 9, sampler=sampler, want_paths=True)
+        paths = torch.zeros((starts.size, 10), dtype=torch.int32, device="cuda")
+        vis = bq.walk_batch(graph, 19, st, 9, sampler=sampler, paths=paths)
+        bq.sync()
+        assert np.array_equal(host_u32(vis), want_v), sampler
+        assert np.array_equal(host_u32(paths), want_p), sampler
+
+
 def test_host_io_matches_device(env):
     bq, torch = env
     g = GRAPHS["gnp60"]
